@@ -1,0 +1,150 @@
+/*
+ * pf.h -- C ABI of the GB300 (sm_103a) library for the explicit time step of the
+ * grand-potential phase-field model of ternary eutectic directional solidification
+ * (Bauer et al., arXiv:1506.01684).
+ *
+ * Model (paper Section 2): four phase fields phi_a (a = 0,1,2 solid, 3 liquid) on the
+ * Gibbs simplex and two chemical potentials mu (K = 3 components), evolved by Eq. 1-2
+ * (phi) and Eq. 3-4 (mu, with the anti-trapping current) under the frozen temperature
+ * T = T0 + G (z - v t), with a moving window along z.  One time step is Algorithm 1:
+ * phi-sweep, then mu-sweep reading phi at both time levels.
+ *
+ * Conventions shared by every entry point:
+ *   - Grid: nx * ny * nz cells, cell (i,j,k), x fastest; periodic in x and y,
+ *     zero-gradient (mirror) in z; cell centres at z = (k + window_offset) * dx.
+ *   - Host field layout (read/write calls): FP64, structure of arrays
+ *     [component][z][y][x]; phi has 4 components, mu has 2.
+ *   - Ownership: the library owns every device buffer and handle it creates; the
+ *     caller owns every host buffer it passes and keeps it alive for the call.
+ *   - Errors: every call returns a status (PF_OK or a negative PF_E_*); nothing
+ *     throws or aborts across the ABI.  Device work is asynchronous on the
+ *     simulation's stream; device-side errors (non-finite values, CUDA faults) are
+ *     latched and returned by the next synchronising call.
+ *   - Threads: a pf_sim is used by one thread at a time; a pf_server is internally
+ *     synchronised.
+ */
+#ifndef PF_GB300_H
+#define PF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+enum {
+    PF_OK = 0,
+    PF_E_INVAL = -1,     /* invalid argument (null pointer, size, parameter) */
+    PF_E_NOMEM = -2,     /* device or host allocation failed / admission refused */
+    PF_E_CUDA = -3,      /* a CUDA call failed */
+    PF_E_UNSTABLE = -4,  /* a non-finite value appeared in phi or mu */
+    PF_E_TIMEOUT = -5,   /* a bounded wait gave up */
+    PF_E_CANCELLED = -6, /* a served request was cancelled */
+    PF_E_PENDING = 1     /* pf_poll only: the request is not finished yet */
+};
+
+/* arithmetic of the stencil kernels and the field storage */
+enum {
+    PF_FP64 = 0,     /* FP64 storage and arithmetic (the plain reference path) */
+    PF_FP32 = 1,     /* FP32 storage and arithmetic */
+    PF_FP32_COMP = 2 /* FP32 arithmetic, state kept as FP32 high + FP32 low words (compensated) */
+};
+
+#define PF_PARAMS_VERSION 1
+
+/*
+ * Physical and numerical parameters, always FP64 (the library converts them to the
+ * kernel precision).  Readings of the paper where it prints no value:
+ *   psi_a(mu,T) = -|mu|^2/(4 A_a) - mu . chat_a(T) + s_a (T - TE),
+ *   chat_a(T) = cE_a + kT_a (T - TE),  c^a = mu/(2 A_a) + chat_a(T),
+ *   h_a = phi_a^2 / sum phi_b^2,  g_a = phi_a,  M = sum_a D_a h_a / (2 A_a),
+ *   a = sum_{a<b} gamma2_ab |phi_a grad phi_b - phi_b grad phi_a|^2,
+ *   omega = (16/pi^2) sum gamma2_ab phi_a phi_b + sum gamma3_abd phi_a phi_b phi_d.
+ */
+typedef struct pf_params {
+    int version;                /* PF_PARAMS_VERSION */
+    int precision;              /* PF_FP64, PF_FP32 or PF_FP32_COMP */
+    double dx, eps, tau, dt;    /* dt <= 0: 0.5 x min(tau dx^2/(12 gamma_max T_max), dx^2/(6 D_max)) */
+    double gamma2[6];           /* pairs 01 02 03 12 13 23 */
+    double gamma3[4];           /* triples 012 013 023 123 */
+    double A[4], cE[4][2], kT[4][2], s[4], D[4], TE;
+    double T0, G, v;            /* frozen temperature T = T0 + G (z - v t) */
+    int seed_layers, n_grains;  /* Voronoi nuclei in the bottom seed_layers planes */
+    double window_trigger_z;    /* > 0: shift the window when the interface height reaches it */
+} pf_params;
+
+typedef struct pf_sim pf_sim;
+typedef struct pf_server pf_server;
+
+/* Human-readable text for a status code (static storage). */
+const char *pf_strerror(int status);
+
+/* Fill *p with the symmetric parameter set: dx = 1, eps = 4, tau = 1, dt = 0 (auto),
+ * gamma2 = 1, gamma3 = 15, A = 1, cE = alpha(0.8,0.1) beta(0.1,0.8) gamma(0.1,0.1)
+ * liquid(1/3,1/3), kT = 0 solids / (0.1,0.1) liquid, s = 1 solids / 0 liquid,
+ * D = 0 solids / 1 liquid, TE = 1, G = 1e-3, v = 1e-2, T0 = TE - 8 G, seed_layers = 8,
+ * n_grains = 12, window off, precision PF_FP64.  Returns PF_E_INVAL for p == NULL. */
+int pf_default_params(pf_params *p);
+
+/* Optional allocator hooks for every device buffer the library allocates (fields and
+ * scratch).  alloc(bytes, stream, ctx) returns a device pointer or NULL; free(ptr, bytes,
+ * stream, ctx) releases it.  Passing NULLs restores cudaMalloc/cudaFree.  Set before
+ * pf_create; buffers are released with the hook that allocated them. */
+typedef void *(*pf_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*pf_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void *ctx);
+
+/* Create a simulation of nx*ny*nz cells on the current CUDA device.  Allocates the
+ * double-buffered phi and mu fields (phi: 4 words/cell, mu: 2 words/cell, words of the
+ * chosen precision; twice that for PF_FP32_COMP) and a small device state.  Copies *p;
+ * dt <= 0 is replaced by the default limit.  The fields start as pure liquid, mu = 0,
+ * t = 0.  stream: a cudaStream_t (NULL: the library creates its own).
+ * Errors: PF_E_INVAL (sizes < 1, bad params/version), PF_E_NOMEM, PF_E_CUDA. */
+int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim **out);
+
+/* Release every device buffer and handle of sim (waits for its pending work). */
+int pf_destroy(pf_sim *sim);
+
+/* The effective parameters (dt resolved), copied into *out. */
+int pf_get_params(const pf_sim *sim, pf_params *out);
+
+/* Initial condition (paper Section 2.1, simulation setting): cells with k < seed_layers
+ * take the phase of the nearest of n_grains Voronoi seeds drawn from splitmix64(seed)
+ * (periodic distance in x and y); liquid above; mu = 0; t = 0; window offset 0. */
+int pf_init(pf_sim *sim, uint64_t seed);
+
+/* Advance nsteps explicit steps (Algorithm 1), asynchronously on the sim's stream.
+ * Each step: phi-sweep, mu-sweep, FP64 reductions, t += dt, moving-window check.
+ * Returns PF_E_INVAL for nsteps < 0, a latched error if one is pending, PF_E_CUDA if a
+ * launch fails. */
+int pf_step(pf_sim *sim, int nsteps);
+
+/* Wait for the sim's stream; returns and clears the latched error (PF_E_UNSTABLE when a
+ * non-finite value appeared in any completed step). */
+int pf_sync(pf_sim *sim);
+
+/* Copy the current fields to host FP64 SoA buffers (phi: 4*nx*ny*nz, mu: 2*nx*ny*nz
+ * doubles; either may be NULL).  cap_cells must be >= nx*ny*nz.  Synchronising. */
+int pf_read_fields(pf_sim *sim, double *phi, double *mu, size_t cap_cells);
+
+/* Overwrite the current fields from host FP64 SoA buffers (both required); time and
+ * window offset are left unchanged.  Synchronising. */
+int pf_write_fields(pf_sim *sim, const double *phi, const double *mu);
+
+/* Mean of each phi_a over all cells, accumulated in FP64 on the device. Synchronising. */
+int pf_phase_fractions(pf_sim *sim, double out[4]);
+
+/* FP64 diagnostics: simulation time t, window offset (planes), solute totals
+ * sum_cells c_i with c = sum_a h_a c^a(mu, T), and interface height
+ * sum(1 - phi_liquid)/(nx ny).  Any output pointer may be NULL.  Synchronising. */
+int pf_stats(pf_sim *sim, double *t, double *window_offset, double solute[2], double *h_int);
+
+/* Number of window shifts (planes moved) since pf_init.  Synchronising. */
+int pf_window_shifts(pf_sim *sim, int *planes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_GB300_H */

@@ -1,0 +1,587 @@
+// pf_api.cpp -- host runtime behind the C ABI of include/pf.h: device buffers, the per-step
+// launch sequence of Algorithm 1 (phi-sweep, mu-sweep, FP64 reductions, window), the
+// Voronoi seeds, and the field/diagnostic transfers.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "pf_internal.h"
+
+using namespace pf;
+
+// ------------------------------------------------------------------------------------------
+// allocator hooks
+// ------------------------------------------------------------------------------------------
+namespace {
+std::mutex g_alloc_mu;
+pf_alloc_fn g_alloc = nullptr;
+pf_free_fn g_free = nullptr;
+void *g_alloc_ctx = nullptr;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    pf_free_fn fr = nullptr;  // hook that allocated it (nullptr: cudaMalloc)
+    void *ctx = nullptr;
+};
+
+int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s)
+{
+    pf_alloc_fn a;
+    pf_free_fn f;
+    void *ctx;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+        f = g_free;
+        ctx = g_alloc_ctx;
+    }
+    b.bytes = bytes;
+    if (a) {
+        b.p = a(bytes, (void *)s, ctx);
+        b.fr = f;
+        b.ctx = ctx;
+        return b.p ? PF_OK : PF_E_NOMEM;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return e == cudaErrorMemoryAllocation ? PF_E_NOMEM : PF_E_CUDA;
+    }
+    return PF_OK;
+}
+
+void dev_free(DevBuf &b, cudaStream_t s)
+{
+    if (!b.p) return;
+    if (b.fr)
+        b.fr(b.p, b.bytes, (void *)s, b.ctx);
+    else
+        cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// splitmix64 (Steele, Lea and Flood 2014): golden-ratio increment, then the variant-13 mixer.
+uint64_t splitmix64_next(uint64_t &state)
+{
+    uint64_t z = (state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+double unit53(uint64_t &state) { return (double)(splitmix64_next(state) >> 11) * (1.0 / 9007199254740992.0); }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// simulation object
+// ------------------------------------------------------------------------------------------
+struct pf_sim {
+    int nx, ny, nz;
+    pf_params p;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Geometry geo;
+    DevBuf phi[2], mu[2];  // AoS fields of the stencil precision
+    DevBuf state;          // DevState
+    DevBuf parts;          // Partial[geo.nparts()]
+    DevBuf tab;            // PlaneT<R>[2 nz]
+    DevBuf seeds;          // Voronoi seeds
+    DevBuf red;            // nz x 8 FP64 plane sums
+    int cur = 0;           // index of the source buffers
+    int latched = PF_OK;
+    size_t ncell() const { return (size_t)nx * ny * nz; }
+    size_t wbytes() const { return p.precision == PF_FP64 ? 8 : 4; }
+};
+
+namespace pf {
+Geometry make_geometry(int nx, int ny, int nz, int zchunk_hint)
+{
+    Geometry g;
+    g.tx = 32;
+    g.ty = 8;
+    g.gx = (nx + g.tx - 1) / g.tx;
+    g.gy = (ny + g.ty - 1) / g.ty;
+    int zc = zchunk_hint;
+    if (zc <= 0) {
+        // aim at >= 16 CTAs per SM of 152 SMs; 8..64 planes per CTA (each chunk re-reads 2 planes)
+        const long tiles = (long)g.gx * g.gy;
+        long chunks = (152L * 16 + tiles - 1) / tiles;
+        zc = (int)((nz + chunks - 1) / chunks);
+        zc = std::max(8, std::min(64, zc));
+    }
+    zc = std::max(1, std::min(zc, nz));
+    g.zchunk = zc;
+    g.gz = (nz + zc - 1) / zc;
+    return g;
+}
+}  // namespace pf
+
+template <typename R>
+static KParams<R> make_kparams(const pf_sim *s)
+{
+    const pf_params &p = s->p;
+    KParams<R> k;
+    memset(&k, 0, sizeof k);
+    k.nx = s->nx;
+    k.ny = s->ny;
+    k.nz = s->nz;
+    k.zchunk = s->geo.zchunk;
+    k.window = p.window_trigger_z > 0.0 ? 1 : 0;
+    k.dx = (R)p.dx;
+    k.inv_dx = (R)(1.0 / p.dx);
+    k.inv_2dx = (R)(1.0 / (2.0 * p.dx));
+    k.inv_4dx = (R)(1.0 / (4.0 * p.dx));
+    k.eps = (R)p.eps;
+    k.inv_eps = (R)(1.0 / p.eps);
+    k.c_phi = (R)(p.dt / (p.tau * p.eps));
+    k.dt = (R)p.dt;
+    k.inv_dt = (R)(1.0 / p.dt);
+    for (int q = 0; q < 6; q++) k.gamma2[q] = (R)p.gamma2[q];
+    for (int q = 0; q < 4; q++) k.gamma3[q] = (R)p.gamma3[q];
+    for (int a = 0; a < 4; a++) {
+        k.inv2A[a] = (R)(1.0 / (2.0 * p.A[a]));
+        k.inv4A[a] = (R)(1.0 / (4.0 * p.A[a]));
+        k.DinvA[a] = (R)(p.D[a] / (2.0 * p.A[a]));
+        k.kT[a][0] = (R)p.kT[a][0];
+        k.kT[a][1] = (R)p.kT[a][1];
+        k.cE[a][0] = p.cE[a][0];
+        k.cE[a][1] = p.cE[a][1];
+        k.kT64[a][0] = p.kT[a][0];
+        k.kT64[a][1] = p.kT[a][1];
+        k.s64[a] = p.s[a];
+        k.A64[a] = p.A[a];
+    }
+    const double pi = 3.14159265358979323846;
+    k.at_pref = (R)(pi * p.eps / 4.0);
+    k.grad_thr = (R)(1e-20 / (p.dx * p.dx));
+    k.obst = (R)(16.0 / (pi * pi));
+    k.dTstep = (R)(-p.G * p.v * p.dt);
+    k.T0 = p.T0;
+    k.G = p.G;
+    k.v = p.v;
+    k.TE = p.TE;
+    k.dx64 = p.dx;
+    k.dt64 = p.dt;
+    k.eps64 = p.eps;
+    k.window_trigger_z = p.window_trigger_z;
+    return k;
+}
+
+// ------------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------------
+static int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return PF_OK;
+    if (e == cudaErrorMemoryAllocation) return PF_E_NOMEM;
+    return PF_E_CUDA;
+}
+
+static int latch(pf_sim *s, int st)
+{
+    if (st != PF_OK && s->latched == PF_OK) s->latched = st;
+    return st;
+}
+
+static double default_dt(const pf_params &p, int nz)
+{
+    double gmax = 0.0, dmax = 0.0;
+    for (int i = 0; i < 6; i++) gmax = p.gamma2[i] > gmax ? p.gamma2[i] : gmax;
+    for (int a = 0; a < 4; a++) dmax = p.D[a] > dmax ? p.D[a] : dmax;
+    const double Ttop = p.T0 + p.G * (double)(nz - 1) * p.dx;
+    const double Tmax = p.T0 > Ttop ? p.T0 : Ttop;
+    const double lim_phi = p.tau * p.dx * p.dx / (12.0 * gmax * Tmax);
+    const double lim_mu = dmax > 0.0 ? p.dx * p.dx / (6.0 * dmax) : lim_phi;
+    return 0.5 * (lim_phi < lim_mu ? lim_phi : lim_mu);
+}
+
+static int check_params(const pf_params *p)
+{
+    if (!p || p->version != PF_PARAMS_VERSION) return PF_E_INVAL;
+    if (p->precision != PF_FP64 && p->precision != PF_FP32) return PF_E_INVAL;
+    if (!(p->dx > 0) || !(p->eps > 0) || !(p->tau > 0)) return PF_E_INVAL;
+    for (int a = 0; a < 4; a++)
+        if (!(p->A[a] > 0) || p->D[a] < 0) return PF_E_INVAL;
+    double gmax = 0;
+    for (int i = 0; i < 6; i++) gmax = std::max(gmax, p->gamma2[i]);
+    if (!(gmax > 0)) return PF_E_INVAL;
+    if (p->seed_layers < 0 || p->n_grains < 0) return PF_E_INVAL;
+    if (!isfinite(p->T0) || !isfinite(p->G) || !isfinite(p->v) || !isfinite(p->TE)) return PF_E_INVAL;
+    return PF_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// precision-dispatched bodies
+// ------------------------------------------------------------------------------------------
+template <typename R>
+static int do_step(pf_sim *s, int n)
+{
+    const KParams<R> kp = make_kparams<R>(s);
+    DevState *st = (DevState *)s->state.p;
+    PlaneT<R> *tab = (PlaneT<R> *)s->tab.p;
+    Partial *parts = (Partial *)s->parts.p;
+    for (int q = 0; q < n; q++) {
+        const int a = s->cur, b = 1 - s->cur;
+        cudaError_t e;
+        e = launch_phi_sweep<R>(kp, s->geo, s->phi[a].p, s->mu[a].p, s->phi[b].p, st, tab, s->stream);
+        if (e == cudaSuccess)
+            e = launch_mu_sweep<R>(kp, s->geo, s->phi[a].p, s->phi[b].p, s->mu[a].p, s->mu[b].p, st, tab, parts,
+                                   s->stream);
+        if (e == cudaSuccess) e = launch_finalize<R>(kp, st, parts, s->geo.nparts(), s->stream);
+        if (e == cudaSuccess) e = launch_post<R>(kp, st, s->phi[b].p, s->mu[b].p, tab, s->stream);
+        if (e != cudaSuccess) return latch(s, cuda_status(e));
+        s->cur = b;
+    }
+    return PF_OK;
+}
+
+template <typename R>
+static int do_init(pf_sim *s, uint64_t seed, int ng)
+{
+    const KParams<R> kp = make_kparams<R>(s);
+    const int H = std::min(s->p.seed_layers, s->nz);
+    std::vector<double> seeds((size_t)std::max(ng, 1) * 4, 0.0);
+    uint64_t stt = seed;
+    for (int g = 0; g < ng; g++) {
+        seeds[4 * g + 0] = unit53(stt) * (double)s->nx;
+        seeds[4 * g + 1] = unit53(stt) * (double)s->ny;
+        seeds[4 * g + 2] = unit53(stt) * (double)s->p.seed_layers;
+        seeds[4 * g + 3] = floor(3.0 * unit53(stt));
+    }
+    const size_t sb = seeds.size() * sizeof(double);
+    if (s->seeds.bytes < sb) {
+        dev_free(s->seeds, s->stream);
+        int r = dev_alloc(s->seeds, sb, s->stream);
+        if (r != PF_OK) return r;
+    }
+    cudaError_t e = cudaMemcpyAsync(s->seeds.p, seeds.data(), sb, cudaMemcpyHostToDevice, s->stream);
+    DevState ds;
+    memset(&ds, 0, sizeof ds);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->state.p, &ds, sizeof ds, cudaMemcpyHostToDevice, s->stream);
+    s->cur = 0;
+    if (e == cudaSuccess) e = launch_init<R>(kp, s->phi[0].p, s->mu[0].p, (const double *)s->seeds.p, ng, H, s->stream);
+    if (e == cudaSuccess)
+        e = launch_post<R>(kp, (const DevState *)s->state.p, s->phi[0].p, s->mu[0].p, (PlaneT<R> *)s->tab.p,
+                           s->stream);
+    // the host buffers above are stack/heap locals: wait for the copies before returning
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return latch(s, cuda_status(e));
+    s->latched = PF_OK;
+    return PF_OK;
+}
+
+static const size_t kChunkCells = (size_t)1 << 22;  // staging chunk for host transfers
+
+template <typename R>
+static int do_read(pf_sim *s, double *phi, double *mu)
+{
+    const KParams<R> kp = make_kparams<R>(s);
+    const size_t plane = (size_t)s->nx * s->ny, n = s->ncell();
+    int pk = (int)std::max<size_t>(1, std::min<size_t>(s->nz, kChunkCells / plane));
+    DevBuf stg;
+    int r = dev_alloc(stg, (size_t)pk * plane * 6 * sizeof(double), s->stream);
+    if (r != PF_OK) return r;
+    double *dphi = (double *)stg.p, *dmu = dphi + (size_t)pk * plane * 4;
+    cudaError_t e = cudaSuccess;
+    for (int k0 = 0; k0 < s->nz && e == cudaSuccess; k0 += pk) {
+        const int nk = std::min(pk, s->nz - k0);
+        const size_t m = (size_t)nk * plane;
+        e = launch_pack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, phi ? dphi : nullptr,
+                           mu ? dmu : nullptr, k0, nk, s->stream);
+        for (int c = 0; c < 4 && phi && e == cudaSuccess; c++)
+            e = cudaMemcpyAsync(phi + (size_t)c * n + (size_t)k0 * plane, dphi + (size_t)c * m, m * sizeof(double),
+                                cudaMemcpyDeviceToHost, s->stream);
+        for (int c = 0; c < 2 && mu && e == cudaSuccess; c++)
+            e = cudaMemcpyAsync(mu + (size_t)c * n + (size_t)k0 * plane, dmu + (size_t)c * m, m * sizeof(double),
+                                cudaMemcpyDeviceToHost, s->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    dev_free(stg, s->stream);
+    return e == cudaSuccess ? PF_OK : latch(s, cuda_status(e));
+}
+
+template <typename R>
+static int do_write(pf_sim *s, const double *phi, const double *mu)
+{
+    const KParams<R> kp = make_kparams<R>(s);
+    const size_t plane = (size_t)s->nx * s->ny, n = s->ncell();
+    int pk = (int)std::max<size_t>(1, std::min<size_t>(s->nz, kChunkCells / plane));
+    DevBuf stg;
+    int r = dev_alloc(stg, (size_t)pk * plane * 6 * sizeof(double), s->stream);
+    if (r != PF_OK) return r;
+    double *dphi = (double *)stg.p, *dmu = dphi + (size_t)pk * plane * 4;
+    cudaError_t e = cudaSuccess;
+    for (int k0 = 0; k0 < s->nz && e == cudaSuccess; k0 += pk) {
+        const int nk = std::min(pk, s->nz - k0);
+        const size_t m = (size_t)nk * plane;
+        for (int c = 0; c < 4 && e == cudaSuccess; c++)
+            e = cudaMemcpyAsync(dphi + (size_t)c * m, phi + (size_t)c * n + (size_t)k0 * plane, m * sizeof(double),
+                                cudaMemcpyHostToDevice, s->stream);
+        for (int c = 0; c < 2 && e == cudaSuccess; c++)
+            e = cudaMemcpyAsync(dmu + (size_t)c * m, mu + (size_t)c * n + (size_t)k0 * plane, m * sizeof(double),
+                                cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = launch_unpack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, dphi, dmu, k0,
+                                 nk, s->stream);
+        // the staging buffer is reused by the next chunk
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    }
+    dev_free(stg, s->stream);
+    return e == cudaSuccess ? PF_OK : latch(s, cuda_status(e));
+}
+
+template <typename R>
+static int do_reduce(pf_sim *s, double out[8])
+{
+    const KParams<R> kp = make_kparams<R>(s);
+    cudaError_t e = launch_reduce<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p,
+                                     (double *)s->red.p, s->stream);
+    std::vector<double> h((size_t)s->nz * 8);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), s->red.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return latch(s, cuda_status(e));
+    for (int q = 0; q < 8; q++) out[q] = 0.0;
+    for (int k = 0; k < s->nz; k++)
+        for (int q = 0; q < 8; q++) out[q] += h[(size_t)k * 8 + q];
+    return PF_OK;
+}
+
+static int read_state(pf_sim *s, DevState *ds)
+{
+    cudaError_t e = cudaMemcpyAsync(ds, s->state.p, sizeof *ds, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? PF_OK : latch(s, cuda_status(e));
+}
+
+#define PF_DISPATCH(s, fn, ...) ((s)->p.precision == PF_FP64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+const char *pf_strerror(int st)
+{
+    switch (st) {
+    case PF_OK: return "ok";
+    case PF_E_INVAL: return "invalid argument";
+    case PF_E_NOMEM: return "out of memory (or admission refused)";
+    case PF_E_CUDA: return "CUDA error";
+    case PF_E_UNSTABLE: return "non-finite value in phi or mu";
+    case PF_E_TIMEOUT: return "timed out";
+    case PF_E_CANCELLED: return "cancelled";
+    case PF_E_PENDING: return "pending";
+    default: return "unknown status";
+    }
+}
+
+int pf_default_params(pf_params *p)
+{
+    if (!p) return PF_E_INVAL;
+    memset(p, 0, sizeof *p);
+    p->version = PF_PARAMS_VERSION;
+    p->precision = PF_FP64;
+    p->dx = 1.0;
+    p->eps = 4.0;
+    p->tau = 1.0;
+    p->dt = 0.0;
+    for (int q = 0; q < 6; q++) p->gamma2[q] = 1.0;
+    for (int q = 0; q < 4; q++) p->gamma3[q] = 15.0;
+    const double cE[4][2] = {{0.8, 0.1}, {0.1, 0.8}, {0.1, 0.1}, {1.0 / 3.0, 1.0 / 3.0}};
+    for (int a = 0; a < 4; a++) {
+        p->A[a] = 1.0;
+        p->cE[a][0] = cE[a][0];
+        p->cE[a][1] = cE[a][1];
+        p->kT[a][0] = p->kT[a][1] = a == 3 ? 0.1 : 0.0;
+        p->s[a] = a == 3 ? 0.0 : 1.0;
+        p->D[a] = a == 3 ? 1.0 : 0.0;
+    }
+    p->TE = 1.0;
+    p->G = 1e-3;
+    p->v = 1e-2;
+    p->seed_layers = 8;
+    p->T0 = p->TE - p->G * (double)p->seed_layers;
+    p->n_grains = 12;
+    p->window_trigger_z = 0.0;
+    return PF_OK;
+}
+
+int pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void *ctx)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return PF_E_INVAL;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_ctx = ctx;
+    return PF_OK;
+}
+
+int pf_destroy(pf_sim *s)
+{
+    if (!s) return PF_E_INVAL;
+    cudaStreamSynchronize(s->stream);
+    for (int b = 0; b < 2; b++) {
+        dev_free(s->phi[b], s->stream);
+        dev_free(s->mu[b], s->stream);
+    }
+    dev_free(s->state, s->stream);
+    dev_free(s->parts, s->stream);
+    dev_free(s->tab, s->stream);
+    dev_free(s->seeds, s->stream);
+    dev_free(s->red, s->stream);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return PF_OK;
+}
+
+int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim **out)
+{
+    if (!out) return PF_E_INVAL;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return PF_E_INVAL;
+    if ((size_t)nx * ny > (size_t)1 << 31 || (size_t)nz > (size_t)1 << 24) return PF_E_INVAL;
+    int r = check_params(p);
+    if (r != PF_OK) return r;
+    pf_sim *s = new (std::nothrow) pf_sim;
+    if (!s) return PF_E_NOMEM;
+    s->nx = nx;
+    s->ny = ny;
+    s->nz = nz;
+    s->p = *p;
+    if (!(s->p.dt > 0.0)) s->p.dt = default_dt(s->p, nz);
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete s;
+            return cuda_status(e);
+        }
+        s->own_stream = true;
+    }
+    s->geo = make_geometry(nx, ny, nz, 0);
+    const size_t n = s->ncell(), w = s->wbytes();
+    const size_t tabsz = (size_t)2 * nz * 16 * w;
+    for (int b = 0; b < 2 && r == PF_OK; b++) {
+        r = dev_alloc(s->phi[b], n * 4 * w, s->stream);
+        if (r == PF_OK) r = dev_alloc(s->mu[b], n * 2 * w, s->stream);
+    }
+    if (r == PF_OK) r = dev_alloc(s->state, sizeof(DevState), s->stream);
+    if (r == PF_OK) r = dev_alloc(s->parts, (size_t)s->geo.nparts() * sizeof(Partial), s->stream);
+    if (r == PF_OK) r = dev_alloc(s->tab, tabsz, s->stream);
+    if (r == PF_OK) r = dev_alloc(s->red, (size_t)nz * 8 * sizeof(double), s->stream);
+    if (r != PF_OK) {
+        pf_destroy(s);
+        return r;
+    }
+    // pure liquid, mu = 0, t = 0 until pf_init / pf_write_fields
+    r = PF_DISPATCH(s, do_init, s, (uint64_t)0, 0);
+    if (r != PF_OK) {
+        pf_destroy(s);
+        return r;
+    }
+    *out = s;
+    return PF_OK;
+}
+
+int pf_get_params(const pf_sim *s, pf_params *out)
+{
+    if (!s || !out) return PF_E_INVAL;
+    *out = s->p;
+    return PF_OK;
+}
+
+int pf_init(pf_sim *s, uint64_t seed)
+{
+    if (!s) return PF_E_INVAL;
+    return PF_DISPATCH(s, do_init, s, seed, s->p.n_grains);
+}
+
+int pf_step(pf_sim *s, int nsteps)
+{
+    if (!s || nsteps < 0) return PF_E_INVAL;
+    if (s->latched != PF_OK) return s->latched;
+    if (nsteps == 0) return PF_OK;
+    return PF_DISPATCH(s, do_step, s, nsteps);
+}
+
+int pf_sync(pf_sim *s)
+{
+    if (!s) return PF_E_INVAL;
+    DevState ds;
+    int r = read_state(s, &ds);
+    if (r == PF_OK && ds.nonfinite) latch(s, PF_E_UNSTABLE);
+    r = s->latched;
+    s->latched = PF_OK;
+    if (r == PF_E_UNSTABLE) {
+        // clear the sticky device flag with the latched error
+        ds.nonfinite = 0;
+        cudaMemcpyAsync(s->state.p, &ds, sizeof ds, cudaMemcpyHostToDevice, s->stream);
+        cudaStreamSynchronize(s->stream);
+    }
+    return r;
+}
+
+int pf_read_fields(pf_sim *s, double *phi, double *mu, size_t cap_cells)
+{
+    if (!s || cap_cells < s->ncell()) return PF_E_INVAL;
+    if (!phi && !mu) return PF_OK;
+    return PF_DISPATCH(s, do_read, s, phi, mu);
+}
+
+int pf_write_fields(pf_sim *s, const double *phi, const double *mu)
+{
+    if (!s || !phi || !mu) return PF_E_INVAL;
+    return PF_DISPATCH(s, do_write, s, phi, mu);
+}
+
+int pf_phase_fractions(pf_sim *s, double out[4])
+{
+    if (!s || !out) return PF_E_INVAL;
+    double acc[8];
+    int r = PF_DISPATCH(s, do_reduce, s, acc);
+    if (r != PF_OK) return r;
+    for (int a = 0; a < 4; a++) out[a] = acc[a] / (double)s->ncell();
+    return PF_OK;
+}
+
+int pf_stats(pf_sim *s, double *t, double *off, double solute[2], double *h_int)
+{
+    if (!s) return PF_E_INVAL;
+    double acc[8];
+    int r = PF_DISPATCH(s, do_reduce, s, acc);
+    if (r != PF_OK) return r;
+    DevState ds;
+    r = read_state(s, &ds);
+    if (r != PF_OK) return r;
+    if (t) *t = ds.t;
+    if (off) *off = ds.off;
+    if (solute) {
+        solute[0] = acc[4];
+        solute[1] = acc[5];
+    }
+    if (h_int) *h_int = acc[6] / ((double)s->nx * (double)s->ny);
+    return PF_OK;
+}
+
+int pf_window_shifts(pf_sim *s, int *planes)
+{
+    if (!s || !planes) return PF_E_INVAL;
+    DevState ds;
+    int r = read_state(s, &ds);
+    if (r != PF_OK) return r;
+    *planes = ds.nshift_total;
+    return PF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// pf_internal.h -- structures and launcher declarations shared by the host runtime and the
+// CUDA kernels of the phase-field time step.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/pf.h"
+
+namespace pf {
+
+// Device-resident state of one simulation.  Kernels read the time, window offset and the
+// ring-buffer base from here, so a sequence of steps needs no host round trip and can be
+// replayed from a captured graph.  Written by finalize_kernel (one thread) and the host.
+struct DevState {
+    double t;          // simulation time of the current source fields
+    double off;        // window offset in planes (FP64, integer valued)
+    double h_int;      // interface height measured after the last step
+    int zbase;         // storage plane of logical plane 0 (moving-window ring buffer)
+    int shift;         // planes shifted by the last finalize (0: none); read by post_kernel
+    int nonfinite;     // sticky: a non-finite value was seen
+    int nshift_total;  // planes shifted since init
+};
+
+// Per-CTA partial sums written by the mu-sweep epilogue (FP64).
+struct Partial {
+    double liq_deficit;  // sum over the CTA's cells of (1 - phi_l^{n+1})
+    double nonfinite;    // > 0 when a cell of the CTA produced a non-finite value
+};
+
+// Temperature-dependent constants of one x-y plane (cell centres) or one z-face level,
+// formed once per plane in FP64 and rounded to the stencil precision (the per-slice
+// precompute of the paper's Section 3.3).  16 words so that it stages with vector loads.
+template <typename R>
+struct PlaneT {
+    R T, epsT, Toeps, pad0;
+    R chat[4][2];  // cE_a + kT_a (T - TE)
+    R sT[4];       // s_a (T - TE)
+};
+
+// Scalar parameters handed to the kernels by value.  R is the stencil precision.
+template <typename R>
+struct KParams {
+    int nx, ny, nz;
+    int zchunk;  // planes per CTA along z
+    int window;  // 1: moving window enabled
+    int pad_;
+    R dx, inv_dx, inv_2dx, inv_4dx;
+    R eps, inv_eps;
+    R c_phi;  // dt / (tau eps)
+    R dt, inv_dt;
+    R gamma2[6], gamma3[4];
+    R inv2A[4];  // 1/(2 A_a)
+    R inv4A[4];  // 1/(4 A_a)
+    R DinvA[4];  // D_a/(2 A_a)
+    R kT[4][2];
+    R at_pref;   // pi eps / 4
+    R grad_thr;  // 1e-20 / dx^2
+    R obst;      // 16 / pi^2
+    R dTstep;    // -G v dt
+    // FP64 data for the plane table, the reductions and the clock
+    double T0, G, v, TE, dx64, dt64, eps64, window_trigger_z;
+    double cE[4][2], kT64[4][2], s64[4], A64[4];
+};
+
+// Launch geometry of the sweep kernels.
+struct Geometry {
+    int tx, ty;     // CTA tile in x and y (columns)
+    int zchunk;     // planes per CTA
+    int gx, gy, gz; // grid
+    int nparts() const { return gx * gy * gz; }
+};
+
+Geometry make_geometry(int nx, int ny, int nz, int zchunk_hint);
+
+// Launchers (defined in pf_kernels.cuh, instantiated for float and double).
+template <typename R>
+cudaError_t launch_phi_sweep(const KParams<R> &kp, const Geometry &g, const void *phi, const void *mu,
+                             void *phi_out, const DevState *st, const PlaneT<R> *tab, cudaStream_t s);
+template <typename R>
+cudaError_t launch_mu_sweep(const KParams<R> &kp, const Geometry &g, const void *phi_old, const void *phi_new,
+                            const void *mu, void *mu_out, const DevState *st, const PlaneT<R> *tab,
+                            Partial *parts, cudaStream_t s);
+template <typename R>
+cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s);
+template <typename R>
+cudaError_t launch_post(const KParams<R> &kp, const DevState *st, void *phi, void *mu, PlaneT<R> *tab,
+                        cudaStream_t s);
+template <typename R>
+cudaError_t launch_init(const KParams<R> &kp, void *phi, void *mu, const double *seeds, int n_grains, int H,
+                        cudaStream_t s);
+template <typename R>
+cudaError_t launch_reduce(const KParams<R> &kp, const DevState *st, const void *phi, const void *mu,
+                          double *plane_sums /* nz x 8 */, cudaStream_t s);
+template <typename R>
+cudaError_t launch_pack(const KParams<R> &kp, const DevState *st, const void *phi, const void *mu, double *phi_soa,
+                        double *mu_soa, int k0, int nk, cudaStream_t s);
+template <typename R>
+cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, void *mu, const double *phi_soa,
+                          const double *mu_soa, int k0, int nk, cudaStream_t s);
+
+}  // namespace pf

@@ -1,0 +1,321 @@
+"""Thin ctypes binding of the C ABI in ``include/pf.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``_lib/libpf_gb300.so``; this module never
+computes any part of the time step.  If the library cannot be loaded the import of the
+functions fails loudly: there is no CPU fallback.
+
+Python names follow the C names (``pf_create``, ``pf_init``, ``pf_step``, ...).  Handles
+are opaque ``ctypes.c_void_p`` values.  Non-OK statuses raise :class:`PfError` (except
+``pf_poll``'s ``PF_E_PENDING``, which is returned).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PF_OK = 0
+PF_E_INVAL = -1
+PF_E_NOMEM = -2
+PF_E_CUDA = -3
+PF_E_UNSTABLE = -4
+PF_E_TIMEOUT = -5
+PF_E_CANCELLED = -6
+PF_E_PENDING = 1
+
+PF_FP64 = 0
+PF_FP32 = 1
+PF_FP32_COMP = 2
+PF_PARAMS_VERSION = 1
+
+PRECISIONS = {"fp64": PF_FP64, "fp32": PF_FP32, "fp32c": PF_FP32_COMP}
+
+
+class PfError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {pf_strerror(status)} ({status})" if what else pf_strerror(status))
+
+
+class pf_params(ctypes.Structure):
+    _fields_ = [
+        ("version", ctypes.c_int), ("precision", ctypes.c_int),
+        ("dx", ctypes.c_double), ("eps", ctypes.c_double), ("tau", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("gamma2", ctypes.c_double * 6), ("gamma3", ctypes.c_double * 4),
+        ("A", ctypes.c_double * 4), ("cE", (ctypes.c_double * 2) * 4),
+        ("kT", (ctypes.c_double * 2) * 4), ("s", ctypes.c_double * 4), ("D", ctypes.c_double * 4),
+        ("TE", ctypes.c_double), ("T0", ctypes.c_double), ("G", ctypes.c_double), ("v", ctypes.c_double),
+        ("seed_layers", ctypes.c_int), ("n_grains", ctypes.c_int),
+        ("window_trigger_z", ctypes.c_double),
+    ]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes); every symbol declared in include/pf.h appears here
+_D = ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+SIGNATURES = {
+    "pf_strerror": (ctypes.c_char_p, [_I]),
+    "pf_default_params": (_I, [ctypes.POINTER(pf_params)]),
+    "pf_set_allocator": (_I, [_ALLOC_FN, _FREE_FN, _VP]),
+    "pf_create": (_I, [_I, _I, _I, ctypes.POINTER(pf_params), _VP, ctypes.POINTER(_VP)]),
+    "pf_destroy": (_I, [_VP]),
+    "pf_get_params": (_I, [_VP, ctypes.POINTER(pf_params)]),
+    "pf_init": (_I, [_VP, ctypes.c_uint64]),
+    "pf_step": (_I, [_VP, _I]),
+    "pf_sync": (_I, [_VP]),
+    "pf_read_fields": (_I, [_VP, _DP, _DP, ctypes.c_size_t]),
+    "pf_write_fields": (_I, [_VP, _DP, _DP]),
+    "pf_phase_fractions": (_I, [_VP, _DP]),
+    "pf_stats": (_I, [_VP, _DP, _DP, _DP, _DP]),
+    "pf_window_shifts": (_I, [_VP, ctypes.POINTER(_I)]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(auto_build: bool = True):
+    """Load the CUDA library (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if auto_build and _build.is_stale():
+                _build.build()
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path} (run paper_1506_01684_gb300.build.build())")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != PF_OK:
+        raise PfError(st, what)
+    return st
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_DP)
+
+
+# ---------------------------------------------------------------------------------------
+# C ABI, one Python function per C entry point
+# ---------------------------------------------------------------------------------------
+
+def pf_strerror(st: int) -> str:
+    try:
+        return lib(auto_build=False).pf_strerror(st).decode()
+    except Exception:  # library not loadable: still give a readable message
+        return f"status {st}"
+
+
+def pf_default_params(precision: int = PF_FP64) -> pf_params:
+    p = pf_params()
+    _check(lib().pf_default_params(ctypes.byref(p)), "pf_default_params")
+    p.precision = precision
+    return p
+
+
+def params_from_dict(d: dict, precision: int = PF_FP64) -> pf_params:
+    """Fill a pf_params from the plain parameter dict used by ``workloads``."""
+    p = pf_params()
+    p.version = PF_PARAMS_VERSION
+    p.precision = precision
+    p.dx, p.eps, p.tau, p.dt = d["dx"], d["eps"], d["tau"], d["dt"]
+    for i in range(6):
+        p.gamma2[i] = d["gamma2"][i]
+    for i in range(4):
+        p.gamma3[i] = d["gamma3"][i]
+    for a in range(4):
+        p.A[a], p.s[a], p.D[a] = d["A"][a], d["s"][a], d["D"][a]
+        for c in range(2):
+            p.cE[a][c] = d["cE"][a][c]
+            p.kT[a][c] = d["kT"][a][c]
+    p.TE, p.T0, p.G, p.v = d["TE"], d["T0"], d["G"], d["v"]
+    p.seed_layers, p.n_grains = int(d["seed_layers"]), int(d["n_grains"])
+    p.window_trigger_z = d["window_trigger_z"]
+    return p
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def pf_set_allocator(alloc, free_fn, ctx=None):
+    """Install device allocator hooks (ctypes callbacks of the pf_alloc_fn / pf_free_fn types);
+    None, None restores cudaMalloc/cudaFree.  The caller keeps the callbacks alive."""
+    return _check(lib().pf_set_allocator(alloc or _ALLOC_FN(), free_fn or _FREE_FN(), ctx), "pf_set_allocator")
+
+
+def pf_create(nx: int, ny: int, nz: int, params: pf_params, stream=None):
+    h = _VP()
+    _check(lib().pf_create(nx, ny, nz, ctypes.byref(params), _stream_handle(stream), ctypes.byref(h)),
+           "pf_create")
+    return h
+
+
+def pf_destroy(sim):
+    return _check(lib().pf_destroy(sim), "pf_destroy")
+
+
+def pf_get_params(sim) -> pf_params:
+    p = pf_params()
+    _check(lib().pf_get_params(sim, ctypes.byref(p)), "pf_get_params")
+    return p
+
+
+def pf_init(sim, seed: int):
+    return _check(lib().pf_init(sim, ctypes.c_uint64(seed)), "pf_init")
+
+
+def pf_step(sim, nsteps: int):
+    return _check(lib().pf_step(sim, nsteps), "pf_step")
+
+
+def pf_sync(sim):
+    return _check(lib().pf_sync(sim), "pf_sync")
+
+
+def pf_read_fields(sim, phi: np.ndarray | None, mu: np.ndarray | None):
+    n = None
+    for a in (phi, mu):
+        if a is not None:
+            n = a.shape[-1] * a.shape[-2] * a.shape[-3]
+    return _check(lib().pf_read_fields(sim, _dp(phi) if phi is not None else None,
+                                       _dp(mu) if mu is not None else None, n or 0), "pf_read_fields")
+
+
+def pf_write_fields(sim, phi: np.ndarray, mu: np.ndarray):
+    return _check(lib().pf_write_fields(sim, _dp(phi), _dp(mu)), "pf_write_fields")
+
+
+def pf_phase_fractions(sim) -> np.ndarray:
+    out = np.zeros(4)
+    _check(lib().pf_phase_fractions(sim, _dp(out)), "pf_phase_fractions")
+    return out
+
+
+def pf_stats(sim):
+    t, off, h = _D(), _D(), _D()
+    sol = np.zeros(2)
+    _check(lib().pf_stats(sim, ctypes.byref(t), ctypes.byref(off), _dp(sol), ctypes.byref(h)), "pf_stats")
+    return {"t": t.value, "window_offset": off.value, "solute": sol, "h_int": h.value}
+
+
+def pf_window_shifts(sim) -> int:
+    n = _I()
+    _check(lib().pf_window_shifts(sim, ctypes.byref(n)), "pf_window_shifts")
+    return n.value
+
+
+# ---------------------------------------------------------------------------------------
+# device memory through PyTorch's caching allocator (optional plumbing)
+# ---------------------------------------------------------------------------------------
+_hooks = None
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route the library's device allocations through torch.cuda's caching allocator."""
+    global _hooks
+    if not enable:
+        _check(lib().pf_set_allocator(_ALLOC_FN(), _FREE_FN(), None), "pf_set_allocator")
+        _hooks = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _hooks = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    _check(lib().pf_set_allocator(_hooks[0], _hooks[1], None), "pf_set_allocator")
+
+
+# ---------------------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------------------
+class Simulation:
+    """Owns one pf_sim handle; numpy in/out in the host layout (component, z, y, x)."""
+
+    def __init__(self, nx, ny, nz, params: dict | pf_params, precision="fp64", stream=None):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        p = params if isinstance(params, pf_params) else params_from_dict(params, prec)
+        p.precision = prec
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.h = pf_create(nx, ny, nz, p, stream)
+
+    def close(self):
+        if self.h:
+            pf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def params(self) -> pf_params:
+        return pf_get_params(self.h)
+
+    def init(self, seed: int):
+        pf_init(self.h, seed)
+        return self
+
+    def step(self, n: int = 1):
+        pf_step(self.h, n)
+        return self
+
+    def sync(self):
+        pf_sync(self.h)
+        return self
+
+    def fields(self):
+        phi = np.empty((4, self.nz, self.ny, self.nx))
+        mu = np.empty((2, self.nz, self.ny, self.nx))
+        pf_read_fields(self.h, phi, mu)
+        return phi, mu
+
+    def set_fields(self, phi, mu):
+        pf_write_fields(self.h, np.ascontiguousarray(phi, dtype=np.float64),
+                        np.ascontiguousarray(mu, dtype=np.float64))
+        return self
+
+    def fractions(self):
+        return pf_phase_fractions(self.h)
+
+    def stats(self):
+        return pf_stats(self.h)
+
+    def shifts(self):
+        return pf_window_shifts(self.h)

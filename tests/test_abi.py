@@ -1,0 +1,62 @@
+"""The C ABI library loads and exports every symbol include/pf.h declares (no GPU needed;
+no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1506_01684_gb300 import build, pf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "pf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(pf_[a-z0-9_]+)\s*\(", text))
+    names -= {"pf_alloc_fn", "pf_free_fn"}
+    return sorted(names)
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    L = ctypes.CDLL(path)
+    declared = _declared()
+    assert "pf_create" in declared and "pf_step" in declared
+    for name in declared:
+        assert hasattr(L, name), name
+    # the binding wraps every declared entry point under the same name
+    for name in declared:
+        assert name in pf.SIGNATURES, name
+        assert callable(getattr(pf, name)), name
+
+
+def test_host_only_entry_points():
+    # calls that touch no device: defaults, error strings, argument checks
+    p = pf.pf_default_params()
+    assert p.version == pf.PF_PARAMS_VERSION and p.eps == 4.0 and p.gamma3[2] == 15.0
+    assert abs(p.T0 - (1.0 - 8e-3)) < 1e-15
+    assert pf.pf_strerror(pf.PF_E_UNSTABLE).startswith("non-finite")
+    L = pf.lib()
+    h = ctypes.c_void_p()
+    assert L.pf_create(0, 4, 4, ctypes.byref(p), None, ctypes.byref(h)) == pf.PF_E_INVAL
+    bad = pf.pf_default_params()
+    bad.version = 99
+    assert L.pf_create(4, 4, 4, ctypes.byref(bad), None, ctypes.byref(h)) == pf.PF_E_INVAL
+    assert L.pf_step(None, 1) == pf.PF_E_INVAL
+    assert L.pf_default_params(None) == pf.PF_E_INVAL
+
+
+def test_default_params_match_the_workload_parameter_set():
+    from paper_1506_01684_gb300 import workloads as W
+    d = W.symmetric_params()
+    p = pf.pf_default_params()
+    q = pf.params_from_dict(d)
+    for f, _ in pf.pf_params._fields_:
+        a, b = getattr(p, f), getattr(q, f)
+        if isinstance(a, (int, float)):
+            assert a == b, f
+        else:
+            assert list(map(lambda x: list(x) if hasattr(x, "__len__") else x, a)) == \
+                list(map(lambda x: list(x) if hasattr(x, "__len__") else x, b)), f

@@ -1,0 +1,224 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (stated by the method's targets):
+  * FP64 GPU vs oracle: 1e-12 -- phi absolute, mu relative to max(|mu_ref|_inf, 1e-8);
+  * FP32 GPU vs oracle: max |dphi| <= 2e-5 and |dmu|/scale <= 2e-5 after 200 steps;
+  * the initial condition and the window shift counts are integer decisions: bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1506_01684_gb300 import pf
+from paper_1506_01684_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pf.lib()  # loads (and if needed builds) the CUDA library; fails loudly if it cannot
+
+
+def _mu_err(mu, ref):
+    return np.abs(mu - ref).max() / max(np.abs(ref).max(), 1e-8)
+
+
+def _pair(params, nx, ny, nz, precision="fp64"):
+    sim = pf.Simulation(nx, ny, nz, params, precision)
+    ref = oracle.State(params, nx, ny, nz)
+    return sim, ref
+
+
+def test_effective_dt_matches_the_oracle_bitwise():
+    for nz in (64, 1024, 7):
+        p = W.symmetric_params()
+        sim = pf.Simulation(8, 8, nz, p)
+        assert sim.params.dt == oracle.default_dt(p, nz)
+        sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,grains,seed", [((32, 32, 64), 12, 0), ((37, 21, 19), 9, 5), ((1, 3, 12), 4, 2)])
+def test_voronoi_initial_condition_is_bit_exact(precision, shape, grains, seed):
+    nx, ny, nz = shape
+    p = W.symmetric_params(n_grains=grains)
+    sim, ref = _pair(p, nx, ny, nz, precision)
+    sim.init(seed)
+    ref.init(seed)
+    phi, mu = sim.fields()
+    assert (phi == ref.phi).all()
+    assert (mu == 0).all()
+    st = sim.stats()
+    assert st["t"] == 0.0 and st["window_offset"] == 0.0
+
+
+def test_fp64_one_step_matches_the_oracle():
+    p = W.symmetric_params()
+    sim, ref = _pair(p, 32, 32, 64)
+    sim.init(0)
+    ref.init(0)
+    sim.step(1)
+    ref.step(1)
+    phi, mu = sim.fields()
+    assert np.abs(phi - ref.phi).max() <= 1e-12
+    assert _mu_err(mu, ref.mu) <= 1e-12
+
+
+def test_fp64_config0_200_steps_match_the_oracle():
+    # 32x32x64, 12 grains, seed 0, 200 steps (the small plain-FP64 configuration)
+    p = W.symmetric_params()
+    sim, ref = _pair(p, 32, 32, 64)
+    sim.init(0)
+    ref.init(0)
+    sim.step(200)
+    ref.step(200)
+    sim.sync()
+    phi, mu = sim.fields()
+    e_phi = np.abs(phi - ref.phi).max()
+    e_mu = _mu_err(mu, ref.mu)
+    print(f"fp64 vs oracle after 200 steps: max|dphi| = {e_phi:.3e}, |dmu|/scale = {e_mu:.3e}")
+    assert e_phi <= 1e-12
+    assert e_mu <= 1e-12
+    st = sim.stats()
+    fr, so, h, bad = ref.reduce()
+    assert st["t"] == ref.t
+    np.testing.assert_allclose(sim.fractions(), fr, rtol=1e-12)
+    np.testing.assert_allclose(st["solute"], so, rtol=1e-12)
+    assert st["h_int"] == pytest.approx(h, rel=1e-12)
+
+
+def test_fp32_config0_200_steps_within_the_stated_tolerance():
+    p = W.symmetric_params()
+    sim, ref = _pair(p, 32, 32, 64, "fp32")
+    sim.init(0)
+    ref.init(0)
+    sim.step(200)
+    ref.step(200)
+    sim.sync()
+    phi, mu = sim.fields()
+    e_phi = np.abs(phi - ref.phi).max()
+    e_mu = _mu_err(mu, ref.mu)
+    print(f"fp32 vs oracle after 200 steps: max|dphi| = {e_phi:.3e}, |dmu|/scale = {e_mu:.3e}")
+    assert e_phi <= 2e-5
+    assert e_mu <= 2e-5
+    # the FP32 state stays on the simplex to FP32 rounding
+    assert np.abs(phi.sum(0) - 1).max() <= 4e-7 and phi.min() >= 0
+
+
+@pytest.mark.parametrize("shape", [(37, 21, 19), (33, 9, 70), (1, 1, 16), (2, 3, 5), (64, 8, 3), (5, 40, 1)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_ragged_and_degenerate_shapes_match_the_oracle(shape, precision, tol):
+    # random phase fields on the simplex (sharp and diffuse cells, interfaces everywhere) and random mu;
+    # tiles of 32x8 columns leave ragged tails; nx = 1 or ny = 1 make a cell its own periodic neighbour
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx * 1000 + ny * 10 + nz)
+    p = W.symmetric_params(G=2e-3)
+    phi0 = W.random_simplex_field(rng, nx, ny, nz, sharp=0.4)
+    mu0 = W.random_mu(rng, nx, ny, nz, scale=0.05)
+    sim, ref = _pair(p, nx, ny, nz, precision)
+    if precision == "fp32":
+        phi0 = phi0.astype(np.float32).astype(np.float64)
+        mu0 = mu0.astype(np.float32).astype(np.float64)
+    sim.set_fields(phi0, mu0)
+    ref.phi, ref.mu = phi0.copy(), mu0.copy()
+    sim.step(5)
+    ref.step(5)
+    phi, mu = sim.fields()
+    assert np.abs(phi - ref.phi).max() <= tol
+    assert _mu_err(mu, ref.mu) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_moving_window_shifts_like_the_oracle(precision, tol):
+    # the small configuration with the trigger at z = 10 (so the shift happens within the run)
+    p = W.symmetric_params(window_trigger_z=7.0)
+    p["seed_layers"] = 10
+    sim, ref = _pair(p, 32, 32, 64, precision)
+    sim.init(3)
+    ref.init(3)
+    sim.step(60)
+    ref.step(60)
+    phi, mu = sim.fields()
+    assert ref.shifts > 0
+    assert sim.shifts() == ref.shifts
+    st = sim.stats()
+    assert st["window_offset"] == ref.off
+    assert np.abs(phi - ref.phi).max() <= tol
+    assert _mu_err(mu, ref.mu) <= tol
+
+
+def test_repeated_runs_are_bitwise_identical():
+    p = W.symmetric_params()
+    out = []
+    for _ in range(2):
+        sim = pf.Simulation(40, 24, 48, p, "fp32")
+        sim.init(11)
+        sim.step(30)
+        out.append(sim.fields())
+        out[-1] += (sim.stats()["h_int"],)
+        sim.close()
+    assert (out[0][0] == out[1][0]).all() and (out[0][1] == out[1][1]).all() and out[0][2] == out[1][2]
+
+
+def test_non_finite_values_are_reported_not_propagated_silently():
+    # failure made on the host: a NaN written into mu; the kernels must report PF_E_UNSTABLE
+    p = W.symmetric_params()
+    sim = pf.Simulation(16, 16, 16, p, "fp32")
+    sim.init(1)
+    phi, mu = sim.fields()
+    mu[0, 5, 5, 5] = np.nan
+    sim.set_fields(phi, mu)
+    sim.step(2)
+    with pytest.raises(pf.PfError) as e:
+        sim.sync()
+    assert e.value.status == pf.PF_E_UNSTABLE
+    # the error is reported once; a rewritten state runs on
+    sim.init(1)
+    sim.step(1)
+    sim.sync()
+
+
+def test_fp32_full_size_step_matches_the_oracle_on_sampled_windows():
+    # 256x256x1024 (the single large domain) in the launch configuration the benchmark times:
+    # advance 20 FP32 steps on the GPU, read the state, take one more GPU step, and compare
+    # windows of the result with one oracle step on the same (FP32-valued) input.  A cell's
+    # update depends on cells at most 2 away, so window interiors are exact.
+    nx, ny, nz = 256, 256, 1024
+    p = W.symmetric_params(n_grains=64, window_trigger_z=512.0)
+    sim = pf.Simulation(nx, ny, nz, p, "fp32")
+    sim.init(0)
+    sim.step(20)
+    phi0, mu0 = sim.fields()
+    st0 = sim.stats()
+    sim.step(1)
+    phi1, mu1 = sim.fields()
+    q = oracle.resolve_params(p, nz)
+    q["dt"] = sim.params.dt
+    rng = np.random.default_rng(0)
+    w, hw = 10, 2
+    # windows around the interface (z ~ 0..16), in the liquid, and at the top boundary
+    centres = [(int(rng.integers(0, nx)), int(rng.integers(0, ny)), int(rng.integers(3, 14))) for _ in range(6)]
+    centres += [(17, 200, 500), (250, 3, nz - 1 - w // 2)]
+    for (ci, cj, ck) in centres:
+        xi = np.arange(ci - w // 2 - hw, ci + w // 2 + hw) % nx
+        yj = np.arange(cj - w // 2 - hw, cj + w // 2 + hw) % ny
+        k0 = max(0, ck - w // 2 - hw)
+        k1 = min(nz, ck + w // 2 + hw)
+        sub = np.ix_(np.arange(4), np.arange(k0, k1), yj, xi)
+        subm = np.ix_(np.arange(2), np.arange(k0, k1), yj, xi)
+        st = oracle.State(q, len(xi), len(yj), k1 - k0)
+        st.phi = np.ascontiguousarray(phi0[sub])
+        st.mu = np.ascontiguousarray(mu0[subm])
+        st.t, st.off = st0["t"], st0["window_offset"] + k0
+        st.params = dict(q, window_trigger_z=0.0)
+        st.step(1)
+        kk = slice(0 if k0 == 0 else hw, (k1 - k0) if k1 == nz else (k1 - k0) - hw)
+        inner = (slice(None), kk, slice(hw, -hw), slice(hw, -hw))
+        e_phi = np.abs(phi1[sub][inner] - st.phi[inner]).max()
+        e_mu = np.abs(mu1[subm][inner] - st.mu[inner]).max() / max(np.abs(st.mu[inner]).max(), 1e-8)
+        assert e_phi <= 2e-5, (ci, cj, ck, e_phi)
+        assert e_mu <= 2e-5, (ci, cj, ck, e_mu)
