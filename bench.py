@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the phi+mu time step (arXiv:1506.01684, Algorithm 1) on GB300.
+
+Workload: the single large domain, 256x256x1024 cells, FP32 stencil arithmetic and
+storage, the symmetric parameter set, 64 Voronoi grains in the bottom 8 planes with
+liquid above, moving-window trigger at z = 512 (synthetic inputs; the paper's Ag-Al-Cu
+data is not available).  A "step" is one full explicit step over the domain: phi-sweep,
+mu-sweep, FP64 reductions, window check.  The fields (1.6 GB FP32) are larger than L2,
+so no cache flush is needed between steps.
+
+Printed: one JSON line with MLUP/s (value), the FP64 GPU path on the same workload, the
+FP32-vs-FP64 error, the dominant kernel's roofline, an end-to-end figure through host
+buffers, the oracle's CPU baseline, clocks and launch counts.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank runs its own replica of the
+workload (the path has no exchange step on one domain per GPU: replicas only, weak
+scaling); value = all ranks' cell updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY, NZ = 256, 256, 1024
+GRAINS = 64
+TRIGGER = 512.0
+SEED = 0
+WORKLOAD = "single domain 256x256x1024, 64 grains, window trigger z=512, symmetric parameter set"
+METRIC = "phi+mu step MLUP/s (FP32 stencil; FP64 GPU path and error reported beside it)"
+
+# algorithmic bytes per cell and launch (FP32): the mu-sweep reads phi^n, phi^{n+1} (16 B each)
+# and mu^n (8 B) and writes mu^{n+1} (8 B); the phi-sweep reads phi^n and mu^n and writes phi^{n+1}
+BYTES_PER_CELL = {"mu_sweep": 48, "phi_sweep": 40}
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv") \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/pf_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(min_seconds: float = 10.0, max_steps: int = 40):
+    """The FP64 C oracle as it stands, on this host's cores, on a bounded sample of the
+    workload: the full 256x256 x-y extent, the bottom 16 planes (the 8 seeded planes with
+    their interface and liquid above), the same grains and seed; steps repeated until
+    min_seconds of CPU work (at least 2)."""
+    import oracle
+    from paper_1506_01684_gb300 import workloads as W
+
+    nzs = 16
+    p = W.symmetric_params(n_grains=GRAINS)
+    st = oracle.State(p, NX, NY, nzs).init(SEED)
+    st.step(1)  # first-touch of the oracle's buffers
+    t0 = time.perf_counter()
+    n = 0
+    while n < 2 or (time.perf_counter() - t0 < min_seconds and n < max_steps):
+        st.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    cells = NX * NY * nzs
+    return {"value": cells * n / dt / 1e6, "unit": "MLUP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{NX}x{NY}x{nzs} bottom slab of the workload (64 grains, seed 0), {n} FP64 steps, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank):
+    """The reference arm: the oracle on the host cores, each step one bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1506_01684_gb300 import workloads as W
+
+    nzs = 16
+    p = W.symmetric_params(n_grains=GRAINS)
+    st = oracle.State(p, NX, NY, nzs).init(SEED)
+    for _ in range(args.warmup):
+        st.step(1)
+    t0 = time.perf_counter()
+    st.step(args.steps)
+    dt = time.perf_counter() - t0
+    cells = NX * NY * nzs
+    v = cells * args.steps / dt / 1e6
+    sample = f"{NX}x{NY}x{nzs} bottom slab of the workload per step (64 grains, seed 0), FP64"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "MLUP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "MLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=None, help="steps of the FP64 comparison run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shape", default=None,
+                    help="NXxNYxNZ: a smaller domain of the same workload (profiling captures)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.shape:
+        global NX, NY, NZ, WORKLOAD
+        NX, NY, NZ = (int(x) for x in args.shape.lower().split("x"))
+        WORKLOAD = f"single domain {NX}x{NY}x{NZ}, {GRAINS} grains, window trigger z=512, symmetric parameter set"
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1506_01684_gb300 import pf
+    from paper_1506_01684_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # CPU baseline first (rank 0 only, N = 1 only), before any GPU work starts
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    params = W.symmetric_params(n_grains=GRAINS, window_trigger_z=TRIGGER)
+    stream = torch.cuda.Stream()
+    cells = NX * NY * NZ
+
+    # ---------------- FP32: the timed run ----------------
+    sim = pf.Simulation(NX, NY, NZ, params, "fp32", stream=stream)
+    sim.init(SEED)
+    sol0 = sim.stats()["solute"]
+    sim.step(args.warmup)
+    sim.sync()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    pf.pf_profile(sim.h, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    pf.pf_profile(sim.h, False)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof = pf.pf_profile_read(sim.h)
+    sim.sync()
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * cells * args.steps / (ms_max / 1e3) / 1e6
+    launches = sum(n for _, n in prof.values())
+
+    # dominant kernel and its roofline
+    hbm, peak_kind = _peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / max(prof[dom][1], 1)
+    kern = {k: {"ms_avg": v[0] / max(v[1], 1), "launches": v[1], "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)}
+            for k, v in prof.items()}
+    achieved = BYTES_PER_CELL.get(dom, 0) * cells / (dom_ms / 1e3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get(dom)
+    except Exception:
+        traffic = None
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
+            "bytes_per_cell": BYTES_PER_CELL.get(dom)}
+    for k in kern:
+        if k in BYTES_PER_CELL:
+            kern[k]["gbs"] = BYTES_PER_CELL[k] * cells / (kern[k]["ms_avg"] / 1e3) / 1e9
+    step_bytes = sum(BYTES_PER_CELL.values()) * cells
+    fused_bound = hbm * 1e9 / (48 * cells) * cells / 1e6  # MLUP/s at 48 B/cell (fused FP32 minimum)
+    unfused_bound = hbm * 1e9 / (88 * cells) * cells / 1e6
+
+    phi32, mu32 = sim.fields()
+    st32 = sim.stats()
+    steps_done = args.warmup + args.steps
+
+    # ---------------- FP64 GPU path on the same workload ----------------
+    n64 = args.fp64_steps if args.fp64_steps is not None else steps_done
+    fp64 = None
+    if n64 > 0:
+        s64 = pf.Simulation(NX, NY, NZ, params, "fp64", stream=stream)
+        s64.init(SEED)
+        w64 = min(args.warmup, n64)
+        s64.step(w64)
+        s64.sync()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.step(n64 - w64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        fp64 = {"mlups": cells * (n64 - w64) / (ms64 / 1e3) / 1e6 if n64 > w64 else None, "steps": n64}
+        if n64 == steps_done:
+            phi64, mu64 = s64.fields()
+            st64 = s64.stats()
+            fp64["max_abs_dphi"] = float(np.abs(phi32 - phi64).max())
+            fp64["max_rel_dmu"] = float(np.abs(mu32 - mu64).max() / max(np.abs(mu64).max(), 1e-8))
+            fp64["solute_drift_fp32"] = [float((st32["solute"][c] - sol0[c]) / sol0[c]) for c in range(2)]
+            fp64["solute_drift_fp64"] = [float((st64["solute"][c] - sol0[c]) / sol0[c]) for c in range(2)]
+            del phi64, mu64
+        s64.close()
+
+    # ---------------- end to end through the public API with host buffers ----------------
+    e2e = None
+    if not args.no_e2e:
+        # pinned host copies of the state (FP64 SoA, the ABI's host layout)
+        hphi = torch.from_numpy(phi32).pin_memory()
+        hmu = torch.from_numpy(mu32).pin_memory()
+        ophi = torch.empty_like(hphi).pin_memory()
+        omu = torch.empty_like(hmu).pin_memory()
+        del phi32, mu32
+        import ctypes
+        L = pf.lib()
+        dp = ctypes.POINTER(ctypes.c_double)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g0.record(stream)
+        rc = L.pf_write_fields(sim.h, ctypes.cast(hphi.data_ptr(), dp), ctypes.cast(hmu.data_ptr(), dp))
+        rc |= L.pf_step(sim.h, args.steps)
+        rc |= L.pf_read_fields(sim.h, ctypes.cast(ophi.data_ptr(), dp), ctypes.cast(omu.data_ptr(), dp), cells)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        assert rc == 0, rc
+        nbytes = cells * 6 * 8
+        e2e = {"value": cells * args.steps / wall / 1e6, "unit": "MLUP/s",
+               "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
+               "what": "pf_write_fields (pinned FP64 host state) + pf_step(K) + pf_read_fields, wall clock"}
+    sim.close()
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "nz": NZ, "cells": cells, "precision": "fp32",
+                   "parallelism": f"replicas x{world}", "l2": "inputs (1.6 GB of fields) larger than L2"},
+        "roofline": roof,
+        "kernels": kern,
+        "bounds_mlups": {"fused_48B": fused_bound, "unfused_88B": unfused_bound,
+                         "this_design_bytes_per_cell": sum(BYTES_PER_CELL.values())},
+        "frac_of_unfused_bound": value / unfused_bound, "frac_of_fused_bound": value / fused_bound,
+        "fp64": fp64, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+        "window": {"h_int": st32["h_int"], "offset": st32["window_offset"]},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

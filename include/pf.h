@@ -144,6 +144,24 @@ int pf_stats(pf_sim *sim, double *t, double *window_offset, double solute[2], do
 /* Number of window shifts (planes moved) since pf_init.  Synchronising. */
 int pf_window_shifts(pf_sim *sim, int *planes);
 
+/* Kernel classes of the per-kernel timers. */
+enum {
+    PF_K_PHI = 0,      /* phi-sweep (Eq. 1-2 and the projection) */
+    PF_K_MU = 1,       /* mu-sweep (Eq. 3-4) with the FP64 partial sums */
+    PF_K_FINALIZE = 2, /* FP64 reduction of the partials, clock, window decision */
+    PF_K_POST = 3,     /* plane-table rebuild and fill of planes entering the window */
+    PF_K_COUNT = 8
+};
+
+/* Per-kernel device timers (the paper measures kernels separately, Section 5.1).  With
+ * enable = 1, every later launch of pf_step is bracketed by CUDA events recorded on the
+ * sim's stream; enable = 0 stops recording (pending records are kept).  Not synchronising. */
+int pf_profile(pf_sim *sim, int enable);
+
+/* Device milliseconds and launch counts per kernel class (arrays of PF_K_COUNT) accumulated
+ * since the last read; resets the accumulators.  Synchronising. */
+int pf_profile_read(pf_sim *sim, double ms[], int launches[]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,7 @@ def lib():
                 "orc_splitmix64_n": (ctypes.c_uint64, [ctypes.c_uint64, _I, _P(ctypes.c_uint64)]),
                 "orc_voronoi_seeds": (None, [_I, _I, _I, _I, ctypes.c_uint64, _DP]),
                 "orc_init": (None, [pp, _I, _I, _I, ctypes.c_uint64, _DP, _DP, _IP]),
+                "orc_num_threads": (_I, []),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -304,6 +305,11 @@ class State:
 
     def reduce(self):
         return reduce(self.params, self.phi, self.mu, self.t, self.off)
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle's sweeps run on."""
+    return int(lib().orc_num_threads())
 
 
 def splitmix64(seed: int, n: int):

@@ -700,3 +700,16 @@ void orc_init(const orc_params *p, int nx, int ny, int nz, uint64_t seed, double
             }
     free(seeds);
 }
+
+/* Number of OpenMP threads the sweeps use (1 without OpenMP). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -98,6 +98,14 @@ struct pf_sim {
     DevBuf red;            // nz x 8 FP64 plane sums
     int cur = 0;           // index of the source buffers
     int latched = PF_OK;
+    // per-kernel timers
+    bool prof = false;
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
     size_t ncell() const { return (size_t)nx * ny * nz; }
     size_t wbytes() const { return p.precision == PF_FP64 ? 8 : 4; }
 };
@@ -222,6 +230,32 @@ static int check_params(const pf_params *p)
 // ------------------------------------------------------------------------------------------
 // precision-dispatched bodies
 // ------------------------------------------------------------------------------------------
+static cudaEvent_t pool_event(pf_sim *s)
+{
+    if (!s->pool.empty()) {
+        cudaEvent_t e = s->pool.back();
+        s->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Launch f() on the sim's stream, bracketed by timing events when profiling is on.
+template <typename F>
+static cudaError_t timed(pf_sim *s, int cls, F &&f)
+{
+    if (!s->prof) return f();
+    cudaEvent_t a = pool_event(s), b = pool_event(s);
+    if (!a || !b) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaEventRecord(a, s->stream);
+    if (e == cudaSuccess) e = f();
+    if (e == cudaSuccess) e = cudaEventRecord(b, s->stream);
+    s->recs.push_back({cls, a, b});
+    return e;
+}
+
 template <typename R>
 static int do_step(pf_sim *s, int n)
 {
@@ -232,12 +266,18 @@ static int do_step(pf_sim *s, int n)
     for (int q = 0; q < n; q++) {
         const int a = s->cur, b = 1 - s->cur;
         cudaError_t e;
-        e = launch_phi_sweep<R>(kp, s->geo, s->phi[a].p, s->mu[a].p, s->phi[b].p, st, tab, s->stream);
+        e = timed(s, PF_K_PHI, [&] {
+            return launch_phi_sweep<R>(kp, s->geo, s->phi[a].p, s->mu[a].p, s->phi[b].p, st, tab, s->stream);
+        });
         if (e == cudaSuccess)
-            e = launch_mu_sweep<R>(kp, s->geo, s->phi[a].p, s->phi[b].p, s->mu[a].p, s->mu[b].p, st, tab, parts,
-                                   s->stream);
-        if (e == cudaSuccess) e = launch_finalize<R>(kp, st, parts, s->geo.nparts(), s->stream);
-        if (e == cudaSuccess) e = launch_post<R>(kp, st, s->phi[b].p, s->mu[b].p, tab, s->stream);
+            e = timed(s, PF_K_MU, [&] {
+                return launch_mu_sweep<R>(kp, s->geo, s->phi[a].p, s->phi[b].p, s->mu[a].p, s->mu[b].p, st, tab,
+                                          parts, s->stream);
+            });
+        if (e == cudaSuccess)
+            e = timed(s, PF_K_FINALIZE, [&] { return launch_finalize<R>(kp, st, parts, s->geo.nparts(), s->stream); });
+        if (e == cudaSuccess)
+            e = timed(s, PF_K_POST, [&] { return launch_post<R>(kp, st, s->phi[b].p, s->mu[b].p, tab, s->stream); });
         if (e != cudaSuccess) return latch(s, cuda_status(e));
         s->cur = b;
     }
@@ -439,6 +479,11 @@ int pf_destroy(pf_sim *s)
     dev_free(s->tab, s->stream);
     dev_free(s->seeds, s->stream);
     dev_free(s->red, s->stream);
+    for (auto &r : s->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : s->pool) cudaEventDestroy(e);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
     return PF_OK;
@@ -581,6 +626,35 @@ int pf_window_shifts(pf_sim *s, int *planes)
     int r = read_state(s, &ds);
     if (r != PF_OK) return r;
     *planes = ds.nshift_total;
+    return PF_OK;
+}
+
+int pf_profile(pf_sim *s, int enable)
+{
+    if (!s) return PF_E_INVAL;
+    s->prof = enable != 0;
+    return PF_OK;
+}
+
+int pf_profile_read(pf_sim *s, double ms[], int launches[])
+{
+    if (!s || !ms || !launches) return PF_E_INVAL;
+    for (int c = 0; c < PF_K_COUNT; c++) {
+        ms[c] = 0.0;
+        launches[c] = 0;
+    }
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return latch(s, cuda_status(e));
+    for (auto &r : s->recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess && r.cls >= 0 && r.cls < PF_K_COUNT) {
+            ms[r.cls] += (double)t;
+            launches[r.cls] += 1;
+        }
+        s->pool.push_back(r.a);
+        s->pool.push_back(r.b);
+    }
+    s->recs.clear();
     return PF_OK;
 }
 

@@ -81,7 +81,12 @@ SIGNATURES = {
     "pf_phase_fractions": (_I, [_VP, _DP]),
     "pf_stats": (_I, [_VP, _DP, _DP, _DP, _DP]),
     "pf_window_shifts": (_I, [_VP, ctypes.POINTER(_I)]),
+    "pf_profile": (_I, [_VP, _I]),
+    "pf_profile_read": (_I, [_VP, _DP, ctypes.POINTER(_I)]),
 }
+
+PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_COUNT = 0, 1, 2, 3, 8
+KERNEL_NAMES = {PF_K_PHI: "phi_sweep", PF_K_MU: "mu_sweep", PF_K_FINALIZE: "finalize", PF_K_POST: "post"}
 
 
 def library_path() -> str:
@@ -230,6 +235,18 @@ def pf_window_shifts(sim) -> int:
     n = _I()
     _check(lib().pf_window_shifts(sim, ctypes.byref(n)), "pf_window_shifts")
     return n.value
+
+
+def pf_profile(sim, enable: bool = True):
+    return _check(lib().pf_profile(sim, 1 if enable else 0), "pf_profile")
+
+
+def pf_profile_read(sim):
+    """{kernel name: (device ms, launches)} accumulated since the last read."""
+    ms = np.zeros(PF_K_COUNT)
+    n = (_I * PF_K_COUNT)()
+    _check(lib().pf_profile_read(sim, _dp(ms), n), "pf_profile_read")
+    return {KERNEL_NAMES.get(c, f"k{c}"): (float(ms[c]), int(n[c])) for c in range(PF_K_COUNT) if n[c] > 0}
 
 
 # ---------------------------------------------------------------------------------------
