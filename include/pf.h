@@ -162,6 +162,50 @@ int pf_profile(pf_sim *sim, int enable);
  * since the last read; resets the accumulators.  Synchronising. */
 int pf_profile_read(pf_sim *sim, double ms[], int launches[]);
 
+/*
+ * Allocation-free step.  The paper has no counterpart; this entry point serves callers that
+ * cannot allocate device memory: code that must live inside a device-memory budget owned by
+ * another allocator (a framework's caching pool or a fixed serving arena, where a private
+ * cudaMalloc would take memory the owner has already promised elsewhere), and code that must
+ * not pay cudaMalloc/cudaFree's implicit device-wide synchronisation in the middle of its work.
+ *
+ * One explicit step (Algorithm 1: phi-sweep, then mu-sweep) on caller-owned device fields,
+ * asynchronously on `stream` (a cudaStream_t; NULL = the legacy default stream).  The call
+ * allocates nothing: it calls no cudaMalloc/cudaFree and no allocating library routine.  Its
+ * scratch (a 64-byte step state, the per-plane temperature table and the per-CTA FP64 partial
+ * sums) lives in one file-scope device array of PF_NOALLOC_SCRATCH_BYTES, which every GPU that
+ * loads this library holds until the process exits.
+ *
+ *   phi_src, mu_src : the state at time t (device, read only), precision p->precision
+ *                     (PF_FP32: float, PF_FP64: double; PF_FP32_COMP is rejected).
+ *                     Layout: array of cells in [z][y][x] order, x fastest; a phi cell is 4
+ *                     consecutive words (phase 3 = liquid), a mu cell 2 words.  phi buffers
+ *                     must be 16-byte aligned, mu buffers 8-byte (FP32) or 16-byte (FP64)
+ *                     aligned; misaligned pointers are rejected with PF_E_INVAL.
+ *   phi_dst, mu_dst : the state at t + dt (device, written), same layout; must not overlap
+ *                     the sources.
+ *   t, window_offset: simulation time and window offset (planes) of the source state.  The
+ *                     window is never shifted by this call.
+ *   h_int_out       : optional host pointer.  When given, the call waits for `stream` and
+ *                     stores the interface height sum(1 - phi_l)/(nx ny) of the new state;
+ *                     then a non-finite value in the new state returns PF_E_UNSTABLE.
+ *
+ * Errors: PF_E_INVAL for null or misaligned fields, sizes < 1, bad parameters, PF_FP32_COMP, or a grid that
+ * needs more scratch than PF_NOALLOC_SCRATCH_BYTES (needed bytes: 256 + 32 w nz rounded up to
+ * 256, plus 16 per CTA of the sweeps = ceil(nx/32) ceil(ny/8) ceil(nz/zchunk); w = 4 or 8;
+ * e.g. 256x256x1024 in FP32 needs about 0.2 MB); PF_E_CUDA if a launch fails.
+ *
+ * Set-up: the first call on each device (with that device current) looks up the scratch
+ * array's device address once; make that first call before any stream capture.  Every call
+ * shares the one array and leaves its contents behind (each call rewrites what it reads), so
+ * calls whose work overlaps on the GPU -- on different streams or different host threads --
+ * race on the scratch and must be serialised by the caller.
+ */
+#define PF_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+int pf_step_noalloc(int nx, int ny, int nz, const pf_params *p, double t, double window_offset,
+                    const void *phi_src, const void *mu_src, void *phi_dst, void *mu_dst, double *h_int_out,
+                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,6 +26,7 @@ UNITS = {
     "pf_kernels_f32.cu": [],
     "pf_kernels_f64.cu": ["-fmad=false"],
     "pf_api.cpp": [],
+    "pf_noalloc.cu": [],
 }
 
 

@@ -187,6 +187,28 @@ static KParams<R> make_kparams(const pf_sim *s)
 // ------------------------------------------------------------------------------------------
 // helpers
 // ------------------------------------------------------------------------------------------
+static double default_dt(const pf_params &p, int nz);
+static int check_params(const pf_params *p);
+
+namespace pf {
+// Kernel parameters for a grid without a pf_sim (used by the allocation-free entry point).
+template <typename R>
+KParams<R> kparams_for(const pf_params &p, int nx, int ny, int nz, const Geometry &g)
+{
+    pf_sim tmp;
+    tmp.nx = nx;
+    tmp.ny = ny;
+    tmp.nz = nz;
+    tmp.p = p;
+    tmp.geo = g;
+    return make_kparams<R>(&tmp);
+}
+template KParams<float> kparams_for<float>(const pf_params &, int, int, int, const Geometry &);
+template KParams<double> kparams_for<double>(const pf_params &, int, int, int, const Geometry &);
+double resolved_dt(const pf_params &p, int nz) { return p.dt > 0.0 ? p.dt : default_dt(p, nz); }
+int validate_params(const pf_params *p) { return check_params(p); }
+}  // namespace pf
+
 static int cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return PF_OK;

@@ -74,6 +74,12 @@ struct Geometry {
 
 Geometry make_geometry(int nx, int ny, int nz, int zchunk_hint);
 
+// Parameter plumbing shared with the allocation-free entry point (pf_noalloc.cu).
+template <typename R>
+KParams<R> kparams_for(const pf_params &p, int nx, int ny, int nz, const Geometry &g);
+double resolved_dt(const pf_params &p, int nz);
+int validate_params(const pf_params *p);
+
 // Launchers (defined in pf_kernels.cuh, instantiated for float and double).
 template <typename R>
 cudaError_t launch_phi_sweep(const KParams<R> &kp, const Geometry &g, const void *phi, const void *mu,

@@ -83,6 +83,7 @@ SIGNATURES = {
     "pf_window_shifts": (_I, [_VP, ctypes.POINTER(_I)]),
     "pf_profile": (_I, [_VP, _I]),
     "pf_profile_read": (_I, [_VP, _DP, ctypes.POINTER(_I)]),
+    "pf_step_noalloc": (_I, [_I, _I, _I, ctypes.POINTER(pf_params), _D, _D, _VP, _VP, _VP, _VP, _DP, _VP]),
 }
 
 PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_COUNT = 0, 1, 2, 3, 8
@@ -247,6 +248,18 @@ def pf_profile_read(sim):
     n = (_I * PF_K_COUNT)()
     _check(lib().pf_profile_read(sim, _dp(ms), n), "pf_profile_read")
     return {KERNEL_NAMES.get(c, f"k{c}"): (float(ms[c]), int(n[c])) for c in range(PF_K_COUNT) if n[c] > 0}
+
+
+def pf_step_noalloc(nx: int, ny: int, nz: int, params: pf_params, t: float, window_offset: float,
+                    phi_src: int, mu_src: int, phi_dst: int, mu_dst: int, want_h_int: bool = True,
+                    stream=None):
+    """One step on caller-owned device fields (device pointers as ints), allocating nothing.
+    Returns the interface height of the new state when want_h_int (this waits for the stream)."""
+    h = _D()
+    _check(lib().pf_step_noalloc(nx, ny, nz, ctypes.byref(params), t, window_offset, phi_src, mu_src,
+                                 phi_dst, mu_dst, ctypes.byref(h) if want_h_int else None,
+                                 _stream_handle(stream)), "pf_step_noalloc")
+    return h.value if want_h_int else None
 
 
 # ---------------------------------------------------------------------------------------
