@@ -150,8 +150,17 @@ enum {
     PF_K_MU = 1,       /* mu-sweep (Eq. 3-4) with the FP64 partial sums */
     PF_K_FINALIZE = 2, /* FP64 reduction of the partials, clock, window decision */
     PF_K_POST = 3,     /* plane-table rebuild and fill of planes entering the window */
+    PF_K_FUSED = 4,    /* fused phi+mu step (both sweeps in one pass) */
     PF_K_COUNT = 8
 };
+
+/* Kernel variants of pf_step.  UNFUSED runs Algorithm 1 as two kernels (the phi-sweep writes
+ * phi^{n+1}, the mu-sweep reads it back: 88 algorithmic bytes per FP32 cell); FUSED computes
+ * phi^{n+1} and mu^{n+1} in one pass (each CTA recomputes phi^{n+1} on a one-cell ring around its
+ * tile: 48 bytes per FP32 cell).  Both give the same result up to rounding order.  AUTO (the
+ * default) picks FUSED for FP32 and UNFUSED for FP64. */
+enum { PF_VARIANT_AUTO = 0, PF_VARIANT_UNFUSED = 1, PF_VARIANT_FUSED = 2 };
+int pf_set_variant(pf_sim *sim, int variant);
 
 /* Per-kernel device timers (the paper measures kernels separately, Section 5.1).  With
  * enable = 1, every later launch of pf_step is bracketed by CUDA events recorded on the

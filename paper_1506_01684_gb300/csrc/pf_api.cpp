@@ -89,7 +89,9 @@ struct pf_sim {
     pf_params p;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    Geometry geo;
+    Geometry geo;          // unfused sweeps
+    Geometry geo_fused;    // fused step (longer z chunks: its prologue recomputes two planes)
+    int variant = PF_VARIANT_AUTO;
     DevBuf phi[2], mu[2];  // AoS fields of the stencil precision
     DevBuf state;          // DevState
     DevBuf parts;          // Partial[geo.nparts()]
@@ -278,26 +280,43 @@ static cudaError_t timed(pf_sim *s, int cls, F &&f)
     return e;
 }
 
+static bool use_fused(const pf_sim *s)
+{
+    if (s->variant == PF_VARIANT_FUSED) return true;
+    if (s->variant == PF_VARIANT_UNFUSED) return false;
+    return s->p.precision != PF_FP64;
+}
+
 template <typename R>
 static int do_step(pf_sim *s, int n)
 {
-    const KParams<R> kp = make_kparams<R>(s);
+    const bool fused = use_fused(s);
+    KParams<R> kp = make_kparams<R>(s);
+    if (fused) kp.zchunk = s->geo_fused.zchunk;
     DevState *st = (DevState *)s->state.p;
     PlaneT<R> *tab = (PlaneT<R> *)s->tab.p;
     Partial *parts = (Partial *)s->parts.p;
+    const int nparts = fused ? s->geo_fused.nparts() : s->geo.nparts();
     for (int q = 0; q < n; q++) {
         const int a = s->cur, b = 1 - s->cur;
         cudaError_t e;
-        e = timed(s, PF_K_PHI, [&] {
-            return launch_phi_sweep<R>(kp, s->geo, s->phi[a].p, s->mu[a].p, s->phi[b].p, st, tab, s->stream);
-        });
-        if (e == cudaSuccess)
-            e = timed(s, PF_K_MU, [&] {
-                return launch_mu_sweep<R>(kp, s->geo, s->phi[a].p, s->phi[b].p, s->mu[a].p, s->mu[b].p, st, tab,
-                                          parts, s->stream);
+        if (fused) {
+            e = timed(s, PF_K_FUSED, [&] {
+                return launch_fused_step<R>(kp, s->geo_fused, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st,
+                                            tab, parts, s->stream);
             });
+        } else {
+            e = timed(s, PF_K_PHI, [&] {
+                return launch_phi_sweep<R>(kp, s->geo, s->phi[a].p, s->mu[a].p, s->phi[b].p, st, tab, s->stream);
+            });
+            if (e == cudaSuccess)
+                e = timed(s, PF_K_MU, [&] {
+                    return launch_mu_sweep<R>(kp, s->geo, s->phi[a].p, s->phi[b].p, s->mu[a].p, s->mu[b].p, st, tab,
+                                              parts, s->stream);
+                });
+        }
         if (e == cudaSuccess)
-            e = timed(s, PF_K_FINALIZE, [&] { return launch_finalize<R>(kp, st, parts, s->geo.nparts(), s->stream); });
+            e = timed(s, PF_K_FINALIZE, [&] { return launch_finalize<R>(kp, st, parts, nparts, s->stream); });
         if (e == cudaSuccess)
             e = timed(s, PF_K_POST, [&] { return launch_post<R>(kp, st, s->phi[b].p, s->mu[b].p, tab, s->stream); });
         if (e != cudaSuccess) return latch(s, cuda_status(e));
@@ -537,6 +556,14 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
         s->own_stream = true;
     }
     s->geo = make_geometry(nx, ny, nz, 0);
+    {
+        // fused: about 6 CTAs per SM in total, 32..256 planes per CTA
+        const long tiles = (long)s->geo.gx * s->geo.gy;
+        long chunks = (152L * 6 + tiles - 1) / tiles;
+        int zc = (int)((nz + chunks - 1) / chunks);
+        zc = std::max(32, std::min(256, zc));
+        s->geo_fused = make_geometry(nx, ny, nz, zc);
+    }
     const size_t n = s->ncell(), w = s->wbytes();
     const size_t tabsz = (size_t)2 * nz * 16 * w;
     for (int b = 0; b < 2 && r == PF_OK; b++) {
@@ -544,7 +571,9 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
         if (r == PF_OK) r = dev_alloc(s->mu[b], n * 2 * w, s->stream);
     }
     if (r == PF_OK) r = dev_alloc(s->state, sizeof(DevState), s->stream);
-    if (r == PF_OK) r = dev_alloc(s->parts, (size_t)s->geo.nparts() * sizeof(Partial), s->stream);
+    if (r == PF_OK)
+        r = dev_alloc(s->parts, (size_t)std::max(s->geo.nparts(), s->geo_fused.nparts()) * sizeof(Partial),
+                      s->stream);
     if (r == PF_OK) r = dev_alloc(s->tab, tabsz, s->stream);
     if (r == PF_OK) r = dev_alloc(s->red, (size_t)nz * 8 * sizeof(double), s->stream);
     if (r != PF_OK) {
@@ -648,6 +677,13 @@ int pf_window_shifts(pf_sim *s, int *planes)
     int r = read_state(s, &ds);
     if (r != PF_OK) return r;
     *planes = ds.nshift_total;
+    return PF_OK;
+}
+
+int pf_set_variant(pf_sim *s, int variant)
+{
+    if (!s || variant < PF_VARIANT_AUTO || variant > PF_VARIANT_FUSED) return PF_E_INVAL;
+    s->variant = variant;
     return PF_OK;
 }
 

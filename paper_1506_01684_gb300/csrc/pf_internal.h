@@ -89,6 +89,10 @@ cudaError_t launch_mu_sweep(const KParams<R> &kp, const Geometry &g, const void 
                             const void *mu, void *mu_out, const DevState *st, const PlaneT<R> *tab,
                             Partial *parts, cudaStream_t s);
 template <typename R>
+cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const void *phi, const void *mu,
+                              void *phi_out, void *mu_out, const DevState *st, const PlaneT<R> *tab, Partial *parts,
+                              cudaStream_t s);
+template <typename R>
 cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s);
 template <typename R>
 cudaError_t launch_post(const KParams<R> &kp, const DevState *st, void *phi, void *mu, PlaneT<R> *tab,

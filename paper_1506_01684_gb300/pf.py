@@ -82,12 +82,16 @@ SIGNATURES = {
     "pf_stats": (_I, [_VP, _DP, _DP, _DP, _DP]),
     "pf_window_shifts": (_I, [_VP, ctypes.POINTER(_I)]),
     "pf_profile": (_I, [_VP, _I]),
+    "pf_set_variant": (_I, [_VP, _I]),
     "pf_profile_read": (_I, [_VP, _DP, ctypes.POINTER(_I)]),
     "pf_step_noalloc": (_I, [_I, _I, _I, ctypes.POINTER(pf_params), _D, _D, _VP, _VP, _VP, _VP, _DP, _VP]),
 }
 
-PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_COUNT = 0, 1, 2, 3, 8
-KERNEL_NAMES = {PF_K_PHI: "phi_sweep", PF_K_MU: "mu_sweep", PF_K_FINALIZE: "finalize", PF_K_POST: "post"}
+PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_FUSED, PF_K_COUNT = 0, 1, 2, 3, 4, 8
+KERNEL_NAMES = {PF_K_PHI: "phi_sweep", PF_K_MU: "mu_sweep", PF_K_FINALIZE: "finalize", PF_K_POST: "post",
+                PF_K_FUSED: "fused_step"}
+PF_VARIANT_AUTO, PF_VARIANT_UNFUSED, PF_VARIANT_FUSED = 0, 1, 2
+VARIANTS = {"auto": PF_VARIANT_AUTO, "unfused": PF_VARIANT_UNFUSED, "fused": PF_VARIANT_FUSED}
 
 
 def library_path() -> str:
@@ -238,6 +242,11 @@ def pf_window_shifts(sim) -> int:
     return n.value
 
 
+def pf_set_variant(sim, variant):
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    return _check(lib().pf_set_variant(sim, v), "pf_set_variant")
+
+
 def pf_profile(sim, enable: bool = True):
     return _check(lib().pf_profile(sim, 1 if enable else 0), "pf_profile")
 
@@ -296,12 +305,13 @@ def use_torch_allocator(enable: bool = True):
 class Simulation:
     """Owns one pf_sim handle; numpy in/out in the host layout (component, z, y, x)."""
 
-    def __init__(self, nx, ny, nz, params: dict | pf_params, precision="fp64", stream=None):
+    def __init__(self, nx, ny, nz, params: dict | pf_params, precision="fp64", stream=None, variant="auto"):
         prec = PRECISIONS[precision] if isinstance(precision, str) else precision
         p = params if isinstance(params, pf_params) else params_from_dict(params, prec)
         p.precision = prec
         self.nx, self.ny, self.nz = nx, ny, nz
         self.h = pf_create(nx, ny, nz, p, stream)
+        pf_set_variant(self.h, variant)
 
     def close(self):
         if self.h:

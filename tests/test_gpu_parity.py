@@ -27,8 +27,8 @@ def _mu_err(mu, ref):
     return np.abs(mu - ref).max() / max(np.abs(ref).max(), 1e-8)
 
 
-def _pair(params, nx, ny, nz, precision="fp64"):
-    sim = pf.Simulation(nx, ny, nz, params, precision)
+def _pair(params, nx, ny, nz, precision="fp64", variant="auto"):
+    sim = pf.Simulation(nx, ny, nz, params, precision, variant=variant)
     ref = oracle.State(params, nx, ny, nz)
     return sim, ref
 
@@ -56,9 +56,10 @@ def test_voronoi_initial_condition_is_bit_exact(precision, shape, grains, seed):
     assert st["t"] == 0.0 and st["window_offset"] == 0.0
 
 
-def test_fp64_one_step_matches_the_oracle():
+@pytest.mark.parametrize("variant", ["unfused", "fused"])
+def test_fp64_one_step_matches_the_oracle(variant):
     p = W.symmetric_params()
-    sim, ref = _pair(p, 32, 32, 64)
+    sim, ref = _pair(p, 32, 32, 64, "fp64", variant)
     sim.init(0)
     ref.init(0)
     sim.step(1)
@@ -68,10 +69,11 @@ def test_fp64_one_step_matches_the_oracle():
     assert _mu_err(mu, ref.mu) <= 1e-12
 
 
-def test_fp64_config0_200_steps_match_the_oracle():
+@pytest.mark.parametrize("variant", ["unfused", "fused"])
+def test_fp64_config0_200_steps_match_the_oracle(variant):
     # 32x32x64, 12 grains, seed 0, 200 steps (the small plain-FP64 configuration)
     p = W.symmetric_params()
-    sim, ref = _pair(p, 32, 32, 64)
+    sim, ref = _pair(p, 32, 32, 64, "fp64", variant)
     sim.init(0)
     ref.init(0)
     sim.step(200)
@@ -80,7 +82,7 @@ def test_fp64_config0_200_steps_match_the_oracle():
     phi, mu = sim.fields()
     e_phi = np.abs(phi - ref.phi).max()
     e_mu = _mu_err(mu, ref.mu)
-    print(f"fp64 vs oracle after 200 steps: max|dphi| = {e_phi:.3e}, |dmu|/scale = {e_mu:.3e}")
+    print(f"fp64 {variant} vs oracle after 200 steps: max|dphi| = {e_phi:.3e}, |dmu|/scale = {e_mu:.3e}")
     assert e_phi <= 1e-12
     assert e_mu <= 1e-12
     st = sim.stats()
@@ -91,9 +93,10 @@ def test_fp64_config0_200_steps_match_the_oracle():
     assert st["h_int"] == pytest.approx(h, rel=1e-12)
 
 
-def test_fp32_config0_200_steps_within_the_stated_tolerance():
+@pytest.mark.parametrize("variant", ["unfused", "fused"])
+def test_fp32_config0_200_steps_within_the_stated_tolerance(variant):
     p = W.symmetric_params()
-    sim, ref = _pair(p, 32, 32, 64, "fp32")
+    sim, ref = _pair(p, 32, 32, 64, "fp32", variant)
     sim.init(0)
     ref.init(0)
     sim.step(200)
@@ -102,7 +105,7 @@ def test_fp32_config0_200_steps_within_the_stated_tolerance():
     phi, mu = sim.fields()
     e_phi = np.abs(phi - ref.phi).max()
     e_mu = _mu_err(mu, ref.mu)
-    print(f"fp32 vs oracle after 200 steps: max|dphi| = {e_phi:.3e}, |dmu|/scale = {e_mu:.3e}")
+    print(f"fp32 {variant} vs oracle after 200 steps: max|dphi| = {e_phi:.3e}, |dmu|/scale = {e_mu:.3e}")
     assert e_phi <= 2e-5
     assert e_mu <= 2e-5
     # the FP32 state stays on the simplex to FP32 rounding
@@ -111,7 +114,8 @@ def test_fp32_config0_200_steps_within_the_stated_tolerance():
 
 @pytest.mark.parametrize("shape", [(37, 21, 19), (33, 9, 70), (1, 1, 16), (2, 3, 5), (64, 8, 3), (5, 40, 1)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
-def test_ragged_and_degenerate_shapes_match_the_oracle(shape, precision, tol):
+@pytest.mark.parametrize("variant", ["unfused", "fused"])
+def test_ragged_and_degenerate_shapes_match_the_oracle(shape, precision, tol, variant):
     # random phase fields on the simplex (sharp and diffuse cells, interfaces everywhere) and random mu;
     # tiles of 32x8 columns leave ragged tails; nx = 1 or ny = 1 make a cell its own periodic neighbour
     nx, ny, nz = shape
@@ -119,7 +123,7 @@ def test_ragged_and_degenerate_shapes_match_the_oracle(shape, precision, tol):
     p = W.symmetric_params(G=2e-3)
     phi0 = W.random_simplex_field(rng, nx, ny, nz, sharp=0.4)
     mu0 = W.random_mu(rng, nx, ny, nz, scale=0.05)
-    sim, ref = _pair(p, nx, ny, nz, precision)
+    sim, ref = _pair(p, nx, ny, nz, precision, variant)
     if precision == "fp32":
         phi0 = phi0.astype(np.float32).astype(np.float64)
         mu0 = mu0.astype(np.float32).astype(np.float64)
@@ -133,11 +137,12 @@ def test_ragged_and_degenerate_shapes_match_the_oracle(shape, precision, tol):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
-def test_moving_window_shifts_like_the_oracle(precision, tol):
-    # the small configuration with the trigger at z = 10 (so the shift happens within the run)
+@pytest.mark.parametrize("variant", ["unfused", "fused"])
+def test_moving_window_shifts_like_the_oracle(precision, tol, variant):
+    # the small configuration with the trigger at z = 7 (so the shift happens within the run)
     p = W.symmetric_params(window_trigger_z=7.0)
     p["seed_layers"] = 10
-    sim, ref = _pair(p, 32, 32, 64, precision)
+    sim, ref = _pair(p, 32, 32, 64, precision, variant)
     sim.init(3)
     ref.init(3)
     sim.step(60)
@@ -151,17 +156,39 @@ def test_moving_window_shifts_like_the_oracle(precision, tol):
     assert _mu_err(mu, ref.mu) <= tol
 
 
-def test_repeated_runs_are_bitwise_identical():
+@pytest.mark.parametrize("variant", ["unfused", "fused"])
+def test_repeated_runs_are_bitwise_identical(variant):
     p = W.symmetric_params()
     out = []
     for _ in range(2):
-        sim = pf.Simulation(40, 24, 48, p, "fp32")
+        sim = pf.Simulation(40, 24, 48, p, "fp32", variant=variant)
         sim.init(11)
         sim.step(30)
         out.append(sim.fields())
         out[-1] += (sim.stats()["h_int"],)
         sim.close()
     assert (out[0][0] == out[1][0]).all() and (out[0][1] == out[1][1]).all() and out[0][2] == out[1][2]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
+def test_fused_and_unfused_steps_agree(precision, tol):
+    # the two kernel variants evaluate the same expressions; they may differ only in rounding order
+    nx, ny, nz = 70, 45, 150
+    p = W.symmetric_params(n_grains=15, window_trigger_z=9.0)
+    p["seed_layers"] = 12
+    res = []
+    for variant in ("unfused", "fused"):
+        sim = pf.Simulation(nx, ny, nz, p, precision, variant=variant)
+        sim.init(21)
+        sim.step(40)
+        res.append(sim.fields() + (sim.shifts(), sim.stats()["window_offset"]))
+        sim.close()
+    (pa, ma, sa, oa), (pb, mb, sb, ob) = res
+    print(f"{precision}: fused vs unfused max|dphi| = {np.abs(pa - pb).max():.3e}, "
+          f"max|dmu| = {np.abs(ma - mb).max():.3e}, shifts {sa}/{sb}")
+    assert sa == sb and oa == ob
+    assert np.abs(pa - pb).max() <= tol
+    assert np.abs(ma - mb).max() / max(np.abs(ma).max(), 1e-8) <= tol
 
 
 def test_non_finite_values_are_reported_not_propagated_silently():
