@@ -158,7 +158,7 @@ enum {
  * phi^{n+1}, the mu-sweep reads it back: 88 algorithmic bytes per FP32 cell); FUSED computes
  * phi^{n+1} and mu^{n+1} in one pass (each CTA recomputes phi^{n+1} on a one-cell ring around its
  * tile: 48 bytes per FP32 cell).  Both give the same result up to rounding order.  AUTO (the
- * default) picks FUSED for FP32 and UNFUSED for FP64. */
+ * default) picks the variant measured fastest for the precision. */
 enum { PF_VARIANT_AUTO = 0, PF_VARIANT_UNFUSED = 1, PF_VARIANT_FUSED = 2 };
 int pf_set_variant(pf_sim *sim, int variant);
 
