@@ -40,7 +40,8 @@ METRIC = "phi+mu step MLUP/s (FP32 stencil; FP64 GPU path and error reported bes
 
 # algorithmic bytes per cell and launch (FP32): the mu-sweep reads phi^n, phi^{n+1} (16 B each)
 # and mu^n (8 B) and writes mu^{n+1} (8 B); the phi-sweep reads phi^n and mu^n and writes phi^{n+1}
-BYTES_PER_CELL = {"mu_sweep": 48, "phi_sweep": 40}
+# and the fused step reads phi^n and mu^n and writes phi^{n+1} and mu^{n+1}
+BYTES_PER_CELL = {"mu_sweep": 48, "phi_sweep": 40, "fused_step": 48}
 
 
 def _env_int(name, default):
@@ -171,6 +172,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="steps of the FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variant", default="auto", choices=["auto", "unfused", "fused"],
+                    help="kernel variant of the FP32 step (auto: the library's choice)")
+    ap.add_argument("--grains", type=int, default=GRAINS,
+                    help="Voronoi grains (0: pure liquid, a bulk-only diagnostic)")
     ap.add_argument("--shape", default=None,
                     help="NXxNYxNZ: a smaller domain of the same workload (profiling captures)")
     args = ap.parse_args()
@@ -178,7 +183,9 @@ def main():
     if args.shape:
         global NX, NY, NZ, WORKLOAD
         NX, NY, NZ = (int(x) for x in args.shape.lower().split("x"))
-        WORKLOAD = f"single domain {NX}x{NY}x{NZ}, {GRAINS} grains, window trigger z=512, symmetric parameter set"
+    if args.shape or args.grains != GRAINS:
+        WORKLOAD = (f"single domain {NX}x{NY}x{NZ}, {args.grains} grains, window trigger z=512, "
+                    "symmetric parameter set")
 
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
@@ -209,12 +216,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
 
-    params = W.symmetric_params(n_grains=GRAINS, window_trigger_z=TRIGGER)
+    params = W.symmetric_params(n_grains=args.grains, window_trigger_z=TRIGGER)
     stream = torch.cuda.Stream()
     cells = NX * NY * NZ
 
     # ---------------- FP32: the timed run ----------------
-    sim = pf.Simulation(NX, NY, NZ, params, "fp32", stream=stream)
+    sim = pf.Simulation(NX, NY, NZ, params, "fp32", stream=stream, variant=args.variant)
     sim.init(SEED)
     sol0 = sim.stats()["solute"]
     sim.step(args.warmup)
@@ -264,7 +271,7 @@ def main():
     for k in kern:
         if k in BYTES_PER_CELL:
             kern[k]["gbs"] = BYTES_PER_CELL[k] * cells / (kern[k]["ms_avg"] / 1e3) / 1e9
-    step_bytes = sum(BYTES_PER_CELL.values()) * cells
+    design_bytes = 48 if "fused_step" in prof else 88
     fused_bound = hbm * 1e9 / (48 * cells) * cells / 1e6  # MLUP/s at 48 B/cell (fused FP32 minimum)
     unfused_bound = hbm * 1e9 / (88 * cells) * cells / 1e6
 
@@ -340,7 +347,8 @@ def main():
         "roofline": roof,
         "kernels": kern,
         "bounds_mlups": {"fused_48B": fused_bound, "unfused_88B": unfused_bound,
-                         "this_design_bytes_per_cell": sum(BYTES_PER_CELL.values())},
+                         "this_design_bytes_per_cell": design_bytes},
+        "variant": "fused" if "fused_step" in prof else "unfused",
         "frac_of_unfused_bound": value / unfused_bound, "frac_of_fused_bound": value / fused_bound,
         "fp64": fp64, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
         "window": {"h_int": st32["h_int"], "offset": st32["window_offset"]},

@@ -93,6 +93,7 @@ struct pf_sim {
     Geometry geo_fused;    // fused step (longer z chunks: its prologue recomputes two planes)
     int variant = PF_VARIANT_AUTO;
     DevBuf phi[2], mu[2];  // AoS fields of the stencil precision
+    DevBuf philo[2], mulo[2];  // low words of the compensated FP32 state (PF_FP32_COMP only)
     DevBuf state;          // DevState
     DevBuf parts;          // Partial[geo.nparts()]
     DevBuf tab;            // PlaneT<R>[2 nz]
@@ -115,6 +116,9 @@ struct pf_sim {
     bool use_graphs = true;
     size_t ncell() const { return (size_t)nx * ny * nz; }
     size_t wbytes() const { return p.precision == PF_FP64 ? 8 : 4; }
+    bool comp() const { return p.precision == PF_FP32_COMP; }
+    void *lo_phi(int b) const { return comp() ? philo[b].p : nullptr; }
+    void *lo_mu(int b) const { return comp() ? mulo[b].p : nullptr; }
 };
 
 namespace pf {
@@ -244,7 +248,7 @@ static double default_dt(const pf_params &p, int nz)
 static int check_params(const pf_params *p)
 {
     if (!p || p->version != PF_PARAMS_VERSION) return PF_E_INVAL;
-    if (p->precision != PF_FP64 && p->precision != PF_FP32) return PF_E_INVAL;
+    if (p->precision != PF_FP64 && p->precision != PF_FP32 && p->precision != PF_FP32_COMP) return PF_E_INVAL;
     if (!(p->dx > 0) || !(p->eps > 0) || !(p->tau > 0)) return PF_E_INVAL;
     for (int a = 0; a < 4; a++)
         if (!(p->A[a] > 0) || p->D[a] < 0) return PF_E_INVAL;
@@ -287,6 +291,7 @@ static cudaError_t timed(pf_sim *s, int cls, F &&f)
 
 static bool use_fused(const pf_sim *s)
 {
+    if (s->comp()) return false;  // the compensated state runs on the two sweeps
     if (s->variant == PF_VARIANT_FUSED) return true;
     if (s->variant == PF_VARIANT_UNFUSED) return false;
     return false;  // AUTO: the unfused sweeps (measured faster on 256x256x1024 FP32 so far)
@@ -310,6 +315,18 @@ static int do_step_direct(pf_sim *s, int n)
                 return launch_fused_step<R>(kp, s->geo_fused, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st,
                                             tab, parts, s->stream);
             });
+        } else if (s->comp()) {
+            const KParams<float> &kf = reinterpret_cast<const KParams<float> &>(kp);
+            const PlaneT<float> *tf = reinterpret_cast<const PlaneT<float> *>(tab);
+            e = timed(s, PF_K_PHI, [&] {
+                return launch_phi_sweep_comp(kf, s->geo, s->phi[a].p, s->philo[a].p, s->mu[a].p, s->phi[b].p,
+                                             s->philo[b].p, st, tf, s->stream);
+            });
+            if (e == cudaSuccess)
+                e = timed(s, PF_K_MU, [&] {
+                    return launch_mu_sweep_comp(kf, s->geo, s->phi[a].p, s->phi[b].p, s->mu[a].p, s->mulo[a].p,
+                                                s->mu[b].p, s->mulo[b].p, st, tf, parts, s->stream);
+                });
         } else {
             e = timed(s, PF_K_PHI, [&] {
                 return launch_phi_sweep<R>(kp, s->geo, s->phi[a].p, s->mu[a].p, s->phi[b].p, st, tab, s->stream);
@@ -323,7 +340,9 @@ static int do_step_direct(pf_sim *s, int n)
         if (e == cudaSuccess)
             e = timed(s, PF_K_FINALIZE, [&] { return launch_finalize<R>(kp, st, parts, nparts, s->stream); });
         if (e == cudaSuccess)
-            e = timed(s, PF_K_POST, [&] { return launch_post<R>(kp, st, s->phi[b].p, s->mu[b].p, tab, s->stream); });
+            e = timed(s, PF_K_POST, [&] {
+                return launch_post<R>(kp, st, s->phi[b].p, s->mu[b].p, tab, s->stream, s->lo_phi(b), s->lo_mu(b));
+            });
         if (e != cudaSuccess) return latch(s, cuda_status(e));
         s->cur = b;
     }
@@ -408,6 +427,9 @@ static int do_init(pf_sim *s, uint64_t seed, int ng)
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->state.p, &ds, sizeof ds, cudaMemcpyHostToDevice, s->stream);
     s->cur = 0;
     if (e == cudaSuccess) e = launch_init<R>(kp, s->phi[0].p, s->mu[0].p, (const double *)s->seeds.p, ng, H, s->stream);
+    if (e == cudaSuccess && s->comp())
+        e = cudaMemsetAsync(s->philo[0].p, 0, s->philo[0].bytes, s->stream);
+    if (e == cudaSuccess && s->comp()) e = cudaMemsetAsync(s->mulo[0].p, 0, s->mulo[0].bytes, s->stream);
     if (e == cudaSuccess)
         e = launch_post<R>(kp, (const DevState *)s->state.p, s->phi[0].p, s->mu[0].p, (PlaneT<R> *)s->tab.p,
                            s->stream);
@@ -435,7 +457,7 @@ static int do_read(pf_sim *s, double *phi, double *mu)
         const int nk = std::min(pk, s->nz - k0);
         const size_t m = (size_t)nk * plane;
         e = launch_pack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, phi ? dphi : nullptr,
-                           mu ? dmu : nullptr, k0, nk, s->stream);
+                           mu ? dmu : nullptr, k0, nk, s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
         for (int c = 0; c < 4 && phi && e == cudaSuccess; c++)
             e = cudaMemcpyAsync(phi + (size_t)c * n + (size_t)k0 * plane, dphi + (size_t)c * m, m * sizeof(double),
                                 cudaMemcpyDeviceToHost, s->stream);
@@ -470,7 +492,7 @@ static int do_write(pf_sim *s, const double *phi, const double *mu)
                                 cudaMemcpyHostToDevice, s->stream);
         if (e == cudaSuccess)
             e = launch_unpack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, dphi, dmu, k0,
-                                 nk, s->stream);
+                                 nk, s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
         // the staging buffer is reused by the next chunk
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     }
@@ -483,7 +505,7 @@ static int do_reduce(pf_sim *s, double out[8])
 {
     const KParams<R> kp = make_kparams<R>(s);
     cudaError_t e = launch_reduce<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p,
-                                     (double *)s->red.p, s->stream);
+                                     (double *)s->red.p, s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
     std::vector<double> h((size_t)s->nz * 8);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h.data(), s->red.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
@@ -572,6 +594,8 @@ int pf_destroy(pf_sim *s)
     for (int b = 0; b < 2; b++) {
         dev_free(s->phi[b], s->stream);
         dev_free(s->mu[b], s->stream);
+        dev_free(s->philo[b], s->stream);
+        dev_free(s->mulo[b], s->stream);
     }
     dev_free(s->state, s->stream);
     dev_free(s->parts, s->stream);
@@ -628,6 +652,8 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
     for (int b = 0; b < 2 && r == PF_OK; b++) {
         r = dev_alloc(s->phi[b], n * 4 * w, s->stream);
         if (r == PF_OK) r = dev_alloc(s->mu[b], n * 2 * w, s->stream);
+        if (r == PF_OK && s->comp()) r = dev_alloc(s->philo[b], n * 4 * w, s->stream);
+        if (r == PF_OK && s->comp()) r = dev_alloc(s->mulo[b], n * 2 * w, s->stream);
     }
     if (r == PF_OK) r = dev_alloc(s->state, sizeof(DevState), s->stream);
     if (r == PF_OK)

@@ -64,6 +64,22 @@ struct KParams {
     double cE[4][2], kT64[4][2], s64[4], A64[4];
 };
 
+// One domain of a batched step: its parameters, ping-pong field buffers, state, plane table and
+// partial sums, and its fused-step tile grid.
+template <typename R>
+struct BatchDomain {
+    KParams<R> kp;
+    void *phi[2], *mu[2];
+    DevState *st;
+    PlaneT<R> *tab;
+    Partial *parts;
+    int gx, gy, gz, pad_;
+};
+// One work item of a batched step: a tile of one domain.
+struct BatchItem {
+    int dom, bx, by, bz;
+};
+
 // Launch geometry of the sweep kernels.
 struct Geometry {
     int tx, ty;     // CTA tile in x and y (columns)
@@ -94,20 +110,39 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
                               cudaStream_t s);
 template <typename R>
 cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s);
+// Batched fused step of ndoms domains: counter reset, persistent kernel (ctas CTAs) over the
+// work items, per-domain finalize and post.  parity: index of the source buffers.
+template <typename R>
+cudaError_t launch_batched_step(const BatchDomain<R> *doms, int ndoms, const BatchItem *items, int nitems,
+                                unsigned *counter, int parity, int ctas, int post_blocks, cudaStream_t s);
+template <typename R>
+int fused_ctas_per_sm();
 template <typename R>
 cudaError_t launch_post(const KParams<R> &kp, const DevState *st, void *phi, void *mu, PlaneT<R> *tab,
-                        cudaStream_t s);
+                        cudaStream_t s, void *phi_lo = nullptr, void *mu_lo = nullptr);
 template <typename R>
 cudaError_t launch_init(const KParams<R> &kp, void *phi, void *mu, const double *seeds, int n_grains, int H,
                         cudaStream_t s);
 template <typename R>
 cudaError_t launch_reduce(const KParams<R> &kp, const DevState *st, const void *phi, const void *mu,
-                          double *plane_sums /* nz x 8 */, cudaStream_t s);
+                          double *plane_sums /* nz x 8 */, cudaStream_t s, const void *phi_lo = nullptr,
+                          const void *mu_lo = nullptr);
 template <typename R>
 cudaError_t launch_pack(const KParams<R> &kp, const DevState *st, const void *phi, const void *mu, double *phi_soa,
-                        double *mu_soa, int k0, int nk, cudaStream_t s);
+                        double *mu_soa, int k0, int nk, cudaStream_t s, const void *phi_lo = nullptr,
+                        const void *mu_lo = nullptr);
 template <typename R>
 cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, void *mu, const double *phi_soa,
-                          const double *mu_soa, int k0, int nk, cudaStream_t s);
+                          const double *mu_soa, int k0, int nk, cudaStream_t s, void *phi_lo = nullptr,
+                          void *mu_lo = nullptr);
+
+// Compensated FP32 (state = hi + lo) variants of the two sweeps.
+cudaError_t launch_phi_sweep_comp(const KParams<float> &kp, const Geometry &g, const void *phi, const void *phi_lo,
+                                  const void *mu, void *phi_out, void *phi_out_lo, const DevState *st,
+                                  const PlaneT<float> *tab, cudaStream_t s);
+cudaError_t launch_mu_sweep_comp(const KParams<float> &kp, const Geometry &g, const void *phi_old,
+                                 const void *phi_new, const void *mu, const void *mu_lo, void *mu_out,
+                                 void *mu_out_lo, const DevState *st, const PlaneT<float> *tab, Partial *parts,
+                                 cudaStream_t s);
 
 }  // namespace pf

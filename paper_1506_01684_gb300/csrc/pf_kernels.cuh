@@ -101,11 +101,13 @@ template <typename R>
 __device__ __forceinline__ int code_of(const Ph<R> &a)
 {
     const R o = R(1), z = R(0);
-    if (a.v[0] == o && a.v[1] == z && a.v[2] == z && a.v[3] == z) return 0;
-    if (a.v[1] == o && a.v[0] == z && a.v[2] == z && a.v[3] == z) return 1;
-    if (a.v[2] == o && a.v[0] == z && a.v[1] == z && a.v[3] == z) return 2;
-    if (a.v[3] == o && a.v[0] == z && a.v[1] == z && a.v[2] == z) return 3;
-    return 4;
+    const bool z0 = a.v[0] == z, z1 = a.v[1] == z, z2 = a.v[2] == z, z3 = a.v[3] == z;
+    int c = 4;
+    c = (a.v[3] == o && z0 && z1 && z2) ? 3 : c;
+    c = (a.v[2] == o && z0 && z1 && z3) ? 2 : c;
+    c = (a.v[1] == o && z0 && z2 && z3) ? 1 : c;
+    c = (a.v[0] == o && z1 && z2 && z3) ? 0 : c;
+    return c;
 }
 template <typename R>
 __device__ __forceinline__ bool onehot(const Ph<R> &a)
@@ -195,15 +197,14 @@ __device__ __forceinline__ Ph<R> project_simplex(const Ph<R> &u)
     return o;
 }
 
-// Full cell update of the phi-sweep at one cell.
+// rhs_a of Eq. 2 at one cell.
 //   xm/xp, ym/yp, zm/zp: the six neighbours; F*: the six face terms (minus/plus side).
 template <typename R>
-__device__ __forceinline__ Ph<R> phi_cell(const KParams<R> &kp, const PlaneT<R> &pc, const Ph<R> &P,
-                                          const Ph<R> &xm, const Ph<R> &xp, const Ph<R> &ym,
-                                          const Ph<R> &yp, const Ph<R> &zm, const Ph<R> &zp,
-                                          const Ph<R> &Fxm, const Ph<R> &Fxp, const Ph<R> &Fym,
-                                          const Ph<R> &Fyp, const Ph<R> &Fzm, const Ph<R> &Fzp,
-                                          const Mu<R> &m)
+__device__ __forceinline__ void phi_rhs(const KParams<R> &kp, const PlaneT<R> &pc, const Ph<R> &P, const Ph<R> &xm,
+                                        const Ph<R> &xp, const Ph<R> &ym, const Ph<R> &yp, const Ph<R> &zm,
+                                        const Ph<R> &zp, const Ph<R> &Fxm, const Ph<R> &Fxp, const Ph<R> &Fym,
+                                        const Ph<R> &Fyp, const Ph<R> &Fzm, const Ph<R> &Fzp, const Mu<R> &m,
+                                        R (&rhs)[4])
 {
     const R *G2 = kp.gamma2;
     const R *G3 = kp.gamma3;
@@ -254,18 +255,134 @@ __device__ __forceinline__ Ph<R> phi_cell(const KParams<R> &kp, const PlaneT<R> 
         psi[a] = -mu2 * kp.inv4A[a] - (m.v[0] * pc.chat[a][0] + m.v[1] * pc.chat[a][1]) + pc.sT[a];
         hpsi = hpsi + p[a] * p[a] * inv_S * psi[a];
     }
-    R rhs[4];
 #pragma unroll
     for (int a = 0; a < 4; a++) {
         R dps = R(2) * p[a] * (psi[a] - hpsi) * inv_S;
         rhs[a] = pc.epsT * (R(2) * dadp[a] - div[a]) + pc.Toeps * dom[a] + dps;
     }
+}
+
+// Full cell update of the phi-sweep at one cell: phi^{n+1} = Proj(phi^n - dt/(tau eps)(rhs - mean rhs)).
+template <typename R>
+__device__ __forceinline__ Ph<R> phi_cell(const KParams<R> &kp, const PlaneT<R> &pc, const Ph<R> &P,
+                                          const Ph<R> &xm, const Ph<R> &xp, const Ph<R> &ym,
+                                          const Ph<R> &yp, const Ph<R> &zm, const Ph<R> &zp,
+                                          const Ph<R> &Fxm, const Ph<R> &Fxp, const Ph<R> &Fym,
+                                          const Ph<R> &Fyp, const Ph<R> &Fzm, const Ph<R> &Fzp,
+                                          const Mu<R> &m)
+{
+    R rhs[4];
+    phi_rhs(kp, pc, P, xm, xp, ym, yp, zm, zp, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, m, rhs);
+    const R *p = P.v;
     R mean = (rhs[0] + rhs[1] + rhs[2] + rhs[3]) * R(0.25);
     Ph<R> st;
 #pragma unroll
     for (int a = 0; a < 4; a++) st.v[a] = p[a] - kp.c_phi * (rhs[a] - mean);
     return project_simplex(st);
 }
+
+// ---------------------------------------------------------------------------------------
+// compensated FP32: a state value is the unevaluated sum hi + lo of two floats; increments
+// computed in FP32 from the hi words are accumulated with error-free transformations
+// (Knuth's two-sum, Dekker's fast two-sum), so that increments below the FP32 spacing of the
+// state are not lost.  The simplex projection then runs in this double-float arithmetic.
+// ---------------------------------------------------------------------------------------
+struct DF {
+    float h, l;
+};
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return DF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b)  // |a| >= |b|
+{
+    const float s = a + b;
+    return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_add_f(DF a, float b)
+{
+    DF s = two_sum(a.h, b);
+    return fast_two_sum(s.h, s.l + a.l);
+}
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    DF s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.h, -b.l}); }
+__device__ __forceinline__ bool df_pos(DF a) { return a.h > 0.f || (a.h == 0.f && a.l > 0.f); }
+__device__ __forceinline__ bool df_less(DF a, DF b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+__device__ __forceinline__ DF df_scale2(DF a, float p2) { return DF{a.h * p2, a.l * p2}; }  // exact: p2 a power of 2
+__device__ __forceinline__ DF df_div3(DF a)
+{
+    const float q1 = a.h / 3.f;
+    const float r = fmaf(-3.f, q1, a.h) + a.l;  // the remainder of a.h is exact in the FMA
+    return fast_two_sum(q1, r / 3.f);
+}
+
+// Euclidean projection onto the simplex (reading R6) of double-float values.
+__device__ __forceinline__ void project_simplex_df(const DF (&u)[4], DF (&o)[4])
+{
+    DF s[4] = {u[0], u[1], u[2], u[3]};
+#define PF_DCS(a, b)                \
+    if (df_less(s[a], s[b])) {      \
+        const DF t_ = s[a];         \
+        s[a] = s[b];                \
+        s[b] = t_;                  \
+    }
+    PF_DCS(0, 1);
+    PF_DCS(2, 3);
+    PF_DCS(0, 2);
+    PF_DCS(1, 3);
+    PF_DCS(1, 2);
+#undef PF_DCS
+    DF theta{0.f, 0.f};
+    DF c = s[0];
+    DF t = df_add_f(c, -1.f);
+    if (df_pos(df_sub(s[0], t))) theta = t;
+    c = df_add(c, s[1]);
+    t = df_scale2(df_add_f(c, -1.f), 0.5f);
+    if (df_pos(df_sub(s[1], t))) theta = t;
+    c = df_add(c, s[2]);
+    t = df_div3(df_add_f(c, -1.f));
+    if (df_pos(df_sub(s[2], t))) theta = t;
+    c = df_add(c, s[3]);
+    t = df_scale2(df_add_f(c, -1.f), 0.25f);
+    if (df_pos(df_sub(s[3], t))) theta = t;
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+        const DF r = df_sub(u[a], theta);
+        o[a] = df_pos(r) ? r : DF{0.f, 0.f};
+    }
+}
+
+// Compensated phi update: the increment -dt/(tau eps)(rhs - mean) is formed in FP32 from the hi
+// words and added to hi + lo; the projection runs in double-float.
+__device__ __forceinline__ void phi_cell_comp(const KParams<float> &kp, const PlaneT<float> &pc, const Ph<float> &P,
+                                              const Ph<float> &Plo, const Ph<float> &xm, const Ph<float> &xp,
+                                              const Ph<float> &ym, const Ph<float> &yp, const Ph<float> &zm,
+                                              const Ph<float> &zp, const Ph<float> &Fxm, const Ph<float> &Fxp,
+                                              const Ph<float> &Fym, const Ph<float> &Fyp, const Ph<float> &Fzm,
+                                              const Ph<float> &Fzp, const Mu<float> &m, Ph<float> &out,
+                                              Ph<float> &out_lo)
+{
+    float rhs[4];
+    phi_rhs(kp, pc, P, xm, xp, ym, yp, zm, zp, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, m, rhs);
+    const float mean = (rhs[0] + rhs[1] + rhs[2] + rhs[3]) * 0.25f;
+    DF u[4], o[4];
+#pragma unroll
+    for (int a = 0; a < 4; a++) u[a] = df_add_f(DF{P.v[a], Plo.v[a]}, -(kp.c_phi * (rhs[a] - mean)));
+    project_simplex_df(u, o);
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+        out.v[a] = o[a].h;
+        out_lo.v[a] = o[a].l;
+    }
+}
+
+
 
 // ---------------------------------------------------------------------------------------
 // small helpers
@@ -484,6 +601,53 @@ __device__ __forceinline__ Mu<R> mu_cell(const KParams<R> &kp, const PlaneT<R> *
     return o;
 }
 
+// Compensated mu update: the increment src/chi is formed in FP32 from the hi words (as in mu_cell)
+// and accumulated into hi + lo.
+__device__ __forceinline__ void mu_cell_comp(const KParams<float> &kp, const PlaneT<float> *__restrict__ tc,
+                                             const Ph<float> &nP, const Ph<float> &oP, const Mu<float> &m,
+                                             const Mu<float> &mlo, float div0, float div1, Mu<float> &out,
+                                             Mu<float> &out_lo)
+{
+    float hN[4];
+    float dphi0 = 0.f, dphi1 = 0.f;
+    if (same(nP, oP) && onehot(nP)) {
+#pragma unroll
+        for (int a = 0; a < 4; a++) hN[a] = nP.v[a];
+    } else {
+        float hO[4];
+        const float iSN = rcp(nP.v[0] * nP.v[0] + nP.v[1] * nP.v[1] + nP.v[2] * nP.v[2] + nP.v[3] * nP.v[3]);
+        const float iSO = rcp(oP.v[0] * oP.v[0] + oP.v[1] * oP.v[1] + oP.v[2] * oP.v[2] + oP.v[3] * oP.v[3]);
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            hN[a] = nP.v[a] * nP.v[a] * iSN;
+            hO[a] = oP.v[a] * oP.v[a] * iSO;
+        }
+        const Chat<float> ch = ldg_chat(tc);
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            const float dh = hN[a] - hO[a];
+            dphi0 = dphi0 + (m.v[0] * kp.inv2A[a] + ch.c[a][0]) * dh;
+            dphi1 = dphi1 + (m.v[1] * kp.inv2A[a] + ch.c[a][1]) * dh;
+        }
+    }
+    float chi = 0.f, dT0 = 0.f, dT1 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+        chi = chi + hN[a] * kp.inv2A[a];
+        dT0 = dT0 + hN[a] * kp.kT[a][0];
+        dT1 = dT1 + hN[a] * kp.kT[a][1];
+    }
+    const float src0 = kp.dt * div0 - dphi0 - dT0 * kp.dTstep;
+    const float src1 = kp.dt * div1 - dphi1 - dT1 * kp.dTstep;
+    const float ichi = rcp(chi);
+    const DF r0 = df_add_f(DF{m.v[0], mlo.v[0]}, src0 * ichi);
+    const DF r1 = df_add_f(DF{m.v[1], mlo.v[1]}, src1 * ichi);
+    out.v[0] = r0.h;
+    out.v[1] = r1.h;
+    out_lo.v[0] = r0.l;
+    out_lo.v[1] = r1.l;
+}
+
 // ---------------------------------------------------------------------------------------
 // phi-sweep kernel: phi^{n+1} = Proj(phi^n - dt/(tau eps) (rhs - mean rhs))   (Eq. 1, Eq. 2)
 //
@@ -495,12 +659,14 @@ __device__ __forceinline__ Mu<R> mu_cell(const KParams<R> &kp, const PlaneT<R> *
 // Each thread loads its own column and, for the first 2(TX+TY)+4 threads, one halo cell; the
 // wrapped (periodic) column offsets are computed once.
 // ---------------------------------------------------------------------------------------
-template <typename R, int TX, int TY>
+template <typename R, int TX, int TY, bool COMP = false>
 __global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
                                                           const Mu<R> *__restrict__ mu,
                                                           Ph<R> *__restrict__ phi_out,
                                                           const DevState *__restrict__ st,
-                                                          const PlaneT<R> *__restrict__ tab)
+                                                          const PlaneT<R> *__restrict__ tab,
+                                                          const Ph<R> *__restrict__ phi_lo = nullptr,
+                                                          Ph<R> *__restrict__ phi_out_lo = nullptr)
 {
     constexpr int NT = TX * TY, SX = TX + 2, SY = TY + 2, SN = SX * SY, NR = SN - NT;
     constexpr int FX = TY * (TX + 1), FY = (TY + 1) * TX;
@@ -510,6 +676,7 @@ __global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, 
     Ph<R> *sFx = sP + 4 * SN;                          // [2][FX]
     Ph<R> *sFy = sFx + 2 * FX;                         // [2][FY]
     Mu<R> *sMu = reinterpret_cast<Mu<R> *>(sFy + 2 * FY);  // [4][NT]: own-column mu
+    Ph<R> *sLo = reinterpret_cast<Ph<R> *>(sMu + 4 * NT);   // [4][NT]: own-column low words (COMP)
 
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     const int tid = threadIdx.x;
@@ -534,19 +701,21 @@ __global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, 
     const bool xtra_y = ty == 0;
     const bool xtra_x = ty == 1 % TY && tx < TY;
 
-    Ph<R> pf0, pf1;
+    Ph<R> pf0, pf1, pfl;
     Mu<R> pfm;
     auto prefetch = [&](int k) {
         const size_t b = plane_off(k, nz, zbase, plane);
         pf0 = ldg_ph(phi + b + col0);
         pfm = ldg_mu(mu + b + col0);
         if (s1 >= 0) pf1 = ldg_ph(phi + b + col1);
+        if constexpr (COMP) pfl = ldg_ph(phi_lo + b + col0);
     };
     auto commit = [&](int k) {
         Ph<R> *d = sP + (k & 3) * SN;
         d[s0] = pf0;
         if (s1 >= 0) d[s1] = pf1;
         sMu[(k & 3) * NT + tid] = pfm;
+        if constexpr (COMP) sLo[(k & 3) * NT + tid] = pfl;
     };
     auto S = [&](int k, int li, int lj) -> const Ph<R> & { return sP[(k & 3) * SN + (lj + 1) * SX + (li + 1)]; };
     // x/y face terms of plane q and the z face (q, q+1) of this column
@@ -577,19 +746,34 @@ __global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, 
         {
             const Ph<R> xm = S(p, tx - 1, ty), xp = S(p, tx + 1, ty);
             const Ph<R> ym = S(p, tx, ty - 1), yp = S(p, tx, ty + 1);
-            const bool bulk = onehot(pc) && same(pc, xm) && same(pc, xp) && same(pc, ym) && same(pc, yp) &&
-                              same(pc, pm) && same(pc, pn);
-            Ph<R> out = pc;
+            bool bulk = onehot(pc) && same(pc, xm) && same(pc, xp) && same(pc, ym) && same(pc, yp) &&
+                        same(pc, pm) && same(pc, pn);
+            Ph<R> out = pc, out_lo;
+            if constexpr (COMP) {
+                // a compensated bulk cell also needs a zero low word to be a fixed point
+                out_lo = sLo[(p & 3) * NT + tid];
+                bulk = bulk && out_lo.v[0] == R(0) && out_lo.v[1] == R(0) && out_lo.v[2] == R(0) && out_lo.v[3] == R(0);
+            }
             // bulk cells (one-hot, all six neighbours equal) are fixed points of the step; a warp
             // whose cells are all bulk skips the cell terms (the shortcuts of Section 3.3)
             if (!__all_sync(0xffffffffu, bulk)) {
                 const Ph<R> *fx = sFx + (p & 1) * FX;
                 const Ph<R> *fy = sFy + (p & 1) * FY;
                 const PlaneT<R> T = ldg_plane(tab + p);
-                out = phi_cell(kp, T, pc, xm, xp, ym, yp, pm, pn, fx[ty * (TX + 1) + tx], fx[ty * (TX + 1) + tx + 1],
-                               fy[ty * TX + tx], fy[(ty + 1) * TX + tx], Fz_prev, Fz_cur, sMu[(p & 3) * NT + tid]);
+                if constexpr (COMP) {
+                    phi_cell_comp(kp, T, pc, out_lo, xm, xp, ym, yp, pm, pn, fx[ty * (TX + 1) + tx],
+                                  fx[ty * (TX + 1) + tx + 1], fy[ty * TX + tx], fy[(ty + 1) * TX + tx], Fz_prev, Fz_cur,
+                                  sMu[(p & 3) * NT + tid], out, out_lo);
+                } else {
+                    out = phi_cell(kp, T, pc, xm, xp, ym, yp, pm, pn, fx[ty * (TX + 1) + tx],
+                                   fx[ty * (TX + 1) + tx + 1], fy[ty * TX + tx], fy[(ty + 1) * TX + tx], Fz_prev, Fz_cur,
+                                   sMu[(p & 3) * NT + tid]);
+                }
             }
-            if (valid) st_ph(phi_out + plane_off(p, nz, zbase, plane) + col0, out);
+            if (valid) {
+                st_ph(phi_out + plane_off(p, nz, zbase, plane) + col0, out);
+                if constexpr (COMP) st_ph(phi_out_lo + plane_off(p, nz, zbase, plane) + col0, out_lo);
+            }
         }
         // B(p+1), A(p+3)
         Ph<R> Fz_next = Fz_cur;
@@ -618,14 +802,16 @@ __global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, 
 // loads of plane p+4).  phi^{n+1} sits in a 4-plane shared ring (the faces of plane q read planes
 // q-1..q+1), phi^n and mu^n in 3-plane rings; the cell update reads its own values from registers.
 // ---------------------------------------------------------------------------------------
-template <typename R, int TX, int TY>
+template <typename R, int TX, int TY, bool COMP = false>
 __global__ void __launch_bounds__(TX *TY) mu_sweep_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi_old,
                                                          const Ph<R> *__restrict__ phi_new,
                                                          const Mu<R> *__restrict__ mu,
                                                          Mu<R> *__restrict__ mu_out,
                                                          const DevState *__restrict__ st,
                                                          const PlaneT<R> *__restrict__ tab,
-                                                         Partial *__restrict__ partials)
+                                                         Partial *__restrict__ partials,
+                                                         const Mu<R> *__restrict__ mu_lo = nullptr,
+                                                         Mu<R> *__restrict__ mu_out_lo = nullptr)
 {
     constexpr int NT = TX * TY, SX = TX + 2, SY = TY + 2, SN = SX * SY, NR = SN - NT;
     constexpr int FX = TY * (TX + 1), FY = (TY + 1) * TX;
@@ -762,7 +948,15 @@ __global__ void __launch_bounds__(TX *TY) mu_sweep_kernel(const KParams<R> kp, c
             div1 = div1 + (vyp.v[1] - vym.v[1]) * kp.inv_dx;
             div0 = div0 + (Vz_cur.v[0] - Vz_prev.v[0]) * kp.inv_dx;
             div1 = div1 + (Vz_cur.v[1] - Vz_prev.v[1]) * kp.inv_dx;
-            const Mu<R> out = mu_cell(kp, tab + p, ownN, ownO, ownM, div0, div1);
+            Mu<R> out;
+            if constexpr (COMP) {
+                const Mu<R> mlo = ldg_mu(mu_lo + plane_off(p, nz, zbase, plane) + col0);
+                Mu<R> out_lo;
+                mu_cell_comp(kp, tab + p, ownN, ownO, ownM, mlo, div0, div1, out, out_lo);
+                if (valid) st_mu(mu_out_lo + plane_off(p, nz, zbase, plane) + col0, out_lo);
+            } else {
+                out = mu_cell(kp, tab + p, ownN, ownO, ownM, div0, div1);
+            }
             if (valid) {
                 st_mu(mu_out + plane_off(p, nz, zbase, plane) + col0, out);
                 liq_def += 1.0 - (double)ownN.v[3];
@@ -868,179 +1062,178 @@ __device__ __forceinline__ Mu<R> mu_cell_coded(const KParams<R> &kp, const Plane
     return mu_cell(kp, tc, nP, oP, m, div0, div1);
 }
 
+// One CTA's work of the fused step: tile (bx, by) of x-y columns, z chunk bz.  Shared by the
+// single-domain kernel (tile = block index) and the batched persistent kernel (tile = work item).
 template <typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) fused_step_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
-                                                           const Mu<R> *__restrict__ mu,
-                                                           Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out,
-                                                           const DevState *__restrict__ st,
-                                                           const PlaneT<R> *__restrict__ tab,
-                                                           Partial *__restrict__ partials)
+__device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__restrict__ phi,
+                                           const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
+                                           Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st,
+                                           const PlaneT<R> *__restrict__ tab, Partial *__restrict__ part, int bx,
+                                           int by, int bz, unsigned char *__restrict__ smem_raw)
 {
     constexpr int NT = TX * TY;
     constexpr int SX = TX + 2, SY = TY + 2, SN = SX * SY, NR = SN - NT;  // tile + 1-ring
     constexpr int SX2 = TX + 4, SY2 = TY + 4, SN2 = SX2 * SY2;           // tile + 2-ring
     constexpr int PFX = (TX + 3) * (TY + 2), PFY = (TX + 2) * (TY + 3);   // phi faces of the 1-ring region
     constexpr int FX = TY * (TX + 1), FY = (TY + 1) * TX;                 // mu faces of the tile
-    constexpr int L2 = (SN2 + NT - 1) / NT, L1 = (SN + NT - 1) / NT;      // load slots per thread
-    static_assert(NR <= NT && L2 <= 2 && L1 <= 2, "tile too small for the slot layout");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Ph<R> *sO = reinterpret_cast<Ph<R> *>(smem_raw);       // [3][SN2] phi^n
-    Ph<R> *sN = sO + 3 * SN2;                                // [3][SN]  phi^{n+1}
-    Ph<R> *sFx = sN + 3 * SN;                                // [PFX]
-    Ph<R> *sFy = sFx + PFX;                                  // [PFY]
-    Mu<R> *sM = reinterpret_cast<Mu<R> *>(sFy + PFY);        // [3][SN]  mu^n
-    Mu<R> *sVx = sM + 3 * SN;                                // [FX]
-    Mu<R> *sVy = sVx + FX;                                   // [FY]
-    unsigned char *cO = reinterpret_cast<unsigned char *>(sVy + FY);  // [3][SN2]
-    unsigned char *cN = cO + 3 * SN2;                                  // [3][SN]
+    static_assert(NR <= NT && SN2 <= 2 * NT, "tile too small for the slot layout");
+    // 4-plane rings: the commit of plane q+3 lands in the slot of plane q-1, which no thread
+    // reads once the barrier of plane q has passed (quiet planes have no later barrier)
+    Ph<R> *sO = reinterpret_cast<Ph<R> *>(smem_raw);  // [4][SN2] phi^n
+    Ph<R> *sN = sO + 4 * SN2;                           // [4][SN]  phi^{n+1}
+    Ph<R> *sF = sN + 4 * SN;                            // [PFX + PFY] phi faces (x, then y)
+    Mu<R> *sM = reinterpret_cast<Mu<R> *>(sF + PFX + PFY);  // [4][SN] mu^n
+    Mu<R> *sVx = sM + 4 * SN;                           // [FX]
+    Mu<R> *sVy = sVx + FX;                              // [FY]
+    Ph<R> *sFz = reinterpret_cast<Ph<R> *>(sVy + FY);  // [2][SN] phi z-face terms of the 1-ring cells
+    unsigned char *cO = reinterpret_cast<unsigned char *>(sFz + 2 * SN);  // [4][SN2]
+    unsigned char *cN = cO + 4 * SN2;                                      // [4][SN]
     __shared__ double red[NT / 32][2];
 
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int i0 = bx * TX, j0 = by * TY;
     const bool valid = i0 + tx < nx && j0 + ty < ny;
-    const int z0 = blockIdx.z * kp.zchunk;
+    const int z0 = bz * kp.zchunk;
     const int z1 = min(z0 + kp.zchunk, nz);
     const int zbase = st->zbase;
     const size_t plane = (size_t)nx * ny;
     const int col_own = wrapi(j0 + ty, ny) * nx + wrapi(i0 + tx, nx);
+    const int t1 = (ty + 1) * SX + (tx + 1);   // own cell, 1-ring layout
+    const int t2 = (ty + 2) * SX2 + (tx + 2);  // own cell, 2-ring layout
 
-    auto mod3 = [](int k) { return (k + 6) % 3; };  // k >= -6
-    auto io = [](int li, int lj) { return (lj + 2) * SX2 + (li + 2); };  // 2-ring layout
-    auto in1 = [](int li, int lj) { return (lj + 1) * SX + (li + 1); };  // 1-ring layout
+    auto mod3 = [](int k) { return k & 3; };  // ring slot of plane k (4 slots; k >= -2)
 
-    // load slots (phi^n on the 2-ring region, mu^n on the 1-ring region), offsets computed once
-    int colO[2], idxO[2], colM[2], idxM[2];
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
-        const int r = tid + s * NT;
-        idxO[s] = r < SN2 ? r : -1;
-        colO[s] = 0;
-        if (r < SN2) colO[s] = wrapi(j0 + r / SX2 - 2, ny) * nx + wrapi(i0 + r % SX2 - 2, nx);
-        idxM[s] = r < SN ? r : -1;
-        colM[s] = 0;
-        if (r < SN) colM[s] = wrapi(j0 + r / SX - 1, ny) * nx + wrapi(i0 + r % SX - 1, nx);
-    }
-    // the thread's phi cells on the 1-ring region: its own tile cell, and one ring cell for tid < NR
-    int cli[2], clj[2];
-    cli[0] = tx;
-    clj[0] = ty;
+    // load slots (phi^n on the 2-ring region, mu^n on the 1-ring region), offsets computed once:
+    // slot 0 is cell tid of each region (always present), slot 1 is cell tid + NT where it exists
+    const bool hasO1 = tid + NT < SN2, hasM1 = tid + NT < SN;
+    const int colO0 = wrapi(j0 + tid / SX2 - 2, ny) * nx + wrapi(i0 + tid % SX2 - 2, nx);
+    const int colO1 = hasO1 ? wrapi(j0 + (tid + NT) / SX2 - 2, ny) * nx + wrapi(i0 + (tid + NT) % SX2 - 2, nx) : 0;
+    const int colM0 = wrapi(j0 + tid / SX - 1, ny) * nx + wrapi(i0 + tid % SX - 1, nx);
+    const int colM1 = hasM1 ? wrapi(j0 + (tid + NT) / SX - 1, ny) * nx + wrapi(i0 + (tid + NT) % SX - 1, nx) : 0;
+    // the thread's phi cells on the 1-ring region: its tile cell, and a ring cell for tid < NR
     const bool has_ring = tid < NR;
-    cli[1] = -1;
-    clj[1] = -1;
-    if (has_ring) ring_cell<TX, TY>(tid, cli[1], clj[1]);
+    int o1[2], o2[2];
+    o1[0] = t1;
+    o2[0] = t2;
+    {
+        int li = 0, lj = 0;
+        if (has_ring) ring_cell<TX, TY>(tid, li, lj);
+        o1[1] = (lj + 1) * SX + (li + 1);
+        o2[1] = (lj + 2) * SX2 + (li + 2);
+    }
     const bool xtra_y = ty == 0;
     const bool xtra_x = ty == 1 % TY && tx < TY;
 
-    Ph<R> pfO[2];
-    Mu<R> pfM[2];
+    Ph<R> pfO0, pfO1;
+    Mu<R> pfM0, pfM1;
     auto prefetch = [&](int k) {
         const size_t b = plane_off(k, nz, zbase, plane);
-#pragma unroll
-        for (int s = 0; s < 2; s++) {
-            if (idxO[s] >= 0) pfO[s] = ldg_ph(phi + b + colO[s]);
-            if (idxM[s] >= 0) pfM[s] = ldg_mu(mu + b + colM[s]);
-        }
+        pfO0 = ldg_ph(phi + b + colO0);
+        pfM0 = ldg_mu(mu + b + colM0);
+        if (hasO1) pfO1 = ldg_ph(phi + b + colO1);
+        if (hasM1) pfM1 = ldg_mu(mu + b + colM1);
     };
-    auto commit = [&](int k) {
+    // store the prefetched plane k with its phase codes; returns whether all of this thread's
+    // phi^n cells of the plane are pure liquid (reduced over the CTA by the caller's barrier)
+    auto commit = [&](int k) -> bool {
         const int so = mod3(k);
-#pragma unroll
-        for (int s = 0; s < 2; s++) {
-            if (idxO[s] >= 0) {
-                sO[so * SN2 + idxO[s]] = pfO[s];
-                cO[so * SN2 + idxO[s]] = (unsigned char)code_of(pfO[s]);
-            }
-            if (idxM[s] >= 0) sM[so * SN + idxM[s]] = pfM[s];
+        const int c0 = code_of(pfO0);
+        sO[so * SN2 + tid] = pfO0;
+        cO[so * SN2 + tid] = (unsigned char)c0;
+        sM[so * SN + tid] = pfM0;
+        bool liq = c0 == 3;
+        if (hasO1) {
+            const int c1 = code_of(pfO1);
+            sO[so * SN2 + tid + NT] = pfO1;
+            cO[so * SN2 + tid + NT] = (unsigned char)c1;
+            liq = liq & (c1 == 3);
         }
+        if (hasM1) sM[so * SN + tid + NT] = pfM1;
+        return liq;
     };
-    auto O = [&](int k, int li, int lj) -> const Ph<R> & { return sO[mod3(k) * SN2 + io(li, lj)]; };
-    auto CO = [&](int k, int li, int lj) -> int { return cO[mod3(k) * SN2 + io(li, lj)]; };
-    auto N = [&](int k, int li, int lj) -> const Ph<R> & { return sN[mod3(k) * SN + in1(li, lj)]; };
-    auto CN = [&](int k, int li, int lj) -> int { return cN[mod3(k) * SN + in1(li, lj)]; };
-    auto Mm = [&](int k, int li, int lj) -> const Mu<R> & { return sM[mod3(k) * SN + in1(li, lj)]; };
 
-    // S1: phi face terms of plane q on the 1-ring region (x faces li|li+1 for li in [-2, TX],
-    // rows [-1, TY]; y faces lj|lj+1 for lj in [-2, TY], columns [-1, TX])
+    // phi face terms of plane q on the 1-ring region (x faces li|li+1, li in [-2, TX], rows
+    // [-1, TY]; y faces lj|lj+1, lj in [-2, TY], columns [-1, TX])
     auto phi_faces = [&](int q) {
+        const Ph<R> *Ob = sO + mod3(q) * SN2;
+        const unsigned char *Cb = cO + mod3(q) * SN2;
         for (int f = tid; f < PFX + PFY; f += NT) {
-            int li, lj, ri, rj;
-            Ph<R> *dst;
+            int l, r;
             if (f < PFX) {
-                li = f % (TX + 3) - 2;
-                lj = f / (TX + 3) - 1;
-                ri = li + 1;
-                rj = lj;
-                dst = sFx + f;
+                l = (f / (TX + 3)) * SX2 + f % (TX + 3) + SX2;  // (li+2) + (lj+2) SX2 with li = f%(TX+3)-2
+                r = l + 1;
             } else {
                 const int g = f - PFX;
-                li = g % (TX + 2) - 1;
-                lj = g / (TX + 2) - 2;
-                ri = li;
-                rj = lj + 1;
-                dst = sFy + g;
+                l = (g / (TX + 2)) * SX2 + g % (TX + 2) + 1;  // li = g%(TX+2)-1, lj = g/(TX+2)-2
+                r = l + SX2;
             }
-            const int a = CO(q, li, lj), b = CO(q, ri, rj);
+            const int a = Cb[l], b = Cb[r];
             if (a == b && a < 4) {
                 Ph<R> z;
                 z.v[0] = z.v[1] = z.v[2] = z.v[3] = R(0);
-                *dst = z;
+                sF[f] = z;
             } else {
-                *dst = face_phi(kp, O(q, li, lj), O(q, ri, rj));
+                sF[f] = face_phi(kp, Ob[l], Ob[r]);
             }
         }
     };
-    auto fx_at = [&](int li, int lj) -> const Ph<R> & { return sFx[(lj + 1) * (TX + 3) + (li + 2)]; };
-    auto fy_at = [&](int li, int lj) -> const Ph<R> & { return sFy[(lj + 2) * (TX + 2) + (li + 1)]; };
-    auto zface_phi = [&](int q, int li, int lj) -> Ph<R> {
-        // z face (q | q+1) of a 1-ring cell; equal one-hot cells give zero
-        const int a = CO(q, li, lj), b = CO(q + 1, li, lj);
+    // z face (q | q+1) of the thread's cell s (equal one-hot cells give zero)
+    auto zface_phi = [&](int q, int s) -> Ph<R> {
+        const int qa = mod3(q) * SN2, qb = mod3(q + 1) * SN2;
+        const int a = cO[qa + o2[s]], b = cO[qb + o2[s]];
         if (a == b && a < 4) {
             Ph<R> z;
             z.v[0] = z.v[1] = z.v[2] = z.v[3] = R(0);
             return z;
         }
-        return face_phi(kp, O(q, li, lj), O(q + 1, li, lj));
+        return face_phi(kp, sO[qa + o2[s]], sO[qb + o2[s]]);
     };
-
-    // S2 for one cell: phi^{n+1}(q) at (li, lj), given its z face terms below / above
-    auto phi_new_cell = [&](int q, int li, int lj, const Ph<R> &Fzm, const Ph<R> &Fzp, bool active) -> Ph<R> {
-        const int c = CO(q, li, lj);
-        const bool bulk = !active || (c < 4 && CO(q, li - 1, lj) == c && CO(q, li + 1, lj) == c &&
-                                      CO(q, li, lj - 1) == c && CO(q, li, lj + 1) == c && CO(q - 1, li, lj) == c &&
-                                      CO(q + 1, li, lj) == c);
-        Ph<R> out = O(q, li, lj);
-        if (!__all_sync(0xffffffffu, bulk)) {
-            if (active) {
-                const PlaneT<R> T = ldg_plane(tab + q);
-                out = phi_cell(kp, T, O(q, li, lj), O(q, li - 1, lj), O(q, li + 1, lj), O(q, li, lj - 1),
-                               O(q, li, lj + 1), O(q - 1, li, lj), O(q + 1, li, lj), fx_at(li - 1, lj), fx_at(li, lj),
-                               fy_at(li, lj - 1), fy_at(li, lj), Fzm, Fzp, Mm(q, li, lj));
-            }
-        }
-        return out;
-    };
-    // S2: phi^{n+1}(q) for the thread's cells (a copy of plane nz-1 / 0 outside the domain)
-    Ph<R> Fz_lo[2], Fz_hi[2];
-    auto phi_new_plane = [&](int q) {
-        const int sn = mod3(q) * SN;
-        if (q >= 0 && q < nz) {
+    // z-face terms of the thread's 1-ring cells live in a 2-slot shared ring indexed by the parity
+    // of the face's lower plane; each thread reads back only what it wrote (no barrier needed)
+    auto Fz = [&](int q, int s) -> Ph<R> & { return sFz[(q & 1) * SN + o1[s]]; };
+    // phi^{n+1}(q) for the thread's cells; `quiet`: the planes q-1..q+1 of phi^n are pure liquid on
+    // the 2-ring region, so phi^{n+1} = phi^n there
+    auto phi_new_plane = [&](int q, bool quiet) {
+        const Ph<R> *Om = sO + mod3(q - 1) * SN2, *Oq = sO + mod3(q) * SN2, *Op = sO + mod3(q + 1) * SN2;
+        const unsigned char *Cm = cO + mod3(q - 1) * SN2, *Cq = cO + mod3(q) * SN2, *Cp = cO + mod3(q + 1) * SN2;
+        Ph<R> *Nq = sN + mod3(q) * SN;
+        unsigned char *CNq = cN + mod3(q) * SN;
+        const Mu<R> *Mq = sM + mod3(q) * SN;
 #pragma unroll
-            for (int s = 0; s < 2; s++) {
-                if (s == 1 && tid >= 96) break;  // warps 0-2 hold the ring cells
-                const bool act = s == 0 || has_ring;
-                const int li = cli[s], lj = clj[s];
-                const Ph<R> v = phi_new_cell(q, act ? li : 0, act ? lj : 0, Fz_lo[s], Fz_hi[s], act);
-                if (act) {
-                    sN[sn + in1(li, lj)] = v;
-                    cN[sn + in1(li, lj)] = (unsigned char)code_of(v);
-                    if (s == 0 && valid && q >= z0 && q < z1) st_ph(phi_out + plane_off(q, nz, zbase, plane) + col_own, v);
+        for (int s = 0; s < 2; s++) {
+            if (s == 1 && tid >= ((NR + 31) / 32) * 32) break;  // the first warps hold the ring cells
+            const bool act = s == 0 || has_ring;
+            const int c2 = o2[s];
+            const Ph<R> P = Oq[c2];
+            const int c = Cq[c2];
+            Ph<R> out = P;
+            int cout = c;
+            if (!quiet) {
+                const bool bulk = !act || (c < 4 && Cq[c2 - 1] == c && Cq[c2 + 1] == c && Cq[c2 - SX2] == c &&
+                                           Cq[c2 + SX2] == c && Cm[c2] == c && Cp[c2] == c);
+                if (!__all_sync(0xffffffffu, bulk)) {
+                    if (act) {
+                        const int li = o1[s] % SX - 1, lj = o1[s] / SX - 1;
+                        const PlaneT<R> T = ldg_plane(tab + q);
+                        const Ph<R> *fx = sF + (lj + 1) * (TX + 3) + (li + 2);
+                        const Ph<R> *fy = sF + PFX + (lj + 1) * (TX + 2) + (li + 1);
+                        out = phi_cell(kp, T, P, Oq[c2 - 1], Oq[c2 + 1], Oq[c2 - SX2], Oq[c2 + SX2], Om[c2], Op[c2],
+                                       fx[-1], fx[0], fy[0], fy[TX + 2], Fz(q - 1, s), Fz(q, s), Mq[o1[s]]);
+                        cout = code_of(out);
+                    }
                 }
             }
+            if (act) {
+                Nq[o1[s]] = out;
+                CNq[o1[s]] = (unsigned char)cout;
+                if (s == 0 && valid && q >= z0 && q < z1)
+                    st_ph(phi_out + plane_off(q, nz, zbase, plane) + col_own, out);
+            }
         }
     };
-    // the mirror planes -1 and nz hold copies of planes 0 and nz-1 (run after a barrier)
-    auto mirror_plane = [&](int q, int from) {
+    auto copy_plane = [&](int q, int from) {
         const int d = mod3(q) * SN, s0 = mod3(from) * SN;
         for (int r = tid; r < SN; r += NT) {
             sN[d + r] = sN[s0 + r];
@@ -1048,107 +1241,164 @@ __global__ void __launch_bounds__(TX *TY) fused_step_kernel(const KParams<R> kp,
         }
     };
 
-    // S3: mu faces of plane q (tile) and the z face (q | q+1) of this column
-    auto xface = [&](int q, int li, int lj) -> Mu<R> {
-        return face_mu_coded(kp, tab + q, CN(q, li, lj), CN(q, li + 1, lj), N(q, li, lj), N(q, li + 1, lj), O(q, li, lj),
-                             O(q, li + 1, lj), Mm(q, li, lj), Mm(q, li + 1, lj), N(q, li, lj + 1), N(q, li, lj - 1),
-                             N(q, li + 1, lj + 1), N(q, li + 1, lj - 1), N(q + 1, li, lj), N(q - 1, li, lj),
-                             N(q + 1, li + 1, lj), N(q - 1, li + 1, lj));
+    // mu face fluxes.  L1/L2: the left (lower) cell in the 1-ring / 2-ring layouts.
+    auto mu_xface = [&](int q, int L1, int L2) -> Mu<R> {
+        const int sq = mod3(q) * SN;
+        const Ph<R> *Nq = sN + sq, *Np = sN + mod3(q + 1) * SN, *Nm = sN + mod3(q - 1) * SN;
+        const Ph<R> *Oq = sO + mod3(q) * SN2;
+        const Mu<R> *Mq = sM + sq;
+        return face_mu_coded(kp, tab + q, cN[sq + L1], cN[sq + L1 + 1], Nq[L1], Nq[L1 + 1], Oq[L2], Oq[L2 + 1],
+                             Mq[L1], Mq[L1 + 1], Nq[L1 + SX], Nq[L1 - SX], Nq[L1 + 1 + SX], Nq[L1 + 1 - SX], Np[L1],
+                             Nm[L1], Np[L1 + 1], Nm[L1 + 1]);
     };
-    auto yface = [&](int q, int li, int lj) -> Mu<R> {
-        return face_mu_coded(kp, tab + q, CN(q, li, lj), CN(q, li, lj + 1), N(q, li, lj), N(q, li, lj + 1), O(q, li, lj),
-                             O(q, li, lj + 1), Mm(q, li, lj), Mm(q, li, lj + 1), N(q, li + 1, lj), N(q, li - 1, lj),
-                             N(q, li + 1, lj + 1), N(q, li - 1, lj + 1), N(q + 1, li, lj), N(q - 1, li, lj),
-                             N(q + 1, li, lj + 1), N(q - 1, li, lj + 1));
+    auto mu_yface = [&](int q, int L1, int L2) -> Mu<R> {
+        const int sq = mod3(q) * SN;
+        const Ph<R> *Nq = sN + sq, *Np = sN + mod3(q + 1) * SN, *Nm = sN + mod3(q - 1) * SN;
+        const Ph<R> *Oq = sO + mod3(q) * SN2;
+        const Mu<R> *Mq = sM + sq;
+        const int R1 = L1 + SX;
+        return face_mu_coded(kp, tab + q, cN[sq + L1], cN[sq + R1], Nq[L1], Nq[R1], Oq[L2], Oq[L2 + SX2], Mq[L1],
+                             Mq[R1], Nq[L1 + 1], Nq[L1 - 1], Nq[R1 + 1], Nq[R1 - 1], Np[L1], Nm[L1], Np[R1], Nm[R1]);
     };
-    auto zface_mu = [&](int q) -> Mu<R> {
+    auto mu_zface = [&](int q) -> Mu<R> {
         if (q < 0 || q >= nz - 1) {
             Mu<R> v;
             v.v[0] = v.v[1] = R(0);
             return v;
         }
-        return face_mu_coded(kp, tab + nz + q, CN(q, tx, ty), CN(q + 1, tx, ty), N(q, tx, ty), N(q + 1, tx, ty),
-                             O(q, tx, ty), O(q + 1, tx, ty), Mm(q, tx, ty), Mm(q + 1, tx, ty), N(q, tx + 1, ty),
-                             N(q, tx - 1, ty), N(q + 1, tx + 1, ty), N(q + 1, tx - 1, ty), N(q, tx, ty + 1),
-                             N(q, tx, ty - 1), N(q + 1, tx, ty + 1), N(q + 1, tx, ty - 1));
+        const int sq = mod3(q) * SN, sp = mod3(q + 1) * SN;
+        const Ph<R> *Nq = sN + sq, *Np = sN + sp;
+        return face_mu_coded(kp, tab + nz + q, cN[sq + t1], cN[sp + t1], Nq[t1], Np[t1], sO[mod3(q) * SN2 + t2],
+                             sO[mod3(q + 1) * SN2 + t2], sM[sq + t1], sM[sp + t1], Nq[t1 + 1], Nq[t1 - 1], Np[t1 + 1],
+                             Np[t1 - 1], Nq[t1 + SX], Nq[t1 - SX], Np[t1 + SX], Np[t1 - SX]);
     };
-    auto mu_faces = [&](int q) {
-        sVx[ty * (TX + 1) + tx] = xface(q, tx - 1, ty);
-        sVy[ty * TX + tx] = yface(q, tx, ty - 1);
-        if (xtra_y) sVy[TY * TX + tx] = yface(q, tx, TY - 1);
-        if (xtra_x) sVx[tx * (TX + 1) + TX] = xface(q, TX - 1, tx);
+    // quiet (pure liquid) planes: constant mobility, no anti-trapping current -- the same
+    // expressions the coded short form evaluates there
+    const R Mliq = kp.DinvA[3];
+    auto mu_faces = [&](int q, bool) {
+        sVx[ty * (TX + 1) + tx] = mu_xface(q, t1 - 1, t2 - 1);
+        sVy[ty * TX + tx] = mu_yface(q, t1 - SX, t2 - SX2);
+        if (xtra_y) sVy[TY * TX + tx] = mu_yface(q, TY * SX + tx + 1, (TY + 1) * SX2 + tx + 2);
+        if (xtra_x) sVx[tx * (TX + 1) + TX] = mu_xface(q, (tx + 1) * SX + TX, (tx + 2) * SX2 + TX + 1);
+    };
+    auto mu_zflux_quiet = [&](int q) -> Mu<R> {
+        Mu<R> v;
+        if (q < 0 || q >= nz - 1) {
+            v.v[0] = v.v[1] = R(0);
+            return v;
+        }
+        const Mu<R> a = sM[mod3(q) * SN + t1], b = sM[mod3(q + 1) * SN + t1];
+        v.v[0] = Mliq * (b.v[0] - a.v[0]) * kp.inv_dx;
+        v.v[1] = Mliq * (b.v[1] - a.v[1]) * kp.inv_dx;
+        return v;
     };
 
     double liq_def = 0.0;
     int solid_cells = 0;
     bool bad = false;
+    unsigned hist = 0;  // bit i: phi^n plane (newest - i) is pure liquid on the 2-ring region
 
     // ---- prologue: phi^{n+1} on planes z0-1 and z0, the z flux below z0 ----
-    prefetch(z0 - 2);
-    commit(z0 - 2);
-    prefetch(z0 - 1);
-    commit(z0 - 1);
-    prefetch(z0);
-    commit(z0);
+    for (int k = z0 - 2; k <= z0; k++) {
+        prefetch(k);
+        hist = (hist << 1) | (__syncthreads_and(commit(k)) ? 1u : 0u);
+    }
     prefetch(z0 + 1);
-    __syncthreads();
-    phi_faces(z0 - 1);
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
-        Fz_lo[s] = zface_phi(z0 - 2, cli[s], clj[s]);
-        Fz_hi[s] = zface_phi(z0 - 1, cli[s], clj[s]);
+    bool quiet = (hist & 7u) == 7u;  // planes z0-2..z0: phi^{n+1}(z0-1) = phi^n(z0-1)
+    if (!quiet) phi_faces(z0 - 1);
+    // (a thread without a ring cell writes only its own tile cell's entries)
+    Fz(z0 - 2, 0) = zface_phi(z0 - 2, 0);
+    Fz(z0 - 1, 0) = zface_phi(z0 - 1, 0);
+    if (has_ring) {
+        Fz(z0 - 2, 1) = zface_phi(z0 - 2, 1);
+        Fz(z0 - 1, 1) = zface_phi(z0 - 1, 1);
     }
     __syncthreads();
-    if (z0 > 0) phi_new_plane(z0 - 1);
+    if (z0 > 0) phi_new_plane(z0 - 1, quiet);
     __syncthreads();
-    commit(z0 + 1);  // replaces plane z0-2, read for the last time above
+    hist = (hist << 1) | (__syncthreads_and(commit(z0 + 1)) ? 1u : 0u);
     prefetch(z0 + 2);
-    phi_faces(z0);  // plane z0 only reads plane z0 (present since the first barrier)
-#pragma unroll
-    for (int s = 0; s < 2; s++) Fz_lo[s] = Fz_hi[s];  // z face (z0-1 | z0)
-    __syncthreads();  // plane z0+1 and the faces of plane z0 are visible
-#pragma unroll
-    for (int s = 0; s < 2; s++) Fz_hi[s] = zface_phi(z0, cli[s], clj[s]);
-    phi_new_plane(z0);
+    quiet = (hist & 7u) == 7u;  // planes z0-1..z0+1
+    if (!quiet) phi_faces(z0);
+    Fz(z0, 0) = zface_phi(z0, 0);  // z0-1 | z0 is already in the ring
+    if (has_ring) Fz(z0, 1) = zface_phi(z0, 1);
+    __syncthreads();
+    phi_new_plane(z0, quiet);
     __syncthreads();
     if (z0 == 0) {
-        mirror_plane(-1, 0);
+        copy_plane(-1, 0);  // the mirror plane below the domain
         __syncthreads();
     }
-    Mu<R> Vz_lo = zface_mu(z0 - 1);
-    __syncthreads();  // plane z0-1 of phi^n / mu^n is replaced by the first commit below
+    Mu<R> Vz_lo = mu_zface(z0 - 1);
+    __syncthreads();  // phi^n / mu^n plane z0-1 is replaced by the first commit below
 
     // ---- main loop over planes ----
     for (int q = z0; q < z1; ++q) {
-        // S0
-        commit(q + 2);
+        // S0: plane q+2 of phi^n / mu^n; the CTA-wide pure-liquid flag comes with the barrier
+        const bool liq = commit(q + 2);
         prefetch(q + 3);
-        __syncthreads();
-        // S1: faces of plane q+1, z faces (q+1 | q+2)
-        phi_faces(q + 1);
-#pragma unroll
-        for (int s = 0; s < 2; s++) {
-            Fz_lo[s] = Fz_hi[s];
-            Fz_hi[s] = zface_phi(q + 1, cli[s], clj[s]);
-        }
-        __syncthreads();
-        // S2: phi^{n+1}(q+1) (a copy of plane nz-1 above the domain)
-        if (q + 1 < nz) {
-            phi_new_plane(q + 1);
+        hist = (hist << 1) | (__syncthreads_and(liq) ? 1u : 0u);
+        const bool phi_quiet = (hist & 7u) == 7u;   // phi^n planes q..q+2
+        const bool mu_quiet = (hist & 31u) == 31u;  // phi^n planes q-2..q+2
+        // S1: phi faces of plane q+1 and the z faces (q+1 | q+2) of the thread's cells
+        if (!phi_quiet) phi_faces(q + 1);
+        if (phi_quiet) {
+            // both phi^n planes are pure liquid here: the z face terms are exactly zero
+            Ph<R> z;
+            z.v[0] = z.v[1] = z.v[2] = z.v[3] = R(0);
+            Fz(q + 1, 0) = z;
+            if (has_ring) Fz(q + 1, 1) = z;
         } else {
-            const int d = mod3(q + 1) * SN, s0 = mod3(q) * SN;
-            for (int r = tid; r < SN; r += NT) {
-                sN[d + r] = sN[s0 + r];
-                cN[d + r] = cN[s0 + r];
-            }
+            Fz(q + 1, 0) = zface_phi(q + 1, 0);
+            if (has_ring) Fz(q + 1, 1) = zface_phi(q + 1, 1);
         }
-        __syncthreads();
-        // S3: mu faces of plane q
-        mu_faces(q);
-        const Mu<R> Vz_hi = zface_mu(q);
-        const Ph<R> nP = N(q, tx, ty), oP = O(q, tx, ty);
-        const int cn = CN(q, tx, ty), co = CO(q, tx, ty);
-        const Mu<R> mP = Mm(q, tx, ty);
+        // a quiet phi plane computes no faces: S2 does not wait for S1
+        if (!phi_quiet) __syncthreads();
+        // S2: phi^{n+1}(q+1) (a copy of plane nz-1 above the domain)
+        if (q + 1 < nz)
+            phi_new_plane(q + 1, phi_quiet);
+        else
+            copy_plane(q + 1, q);
+        if (mu_quiet) {
+            // S3+S4 of a pure-liquid plane: the flux of a face is one subtraction and two products,
+            // so each cell evaluates its four in-plane faces from mu^n directly (both cells of a face
+            // evaluate the same expression: the result is that of the staged faces) -- no barrier
+            const Mu<R> *Mq = sM + mod3(q) * SN;
+            const Mu<R> mP = Mq[t1], mxm = Mq[t1 - 1], mxp = Mq[t1 + 1], mym = Mq[t1 - SX], myp = Mq[t1 + SX];
+            const Mu<R> Vz_hi = mu_zflux_quiet(q);
+            Mu<R> vxm, vxp, vym, vyp;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                vxm.v[c] = Mliq * (mP.v[c] - mxm.v[c]) * kp.inv_dx;
+                vxp.v[c] = Mliq * (mxp.v[c] - mP.v[c]) * kp.inv_dx;
+                vym.v[c] = Mliq * (mP.v[c] - mym.v[c]) * kp.inv_dx;
+                vyp.v[c] = Mliq * (myp.v[c] - mP.v[c]) * kp.inv_dx;
+            }
+            R div0 = (vxp.v[0] - vxm.v[0]) * kp.inv_dx;
+            R div1 = (vxp.v[1] - vxm.v[1]) * kp.inv_dx;
+            div0 = div0 + (vyp.v[0] - vym.v[0]) * kp.inv_dx;
+            div1 = div1 + (vyp.v[1] - vym.v[1]) * kp.inv_dx;
+            div0 = div0 + (Vz_hi.v[0] - Vz_lo.v[0]) * kp.inv_dx;
+            div1 = div1 + (Vz_hi.v[1] - Vz_lo.v[1]) * kp.inv_dx;
+            Ph<R> liquid;
+            liquid.v[0] = liquid.v[1] = liquid.v[2] = R(0);
+            liquid.v[3] = R(1);
+            const Mu<R> out = mu_cell_coded(kp, tab + q, 3, 3, liquid, liquid, mP, div0, div1);
+            if (valid) {
+                st_mu(mu_out + plane_off(q, nz, zbase, plane) + col_own, out);
+                bad = bad | !isfinite(out.v[0] + out.v[1]);
+            }
+            Vz_lo = Vz_hi;
+            continue;
+        }
+        __syncthreads();  // S3 reads phi^{n+1}(q+1) written by other threads in S2
+        // S3: mu face fluxes of plane q, the z flux (q | q+1)
+        mu_faces(q, false);
+        const Mu<R> Vz_hi = mu_zface(q);
+        const int sq1 = mod3(q) * SN;
+        const Mu<R> mP = sM[sq1 + t1];
+        const Ph<R> nP = sN[sq1 + t1], oP = sO[mod3(q) * SN2 + t2];
+        const int cn = cN[sq1 + t1], co = cO[mod3(q) * SN2 + t2];
         __syncthreads();
         // S4: mu^{n+1}(q)
         {
@@ -1163,13 +1413,14 @@ __global__ void __launch_bounds__(TX *TY) fused_step_kernel(const KParams<R> kp,
             const Mu<R> out = mu_cell_coded(kp, tab + q, cn, co, nP, oP, mP, div0, div1);
             if (valid) {
                 st_mu(mu_out + plane_off(q, nz, zbase, plane) + col_own, out);
-                if (cn == 3) {
-                } else if (cn < 3) {
-                    solid_cells++;
-                } else {
-                    liq_def += 1.0 - (double)nP.v[3];
+                if (cn != 3) {
+                    if (cn < 3)
+                        solid_cells++;
+                    else
+                        liq_def += 1.0 - (double)nP.v[3];
                 }
-                bad = bad || !isfinite(out.v[0]) || !isfinite(out.v[1]) || !finite4(nP);
+                // a non-finite phi^{n+1} reaches mu^{n+1} through h (such a cell is never quiet)
+                bad = bad | !isfinite(out.v[0] + out.v[1]);
             }
         }
         Vz_lo = Vz_hi;
@@ -1195,9 +1446,57 @@ __global__ void __launch_bounds__(TX *TY) fused_step_kernel(const KParams<R> kp,
             a += red[q][0];
             b += red[q][1];
         }
-        const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        partials[bid].liq_deficit = a;
-        partials[bid].nonfinite = b;
+        part->liq_deficit = a;
+        part->nonfinite = b;
+    }
+}
+
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) fused_step_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
+                                                           const Mu<R> *__restrict__ mu,
+                                                           Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out,
+                                                           const DevState *__restrict__ st,
+                                                           const PlaneT<R> *__restrict__ tab,
+                                                           Partial *__restrict__ partials)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    fused_tile<R, TX, TY>(kp, phi, mu, phi_out, mu_out, st, tab, partials + bid, blockIdx.x, blockIdx.y, blockIdx.z,
+                          smem_raw);
+}
+
+// ---------------------------------------------------------------------------------------
+// batched step: many independent domains of uneven size in one persistent launch.  Each CTA
+// pulls (domain, tile, z chunk) work items from a table through an atomic counter (largest
+// chunks first in the table), copies that domain's parameters into shared memory and runs the
+// same tile body as the single-domain kernel.
+// ---------------------------------------------------------------------------------------
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) batched_fused_kernel(const BatchDomain<R> *__restrict__ doms,
+                                                              const BatchItem *__restrict__ items, int nitems,
+                                                              unsigned *__restrict__ counter, int parity)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    __shared__ __align__(16) KParams<R> s_kp;
+    for (;;) {
+        __syncthreads();  // the previous item's readers of s_kp and shared memory are done
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const BatchItem w = items[it];
+        const BatchDomain<R> *d = doms + w.dom;
+        {
+            const int *src = reinterpret_cast<const int *>(&d->kp);
+            int *dst = reinterpret_cast<int *>(&s_kp);
+            for (int q = threadIdx.x; q < (int)(sizeof(KParams<R>) / sizeof(int)); q += TX * TY) dst[q] = src[q];
+        }
+        __syncthreads();
+        const int a = parity, b = parity ^ 1;
+        Partial *part = d->parts + ((size_t)w.bz * d->gy + w.by) * d->gx + w.bx;
+        fused_tile<R, TX, TY>(s_kp, (const Ph<R> *)d->phi[a], (const Mu<R> *)d->mu[a], (Ph<R> *)d->phi[b],
+                              (Mu<R> *)d->mu[b], d->st, d->tab, part, w.bx, w.by, w.bz, smem_raw);
     }
 }
 
@@ -1228,8 +1527,8 @@ __device__ __forceinline__ void make_plane(const KParams<R> &kp, double zc, doub
 // One block: reduce the mu-sweep partials in a fixed order, advance t, latch non-finite
 // values, and decide the moving-window shift (reading R11).
 template <typename R>
-__global__ void __launch_bounds__(256) finalize_kernel(const KParams<R> kp, DevState *__restrict__ st,
-                                                      const Partial *__restrict__ parts, int nparts)
+__device__ __forceinline__ void finalize_body(const KParams<R> &kp, DevState *__restrict__ st,
+                                              const Partial *__restrict__ parts, int nparts)
 {
     __shared__ double sa[256], sb[256];
     double a = 0.0, b = 0.0;
@@ -1269,18 +1568,32 @@ __global__ void __launch_bounds__(256) finalize_kernel(const KParams<R> kp, DevS
     }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) finalize_kernel(const KParams<R> kp, DevState *__restrict__ st,
+                                                      const Partial *__restrict__ parts, int nparts)
+{
+    finalize_body(kp, st, parts, nparts);
+}
+
+// one block per domain
+template <typename R>
+__global__ void __launch_bounds__(256) batched_finalize_kernel(const BatchDomain<R> *__restrict__ doms)
+{
+    const BatchDomain<R> *d = doms + blockIdx.x;
+    finalize_body(d->kp, d->st, d->parts, d->gx * d->gy * d->gz);
+}
+
 // After finalize: rebuild the plane table for the new (t, offset) and fill the planes that
 // entered the window (phi = liquid, mu = the previous top plane's mu).
 template <typename R>
-__global__ void __launch_bounds__(256) post_kernel(const KParams<R> kp, const DevState *__restrict__ st,
-                                                  Ph<R> *__restrict__ phi, Mu<R> *__restrict__ mu,
-                                                  PlaneT<R> *__restrict__ tab)
+__device__ __forceinline__ void post_body(const KParams<R> &kp, const DevState *__restrict__ st,
+                                          Ph<R> *__restrict__ phi, Mu<R> *__restrict__ mu,
+                                          PlaneT<R> *__restrict__ tab, Ph<R> *__restrict__ phi_lo,
+                                          Mu<R> *__restrict__ mu_lo, size_t tid, size_t nth)
 {
     const double t = st->t, off = st->off;
     const int s = st->shift, zbase = st->zbase;
     const int nz = kp.nz;
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t nth = (size_t)gridDim.x * blockDim.x;
     for (size_t e = tid; e < (size_t)2 * nz; e += nth) {
         if (e < (size_t)nz)
             make_plane(kp, (double)e + off, t, tab + e);
@@ -1299,8 +1612,33 @@ __global__ void __launch_bounds__(256) post_kernel(const KParams<R> kp, const De
             liq.v[3] = R(1);
             st_ph(phi + dst, liq);
             st_mu(mu + dst, mu[src + c]);
+            if (phi_lo) {
+                Ph<R> z;
+                z.v[0] = z.v[1] = z.v[2] = z.v[3] = R(0);
+                st_ph(phi_lo + dst, z);
+            }
+            if (mu_lo) st_mu(mu_lo + dst, mu_lo[src + c]);
         }
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) post_kernel(const KParams<R> kp, const DevState *__restrict__ st,
+                                                  Ph<R> *__restrict__ phi, Mu<R> *__restrict__ mu,
+                                                  PlaneT<R> *__restrict__ tab, Ph<R> *__restrict__ phi_lo,
+                                                  Mu<R> *__restrict__ mu_lo)
+{
+    post_body(kp, st, phi, mu, tab, phi_lo, mu_lo, (size_t)blockIdx.x * blockDim.x + threadIdx.x,
+              (size_t)gridDim.x * blockDim.x);
+}
+
+// grid (blocks per domain, domains); the new source fields of each domain are phi/mu[parity ^ 1]
+template <typename R>
+__global__ void __launch_bounds__(256) batched_post_kernel(const BatchDomain<R> *__restrict__ doms, int parity)
+{
+    const BatchDomain<R> *d = doms + blockIdx.y;
+    post_body(d->kp, d->st, (Ph<R> *)d->phi[parity ^ 1], (Mu<R> *)d->mu[parity ^ 1], d->tab, (Ph<R> *)nullptr,
+              (Mu<R> *)nullptr, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
 }
 
 // Voronoi nuclei (reading R13): cells with k < H take the phase of the nearest seed
@@ -1351,7 +1689,8 @@ __global__ void __launch_bounds__(256) init_kernel(const KParams<R> kp, Ph<R> *_
 template <typename R>
 __global__ void __launch_bounds__(256) reduce_kernel(const KParams<R> kp, const DevState *__restrict__ st,
                                                     const Ph<R> *__restrict__ phi, const Mu<R> *__restrict__ mu,
-                                                    double *__restrict__ out)
+                                                    double *__restrict__ out, const Ph<R> *__restrict__ phi_lo,
+                                                    const Mu<R> *__restrict__ mu_lo)
 {
     __shared__ double sh[8][256];
     const int k = blockIdx.x;
@@ -1362,12 +1701,18 @@ __global__ void __launch_bounds__(256) reduce_kernel(const KParams<R> kp, const 
     for (size_t q = threadIdx.x; q < plane; q += 256) {
         const Ph<R> p = ldg_ph(phi + base + q);
         const Mu<R> m = ldg_mu(mu + base + q);
+        Ph<R> pl;
+        Mu<R> ml;
+        pl.v[0] = pl.v[1] = pl.v[2] = pl.v[3] = R(0);
+        ml.v[0] = ml.v[1] = R(0);
+        if (phi_lo) pl = ldg_ph(phi_lo + base + q);
+        if (mu_lo) ml = ldg_mu(mu_lo + base + q);
         double ph[4], S = 0.0;
         for (int a = 0; a < 4; a++) {
-            ph[a] = (double)p.v[a];
+            ph[a] = (double)p.v[a] + (double)pl.v[a];
             S += ph[a] * ph[a];
         }
-        const double m0 = (double)m.v[0], m1 = (double)m.v[1];
+        const double m0 = (double)m.v[0] + (double)ml.v[0], m1 = (double)m.v[1] + (double)ml.v[1];
         bool bad = !isfinite(m0) || !isfinite(m1);
         double c0 = 0.0, c1 = 0.0;
         for (int a = 0; a < 4; a++) {
@@ -1397,7 +1742,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) pack_kernel(const KParams<R> kp, const DevState *__restrict__ st,
                                                   const Ph<R> *__restrict__ phi, const Mu<R> *__restrict__ mu,
                                                   double *__restrict__ phi_soa, double *__restrict__ mu_soa,
-                                                  int k0, int nk)
+                                                  int k0, int nk, const Ph<R> *__restrict__ phi_lo,
+                                                  const Mu<R> *__restrict__ mu_lo)
 {
     const size_t plane = (size_t)kp.nx * kp.ny, n = plane * nk;
     const int zbase = st->zbase;
@@ -1408,11 +1754,20 @@ __global__ void __launch_bounds__(256) pack_kernel(const KParams<R> kp, const De
         if (phi_soa) {
             const Ph<R> p = ldg_ph(phi + g);
             for (int a = 0; a < 4; a++) phi_soa[(size_t)a * n + q] = (double)p.v[a];
+            if (phi_lo) {
+                const Ph<R> l = ldg_ph(phi_lo + g);
+                for (int a = 0; a < 4; a++) phi_soa[(size_t)a * n + q] += (double)l.v[a];
+            }
         }
         if (mu_soa) {
             const Mu<R> m = ldg_mu(mu + g);
             mu_soa[q] = (double)m.v[0];
             mu_soa[n + q] = (double)m.v[1];
+            if (mu_lo) {
+                const Mu<R> l = ldg_mu(mu_lo + g);
+                mu_soa[q] += (double)l.v[0];
+                mu_soa[n + q] += (double)l.v[1];
+            }
         }
     }
 }
@@ -1421,7 +1776,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) unpack_kernel(const KParams<R> kp, const DevState *__restrict__ st,
                                                     Ph<R> *__restrict__ phi, Mu<R> *__restrict__ mu,
                                                     const double *__restrict__ phi_soa,
-                                                    const double *__restrict__ mu_soa, int k0, int nk)
+                                                    const double *__restrict__ mu_soa, int k0, int nk,
+                                                    Ph<R> *__restrict__ phi_lo, Mu<R> *__restrict__ mu_lo)
 {
     const size_t plane = (size_t)kp.nx * kp.ny, n = plane * nk;
     const int zbase = st->zbase;
@@ -1429,13 +1785,22 @@ __global__ void __launch_bounds__(256) unpack_kernel(const KParams<R> kp, const 
         const int kk = (int)(q / plane);
         const size_t c = q % plane;
         const size_t g = plane_off(k0 + kk, kp.nz, zbase, plane) + c;
-        Ph<R> p;
-        for (int a = 0; a < 4; a++) p.v[a] = (R)phi_soa[(size_t)a * n + q];
+        Ph<R> p, pl;
+        for (int a = 0; a < 4; a++) {
+            const double x = phi_soa[(size_t)a * n + q];
+            p.v[a] = (R)x;
+            pl.v[a] = (R)(x - (double)p.v[a]);
+        }
         st_ph(phi + g, p);
-        Mu<R> m;
-        m.v[0] = (R)mu_soa[q];
-        m.v[1] = (R)mu_soa[n + q];
+        if (phi_lo) st_ph(phi_lo + g, pl);
+        Mu<R> m, ml;
+        for (int c = 0; c < 2; c++) {
+            const double x = mu_soa[(size_t)c * n + q];
+            m.v[c] = (R)x;
+            ml.v[c] = (R)(x - (double)m.v[c]);
+        }
         st_mu(mu + g, m);
+        if (mu_lo) st_mu(mu_lo + g, ml);
     }
 }
 
@@ -1508,7 +1873,8 @@ static size_t fused_smem_bytes()
     constexpr int SN = (kTX + 2) * (kTY + 2), SN2 = (kTX + 4) * (kTY + 4);
     constexpr int PFX = (kTX + 3) * (kTY + 2), PFY = (kTX + 2) * (kTY + 3);
     constexpr int FX = kTY * (kTX + 1), FY = (kTY + 1) * kTX;
-    return sizeof(Ph<R>) * (3 * SN2 + 3 * SN + PFX + PFY) + sizeof(Mu<R>) * (3 * SN + FX + FY) + 3 * SN2 + 3 * SN;
+    return sizeof(Ph<R>) * (4 * SN2 + 4 * SN + PFX + PFY + 2 * SN) + sizeof(Mu<R>) * (4 * SN + FX + FY) + 4 * SN2 +
+           4 * SN;
 }
 
 template <typename R>
@@ -1530,6 +1896,80 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
     return cudaGetLastError();
 }
 
+#ifdef PF_FLOAT_UNIT
+// compensated FP32 sweeps (the low words of the state ride along); defined in the FP32 unit only
+cudaError_t launch_phi_sweep_comp(const KParams<float> &kp, const Geometry &g, const void *phi, const void *phi_lo,
+                                  const void *mu, void *phi_out, void *phi_out_lo, const DevState *st,
+                                  const PlaneT<float> *tab, cudaStream_t s)
+{
+    static bool attr = false;
+    const size_t sm = phi_smem_bytes<float>() + sizeof(Ph<float>) * 4 * kTX * kTY;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(phi_sweep_kernel<float, kTX, kTY, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(g.gx, g.gy, g.gz);
+    phi_sweep_kernel<float, kTX, kTY, true><<<grid, kTX * kTY, sm, s>>>(
+        kp, (const Ph<float> *)phi, (const Mu<float> *)mu, (Ph<float> *)phi_out, st, tab, (const Ph<float> *)phi_lo,
+        (Ph<float> *)phi_out_lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mu_sweep_comp(const KParams<float> &kp, const Geometry &g, const void *phi_old,
+                                 const void *phi_new, const void *mu, const void *mu_lo, void *mu_out,
+                                 void *mu_out_lo, const DevState *st, const PlaneT<float> *tab, Partial *parts,
+                                 cudaStream_t s)
+{
+    static bool attr = false;
+    const size_t sm = mu_smem_bytes<float>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(mu_sweep_kernel<float, kTX, kTY, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(g.gx, g.gy, g.gz);
+    mu_sweep_kernel<float, kTX, kTY, true><<<grid, kTX * kTY, sm, s>>>(
+        kp, (const Ph<float> *)phi_old, (const Ph<float> *)phi_new, (const Mu<float> *)mu, (Mu<float> *)mu_out, st,
+        tab, parts, (const Mu<float> *)mu_lo, (Mu<float> *)mu_out_lo);
+    return cudaGetLastError();
+}
+#endif
+
+template <typename R>
+cudaError_t launch_batched_step(const BatchDomain<R> *doms, int ndoms, const BatchItem *items, int nitems,
+                                unsigned *counter, int parity, int ctas, int post_blocks, cudaStream_t s)
+{
+    static bool attr = false;
+    const size_t sm = fused_smem_bytes<R>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(batched_fused_kernel<R, kTX, kTY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    batched_fused_kernel<R, kTX, kTY><<<ctas, kTX * kTY, sm, s>>>(doms, items, nitems, counter, parity);
+    batched_finalize_kernel<R><<<ndoms, 256, 0, s>>>(doms);
+    batched_post_kernel<R><<<dim3(post_blocks, ndoms), 256, 0, s>>>(doms, parity);
+    return cudaGetLastError();
+}
+
+template <typename R>
+int fused_ctas_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_fused_kernel<R, kTX, kTY>, kTX * kTY,
+                                                      fused_smem_bytes<R>()) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
 template <typename R>
 cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s)
 {
@@ -1539,12 +1979,12 @@ cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *p
 
 template <typename R>
 cudaError_t launch_post(const KParams<R> &kp, const DevState *st, void *phi, void *mu, PlaneT<R> *tab,
-                        cudaStream_t s)
+                        cudaStream_t s, void *phi_lo, void *mu_lo)
 {
     // enough threads to fill one full plane per thread-sweep when the window moves
     const size_t work = (size_t)kp.nx * kp.ny;
     post_kernel<R><<<grid1d(work > (size_t)2 * kp.nz ? work : (size_t)2 * kp.nz), 256, 0, s>>>(
-        kp, st, (Ph<R> *)phi, (Mu<R> *)mu, tab);
+        kp, st, (Ph<R> *)phi, (Mu<R> *)mu, tab, (Ph<R> *)phi_lo, (Mu<R> *)mu_lo);
     return cudaGetLastError();
 }
 
@@ -1559,27 +1999,30 @@ cudaError_t launch_init(const KParams<R> &kp, void *phi, void *mu, const double 
 
 template <typename R>
 cudaError_t launch_reduce(const KParams<R> &kp, const DevState *st, const void *phi, const void *mu,
-                          double *plane_sums, cudaStream_t s)
+                          double *plane_sums, cudaStream_t s, const void *phi_lo, const void *mu_lo)
 {
-    reduce_kernel<R><<<kp.nz, 256, 0, s>>>(kp, st, (const Ph<R> *)phi, (const Mu<R> *)mu, plane_sums);
+    reduce_kernel<R><<<kp.nz, 256, 0, s>>>(kp, st, (const Ph<R> *)phi, (const Mu<R> *)mu, plane_sums,
+                                           (const Ph<R> *)phi_lo, (const Mu<R> *)mu_lo);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_pack(const KParams<R> &kp, const DevState *st, const void *phi, const void *mu, double *phi_soa,
-                        double *mu_soa, int k0, int nk, cudaStream_t s)
+                        double *mu_soa, int k0, int nk, cudaStream_t s, const void *phi_lo, const void *mu_lo)
 {
     const size_t n = (size_t)kp.nx * kp.ny * nk;
-    pack_kernel<R><<<grid1d(n), 256, 0, s>>>(kp, st, (const Ph<R> *)phi, (const Mu<R> *)mu, phi_soa, mu_soa, k0, nk);
+    pack_kernel<R><<<grid1d(n), 256, 0, s>>>(kp, st, (const Ph<R> *)phi, (const Mu<R> *)mu, phi_soa, mu_soa, k0, nk,
+                                             (const Ph<R> *)phi_lo, (const Mu<R> *)mu_lo);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, void *mu, const double *phi_soa,
-                          const double *mu_soa, int k0, int nk, cudaStream_t s)
+                          const double *mu_soa, int k0, int nk, cudaStream_t s, void *phi_lo, void *mu_lo)
 {
     const size_t n = (size_t)kp.nx * kp.ny * nk;
-    unpack_kernel<R><<<grid1d(n), 256, 0, s>>>(kp, st, (Ph<R> *)phi, (Mu<R> *)mu, phi_soa, mu_soa, k0, nk);
+    unpack_kernel<R><<<grid1d(n), 256, 0, s>>>(kp, st, (Ph<R> *)phi, (Mu<R> *)mu, phi_soa, mu_soa, k0, nk,
+                                               (Ph<R> *)phi_lo, (Mu<R> *)mu_lo);
     return cudaGetLastError();
 }
 
@@ -1592,16 +2035,19 @@ cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, v
     template cudaError_t launch_fused_step<R>(const KParams<R> &, const Geometry &, const void *, const void *, \
                                               void *, void *, const DevState *, const PlaneT<R> *, Partial *,     \
                                               cudaStream_t);                                                      \
+    template cudaError_t launch_batched_step<R>(const BatchDomain<R> *, int, const BatchItem *, int, unsigned *, \
+                                                int, int, int, cudaStream_t);                                    \
+    template int fused_ctas_per_sm<R>();                                                                         \
     template cudaError_t launch_finalize<R>(const KParams<R> &, DevState *, const Partial *, int, cudaStream_t); \
     template cudaError_t launch_post<R>(const KParams<R> &, const DevState *, void *, void *, PlaneT<R> *,       \
-                                        cudaStream_t);                                                           \
+                                        cudaStream_t, void *, void *);                                           \
     template cudaError_t launch_init<R>(const KParams<R> &, void *, void *, const double *, int, int,            \
                                         cudaStream_t);                                                           \
     template cudaError_t launch_reduce<R>(const KParams<R> &, const DevState *, const void *, const void *,      \
-                                          double *, cudaStream_t);                                               \
+                                          double *, cudaStream_t, const void *, const void *);                   \
     template cudaError_t launch_pack<R>(const KParams<R> &, const DevState *, const void *, const void *,        \
-                                        double *, double *, int, int, cudaStream_t);                             \
+                                        double *, double *, int, int, cudaStream_t, const void *, const void *); \
     template cudaError_t launch_unpack<R>(const KParams<R> &, const DevState *, void *, void *, const double *,  \
-                                          const double *, int, int, cudaStream_t);
+                                          const double *, int, int, cudaStream_t, void *, void *);
 
 }  // namespace pf

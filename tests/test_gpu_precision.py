@@ -1,0 +1,95 @@
+"""Compensated FP32 (PF_FP32_COMP): the state is kept as hi + lo FP32 pairs; increments formed in
+FP32 are accumulated without loss.  Checked against the oracle and against closed forms."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1506_01684_gb300 import pf
+from paper_1506_01684_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pf.lib()
+
+
+def test_compensated_state_keeps_increments_below_the_fp32_spacing():
+    # pure liquid, uniform mu = 1: each step adds 2 A kT G v dt (the dc/dT dT/dt source, Eq. 3),
+    # about 7.9e-8, less than half the FP32 spacing at 1.0 -- plain FP32 rounds every step
+    nx = ny = nz = 8
+    p = W.symmetric_params(G=1e-3, v=1e-2)
+    phi = np.zeros((4, nz, ny, nx))
+    phi[3] = 1.0
+    mu = np.ones((2, nz, ny, nx))
+    n = 1000
+    res = {}
+    for prec in ("fp32", "fp32c", "fp64"):
+        sim = pf.Simulation(nx, ny, nz, p, prec)
+        sim.set_fields(phi, mu)
+        sim.step(n)
+        res[prec] = sim.fields()[1]
+        dt = sim.params.dt
+        sim.close()
+    q = oracle.resolve_params(p, nz)
+    assert q["dt"] == dt
+    want = 1.0 + n * 2 * 1.0 * 0.1 * p["G"] * p["v"] * dt
+    err = {k: np.abs(v - want).max() / (want - 1.0) for k, v in res.items()}
+    print("relative error of the accumulated drift:", err)
+    # FP64 accumulates ~1000 half-ulp roundings of 1.0 against a drift of ~8e-5: ~1e-9 relative;
+    # compensated FP32 keeps every increment (its error is the FP32 rounding of the increment);
+    # plain FP32 rounds each increment to a whole spacing of 1.0
+    assert err["fp64"] < 1e-8
+    assert err["fp32c"] < 1e-7
+    assert err["fp32"] > 1e4 * err["fp32c"]
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 64), (37, 21, 19), (1, 1, 16)])
+def test_compensated_path_matches_the_oracle(shape):
+    nx, ny, nz = shape
+    p = W.symmetric_params(n_grains=6)
+    sim = pf.Simulation(nx, ny, nz, p, "fp32c")
+    ref = oracle.State(p, nx, ny, nz)
+    sim.init(7)
+    ref.init(7)
+    sim.step(100)
+    ref.step(100)
+    phi, mu = sim.fields()
+    e_phi = np.abs(phi - ref.phi).max()
+    e_mu = np.abs(mu - ref.mu).max() / max(np.abs(ref.mu).max(), 1e-8)
+    print(f"fp32c vs oracle {shape}: {e_phi:.3e} {e_mu:.3e}")
+    assert e_phi <= 2e-5 and e_mu <= 2e-5
+    # the compensated state sums to one far below the FP32 spacing
+    assert np.abs(phi.sum(0) - 1).max() <= 1e-12 and phi.min() >= 0
+
+
+def test_compensated_fields_round_trip_through_the_host():
+    rng = np.random.default_rng(4)
+    nx, ny, nz = 9, 7, 5
+    phi = W.random_simplex_field(rng, nx, ny, nz)
+    mu = W.random_mu(rng, nx, ny, nz)
+    sim = pf.Simulation(nx, ny, nz, W.symmetric_params(), "fp32c")
+    sim.set_fields(phi, mu)
+    phi2, mu2 = sim.fields()
+    # hi + lo carries 48 significant bits
+    assert np.abs(phi2 - phi).max() <= 1e-14
+    assert np.abs(mu2 - mu).max() <= 1e-14
+
+
+def test_compensated_window_shift_matches_the_oracle():
+    p = W.symmetric_params(window_trigger_z=7.0)
+    p["seed_layers"] = 10
+    sim = pf.Simulation(32, 32, 64, p, "fp32c")
+    ref = oracle.State(p, 32, 32, 64)
+    sim.init(3)
+    ref.init(3)
+    sim.step(60)
+    ref.step(60)
+    assert ref.shifts > 0 and sim.shifts() == ref.shifts
+    phi, mu = sim.fields()
+    assert np.abs(phi - ref.phi).max() <= 2e-5
+    assert np.abs(mu - ref.mu).max() / max(np.abs(ref.mu).max(), 1e-8) <= 2e-5
