@@ -163,6 +163,62 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched_study(args):
+    """64 independent domains of uneven size (x, y in {32, 64, 96, 128}, z in {128, 256, 512}),
+    each with its own pulling velocity and gradient, FP32: the autotuned batched launch (one
+    persistent kernel per step, graph-replayed) against the same domains stepped one by one."""
+    import torch
+
+    from paper_1506_01684_gb300 import pf
+    from paper_1506_01684_gb300 import workloads as W
+
+    doms = W.batched_domains(64, seed=0)
+    shapes = [(d["nx"], d["ny"], d["nz"]) for d in doms]
+    params = [W.symmetric_params(G=d["G"], v=d["v"], n_grains=12) for d in doms]
+    seeds = [d["seed"] for d in doms]
+    cells = sum(a * b * c for a, b, c in shapes)
+    stream = torch.cuda.Stream()
+    b = pf.Batch(shapes, params, "fp32", stream=stream)
+    b.init(seeds)
+    zc, tune_ms = pf.pf_batch_autotune(b.h, 5)
+    b.step(args.warmup)
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / args.steps
+    b.sync()
+    b.close()
+    # one by one: each domain its own pf_sim (fused kernel, graph replay), run back to back
+    sims = []
+    for shp, p, sd in zip(shapes, params, seeds):
+        sim = pf.Simulation(*shp, p, "fp32", stream=stream, variant="fused")
+        sim.init(sd)
+        sim.step(args.warmup)
+        sims.append(sim)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for sim in sims:
+        sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_single = e0.elapsed_time(e1) / args.steps
+    for sim in sims:
+        sim.close()
+    line = {"metric": "batched phi+mu step MLUP/s, 64 uneven domains (FP32)", "unit": "MLUP/s",
+            "value": cells / (ms_batch / 1e3) / 1e6, "one_by_one": cells / (ms_single / 1e3) / 1e6,
+            "speedup_vs_one_by_one": ms_single / ms_batch, "ms_per_step": ms_batch,
+            "ms_per_step_one_by_one": ms_single, "cells": cells, "domains": len(shapes),
+            "autotuned_zchunk": zc, "autotune_ms_per_step": tune_ms, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 domains, x,y in {32,64,96,128}, z in {128,256,512}, v in [5e-3,2e-2], "
+                                   "G in [5e-4,2e-3], 12 grains each (numpy PCG64 seed 0)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,6 +228,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="steps of the FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--study", default=None, choices=["batched"],
+                    help="run a secondary study instead of the headline line")
     ap.add_argument("--variant", default="auto", choices=["auto", "unfused", "fused"],
                     help="kernel variant of the FP32 step (auto: the library's choice)")
     ap.add_argument("--grains", type=int, default=GRAINS,
@@ -202,6 +260,9 @@ def main():
     from paper_1506_01684_gb300 import workloads as W
 
     torch.cuda.set_device(local)
+    if args.study == "batched":
+        run_batched_study(args)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -172,6 +172,38 @@ int pf_profile(pf_sim *sim, int enable);
 int pf_profile_read(pf_sim *sim, double ms[], int launches[]);
 
 /*
+ * Batched launch: many independent domains of uneven size stepped together.  Each step is one
+ * persistent fused kernel whose CTAs pull (domain, tile, z chunk) work items -- largest first --
+ * from a device table through an atomic counter, followed by a per-domain FP64 finalize and a
+ * per-domain post kernel; steps are replayed from a captured CUDA graph.  Every domain is a
+ * pf_sim of its own (fields, clock, window, parameters), reachable with pf_batch_domain for
+ * pf_read_fields / pf_write_fields / pf_phase_fractions / pf_stats; it must not be stepped on its
+ * own while it belongs to the batch.  All domains share one precision (PF_FP32 or PF_FP64).
+ */
+typedef struct pf_batch pf_batch;
+
+/* Create ndomains simulations (nx[d] x ny[d] x nz[d] cells, parameters params[d]) on one stream
+ * (NULL: the library creates one).  Errors as pf_create; PF_E_INVAL for mixed or compensated
+ * precision. */
+int pf_batch_create(int ndomains, const int *nx, const int *ny, const int *nz, const pf_params *params,
+                    void *stream, pf_batch **out);
+int pf_batch_destroy(pf_batch *b);
+/* The simulation of domain d (owned by the batch). */
+int pf_batch_domain(pf_batch *b, int d, pf_sim **sim);
+/* pf_init of every domain with seeds[d]. */
+int pf_batch_init(pf_batch *b, const uint64_t *seeds);
+/* nsteps steps of every domain (asynchronous).  PF_E_INVAL if a domain was stepped on its own. */
+int pf_batch_step(pf_batch *b, int nsteps);
+/* Wait for the batch's stream; returns the first latched error of any domain. */
+int pf_batch_sync(pf_batch *b);
+/* z planes per work item (0: the default, about 6 CTAs of work per SM in total). */
+int pf_batch_set_zchunk(pf_batch *b, int zchunk);
+/* Autotuner: times trial_steps steps for each candidate z-chunk depth on the batch itself (the
+ * fields, clocks and windows are restored afterwards), keeps the fastest and returns it in
+ * *best (may be NULL) and its measured milliseconds per step in *best_ms (may be NULL). */
+int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms);
+
+/*
  * Allocation-free step.  The paper has no counterpart; this entry point serves callers that
  * cannot allocate device memory: code that must live inside a device-memory budget owned by
  * another allocator (a framework's caching pool or a fixed serving arena, where a private

@@ -802,3 +802,349 @@ int pf_profile_read(pf_sim *s, double ms[], int launches[])
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// batched launch
+// ------------------------------------------------------------------------------------------
+struct pf_batch {
+    std::vector<pf_sim *> sims;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int precision = PF_FP32;
+    int zchunk = 0;
+    DevBuf doms;     // BatchDomain<R>[n]
+    DevBuf items;    // BatchItem[nitems]
+    DevBuf parts;    // Partial[sum of tiles]
+    DevBuf counter;  // work-item counter
+    int nitems = 0, ctas = 0, post_blocks = 1;
+    bool built = false;
+    cudaGraphExec_t graph = nullptr;
+    int direct_steps = 0;
+};
+
+template <typename R>
+static int batch_build(pf_batch *b)
+{
+    const int n = (int)b->sims.size();
+    std::vector<BatchDomain<R>> d(n);
+    std::vector<size_t> part_off(n);
+    std::vector<BatchItem> items;
+    std::vector<std::pair<long, int>> order;  // (cost, item) for the largest-first sort
+    size_t part_total = 0;
+    int post = 1;
+    for (int q = 0; q < n; q++) {
+        pf_sim *s = b->sims[q];
+        int zc = b->zchunk;
+        if (zc <= 0) zc = s->geo_fused.zchunk;
+        const Geometry g = make_geometry(s->nx, s->ny, s->nz, zc);
+        KParams<R> kp = make_kparams<R>(s);
+        kp.zchunk = g.zchunk;
+        d[q].kp = kp;
+        for (int k = 0; k < 2; k++) {
+            d[q].phi[k] = s->phi[k].p;
+            d[q].mu[k] = s->mu[k].p;
+        }
+        d[q].st = (DevState *)s->state.p;
+        d[q].tab = (PlaneT<R> *)s->tab.p;
+        d[q].parts = nullptr;  // set once the partial-sum array exists
+        part_off[q] = part_total;
+        d[q].gx = g.gx;
+        d[q].gy = g.gy;
+        d[q].gz = g.gz;
+        part_total += (size_t)g.nparts();
+        for (int bz = 0; bz < g.gz; bz++)
+            for (int by = 0; by < g.gy; by++)
+                for (int bx = 0; bx < g.gx; bx++) {
+                    const int planes = std::min(g.zchunk, s->nz - bz * g.zchunk);
+                    // cost ~ planes + the chunk's two recomputed planes; the chunk at the bottom of
+                    // the window holds the solidification front
+                    const long cost = (long)(planes + 3) * (bz == 0 ? 4 : 1);
+                    order.push_back({cost, (int)items.size()});
+                    items.push_back({q, bx, by, bz});
+                }
+        const long pw = std::max<long>((long)s->nx * s->ny, 2L * s->nz);
+        post = std::max(post, (int)std::min<long>(64, (pw + 255) / 256));
+    }
+    std::stable_sort(order.begin(), order.end(), [](const std::pair<long, int> &x, const std::pair<long, int> &y) {
+        return x.first > y.first;
+    });
+    std::vector<BatchItem> sorted(items.size());
+    for (size_t q = 0; q < order.size(); q++) sorted[q] = items[order[q].second];
+    dev_free(b->items, b->stream);
+    dev_free(b->parts, b->stream);
+    int r = dev_alloc(b->items, std::max<size_t>(1, sorted.size()) * sizeof(BatchItem), b->stream);
+    if (r == PF_OK) r = dev_alloc(b->parts, std::max<size_t>(1, part_total) * sizeof(Partial), b->stream);
+    if (r == PF_OK && !b->doms.p) r = dev_alloc(b->doms, (size_t)n * sizeof(BatchDomain<R>), b->stream);
+    if (r == PF_OK && !b->counter.p) r = dev_alloc(b->counter, 256, b->stream);
+    if (r != PF_OK) return r;
+    for (int q = 0; q < n; q++) d[q].parts = (Partial *)b->parts.p + part_off[q];
+    cudaError_t e = cudaMemcpyAsync(b->items.p, sorted.data(), sorted.size() * sizeof(BatchItem),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->doms.p, d.data(), (size_t)n * sizeof(BatchDomain<R>), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host vectors go out of scope
+    if (e != cudaSuccess) return cuda_status(e);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->ctas = std::max(1, std::min((int)sorted.size(), fused_ctas_per_sm<R>() * sms));
+    b->nitems = (int)sorted.size();
+    b->post_blocks = post;
+    b->built = true;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return PF_OK;
+}
+
+template <typename R>
+static int batch_step_direct(pf_batch *b, int n)
+{
+    for (int q = 0; q < n; q++) {
+        const int par = b->sims[0]->cur;
+        cudaError_t e = launch_batched_step<R>((const BatchDomain<R> *)b->doms.p, (int)b->sims.size(),
+                                               (const BatchItem *)b->items.p, b->nitems, (unsigned *)b->counter.p,
+                                               par, b->ctas, b->post_blocks, b->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        for (pf_sim *s : b->sims) s->cur = 1 - s->cur;
+    }
+    return PF_OK;
+}
+
+template <typename R>
+static int batch_step(pf_batch *b, int n)
+{
+    if (!b->built) {
+        int r = batch_build<R>(b);
+        if (r != PF_OK) return r;
+    }
+    const int par = b->sims[0]->cur;
+    for (pf_sim *s : b->sims)
+        if (s->cur != par) return PF_E_INVAL;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(b->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+    }
+    if (n < 4 || b->direct_steps < 2 || cs != cudaStreamCaptureStatusNone) {
+        int r = batch_step_direct<R>(b, n);
+        if (r == PF_OK) b->direct_steps += n;
+        return r;
+    }
+    if (par != 0) {
+        int r = batch_step_direct<R>(b, 1);
+        if (r != PF_OK) return r;
+        n -= 1;
+    }
+    if (!b->graph) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_status(e);
+        int r = batch_step_direct<R>(b, 2);  // recorded; parity returns to 0
+        e = cudaStreamEndCapture(b->stream, &g);
+        if (r != PF_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return r != PF_OK ? r : cuda_status(e);
+        }
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->graph = nullptr;
+            return cuda_status(e);
+        }
+    }
+    for (int q = 0; q + 1 < n; q += 2) {
+        cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (n & 1) return batch_step_direct<R>(b, 1);
+    return PF_OK;
+}
+
+#define PF_BDISPATCH(b, fn, ...) ((b)->precision == PF_FP64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+
+extern "C" {
+
+int pf_batch_destroy(pf_batch *b)
+{
+    if (!b) return PF_E_INVAL;
+    cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (pf_sim *s : b->sims)
+        if (s) pf_destroy(s);
+    dev_free(b->doms, b->stream);
+    dev_free(b->items, b->stream);
+    dev_free(b->parts, b->stream);
+    dev_free(b->counter, b->stream);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return PF_OK;
+}
+
+int pf_batch_create(int n, const int *nx, const int *ny, const int *nz, const pf_params *params, void *stream,
+                    pf_batch **out)
+{
+    if (!out || n < 1 || !nx || !ny || !nz || !params) return PF_E_INVAL;
+    *out = nullptr;
+    const int prec = params[0].precision;
+    if (prec != PF_FP32 && prec != PF_FP64) return PF_E_INVAL;
+    for (int q = 0; q < n; q++)
+        if (params[q].precision != prec) return PF_E_INVAL;
+    pf_batch *b = new (std::nothrow) pf_batch;
+    if (!b) return PF_E_NOMEM;
+    b->precision = prec;
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete b;
+            return cuda_status(e);
+        }
+        b->own_stream = true;
+    }
+    for (int q = 0; q < n; q++) {
+        pf_sim *s = nullptr;
+        int r = pf_create(nx[q], ny[q], nz[q], &params[q], (void *)b->stream, &s);
+        if (r != PF_OK) {
+            pf_batch_destroy(b);
+            return r;
+        }
+        b->sims.push_back(s);
+    }
+    *out = b;
+    return PF_OK;
+}
+
+int pf_batch_domain(pf_batch *b, int d, pf_sim **sim)
+{
+    if (!b || !sim || d < 0 || d >= (int)b->sims.size()) return PF_E_INVAL;
+    *sim = b->sims[d];
+    return PF_OK;
+}
+
+int pf_batch_init(pf_batch *b, const uint64_t *seeds)
+{
+    if (!b || !seeds) return PF_E_INVAL;
+    for (size_t q = 0; q < b->sims.size(); q++) {
+        int r = pf_init(b->sims[q], seeds[q]);
+        if (r != PF_OK) return r;
+    }
+    return PF_OK;
+}
+
+int pf_batch_step(pf_batch *b, int nsteps)
+{
+    if (!b || nsteps < 0) return PF_E_INVAL;
+    if (nsteps == 0) return PF_OK;
+    return PF_BDISPATCH(b, batch_step, b, nsteps);
+}
+
+int pf_batch_sync(pf_batch *b)
+{
+    if (!b) return PF_E_INVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int first = PF_OK;
+    for (pf_sim *s : b->sims) {
+        int r = pf_sync(s);
+        if (first == PF_OK && r != PF_OK) first = r;
+    }
+    return first;
+}
+
+int pf_batch_set_zchunk(pf_batch *b, int zchunk)
+{
+    if (!b || zchunk < 0) return PF_E_INVAL;
+    if (zchunk != b->zchunk) {
+        b->zchunk = zchunk;
+        b->built = false;
+    }
+    return PF_OK;
+}
+
+int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
+{
+    if (!b || trial_steps < 2) return PF_E_INVAL;
+    const int n = (int)b->sims.size();
+    int nzmax = 1;
+    for (pf_sim *s : b->sims) nzmax = std::max(nzmax, s->nz);
+    // snapshot of every domain's current fields and device state
+    std::vector<DevBuf> snap(n);
+    std::vector<DevState> ds(n);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    for (int q = 0; q < n && e == cudaSuccess; q++) {
+        pf_sim *s = b->sims[q];
+        const size_t fb = s->phi[0].bytes + s->mu[0].bytes;
+        int r = dev_alloc(snap[q], fb, b->stream);
+        if (r != PF_OK) {
+            for (auto &x : snap) dev_free(x, b->stream);
+            return r;
+        }
+        e = cudaMemcpyAsync(snap[q].p, s->phi[s->cur].p, s->phi[0].bytes, cudaMemcpyDeviceToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((char *)snap[q].p + s->phi[0].bytes, s->mu[s->cur].p, s->mu[0].bytes,
+                                cudaMemcpyDeviceToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ds[q], s->state.p, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    std::vector<int> cur(n);
+    for (int q = 0; q < n; q++) cur[q] = b->sims[q]->cur;
+    auto restore = [&]() -> cudaError_t {
+        cudaError_t x = cudaSuccess;
+        for (int q = 0; q < n && x == cudaSuccess; q++) {
+            pf_sim *s = b->sims[q];
+            s->cur = cur[q];
+            x = cudaMemcpyAsync(s->phi[s->cur].p, snap[q].p, s->phi[0].bytes, cudaMemcpyDeviceToDevice, b->stream);
+            if (x == cudaSuccess)
+                x = cudaMemcpyAsync(s->mu[s->cur].p, (char *)snap[q].p + s->phi[0].bytes, s->mu[0].bytes,
+                                    cudaMemcpyDeviceToDevice, b->stream);
+            if (x == cudaSuccess)
+                x = cudaMemcpyAsync(s->state.p, &ds[q], sizeof(DevState), cudaMemcpyHostToDevice, b->stream);
+        }
+        if (x == cudaSuccess) x = cudaStreamSynchronize(b->stream);
+        return x;
+    };
+    const int cands[] = {16, 32, 64, 128, 256, 512};
+    int bestz = b->zchunk;
+    double bestt = 1e300;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int zc : cands) {
+        if (e != cudaSuccess) break;
+        if (zc > 2 * nzmax && zc != cands[0]) continue;
+        b->zchunk = zc;
+        b->built = false;
+        b->direct_steps = 0;
+        int r = PF_BDISPATCH(b, batch_step, b, 1);  // builds the table, warms up
+        if (r != PF_OK) break;
+        e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) {
+            r = PF_BDISPATCH(b, batch_step_direct, b, trial_steps);
+            if (r != PF_OK) break;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms / trial_steps < bestt) {
+            bestt = ms / trial_steps;
+            bestz = zc;
+        }
+        if (e == cudaSuccess) e = restore();
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (auto &x : snap) dev_free(x, b->stream);
+    b->zchunk = bestz;
+    b->built = false;
+    b->direct_steps = 0;
+    if (e != cudaSuccess) return cuda_status(e);
+    if (best) *best = bestz;
+    if (best_ms) *best_ms = bestt;
+    return PF_OK;
+}
+
+}  // extern "C"

@@ -85,6 +85,15 @@ SIGNATURES = {
     "pf_set_variant": (_I, [_VP, _I]),
     "pf_profile_read": (_I, [_VP, _DP, ctypes.POINTER(_I)]),
     "pf_step_noalloc": (_I, [_I, _I, _I, ctypes.POINTER(pf_params), _D, _D, _VP, _VP, _VP, _VP, _DP, _VP]),
+    "pf_batch_create": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(pf_params),
+                             _VP, ctypes.POINTER(_VP)]),
+    "pf_batch_destroy": (_I, [_VP]),
+    "pf_batch_domain": (_I, [_VP, _I, ctypes.POINTER(_VP)]),
+    "pf_batch_init": (_I, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
+    "pf_batch_step": (_I, [_VP, _I]),
+    "pf_batch_sync": (_I, [_VP]),
+    "pf_batch_set_zchunk": (_I, [_VP, _I]),
+    "pf_batch_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), _DP]),
 }
 
 PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_FUSED, PF_K_COUNT = 0, 1, 2, 3, 4, 8
@@ -269,6 +278,104 @@ def pf_step_noalloc(nx: int, ny: int, nz: int, params: pf_params, t: float, wind
                                  phi_dst, mu_dst, ctypes.byref(h) if want_h_int else None,
                                  _stream_handle(stream)), "pf_step_noalloc")
     return h.value if want_h_int else None
+
+
+def pf_batch_create(shapes, params_list, stream=None):
+    n = len(shapes)
+    nx = (_I * n)(*[s[0] for s in shapes])
+    ny = (_I * n)(*[s[1] for s in shapes])
+    nz = (_I * n)(*[s[2] for s in shapes])
+    ps = (pf_params * n)(*params_list)
+    h = _VP()
+    _check(lib().pf_batch_create(n, nx, ny, nz, ps, _stream_handle(stream), ctypes.byref(h)), "pf_batch_create")
+    return h
+
+
+def pf_batch_destroy(b):
+    return _check(lib().pf_batch_destroy(b), "pf_batch_destroy")
+
+
+def pf_batch_domain(b, d):
+    h = _VP()
+    _check(lib().pf_batch_domain(b, d, ctypes.byref(h)), "pf_batch_domain")
+    return h
+
+
+def pf_batch_init(b, seeds):
+    arr = (ctypes.c_uint64 * len(seeds))(*[int(x) for x in seeds])
+    return _check(lib().pf_batch_init(b, arr), "pf_batch_init")
+
+
+def pf_batch_step(b, nsteps):
+    return _check(lib().pf_batch_step(b, nsteps), "pf_batch_step")
+
+
+def pf_batch_sync(b):
+    return _check(lib().pf_batch_sync(b), "pf_batch_sync")
+
+
+def pf_batch_set_zchunk(b, zchunk):
+    return _check(lib().pf_batch_set_zchunk(b, zchunk), "pf_batch_set_zchunk")
+
+
+def pf_batch_autotune(b, trial_steps=10):
+    best = _I()
+    ms = _D()
+    _check(lib().pf_batch_autotune(b, trial_steps, ctypes.byref(best), ctypes.byref(ms)), "pf_batch_autotune")
+    return best.value, ms.value
+
+
+class Batch:
+    """Owns one pf_batch: domains of uneven size stepped by one persistent launch per step."""
+
+    def __init__(self, shapes, params_list, precision="fp32", stream=None):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        ps = []
+        for p in params_list:
+            q = p if isinstance(p, pf_params) else params_from_dict(p, prec)
+            q.precision = prec
+            ps.append(q)
+        self.shapes = [tuple(s) for s in shapes]
+        self.h = pf_batch_create(self.shapes, ps, stream)
+
+    def close(self):
+        if self.h:
+            pf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def domain(self, d):
+        return pf_batch_domain(self.h, d)
+
+    def init(self, seeds):
+        pf_batch_init(self.h, seeds)
+        return self
+
+    def step(self, n=1):
+        pf_batch_step(self.h, n)
+        return self
+
+    def sync(self):
+        pf_batch_sync(self.h)
+        return self
+
+    def fields(self, d):
+        nx, ny, nz = self.shapes[d]
+        phi = np.empty((4, nz, ny, nx))
+        mu = np.empty((2, nz, ny, nx))
+        pf_read_fields(self.domain(d), phi, mu)
+        return phi, mu
+
+    def stats(self, d):
+        return pf_stats(self.domain(d))
+
+    def shifts(self, d):
+        return pf_window_shifts(self.domain(d))
 
 
 # ---------------------------------------------------------------------------------------

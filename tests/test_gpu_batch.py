@@ -1,0 +1,101 @@
+"""Batched launch of uneven domains (one persistent fused kernel per step)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1506_01684_gb300 import pf
+from paper_1506_01684_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pf.lib()
+
+
+SHAPES = [(32, 32, 64), (37, 21, 40), (64, 16, 96), (8, 40, 33), (1, 3, 20)]
+
+
+def _params(i, window=0.0):
+    rng = np.random.default_rng(100 + i)
+    p = W.symmetric_params(G=float(rng.uniform(5e-4, 2e-3)), v=float(rng.uniform(5e-3, 2e-2)),
+                           n_grains=int(rng.integers(2, 9)), window_trigger_z=window)
+    return p
+
+
+@pytest.mark.parametrize("nsteps", [7, 30])
+def test_batched_domains_equal_their_own_fused_runs_bitwise(nsteps):
+    params = [_params(i) for i in range(len(SHAPES))]
+    seeds = [11 * i + 1 for i in range(len(SHAPES))]
+    b = pf.Batch(SHAPES, params, "fp32")
+    b.init(seeds)
+    b.step(nsteps)
+    b.sync()
+    for d, (shape, p) in enumerate(zip(SHAPES, params)):
+        sim = pf.Simulation(*shape, p, "fp32", variant="fused")
+        sim.init(seeds[d])
+        sim.step(nsteps)
+        a_phi, a_mu = b.fields(d)
+        s_phi, s_mu = sim.fields()
+        assert (a_phi == s_phi).all() and (a_mu == s_mu).all(), d
+        assert b.stats(d)["t"] == sim.stats()["t"]
+        sim.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-5), ("fp64", 1e-12)])
+def test_batched_domains_match_the_oracle(precision, tol):
+    params = [_params(i, window=9.0 if i == 0 else 0.0) for i in range(len(SHAPES))]
+    params[0]["seed_layers"] = 12
+    seeds = [3 * i + 5 for i in range(len(SHAPES))]
+    b = pf.Batch(SHAPES, params, precision)
+    b.init(seeds)
+    b.step(25)
+    b.sync()
+    for d, (shape, p) in enumerate(zip(SHAPES, params)):
+        ref = oracle.State(p, *shape).init(seeds[d])
+        ref.step(25)
+        phi, mu = b.fields(d)
+        assert np.abs(phi - ref.phi).max() <= tol, d
+        assert np.abs(mu - ref.mu).max() / max(np.abs(ref.mu).max(), 1e-8) <= tol, d
+        assert b.shifts(d) == ref.shifts, d
+    assert b.shifts(0) > 0  # the window of domain 0 moved inside the batch
+    b.close()
+
+
+def test_autotune_restores_the_state_and_keeps_results():
+    params = [_params(i) for i in range(len(SHAPES))]
+    seeds = list(range(1, len(SHAPES) + 1))
+    b = pf.Batch(SHAPES, params, "fp32")
+    b.init(seeds)
+    b.step(3)
+    before = [b.fields(d) for d in range(len(SHAPES))]
+    t_before = [b.stats(d)["t"] for d in range(len(SHAPES))]
+    zc, ms = pf.pf_batch_autotune(b.h, 4)
+    assert zc in (16, 32, 64, 128, 256, 512) and ms > 0
+    for d in range(len(SHAPES)):
+        phi, mu = b.fields(d)
+        assert (phi == before[d][0]).all() and (mu == before[d][1]).all()
+        assert b.stats(d)["t"] == t_before[d]
+    # results after tuning agree with the oracle (the z chunk only changes the schedule)
+    b.step(10)
+    for d, (shape, p) in enumerate(zip(SHAPES, params)):
+        ref = oracle.State(p, *shape).init(seeds[d])
+        ref.step(13)
+        phi, mu = b.fields(d)
+        assert np.abs(phi - ref.phi).max() <= 2e-5
+    b.close()
+
+
+def test_a_domain_stepped_on_its_own_is_refused():
+    b = pf.Batch(SHAPES[:2], [_params(0), _params(1)], "fp32")
+    b.init([1, 2])
+    pf.pf_step(b.domain(1), 1)
+    with pytest.raises(pf.PfError) as e:
+        b.step(2)
+    assert e.value.status == pf.PF_E_INVAL
+    b.close()
