@@ -42,6 +42,10 @@ METRIC = "phi+mu step MLUP/s (FP32 stencil; FP64 GPU path and error reported bes
 # and mu^n (8 B) and writes mu^{n+1} (8 B); the phi-sweep reads phi^n and mu^n and writes phi^{n+1}
 # and the fused step reads phi^n and mu^n and writes phi^{n+1} and mu^{n+1}
 BYTES_PER_CELL = {"mu_sweep": 48, "phi_sweep": 40, "fused_step": 48}
+# DRAM bytes per cell per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of
+# the kernel as it is now, on 128x128x512 with the same workload recipe, scaled by cells (the capture
+# file and its command are in profiles/); remove an entry when its kernel changes
+TRAFFIC_BYTES_PER_CELL = {}
 
 
 def _env_int(name, default):
@@ -109,6 +113,21 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(ms: float, dist=None, device: str = "cpu") -> float:
+    """The slowest rank's time (the timed region of every rank ends at the same barrier)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, cells_per_rank: int, steps: int, ms_max: float) -> float:
+    """Cell updates of all ranks (one replica of the workload each) / the slowest rank's time."""
+    return world * cells_per_rank * steps / (ms_max / 1e3) / 1e6
 
 
 def cpu_baseline(min_seconds: float = 10.0, max_steps: int = 40):
@@ -219,6 +238,70 @@ def run_batched_study(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving_study(args):
+    """Poisson stream of solidification requests (sizes as the batched study plus a fraction at
+    256x256x512, steps uniform in a range, random v, G and seed) served with continuous batching;
+    the arrival rate puts the offered load at `load` x the measured batched capacity.  Reports
+    p50/p99 latency (submission to result) and the aggregate MLUP/s."""
+    import time as _t
+
+    import numpy as np
+    import torch
+
+    from paper_1506_01684_gb300 import pf
+    from paper_1506_01684_gb300 import workloads as W
+
+    reqs = W.serving_requests(args.requests, seed=0, big_fraction=0.1,
+                              steps_range=(args.min_steps, args.max_steps))
+    work = np.array([r["nx"] * r["ny"] * r["nz"] * r["steps"] for r in reqs], dtype=float)
+    # capacity: the batched launch on a sample of the request mix
+    sample = reqs[: min(16, len(reqs))]
+    b = pf.Batch([(r["nx"], r["ny"], r["nz"]) for r in sample],
+                 [W.symmetric_params(G=r["G"], v=r["v"]) for r in sample], "fp32")
+    b.init([r["seed"] for r in sample])
+    b.step(4)
+    b.sync()
+    t0 = _t.perf_counter()
+    b.step(20)
+    b.sync()
+    cap = sum(r["nx"] * r["ny"] * r["nz"] for r in sample) * 20 / (_t.perf_counter() - t0)  # cells/s
+    b.close()
+    mean_gap = work.mean() / (args.load * cap)
+    arrivals = np.array([r["arrival"] for r in reqs]) * mean_gap
+    srv = pf.pf_server_create(0, 0, args.chunk)
+    tickets = {}
+    lat = {}
+    t_start = _t.perf_counter()
+    nxt = 0
+    while len(lat) < len(reqs):
+        now = _t.perf_counter() - t_start
+        while nxt < len(reqs) and arrivals[nxt] <= now:
+            r = reqs[nxt]
+            tickets[nxt] = pf.pf_submit(srv, r["nx"], r["ny"], r["nz"],
+                                        pf.params_from_dict(W.symmetric_params(G=r["G"], v=r["v"]), pf.PF_FP32),
+                                        r["seed"], r["steps"])
+            nxt += 1
+        for i in [i for i in tickets if i not in lat]:
+            res = pf.pf_poll(srv, tickets[i])
+            if res is not None:
+                lat[i] = res[2]
+        _t.sleep(0.0005)
+    makespan = _t.perf_counter() - t_start
+    st = pf.pf_server_stats(srv)
+    pf.pf_server_destroy(srv)
+    L = np.array([lat[i] for i in range(len(reqs))])
+    line = {"metric": "served solidification requests: p50/p99 latency and aggregate MLUP/s (FP32)",
+            "unit": "s", "p50_latency_s": float(np.percentile(L, 50)), "p99_latency_s": float(np.percentile(L, 99)),
+            "mean_latency_s": float(L.mean()), "aggregate_mlups": float(work.sum() / makespan / 1e6),
+            "busy_mlups": st["mlups"], "makespan_s": makespan, "requests": len(reqs),
+            "offered_load": args.load, "capacity_mlups_estimate": cap / 1e6, "chunk_steps": args.chunk,
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{len(reqs)} Poisson arrivals, sizes x,y in {{32,64,96,128}}, z in {{128,256,512}} "
+                                   f"plus 10% at 256x256x512, steps U[{args.min_steps},{args.max_steps}], random v, G, "
+                                   "seed (numpy PCG64 seed 1)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -228,8 +311,13 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="steps of the FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=["batched"],
+    ap.add_argument("--study", default=None, choices=["batched", "serving"],
                     help="run a secondary study instead of the headline line")
+    ap.add_argument("--requests", type=int, default=100, help="serving study: number of requests")
+    ap.add_argument("--min-steps", type=int, default=100, help="serving study: fewest steps per request")
+    ap.add_argument("--max-steps", type=int, default=1000, help="serving study: most steps per request")
+    ap.add_argument("--load", type=float, default=0.8, help="serving study: offered load / capacity")
+    ap.add_argument("--chunk", type=int, default=64, help="serving study: steps per scheduling round")
     ap.add_argument("--variant", default="auto", choices=["auto", "unfused", "fused"],
                     help="kernel variant of the FP32 step (auto: the library's choice)")
     ap.add_argument("--grains", type=int, default=GRAINS,
@@ -262,6 +350,9 @@ def main():
     torch.cuda.set_device(local)
     if args.study == "batched":
         run_batched_study(args)
+        return
+    if args.study == "serving":
+        run_serving_study(args)
         return
     dist = None
     if world > 1:
@@ -305,12 +396,8 @@ def main():
     clk = clocks.stop()
     prof = pf.pf_profile_read(sim.h)
     sim.sync()
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * cells * args.steps / (ms_max / 1e3) / 1e6
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_mlups(world, cells, args.steps, ms_max)
     launches = sum(n for _, n in prof.values())
 
     # dominant kernel and its roofline
@@ -321,11 +408,8 @@ def main():
             for k, v in prof.items()}
     achieved = BYTES_PER_CELL.get(dom, 0) * cells / (dom_ms / 1e3) / 1e9
     traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get(dom)
-    except Exception:
-        traffic = None
+    if dom in TRAFFIC_BYTES_PER_CELL and NX * NY * NZ >= 8 << 20:
+        traffic = TRAFFIC_BYTES_PER_CELL[dom] * cells
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
             "bytes_per_cell": BYTES_PER_CELL.get(dom)}

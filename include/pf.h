@@ -204,6 +204,38 @@ int pf_batch_set_zchunk(pf_batch *b, int zchunk);
 int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms);
 
 /*
+ * Serving: solidification runs submitted as they arrive, run with continuous batching.  A
+ * scheduler thread admits queued requests as device memory frees up (admission by HBM footprint
+ * of their double-buffered fields against the server's budget; the oldest waiting request keeps
+ * a reservation so that large requests are not starved), keeps each run's fields resident, and
+ * steps all running requests together with the batched launch in chunks of at most `chunk`
+ * steps (a chunk ends where the next request finishes).  Requests arriving meanwhile join at the
+ * next chunk boundary.  A request's result does not depend on the mix it ran in: the batched
+ * kernel computes each domain exactly as it would alone.  FP32 only.
+ */
+/* Create a server with a device-memory budget (bytes, 0: 90% of the free memory) and at most
+ * max_active concurrently running requests (0: 256); chunk = steps per scheduling round (0: 64). */
+int pf_server_create(size_t hbm_budget_bytes, int max_active, int chunk, pf_server **out);
+/* Stop the scheduler (running requests are cancelled) and release everything. */
+int pf_server_destroy(pf_server *srv);
+/* Queue a run: nx*ny*nz cells, parameters p (precision must be PF_FP32), Voronoi seed, nsteps
+ * steps.  Returns a ticket.  PF_E_NOMEM if the run alone exceeds the budget. */
+int pf_submit(pf_server *srv, int nx, int ny, int nz, const pf_params *p, uint64_t seed, int nsteps,
+              uint64_t *ticket);
+/* Result of a finished run: the phase fractions, the phi slab (4 x nx x ny floats, component
+ * major, of the plane z = max(0, floor(h_int) - 8): just inside the solid, where the pattern is
+ * frozen; may be NULL), and the latency from submission to completion in seconds (may be NULL).
+ * Returns PF_E_PENDING while queued or running, PF_OK once (the record is then released), the
+ * run's error (e.g. PF_E_UNSTABLE) if it failed, PF_E_CANCELLED, or PF_E_INVAL for an unknown
+ * ticket. */
+int pf_poll(pf_server *srv, uint64_t ticket, double fractions[4], float *slab, double *latency_s);
+/* Cancel a queued or running request (its record is released on the next pf_poll). */
+int pf_cancel(pf_server *srv, uint64_t ticket);
+/* Aggregate throughput so far (cell updates / busy seconds / 1e6), running and queued counts and
+ * the device bytes held by running requests; any pointer may be NULL. */
+int pf_server_stats(pf_server *srv, double *mlups, int *running, int *queued, size_t *used_bytes);
+
+/*
  * Allocation-free step.  The paper has no counterpart; this entry point serves callers that
  * cannot allocate device memory: code that must live inside a device-memory budget owned by
  * another allocator (a framework's caching pool or a fixed serving arena, where a private

@@ -7,8 +7,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <mutex>
 #include <new>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "pf_internal.h"
@@ -294,7 +299,7 @@ static bool use_fused(const pf_sim *s)
     if (s->comp()) return false;  // the compensated state runs on the two sweeps
     if (s->variant == PF_VARIANT_FUSED) return true;
     if (s->variant == PF_VARIANT_UNFUSED) return false;
-    return false;  // AUTO: the unfused sweeps (measured faster on 256x256x1024 FP32 so far)
+    return s->p.precision == PF_FP32;  // AUTO: fused for FP32 (measured faster), the two sweeps for FP64
 }
 
 template <typename R>
@@ -820,6 +825,12 @@ struct pf_batch {
     bool built = false;
     cudaGraphExec_t graph = nullptr;
     int direct_steps = 0;
+    // descriptors are built relative to each domain's current buffer: parity counts the steps since
+    // the build (mod 2); cur0 holds each domain's buffer index at the build
+    int parity = 0;
+    std::vector<int> cur0;
+    size_t dom_capacity = 0;
+    bool owns_sims = true;
 };
 
 template <typename R>
@@ -841,8 +852,8 @@ static int batch_build(pf_batch *b)
         kp.zchunk = g.zchunk;
         d[q].kp = kp;
         for (int k = 0; k < 2; k++) {
-            d[q].phi[k] = s->phi[k].p;
-            d[q].mu[k] = s->mu[k].p;
+            d[q].phi[k] = s->phi[k ^ s->cur].p;
+            d[q].mu[k] = s->mu[k ^ s->cur].p;
         }
         d[q].st = (DevState *)s->state.p;
         d[q].tab = (PlaneT<R> *)s->tab.p;
@@ -874,7 +885,11 @@ static int batch_build(pf_batch *b)
     dev_free(b->parts, b->stream);
     int r = dev_alloc(b->items, std::max<size_t>(1, sorted.size()) * sizeof(BatchItem), b->stream);
     if (r == PF_OK) r = dev_alloc(b->parts, std::max<size_t>(1, part_total) * sizeof(Partial), b->stream);
-    if (r == PF_OK && !b->doms.p) r = dev_alloc(b->doms, (size_t)n * sizeof(BatchDomain<R>), b->stream);
+    if (r == PF_OK && b->dom_capacity < (size_t)n) {
+        dev_free(b->doms, b->stream);
+        r = dev_alloc(b->doms, (size_t)n * sizeof(BatchDomain<R>), b->stream);
+        b->dom_capacity = r == PF_OK ? (size_t)n : 0;
+    }
     if (r == PF_OK && !b->counter.p) r = dev_alloc(b->counter, 256, b->stream);
     if (r != PF_OK) return r;
     for (int q = 0; q < n; q++) d[q].parts = (Partial *)b->parts.p + part_off[q];
@@ -891,6 +906,9 @@ static int batch_build(pf_batch *b)
     b->nitems = (int)sorted.size();
     b->post_blocks = post;
     b->built = true;
+    b->parity = 0;
+    b->cur0.resize(n);
+    for (int q = 0; q < n; q++) b->cur0[q] = b->sims[q]->cur;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -902,11 +920,11 @@ template <typename R>
 static int batch_step_direct(pf_batch *b, int n)
 {
     for (int q = 0; q < n; q++) {
-        const int par = b->sims[0]->cur;
         cudaError_t e = launch_batched_step<R>((const BatchDomain<R> *)b->doms.p, (int)b->sims.size(),
                                                (const BatchItem *)b->items.p, b->nitems, (unsigned *)b->counter.p,
-                                               par, b->ctas, b->post_blocks, b->stream);
+                                               b->parity, b->ctas, b->post_blocks, b->stream);
         if (e != cudaSuccess) return cuda_status(e);
+        b->parity ^= 1;
         for (pf_sim *s : b->sims) s->cur = 1 - s->cur;
     }
     return PF_OK;
@@ -919,9 +937,8 @@ static int batch_step(pf_batch *b, int n)
         int r = batch_build<R>(b);
         if (r != PF_OK) return r;
     }
-    const int par = b->sims[0]->cur;
-    for (pf_sim *s : b->sims)
-        if (s->cur != par) return PF_E_INVAL;
+    for (size_t q = 0; q < b->sims.size(); q++)
+        if (b->sims[q]->cur != (b->cur0[q] ^ b->parity)) return PF_E_INVAL;  // stepped on its own
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(b->stream, &cs) != cudaSuccess) {
         cudaGetLastError();
@@ -932,7 +949,7 @@ static int batch_step(pf_batch *b, int n)
         if (r == PF_OK) b->direct_steps += n;
         return r;
     }
-    if (par != 0) {
+    if (b->parity != 0) {  // the graph starts from the build's buffers
         int r = batch_step_direct<R>(b, 1);
         if (r != PF_OK) return r;
         n -= 1;
@@ -971,8 +988,9 @@ int pf_batch_destroy(pf_batch *b)
     if (!b) return PF_E_INVAL;
     cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
-    for (pf_sim *s : b->sims)
-        if (s) pf_destroy(s);
+    if (b->owns_sims)
+        for (pf_sim *s : b->sims)
+            if (s) pf_destroy(s);
     dev_free(b->doms, b->stream);
     dev_free(b->items, b->stream);
     dev_free(b->parts, b->stream);
@@ -1144,6 +1162,324 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
     if (e != cudaSuccess) return cuda_status(e);
     if (best) *best = bestz;
     if (best_ms) *best_ms = bestt;
+    return PF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// serving loop
+// ------------------------------------------------------------------------------------------
+namespace {
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+enum { REQ_QUEUED = 0, REQ_RUNNING = 1, REQ_DONE = 2, REQ_FAILED = 3, REQ_CANCELLED = 4 };
+
+struct ServeReq {
+    uint64_t id = 0;
+    int nx = 0, ny = 0, nz = 0, nsteps = 0, done_steps = 0;
+    pf_params p{};
+    uint64_t seed = 0;
+    size_t footprint = 0;
+    double t_submit = 0.0, t_done = 0.0;
+    int state = REQ_QUEUED, status = PF_OK;
+    bool cancel = false;
+    pf_sim *sim = nullptr;
+    double fractions[4] = {0, 0, 0, 0};
+    std::vector<float> slab;
+};
+
+// device bytes a request holds while it runs: double-buffered FP32 fields plus its small buffers
+size_t footprint_of(int nx, int ny, int nz)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    const Geometry g = make_geometry(nx, ny, nz, 0);
+    return 2 * n * (16 + 8) + (size_t)2 * nz * 64 + (size_t)g.nparts() * sizeof(Partial) + (size_t)nz * 64 + 4096;
+}
+}  // namespace
+
+struct pf_server {
+    size_t budget = 0, used = 0;
+    int device = 0, max_active = 256, chunk = 64;
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<ServeReq *> queue;
+    std::vector<ServeReq *> running;
+    std::unordered_map<uint64_t, ServeReq *> all;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread th;
+    pf_batch *batch = nullptr;
+    double cell_steps = 0.0, busy = 0.0;
+};
+
+// the plane k of a simulation's phi as FP32, component major (4 x nx x ny)
+static int read_phi_plane(pf_sim *s, int k, std::vector<float> &out)
+{
+    const size_t plane = (size_t)s->nx * s->ny;
+    DevBuf stg;
+    int r = dev_alloc(stg, plane * 4 * sizeof(double), s->stream);
+    if (r != PF_OK) return r;
+    const KParams<float> kp = make_kparams<float>(s);
+    cudaError_t e = launch_pack<float>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p,
+                                       (double *)stg.p, nullptr, k, 1, s->stream);
+    std::vector<double> h(plane * 4);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), stg.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    dev_free(stg, s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    out.resize(h.size());
+    for (size_t q = 0; q < h.size(); q++) out[q] = (float)h[q];
+    return PF_OK;
+}
+
+static void finish_request(pf_server *v, ServeReq *r)
+{
+    int st = r->cancel ? PF_E_CANCELLED : pf_sync(r->sim);
+    if (st == PF_OK) st = pf_phase_fractions(r->sim, r->fractions);
+    double h = 0.0;
+    if (st == PF_OK) st = pf_stats(r->sim, nullptr, nullptr, nullptr, &h);
+    if (st == PF_OK) {
+        int zs = (int)floor(h) - 8;
+        zs = std::max(0, std::min(r->nz - 1, zs));
+        st = read_phi_plane(r->sim, zs, r->slab);
+    }
+    pf_destroy(r->sim);
+    r->sim = nullptr;
+    std::lock_guard<std::mutex> lk(v->mu);
+    v->used -= r->footprint;
+    r->t_done = now_s();
+    r->status = st;
+    r->state = r->cancel ? REQ_CANCELLED : (st == PF_OK ? REQ_DONE : REQ_FAILED);
+}
+
+static void server_loop(pf_server *v)
+{
+    cudaSetDevice(v->device);
+    for (;;) {
+        std::vector<ServeReq *> admit;
+        {
+            std::unique_lock<std::mutex> lk(v->mu);
+            v->cv.wait(lk, [&] { return v->stop || !v->queue.empty() || !v->running.empty(); });
+            if (v->stop) break;
+            // admission: arrival order; requests behind a waiting one may use only what leaves room for it
+            size_t reserve = 0;
+            int slots = v->max_active - (int)v->running.size();
+            for (auto it = v->queue.begin(); it != v->queue.end() && slots > 0;) {
+                ServeReq *r = *it;
+                if (r->cancel) {
+                    r->state = REQ_CANCELLED;
+                    r->status = PF_E_CANCELLED;
+                    it = v->queue.erase(it);
+                    continue;
+                }
+                if (v->used + reserve + r->footprint <= v->budget) {
+                    v->used += r->footprint;
+                    admit.push_back(r);
+                    it = v->queue.erase(it);
+                    slots--;
+                } else {
+                    if (reserve == 0) reserve = r->footprint;
+                    ++it;
+                }
+            }
+        }
+        for (ServeReq *r : admit) {
+            pf_sim *sim = nullptr;
+            int st = pf_create(r->nx, r->ny, r->nz, &r->p, (void *)v->stream, &sim);
+            if (st == PF_OK) pf_set_variant(sim, PF_VARIANT_FUSED);
+            if (st == PF_OK) st = pf_init(sim, r->seed);
+            std::lock_guard<std::mutex> lk(v->mu);
+            if (st != PF_OK) {
+                if (sim) pf_destroy(sim);
+                v->used -= r->footprint;
+                r->status = st;
+                r->state = REQ_FAILED;
+                r->t_done = now_s();
+                continue;
+            }
+            r->sim = sim;
+            r->state = REQ_RUNNING;
+            v->running.push_back(r);
+            v->batch->built = false;
+        }
+        if (v->running.empty()) continue;
+        // one chunk for every running request: it ends where the next request finishes
+        int c = v->chunk;
+        for (ServeReq *r : v->running) c = std::min(c, r->nsteps - r->done_steps);
+        v->batch->sims.clear();
+        for (ServeReq *r : v->running) v->batch->sims.push_back(r->sim);
+        const double t0 = now_s();
+        int st = c > 0 ? batch_step<float>(v->batch, c) : PF_OK;
+        cudaError_t e = cudaStreamSynchronize(v->stream);
+        const double t1 = now_s();
+        double cells = 0.0;
+        for (ServeReq *r : v->running) {
+            r->done_steps += c;
+            cells += (double)r->nx * r->ny * r->nz;
+        }
+        std::vector<ServeReq *> keep, done;
+        {
+            std::lock_guard<std::mutex> lk(v->mu);
+            v->cell_steps += cells * c;
+            v->busy += t1 - t0;
+            for (ServeReq *r : v->running) {
+                if (st != PF_OK || e != cudaSuccess || r->cancel || r->done_steps >= r->nsteps)
+                    done.push_back(r);
+                else
+                    keep.push_back(r);
+            }
+            v->running = keep;
+        }
+        if (!done.empty()) v->batch->built = false;
+        for (ServeReq *r : done) {
+            if (st != PF_OK || e != cudaSuccess) r->cancel = false;
+            finish_request(v, r);
+            if (st != PF_OK && r->status == PF_OK) r->status = st;
+        }
+        v->cv.notify_all();
+    }
+    // shutdown: release whatever still runs
+    for (ServeReq *r : v->running) {
+        r->cancel = true;
+        if (r->sim) pf_destroy(r->sim);
+        r->sim = nullptr;
+        r->state = REQ_CANCELLED;
+    }
+    v->running.clear();
+}
+
+extern "C" {
+
+int pf_server_create(size_t hbm_budget_bytes, int max_active, int chunk, pf_server **out)
+{
+    if (!out || max_active < 0 || chunk < 0) return PF_E_INVAL;
+    *out = nullptr;
+    pf_server *v = new (std::nothrow) pf_server;
+    if (!v) return PF_E_NOMEM;
+    cudaGetDevice(&v->device);
+    if (hbm_budget_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            delete v;
+            return PF_E_CUDA;
+        }
+        hbm_budget_bytes = fr / 10 * 9;
+    }
+    v->budget = hbm_budget_bytes;
+    if (max_active > 0) v->max_active = max_active;
+    if (chunk > 0) v->chunk = chunk;
+    cudaError_t e = cudaStreamCreateWithFlags(&v->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete v;
+        return cuda_status(e);
+    }
+    v->batch = new (std::nothrow) pf_batch;
+    if (!v->batch) {
+        cudaStreamDestroy(v->stream);
+        delete v;
+        return PF_E_NOMEM;
+    }
+    v->batch->stream = v->stream;
+    v->batch->owns_sims = false;
+    v->batch->precision = PF_FP32;
+    v->th = std::thread(server_loop, v);
+    *out = v;
+    return PF_OK;
+}
+
+int pf_server_destroy(pf_server *v)
+{
+    if (!v) return PF_E_INVAL;
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        v->stop = true;
+    }
+    v->cv.notify_all();
+    if (v->th.joinable()) v->th.join();
+    v->batch->sims.clear();
+    pf_batch_destroy(v->batch);  // does not own the (already released) simulations
+    for (auto &kv : v->all) delete kv.second;  // every queued, running or finished record
+    v->all.clear();
+    v->queue.clear();
+    cudaStreamDestroy(v->stream);
+    delete v;
+    return PF_OK;
+}
+
+int pf_submit(pf_server *v, int nx, int ny, int nz, const pf_params *p, uint64_t seed, int nsteps, uint64_t *ticket)
+{
+    if (!v || !p || !ticket || nx < 1 || ny < 1 || nz < 1 || nsteps < 0) return PF_E_INVAL;
+    if (p->precision != PF_FP32 || check_params(p) != PF_OK) return PF_E_INVAL;
+    ServeReq *r = new (std::nothrow) ServeReq;
+    if (!r) return PF_E_NOMEM;
+    r->nx = nx;
+    r->ny = ny;
+    r->nz = nz;
+    r->p = *p;
+    r->seed = seed;
+    r->nsteps = nsteps;
+    r->footprint = footprint_of(nx, ny, nz);
+    r->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        if (r->footprint > v->budget) {
+            delete r;
+            return PF_E_NOMEM;
+        }
+        r->id = v->next_id++;
+        v->all[r->id] = r;
+        v->queue.push_back(r);
+        *ticket = r->id;
+    }
+    v->cv.notify_all();
+    return PF_OK;
+}
+
+int pf_poll(pf_server *v, uint64_t ticket, double fractions[4], float *slab, double *latency_s)
+{
+    if (!v) return PF_E_INVAL;
+    std::lock_guard<std::mutex> lk(v->mu);
+    auto it = v->all.find(ticket);
+    if (it == v->all.end()) return PF_E_INVAL;
+    ServeReq *r = it->second;
+    if (r->state == REQ_QUEUED || r->state == REQ_RUNNING) return PF_E_PENDING;
+    int st = r->state == REQ_DONE ? PF_OK : (r->state == REQ_CANCELLED ? PF_E_CANCELLED : r->status);
+    if (r->state == REQ_DONE) {
+        if (fractions)
+            for (int a = 0; a < 4; a++) fractions[a] = r->fractions[a];
+        if (slab && !r->slab.empty()) memcpy(slab, r->slab.data(), r->slab.size() * sizeof(float));
+    }
+    if (latency_s) *latency_s = r->t_done - r->t_submit;
+    v->all.erase(it);
+    delete r;
+    return st;
+}
+
+int pf_cancel(pf_server *v, uint64_t ticket)
+{
+    if (!v) return PF_E_INVAL;
+    std::lock_guard<std::mutex> lk(v->mu);
+    auto it = v->all.find(ticket);
+    if (it == v->all.end()) return PF_E_INVAL;
+    it->second->cancel = true;
+    return PF_OK;
+}
+
+int pf_server_stats(pf_server *v, double *mlups, int *running, int *queued, size_t *used_bytes)
+{
+    if (!v) return PF_E_INVAL;
+    std::lock_guard<std::mutex> lk(v->mu);
+    if (mlups) *mlups = v->busy > 0 ? v->cell_steps / v->busy / 1e6 : 0.0;
+    if (running) *running = (int)v->running.size();
+    if (queued) *queued = (int)v->queue.size();
+    if (used_bytes) *used_bytes = v->used;
     return PF_OK;
 }
 

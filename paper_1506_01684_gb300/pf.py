@@ -94,6 +94,13 @@ SIGNATURES = {
     "pf_batch_sync": (_I, [_VP]),
     "pf_batch_set_zchunk": (_I, [_VP, _I]),
     "pf_batch_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), _DP]),
+    "pf_server_create": (_I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_VP)]),
+    "pf_server_destroy": (_I, [_VP]),
+    "pf_submit": (_I, [_VP, _I, _I, _I, ctypes.POINTER(pf_params), ctypes.c_uint64, _I,
+                       ctypes.POINTER(ctypes.c_uint64)]),
+    "pf_poll": (_I, [_VP, ctypes.c_uint64, _DP, ctypes.POINTER(ctypes.c_float), _DP]),
+    "pf_cancel": (_I, [_VP, ctypes.c_uint64]),
+    "pf_server_stats": (_I, [_VP, _DP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
 }
 
 PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_FUSED, PF_K_COUNT = 0, 1, 2, 3, 4, 8
@@ -323,6 +330,50 @@ def pf_batch_autotune(b, trial_steps=10):
     ms = _D()
     _check(lib().pf_batch_autotune(b, trial_steps, ctypes.byref(best), ctypes.byref(ms)), "pf_batch_autotune")
     return best.value, ms.value
+
+
+def pf_server_create(hbm_budget_bytes: int = 0, max_active: int = 0, chunk: int = 0):
+    h = _VP()
+    _check(lib().pf_server_create(hbm_budget_bytes, max_active, chunk, ctypes.byref(h)), "pf_server_create")
+    return h
+
+
+def pf_server_destroy(srv):
+    return _check(lib().pf_server_destroy(srv), "pf_server_destroy")
+
+
+def pf_submit(srv, nx, ny, nz, params: pf_params, seed: int, nsteps: int) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().pf_submit(srv, nx, ny, nz, ctypes.byref(params), ctypes.c_uint64(seed), nsteps, ctypes.byref(t)),
+           "pf_submit")
+    return t.value
+
+
+def pf_poll(srv, ticket: int, nx: int = 0, ny: int = 0):
+    """None while pending; else (fractions, slab (4, ny, nx) float32 or None, latency_s).  Raises on failure."""
+    fr = np.zeros(4)
+    slab = np.zeros((4, ny, nx), dtype=np.float32) if nx and ny else None
+    lat = _D()
+    st = lib().pf_poll(srv, ctypes.c_uint64(ticket), _dp(fr),
+                       slab.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if slab is not None else None,
+                       ctypes.byref(lat))
+    if st == PF_E_PENDING:
+        return None
+    _check(st, "pf_poll")
+    return fr, slab, lat.value
+
+
+def pf_cancel(srv, ticket: int):
+    return _check(lib().pf_cancel(srv, ctypes.c_uint64(ticket)), "pf_cancel")
+
+
+def pf_server_stats(srv):
+    m = _D()
+    r, q = _I(), _I()
+    u = ctypes.c_size_t()
+    _check(lib().pf_server_stats(srv, ctypes.byref(m), ctypes.byref(r), ctypes.byref(q), ctypes.byref(u)),
+           "pf_server_stats")
+    return {"mlups": m.value, "running": r.value, "queued": q.value, "used_bytes": u.value}
 
 
 class Batch:

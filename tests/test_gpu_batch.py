@@ -92,8 +92,11 @@ def test_autotune_restores_the_state_and_keeps_results():
 
 
 def test_a_domain_stepped_on_its_own_is_refused():
+    # the batch adopts each domain's buffers when it builds its work table (first step); a domain
+    # stepped on its own after that would desynchronise the table and is refused
     b = pf.Batch(SHAPES[:2], [_params(0), _params(1)], "fp32")
     b.init([1, 2])
+    b.step(1)
     pf.pf_step(b.domain(1), 1)
     with pytest.raises(pf.PfError) as e:
         b.step(2)
