@@ -45,7 +45,7 @@ BYTES_PER_CELL = {"mu_sweep": 48, "phi_sweep": 40, "fused_step": 48}
 # DRAM bytes per cell per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of
 # the kernel as it is now, on 128x128x512 with the same workload recipe, scaled by cells (the capture
 # file and its command are in profiles/); remove an entry when its kernel changes
-TRAFFIC_BYTES_PER_CELL = {}
+TRAFFIC_BYTES_PER_CELL = {"fused_step": 44.72}  # profiles/fused_step_fp32_128x128x512.md
 
 
 def _env_int(name, default):
@@ -302,6 +302,67 @@ def run_serving_study(args):
     print(json.dumps(line), flush=True)
 
 
+def run_precision_study(args):
+    """128x128x512 cells, 20000 steps by default: compensated FP32 vs plain FP32 vs FP64 on the GPU.
+    First each GPU path's agreement with the CPU oracle on the small case (32x32x64, 200 steps);
+    then, on the study case, the error of phase fractions and lamella counts against the FP64 run."""
+    import time as _t
+
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1506_01684_gb300 import analysis, pf
+    from paper_1506_01684_gb300 import workloads as W
+
+    small = {}
+    p0 = W.symmetric_params()
+    ref = oracle.State(p0, 32, 32, 64).init(0)
+    ref.step(200)
+    for prec in ("fp64", "fp32", "fp32c"):
+        sim = pf.Simulation(32, 32, 64, p0, prec)
+        sim.init(0)
+        sim.step(200)
+        phi, mu = sim.fields()
+        small[prec] = {"max_abs_dphi": float(np.abs(phi - ref.phi).max()),
+                       "max_rel_dmu": float(np.abs(mu - ref.mu).max() / max(np.abs(ref.mu).max(), 1e-8))}
+        sim.close()
+    nx, ny, nz = (int(x) for x in args.study_shape.split("x"))
+    p = W.symmetric_params(n_grains=20)
+    res = {}
+    for prec in ("fp64", "fp32c", "fp32"):
+        sim = pf.Simulation(nx, ny, nz, p, prec)
+        sim.init(0)
+        sol0 = sim.stats()["solute"]
+        torch.cuda.synchronize()
+        t0 = _t.perf_counter()
+        sim.step(args.study_steps)
+        sim.sync()
+        dt = _t.perf_counter() - t0
+        st = sim.stats()
+        phi, mu = sim.fields()
+        res[prec] = {"mlups": nx * ny * nz * args.study_steps / dt / 1e6, "seconds": dt,
+                     "fractions": [float(x) for x in sim.fractions()], "h_int": st["h_int"],
+                     "lamellae": analysis.lamella_count(phi, st["h_int"]),
+                     "solute_drift": [float((st["solute"][c] - sol0[c]) / sol0[c]) for c in range(2)],
+                     "_phi": phi, "_mu": mu}
+        sim.close()
+    base = res["fp64"]
+    for prec in ("fp32c", "fp32"):
+        r = res[prec]
+        r["max_abs_dphi_vs_fp64"] = float(np.abs(r["_phi"] - base["_phi"]).max())
+        r["max_rel_dmu_vs_fp64"] = float(np.abs(r["_mu"] - base["_mu"]).max() / max(np.abs(base["_mu"]).max(), 1e-8))
+        r["max_abs_dfraction_vs_fp64"] = float(np.abs(np.array(r["fractions"]) - np.array(base["fractions"])).max())
+        r["lamella_diff_vs_fp64"] = [a - b for a, b in zip(r["lamellae"], base["lamellae"])]
+    for r in res.values():
+        r.pop("_phi")
+        r.pop("_mu")
+    line = {"metric": "precision study: FP32 / compensated FP32 vs FP64 on the GPU", "config": {
+        "workload": f"{nx}x{ny}x{nz}, 20 grains, seed 0, {args.study_steps} steps, symmetric parameter set"},
+        "small_case_vs_oracle": small, "results": res, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -311,13 +372,15 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="steps of the FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=["batched", "serving"],
+    ap.add_argument("--study", default=None, choices=["batched", "serving", "precision"],
                     help="run a secondary study instead of the headline line")
     ap.add_argument("--requests", type=int, default=100, help="serving study: number of requests")
     ap.add_argument("--min-steps", type=int, default=100, help="serving study: fewest steps per request")
     ap.add_argument("--max-steps", type=int, default=1000, help="serving study: most steps per request")
     ap.add_argument("--load", type=float, default=0.8, help="serving study: offered load / capacity")
     ap.add_argument("--chunk", type=int, default=64, help="serving study: steps per scheduling round")
+    ap.add_argument("--study-shape", default="128x128x512", help="precision study: domain")
+    ap.add_argument("--study-steps", type=int, default=20000, help="precision study: steps")
     ap.add_argument("--variant", default="auto", choices=["auto", "unfused", "fused"],
                     help="kernel variant of the FP32 step (auto: the library's choice)")
     ap.add_argument("--grains", type=int, default=GRAINS,
@@ -353,6 +416,9 @@ def main():
         return
     if args.study == "serving":
         run_serving_study(args)
+        return
+    if args.study == "precision":
+        run_precision_study(args)
         return
     dist = None
     if world > 1:

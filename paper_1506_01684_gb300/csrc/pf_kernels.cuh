@@ -1697,6 +1697,12 @@ __global__ void __launch_bounds__(256) reduce_kernel(const KParams<R> kp, const 
     const size_t plane = (size_t)kp.nx * kp.ny;
     const size_t base = plane_off(k, kp.nz, st->zbase, plane);
     const double T = kp.T0 + kp.G * (((double)k + st->off) * kp.dx64 - kp.v * st->t);
+    double i2A[4], ch[4][2];  // per-plane constants: 1/(2 A_a), cE_a + kT_a (T - TE)
+    for (int a = 0; a < 4; a++) {
+        i2A[a] = 1.0 / (2.0 * kp.A64[a]);
+        ch[a][0] = kp.cE[a][0] + kp.kT64[a][0] * (T - kp.TE);
+        ch[a][1] = kp.cE[a][1] + kp.kT64[a][1] * (T - kp.TE);
+    }
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (size_t q = threadIdx.x; q < plane; q += 256) {
         const Ph<R> p = ldg_ph(phi + base + q);
@@ -1715,12 +1721,13 @@ __global__ void __launch_bounds__(256) reduce_kernel(const KParams<R> kp, const 
         const double m0 = (double)m.v[0] + (double)ml.v[0], m1 = (double)m.v[1] + (double)ml.v[1];
         bool bad = !isfinite(m0) || !isfinite(m1);
         double c0 = 0.0, c1 = 0.0;
+        const double iS = 1.0 / S;  // one FP64 division per cell (the FP64 rate is low on this part)
         for (int a = 0; a < 4; a++) {
             bad = bad || !isfinite(ph[a]);
             acc[a] += ph[a];
-            const double h = ph[a] * ph[a] / S;
-            c0 += h * (m0 / (2.0 * kp.A64[a]) + (kp.cE[a][0] + kp.kT64[a][0] * (T - kp.TE)));
-            c1 += h * (m1 / (2.0 * kp.A64[a]) + (kp.cE[a][1] + kp.kT64[a][1] * (T - kp.TE)));
+            const double h = ph[a] * ph[a] * iS;
+            c0 += h * (m0 * i2A[a] + ch[a][0]);
+            c1 += h * (m1 * i2A[a] + ch[a][1]);
         }
         acc[4] += c0;
         acc[5] += c1;
