@@ -363,6 +363,52 @@ def run_precision_study(args):
     print(json.dumps(line), flush=True)
 
 
+def run_region_study(args):
+    """The paper's block compositions (Section 4: liquid, solid and interface blocks) at one
+    domain size: FP32 MLUP/s of the fused step and of the two sweeps on each, after a warm-up
+    that gives the initially sharp interfaces their diffuse profile."""
+    import time as _t
+
+    import numpy as np
+
+    from paper_1506_01684_gb300 import pf
+    from paper_1506_01684_gb300 import workloads as W
+
+    nx, ny, nz = (int(x) for x in args.region_shape.split("x"))
+    p = W.symmetric_params()
+    out = {}
+    for kind in W.REGION_KINDS:
+        phi0, mu0 = W.region_fields(kind, nx, ny, nz, seed=0)
+        row = {}
+        for variant in ("fused", "unfused"):
+            sim = pf.Simulation(nx, ny, nz, p, "fp32", variant=variant)
+            sim.set_fields(phi0, mu0)
+            sim.step(20)
+            sim.sync()
+            if variant == "fused":
+                phi, _ = sim.fields()
+                onehot = (phi == 1.0).any(axis=0)
+                row["interface_cell_fraction"] = float(1.0 - onehot.mean())
+                row["liquid_cell_fraction"] = float((phi[3] == 1.0).mean())
+            sim.step(args.warmup)
+            sim.sync()
+            t0 = _t.perf_counter()
+            sim.step(args.steps)
+            sim.sync()
+            dt = _t.perf_counter() - t0
+            row[variant + "_mlups"] = nx * ny * nz * args.steps / dt / 1e6
+            sim.close()
+        out[kind] = row
+        del phi0, mu0
+    line = {"metric": "FP32 step MLUP/s on the paper's block compositions (liquid, solid, interface)",
+            "unit": "MLUP/s", "higher_is_better": True, "steps": args.steps, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{nx}x{ny}x{nz} blocks: liquid; 3D solid grains ~48 cells; columnar "
+                                   "grains ~12 cells below z = nz/2 with liquid above; 20 relaxation steps",
+                       "timing": "wall clock around pf_step(K) + pf_sync, graph replay"},
+            "regions": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,7 +418,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="steps of the FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=["batched", "serving", "precision"],
+    ap.add_argument("--study", default=None, choices=["batched", "serving", "precision", "regions"],
                     help="run a secondary study instead of the headline line")
     ap.add_argument("--requests", type=int, default=100, help="serving study: number of requests")
     ap.add_argument("--min-steps", type=int, default=100, help="serving study: fewest steps per request")
@@ -381,6 +427,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=64, help="serving study: steps per scheduling round")
     ap.add_argument("--study-shape", default="128x128x512", help="precision study: domain")
     ap.add_argument("--study-steps", type=int, default=20000, help="precision study: steps")
+    ap.add_argument("--region-shape", default="256x256x256", help="region study: block size")
     ap.add_argument("--variant", default="auto", choices=["auto", "unfused", "fused"],
                     help="kernel variant of the FP32 step (auto: the library's choice)")
     ap.add_argument("--grains", type=int, default=GRAINS,
@@ -419,6 +466,9 @@ def main():
         return
     if args.study == "precision":
         run_precision_study(args)
+        return
+    if args.study == "regions":
+        run_region_study(args)
         return
     dist = None
     if world > 1:

@@ -84,7 +84,7 @@ const char *pf_strerror(int status);
 /* Fill *p with the symmetric parameter set: dx = 1, eps = 4, tau = 1, dt = 0 (auto),
  * gamma2 = 1, gamma3 = 15, A = 1, cE = alpha(0.8,0.1) beta(0.1,0.8) gamma(0.1,0.1)
  * liquid(1/3,1/3), kT = 0 solids / (0.1,0.1) liquid, s = 1 solids / 0 liquid,
- * D = 0 solids / 1 liquid, TE = 1, G = 1e-3, v = 1e-2, T0 = TE - 8 G, seed_layers = 8,
+ * D = 0 solids / 1 liquid, TE = 1, G = 1e-3, v = 1e-2, T0 = TE - 8 G - 0.15, seed_layers = 8,
  * n_grains = 12, window off, precision PF_FP64.  Returns PF_E_INVAL for p == NULL. */
 int pf_default_params(pf_params *p);
 

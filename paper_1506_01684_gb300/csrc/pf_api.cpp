@@ -99,6 +99,11 @@ struct pf_sim {
     int variant = PF_VARIANT_AUTO;
     DevBuf phi[2], mu[2];  // AoS fields of the stencil precision
     DevBuf philo[2], mulo[2];  // low words of the compensated FP32 state (PF_FP32_COMP only)
+    // liquid maps of the two field buffers (one byte per storage plane and fused-step tile: 1 when
+    // the tile's cells of that plane are exactly pure liquid); written by every fused step for its
+    // new field, rebuilt by the classify kernel where tmap_ok says the map is stale
+    DevBuf tmap[2];
+    bool tmap_ok[2] = {false, false};
     DevBuf state;          // DevState
     DevBuf parts;          // Partial[geo.nparts()]
     DevBuf tab;            // PlaneT<R>[2 nz]
@@ -160,6 +165,8 @@ static KParams<R> make_kparams(const pf_sim *s)
     k.nz = s->nz;
     k.zchunk = s->geo.zchunk;
     k.window = p.window_trigger_z > 0.0 ? 1 : 0;
+    k.tgx = s->geo_fused.gx;
+    k.tgy = s->geo_fused.gy;
     k.dx = (R)p.dx;
     k.inv_dx = (R)(1.0 / p.dx);
     k.inv_2dx = (R)(1.0 / (2.0 * p.dx));
@@ -217,6 +224,7 @@ KParams<R> kparams_for(const pf_params &p, int nx, int ny, int nz, const Geometr
     tmp.nz = nz;
     tmp.p = p;
     tmp.geo = g;
+    tmp.geo_fused = g;
     return make_kparams<R>(&tmp);
 }
 template KParams<float> kparams_for<float>(const pf_params &, int, int, int, const Geometry &);
@@ -316,10 +324,17 @@ static int do_step_direct(pf_sim *s, int n)
         const int a = s->cur, b = 1 - s->cur;
         cudaError_t e;
         if (fused) {
-            e = timed(s, PF_K_FUSED, [&] {
-                return launch_fused_step<R>(kp, s->geo_fused, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st,
-                                            tab, parts, s->stream);
-            });
+            e = cudaSuccess;
+            if (!s->tmap_ok[a]) {
+                e = launch_classify<R>(kp, st, s->phi[a].p, (unsigned char *)s->tmap[a].p, s->stream);
+                s->tmap_ok[a] = e == cudaSuccess;
+            }
+            if (e == cudaSuccess)
+                e = timed(s, PF_K_FUSED, [&] {
+                    return launch_fused_step<R>(kp, s->geo_fused, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p,
+                                                st, tab, parts, s->stream, (const unsigned char *)s->tmap[a].p,
+                                                (unsigned char *)s->tmap[b].p);
+                });
         } else if (s->comp()) {
             const KParams<float> &kf = reinterpret_cast<const KParams<float> &>(kp);
             const PlaneT<float> *tf = reinterpret_cast<const PlaneT<float> *>(tab);
@@ -346,9 +361,11 @@ static int do_step_direct(pf_sim *s, int n)
             e = timed(s, PF_K_FINALIZE, [&] { return launch_finalize<R>(kp, st, parts, nparts, s->stream); });
         if (e == cudaSuccess)
             e = timed(s, PF_K_POST, [&] {
-                return launch_post<R>(kp, st, s->phi[b].p, s->mu[b].p, tab, s->stream, s->lo_phi(b), s->lo_mu(b));
+                return launch_post<R>(kp, st, s->phi[b].p, s->mu[b].p, tab, s->stream, s->lo_phi(b), s->lo_mu(b),
+                                      fused ? (unsigned char *)s->tmap[b].p : nullptr);
             });
         if (e != cudaSuccess) return latch(s, cuda_status(e));
+        s->tmap_ok[b] = fused;
         s->cur = b;
     }
     return PF_OK;
@@ -377,6 +394,14 @@ static int do_step(pf_sim *s, int n)
         n -= 1;
     }
     const int want = use_fused(s) ? 1 : 0;
+    if (want && !s->tmap_ok[0]) {
+        // the graph's fused steps take the liquid map of buffer 0 as valid
+        const KParams<R> kp = make_kparams<R>(s);
+        cudaError_t e = launch_classify<R>(kp, (const DevState *)s->state.p, s->phi[0].p,
+                                           (unsigned char *)s->tmap[0].p, s->stream);
+        if (e != cudaSuccess) return latch(s, cuda_status(e));
+        s->tmap_ok[0] = true;
+    }
     if (!s->graph || s->graph_variant != want) {
         if (s->graph) {
             cudaGraphExecDestroy(s->graph);
@@ -431,6 +456,7 @@ static int do_init(pf_sim *s, uint64_t seed, int ng)
     memset(&ds, 0, sizeof ds);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->state.p, &ds, sizeof ds, cudaMemcpyHostToDevice, s->stream);
     s->cur = 0;
+    s->tmap_ok[0] = s->tmap_ok[1] = false;
     if (e == cudaSuccess) e = launch_init<R>(kp, s->phi[0].p, s->mu[0].p, (const double *)s->seeds.p, ng, H, s->stream);
     if (e == cudaSuccess && s->comp())
         e = cudaMemsetAsync(s->philo[0].p, 0, s->philo[0].bytes, s->stream);
@@ -486,6 +512,7 @@ static int do_write(pf_sim *s, const double *phi, const double *mu)
     if (r != PF_OK) return r;
     double *dphi = (double *)stg.p, *dmu = dphi + (size_t)pk * plane * 4;
     cudaError_t e = cudaSuccess;
+    s->tmap_ok[0] = s->tmap_ok[1] = false;
     for (int k0 = 0; k0 < s->nz && e == cudaSuccess; k0 += pk) {
         const int nk = std::min(pk, s->nz - k0);
         const size_t m = (size_t)nk * plane;
@@ -576,7 +603,7 @@ int pf_default_params(pf_params *p)
     p->G = 1e-3;
     p->v = 1e-2;
     p->seed_layers = 8;
-    p->T0 = p->TE - p->G * (double)p->seed_layers;
+    p->T0 = p->TE - p->G * (double)p->seed_layers - 0.15;  // the seeds start 0.15 below TE
     p->n_grains = 12;
     p->window_trigger_z = 0.0;
     return PF_OK;
@@ -601,6 +628,7 @@ int pf_destroy(pf_sim *s)
         dev_free(s->mu[b], s->stream);
         dev_free(s->philo[b], s->stream);
         dev_free(s->mulo[b], s->stream);
+        dev_free(s->tmap[b], s->stream);
     }
     dev_free(s->state, s->stream);
     dev_free(s->parts, s->stream);
@@ -660,6 +688,8 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
         if (r == PF_OK && s->comp()) r = dev_alloc(s->philo[b], n * 4 * w, s->stream);
         if (r == PF_OK && s->comp()) r = dev_alloc(s->mulo[b], n * 2 * w, s->stream);
     }
+    for (int b = 0; b < 2 && r == PF_OK; b++)
+        r = dev_alloc(s->tmap[b], (size_t)nz * s->geo_fused.gx * s->geo_fused.gy, s->stream);
     if (r == PF_OK) r = dev_alloc(s->state, sizeof(DevState), s->stream);
     if (r == PF_OK)
         r = dev_alloc(s->parts, (size_t)std::max(s->geo.nparts(), s->geo_fused.nparts()) * sizeof(Partial),
@@ -854,6 +884,7 @@ static int batch_build(pf_batch *b)
         for (int k = 0; k < 2; k++) {
             d[q].phi[k] = s->phi[k ^ s->cur].p;
             d[q].mu[k] = s->mu[k ^ s->cur].p;
+            d[q].tmap[k] = (unsigned char *)s->tmap[k ^ s->cur].p;
         }
         d[q].st = (DevState *)s->state.p;
         d[q].tab = (PlaneT<R> *)s->tab.p;
@@ -925,7 +956,10 @@ static int batch_step_direct(pf_batch *b, int n)
                                                b->parity, b->ctas, b->post_blocks, b->stream);
         if (e != cudaSuccess) return cuda_status(e);
         b->parity ^= 1;
-        for (pf_sim *s : b->sims) s->cur = 1 - s->cur;
+        for (pf_sim *s : b->sims) {
+            s->cur = 1 - s->cur;
+            s->tmap_ok[s->cur] = true;  // written by the fused tiles and the window fill
+        }
     }
     return PF_OK;
 }
@@ -939,6 +973,14 @@ static int batch_step(pf_batch *b, int n)
     }
     for (size_t q = 0; q < b->sims.size(); q++)
         if (b->sims[q]->cur != (b->cur0[q] ^ b->parity)) return PF_E_INVAL;  // stepped on its own
+    for (pf_sim *s : b->sims)
+        if (!s->tmap_ok[s->cur]) {  // fields written since its last fused step: rebuild its liquid map
+            const KParams<R> kp = make_kparams<R>(s);
+            cudaError_t e = launch_classify<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p,
+                                               (unsigned char *)s->tmap[s->cur].p, b->stream);
+            if (e != cudaSuccess) return cuda_status(e);
+            s->tmap_ok[s->cur] = true;
+        }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(b->stream, &cs) != cudaSuccess) {
         cudaGetLastError();
@@ -1114,6 +1156,7 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
         for (int q = 0; q < n && x == cudaSuccess; q++) {
             pf_sim *s = b->sims[q];
             s->cur = cur[q];
+            s->tmap_ok[0] = s->tmap_ok[1] = false;
             x = cudaMemcpyAsync(s->phi[s->cur].p, snap[q].p, s->phi[0].bytes, cudaMemcpyDeviceToDevice, b->stream);
             if (x == cudaSuccess)
                 x = cudaMemcpyAsync(s->mu[s->cur].p, (char *)snap[q].p + s->phi[0].bytes, s->mu[0].bytes,
@@ -1197,7 +1240,8 @@ size_t footprint_of(int nx, int ny, int nz)
 {
     const size_t n = (size_t)nx * ny * nz;
     const Geometry g = make_geometry(nx, ny, nz, 0);
-    return 2 * n * (16 + 8) + (size_t)2 * nz * 64 + (size_t)g.nparts() * sizeof(Partial) + (size_t)nz * 64 + 4096;
+    return 2 * n * (16 + 8) + (size_t)2 * nz * 64 + (size_t)g.nparts() * sizeof(Partial) + (size_t)nz * 64 +
+           (size_t)2 * nz * g.gx * g.gy + 4096;
 }
 }  // namespace
 

@@ -45,6 +45,7 @@ struct KParams {
     int nx, ny, nz;
     int zchunk;  // planes per CTA along z
     int window;  // 1: moving window enabled
+    int tgx, tgy;  // tile grid of the fused step (liquid map layout)
     int pad_;
     R dx, inv_dx, inv_2dx, inv_4dx;
     R eps, inv_eps;
@@ -70,6 +71,7 @@ template <typename R>
 struct BatchDomain {
     KParams<R> kp;
     void *phi[2], *mu[2];
+    unsigned char *tmap[2];  // liquid maps of the two field buffers
     DevState *st;
     PlaneT<R> *tab;
     Partial *parts;
@@ -104,10 +106,18 @@ template <typename R>
 cudaError_t launch_mu_sweep(const KParams<R> &kp, const Geometry &g, const void *phi_old, const void *phi_new,
                             const void *mu, void *mu_out, const DevState *st, const PlaneT<R> *tab,
                             Partial *parts, cudaStream_t s);
+// tmap_in / tmap_out: the liquid maps (one byte per storage plane and tile of the fused grid:
+// 1 = every cell of the tile in that plane is exactly pure liquid) of the source and the new
+// fields; nullptr disables the lean path.
 template <typename R>
 cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const void *phi, const void *mu,
                               void *phi_out, void *mu_out, const DevState *st, const PlaneT<R> *tab, Partial *parts,
-                              cudaStream_t s);
+                              cudaStream_t s, const unsigned char *tmap_in = nullptr,
+                              unsigned char *tmap_out = nullptr);
+// liquid map of a field (for states not produced by a fused step)
+template <typename R>
+cudaError_t launch_classify(const KParams<R> &kp, const DevState *st, const void *phi, unsigned char *tmap,
+                            cudaStream_t s);
 template <typename R>
 cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s);
 // Batched fused step of ndoms domains: counter reset, persistent kernel (ctas CTAs) over the
@@ -119,7 +129,8 @@ template <typename R>
 int fused_ctas_per_sm();
 template <typename R>
 cudaError_t launch_post(const KParams<R> &kp, const DevState *st, void *phi, void *mu, PlaneT<R> *tab,
-                        cudaStream_t s, void *phi_lo = nullptr, void *mu_lo = nullptr);
+                        cudaStream_t s, void *phi_lo = nullptr, void *mu_lo = nullptr,
+                        unsigned char *tmap = nullptr);
 template <typename R>
 cudaError_t launch_init(const KParams<R> &kp, void *phi, void *mu, const double *seeds, int n_grains, int H,
                         cudaStream_t s);

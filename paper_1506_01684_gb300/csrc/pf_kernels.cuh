@@ -14,6 +14,7 @@
 // staggered-value buffering of Section 3.3).
 #pragma once
 
+#include <climits>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -114,6 +115,22 @@ __device__ __forceinline__ bool onehot(const Ph<R> &a)
 {
     return code_of(a) < 4;
 }
+// phase code with a 4-instruction exact test for pure liquid first (bit patterns 0, 0, 0, 1.0f); a
+// cell holding -0.0 fails the bit test and gets its code from the full test instead
+__device__ __forceinline__ int code_fast(const Ph<float> &a)
+{
+    const unsigned u0 = __float_as_uint(a.v[0]), u1 = __float_as_uint(a.v[1]), u2 = __float_as_uint(a.v[2]);
+    if ((u0 | u1 | u2) == 0u && __float_as_uint(a.v[3]) == 0x3F800000u) return 3;
+    return code_of(a);
+}
+__device__ __forceinline__ int code_fast(const Ph<double> &a)
+{
+    const unsigned long long u0 = __double_as_longlong(a.v[0]), u1 = __double_as_longlong(a.v[1]),
+                             u2 = __double_as_longlong(a.v[2]);
+    if ((u0 | u1 | u2) == 0ull && __double_as_longlong(a.v[3]) == 0x3FF0000000000000ll) return 3;
+    return code_of(a);
+}
+
 // c-th entry of a 4-vector held in kernel parameters, without dynamic indexing
 template <typename R>
 __device__ __forceinline__ R pick4(const R (&v)[4], int c)
@@ -1064,12 +1081,52 @@ __device__ __forceinline__ Mu<R> mu_cell_coded(const KParams<R> &kp, const Plane
 
 // One CTA's work of the fused step: tile (bx, by) of x-y columns, z chunk bz.  Shared by the
 // single-domain kernel (tile = block index) and the batched persistent kernel (tile = work item).
+// Fluxes and mu^{n+1} of a pure-liquid cell whose neighbourhood is pure liquid in phi^n and
+// phi^{n+1}: constant mobility, no anti-trapping current, h = phi -- the short forms of
+// face_mu_coded and mu_cell_coded for equal codes, kept in one place so that every path that
+// takes them evaluates the same expressions.
+template <typename R>
+__device__ __forceinline__ Mu<R> quiet_zflux(const KParams<R> &kp, const Mu<R> &a, const Mu<R> &b)
+{
+    Mu<R> v;
+    v.v[0] = kp.DinvA[3] * (b.v[0] - a.v[0]) * kp.inv_dx;
+    v.v[1] = kp.DinvA[3] * (b.v[1] - a.v[1]) * kp.inv_dx;
+    return v;
+}
+template <typename R>
+__device__ __forceinline__ Mu<R> quiet_mu_cell(const KParams<R> &kp, const PlaneT<R> *__restrict__ tc, const Mu<R> &mP,
+                                               const Mu<R> &mxm, const Mu<R> &mxp, const Mu<R> &mym,
+                                               const Mu<R> &myp, const Mu<R> &Vz_lo, const Mu<R> &Vz_hi)
+{
+    const R Mliq = kp.DinvA[3];
+    Mu<R> vxm, vxp, vym, vyp;
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        vxm.v[c] = Mliq * (mP.v[c] - mxm.v[c]) * kp.inv_dx;
+        vxp.v[c] = Mliq * (mxp.v[c] - mP.v[c]) * kp.inv_dx;
+        vym.v[c] = Mliq * (mP.v[c] - mym.v[c]) * kp.inv_dx;
+        vyp.v[c] = Mliq * (myp.v[c] - mP.v[c]) * kp.inv_dx;
+    }
+    R div0 = (vxp.v[0] - vxm.v[0]) * kp.inv_dx;
+    R div1 = (vxp.v[1] - vxm.v[1]) * kp.inv_dx;
+    div0 = div0 + (vyp.v[0] - vym.v[0]) * kp.inv_dx;
+    div1 = div1 + (vyp.v[1] - vym.v[1]) * kp.inv_dx;
+    div0 = div0 + (Vz_hi.v[0] - Vz_lo.v[0]) * kp.inv_dx;
+    div1 = div1 + (Vz_hi.v[1] - Vz_lo.v[1]) * kp.inv_dx;
+    Ph<R> liquid;
+    liquid.v[0] = liquid.v[1] = liquid.v[2] = R(0);
+    liquid.v[3] = R(1);
+    return mu_cell_coded(kp, tc, 3, 3, liquid, liquid, mP, div0, div1);
+}
+
 template <typename R, int TX, int TY>
 __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__restrict__ phi,
                                            const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
                                            Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st,
                                            const PlaneT<R> *__restrict__ tab, Partial *__restrict__ part, int bx,
-                                           int by, int bz, unsigned char *__restrict__ smem_raw)
+                                           int by, int bz, unsigned char *__restrict__ smem_raw,
+                                           const unsigned char *__restrict__ tmap_in,
+                                           unsigned char *__restrict__ tmap_out)
 {
     constexpr int NT = TX * TY;
     constexpr int SX = TX + 2, SY = TY + 2, SN = SX * SY, NR = SN - NT;  // tile + 1-ring
@@ -1089,19 +1146,165 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
     unsigned char *cO = reinterpret_cast<unsigned char *>(sFz + 2 * SN);  // [4][SN2]
     unsigned char *cN = cO + 4 * SN2;                                      // [4][SN]
     __shared__ double red[NT / 32][2];
+    __shared__ int kred[NT / 32][2];
 
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int i0 = bx * TX, j0 = by * TY;
     const bool valid = i0 + tx < nx && j0 + ty < ny;
-    const int z0 = bz * kp.zchunk;
-    const int z1 = min(z0 + kp.zchunk, nz);
+    int z0 = bz * kp.zchunk;  // narrowed to the planes of the general path below
+    int z1 = min(z0 + kp.zchunk, nz);
     const int zbase = st->zbase;
     const size_t plane = (size_t)nx * ny;
     const int col_own = wrapi(j0 + ty, ny) * nx + wrapi(i0 + tx, nx);
     const int t1 = (ty + 1) * SX + (tx + 1);   // own cell, 1-ring layout
     const int t2 = (ty + 2) * SX2 + (tx + 2);  // own cell, 2-ring layout
+    const int ntl = kp.tgx * kp.tgy, tile = by * kp.tgx + bx;
+    auto splane = [&](int k) {  // storage plane of logical plane k (zero-gradient mirror first)
+        const int kc = k < 0 ? 0 : (k >= nz ? nz - 1 : k);
+        const int sp = kc + zbase;
+        return sp >= nz ? sp - nz : sp;
+    };
+
+    // FP64 per-CTA partials (fixed order: lanes by a shuffle tree, then warps in order)
+    auto epilogue = [&](double liq_def, bool bad) {
+        double badv = bad ? 1.0 : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            liq_def += __shfl_down_sync(0xffffffffu, liq_def, o);
+            badv += __shfl_down_sync(0xffffffffu, badv, o);
+        }
+        const int w = tid >> 5, lane = tid & 31;
+        if (lane == 0) {
+            red[w][0] = liq_def;
+            red[w][1] = badv;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int q = 0; q < NT / 32; q++) {
+                a += red[q][0];
+                b += red[q][1];
+            }
+            part->liq_deficit = a;
+            part->nonfinite = b;
+        }
+    };
+
+    // ---- lean segments.  Plane q of the chunk is lean when phi^n is pure liquid on the tile's
+    // 2-ring region over the planes q-2 .. q+2 (read from the liquid map of the source field):
+    // then phi^{n+1}(q) = phi^n(q) and every mu face of the plane takes the quiet form, so the
+    // plane needs no shared memory and no barrier.  With kmin / kmax the lowest / highest plane
+    // of z0-2 .. z1+1 that is not pure liquid, the lean planes are [z0, kmin-2) and
+    // [kmax+3, z1); the planes between run the general path below.
+    bool bad = false;
+    if (tmap_in) {
+        // tiles that hold the 2-ring region: own, and those of the columns i0-2, i0-1, i0+w, i0+w+1
+        // (rows alike) -- with a narrow last tile these can lie two tiles away
+        const int w = min(TX, nx - i0), hgt = min(TY, ny - j0);
+        const int xa = wrapi(i0 - 2, nx) / TX, xb = wrapi(i0 - 1, nx) / TX, xc = wrapi(i0 + w, nx) / TX,
+                  xd = wrapi(i0 + w + 1, nx) / TX;
+        const int ya = wrapi(j0 - 2, ny) / TY, yb = wrapi(j0 - 1, ny) / TY, yc = wrapi(j0 + hgt, ny) / TY,
+                  yd = wrapi(j0 + hgt + 1, ny) / TY;
+        // one entry per distinct tile: a candidate is skipped when an earlier one names the same tile
+        const bool ux[5] = {true, xa != bx, xb != bx && xb != xa, xc != bx && xc != xa && xc != xb,
+                            xd != bx && xd != xa && xd != xb && xd != xc};
+        const bool uy[5] = {true, ya != by, yb != by && yb != ya, yc != by && yc != ya && yc != yb,
+                            yd != by && yd != ya && yd != yb && yd != yc};
+        int kmin = INT_MAX, kmax = INT_MIN;
+        for (int k = z0 - 2 + tid; k < z1 + 2; k += NT) {
+            const unsigned char *m = tmap_in + (size_t)splane(k) * ntl;
+            bool ok = true;
+#pragma unroll
+            for (int r = 0; r < 5; r++) {
+                const int yy = r == 0 ? by : (r == 1 ? ya : (r == 2 ? yb : (r == 3 ? yc : yd)));
+#pragma unroll
+                for (int c = 0; c < 5; c++) {
+                    const int xx = c == 0 ? bx : (c == 1 ? xa : (c == 2 ? xb : (c == 3 ? xc : xd)));
+                    if (uy[r] && ux[c]) ok = ok & (m[yy * kp.tgx + xx] == 1);
+                }
+            }
+            if (!ok) {
+                kmin = min(kmin, k);
+                kmax = max(kmax, k);
+            }
+        }
+        kmin = __reduce_min_sync(0xffffffffu, kmin);
+        kmax = __reduce_max_sync(0xffffffffu, kmax);
+        if ((tid & 31) == 0) {
+            kred[tid >> 5][0] = kmin;
+            kred[tid >> 5][1] = kmax;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NT / 32; q++) {
+            kmin = min(kmin, kred[q][0]);
+            kmax = max(kmax, kred[q][1]);
+        }
+        const int lo_end = kmin == INT_MAX ? z1 : max(z0, min(z1, kmin - 2));
+        const int hi_beg = kmin == INT_MAX ? z1 : min(z1, max(lo_end, kmax + 3));
+
+        const int i = i0 + tx, j = j0 + ty;
+        const int cxm = wrapi(j, ny) * nx + wrapi(i - 1, nx), cxp = wrapi(j, ny) * nx + wrapi(i + 1, nx);
+        const int cym = wrapi(j - 1, ny) * nx + wrapi(i, nx), cyp = wrapi(j + 1, ny) * nx + wrapi(i, nx);
+        // one lean segment [qa, qb).  Register slots hold LD planes in flight (phi, mu and its four
+        // in-plane neighbours); plane q is computed from slot q mod LD, whose loads for plane q+LD
+        // are issued right after.  Loads past the segment read clamped planes and are not used.
+        auto lean = [&](int qa, int qb) {
+            constexpr int LD = 4;
+            Ph<R> pv[LD];
+            Mu<R> mo[LD], mxm[LD], mxp[LD], mym[LD], myp[LD];
+            auto load = [&](int u, int k) {
+                const size_t o = (size_t)splane(k) * plane;
+                pv[u] = ldg_ph(phi + o + col_own);
+                mo[u] = ldg_mu(mu + o + col_own);
+                mxm[u] = ldg_mu(mu + o + cxm);
+                mxp[u] = ldg_mu(mu + o + cxp);
+                mym[u] = ldg_mu(mu + o + cym);
+                myp[u] = ldg_mu(mu + o + cyp);
+            };
+#pragma unroll
+            for (int u = 0; u < LD; u++) load(u, qa + u);
+            Mu<R> Vz_lo;
+            Vz_lo.v[0] = Vz_lo.v[1] = R(0);
+            if (qa > 0) Vz_lo = quiet_zflux(kp, ldg_mu(mu + (size_t)splane(qa - 1) * plane + col_own), mo[0]);
+            for (int q0 = qa; q0 < qb; q0 += LD) {
+#pragma unroll
+                for (int u = 0; u < LD; u++) {
+                    const int q = q0 + u;
+                    if (q < qb) {
+                        // mu of plane q+1: the next slot (for u = LD-1 the slot reloaded at u = 0)
+                        const Mu<R> m_next = u + 1 < LD ? mo[u + 1] : mo[0];
+                        Mu<R> Vz_hi;
+                        Vz_hi.v[0] = Vz_hi.v[1] = R(0);
+                        if (q < nz - 1) Vz_hi = quiet_zflux(kp, mo[u], m_next);
+                        const Mu<R> out =
+                            quiet_mu_cell(kp, tab + q, mo[u], mxm[u], mxp[u], mym[u], myp[u], Vz_lo, Vz_hi);
+                        const size_t o = (size_t)splane(q) * plane;
+                        if (valid) {
+                            st_ph(phi_out + o + col_own, pv[u]);
+                            st_mu(mu_out + o + col_own, out);
+                            bad = bad | !isfinite(out.v[0] + out.v[1]);
+                        }
+                        Vz_lo = Vz_hi;
+                        if (q + LD <= qb) load(u, q + LD);
+                    }
+                }
+            }
+            if (tmap_out)
+                for (int q = qa + tid; q < qb; q += NT) tmap_out[(size_t)splane(q) * ntl + tile] = 1;
+        };
+        if (lo_end > z0) lean(z0, lo_end);
+        if (z1 > hi_beg) lean(hi_beg, z1);
+        // the general path runs on the planes in between
+        z0 = lo_end;
+        z1 = hi_beg;
+        if (z0 >= z1) {
+            epilogue(0.0, bad);
+            return;
+        }
+    }
 
     auto mod3 = [](int k) { return k & 3; };  // ring slot of plane k (4 slots; k >= -2)
 
@@ -1128,8 +1331,20 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
 
     Ph<R> pfO0, pfO1;
     Mu<R> pfM0, pfM1;
+    // storage offset of logical plane k: planes inside the domain follow each other in the ring,
+    // so the offset of k+1 is the offset of k plus one plane (modulo the ring)
+    const size_t ring = (size_t)nz * plane;
+    auto next_off = [&](int k, size_t off_k) -> size_t {
+        if (k < 0 || k >= nz - 1) return plane_off(k + 1, nz, zbase, plane);
+        const size_t o = off_k + plane;
+        return o >= ring ? o - ring : o;
+    };
+    int pk = -1000;  // plane whose offset pko holds
+    size_t pko = 0;
     auto prefetch = [&](int k) {
-        const size_t b = plane_off(k, nz, zbase, plane);
+        const size_t b = (k == pk + 1) ? next_off(pk, pko) : plane_off(k, nz, zbase, plane);
+        pk = k;
+        pko = b;
         pfO0 = ldg_ph(phi + b + colO0);
         pfM0 = ldg_mu(mu + b + colM0);
         if (hasO1) pfO1 = ldg_ph(phi + b + colO1);
@@ -1139,13 +1354,13 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
     // phi^n cells of the plane are pure liquid (reduced over the CTA by the caller's barrier)
     auto commit = [&](int k) -> bool {
         const int so = mod3(k);
-        const int c0 = code_of(pfO0);
+        const int c0 = code_fast(pfO0);
         sO[so * SN2 + tid] = pfO0;
         cO[so * SN2 + tid] = (unsigned char)c0;
         sM[so * SN + tid] = pfM0;
         bool liq = c0 == 3;
         if (hasO1) {
-            const int c1 = code_of(pfO1);
+            const int c1 = code_fast(pfO1);
             sO[so * SN2 + tid + NT] = pfO1;
             cO[so * SN2 + tid + NT] = (unsigned char)c1;
             liq = liq & (c1 == 3);
@@ -1195,6 +1410,7 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
     auto Fz = [&](int q, int s) -> Ph<R> & { return sFz[(q & 1) * SN + o1[s]]; };
     // phi^{n+1}(q) for the thread's cells; `quiet`: the planes q-1..q+1 of phi^n are pure liquid on
     // the 2-ring region, so phi^{n+1} = phi^n there
+    bool own_liq = true;  // the thread's tile cell of the last phi^{n+1} plane is pure liquid (or absent)
     auto phi_new_plane = [&](int q, bool quiet) {
         const Ph<R> *Om = sO + mod3(q - 1) * SN2, *Oq = sO + mod3(q) * SN2, *Op = sO + mod3(q + 1) * SN2;
         const unsigned char *Cm = cO + mod3(q - 1) * SN2, *Cq = cO + mod3(q) * SN2, *Cp = cO + mod3(q + 1) * SN2;
@@ -1225,6 +1441,7 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
                     }
                 }
             }
+            if (s == 0) own_liq = !valid || cout == 3;
             if (act) {
                 Nq[o1[s]] = out;
                 CNq[o1[s]] = (unsigned char)cout;
@@ -1274,7 +1491,6 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
     };
     // quiet (pure liquid) planes: constant mobility, no anti-trapping current -- the same
     // expressions the coded short form evaluates there
-    const R Mliq = kp.DinvA[3];
     auto mu_faces = [&](int q, bool) {
         sVx[ty * (TX + 1) + tx] = mu_xface(q, t1 - 1, t2 - 1);
         sVy[ty * TX + tx] = mu_yface(q, t1 - SX, t2 - SX2);
@@ -1287,15 +1503,11 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
             v.v[0] = v.v[1] = R(0);
             return v;
         }
-        const Mu<R> a = sM[mod3(q) * SN + t1], b = sM[mod3(q + 1) * SN + t1];
-        v.v[0] = Mliq * (b.v[0] - a.v[0]) * kp.inv_dx;
-        v.v[1] = Mliq * (b.v[1] - a.v[1]) * kp.inv_dx;
-        return v;
+        return quiet_zflux(kp, sM[mod3(q) * SN + t1], sM[mod3(q + 1) * SN + t1]);
     };
 
     double liq_def = 0.0;
     int solid_cells = 0;
-    bool bad = false;
     unsigned hist = 0;  // bit i: phi^n plane (newest - i) is pure liquid on the 2-ring region
 
     // ---- prologue: phi^{n+1} on planes z0-1 and z0, the z flux below z0 ----
@@ -1324,7 +1536,11 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
     if (has_ring) Fz(z0, 1) = zface_phi(z0, 1);
     __syncthreads();
     phi_new_plane(z0, quiet);
-    __syncthreads();
+    {
+        // the barrier also gives the liquid-map entry of phi^{n+1}(z0)
+        const int liq_z0 = __syncthreads_and(own_liq);
+        if (tmap_out && tid == 0) tmap_out[(size_t)splane(z0) * ntl + tile] = liq_z0 ? 1 : 0;
+    }
     if (z0 == 0) {
         copy_plane(-1, 0);  // the mirror plane below the domain
         __syncthreads();
@@ -1363,27 +1579,13 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
             // S3+S4 of a pure-liquid plane: the flux of a face is one subtraction and two products,
             // so each cell evaluates its four in-plane faces from mu^n directly (both cells of a face
             // evaluate the same expression: the result is that of the staged faces) -- no barrier
+            // (phi^{n+1}(q+1) = phi^n(q+1) is pure liquid on the tile: its liquid-map entry is 1)
+            if (tmap_out && tid == 0 && q + 1 < z1) tmap_out[(size_t)splane(q + 1) * ntl + tile] = 1;
             const Mu<R> *Mq = sM + mod3(q) * SN;
-            const Mu<R> mP = Mq[t1], mxm = Mq[t1 - 1], mxp = Mq[t1 + 1], mym = Mq[t1 - SX], myp = Mq[t1 + SX];
+            const Mu<R> mP = Mq[t1];
             const Mu<R> Vz_hi = mu_zflux_quiet(q);
-            Mu<R> vxm, vxp, vym, vyp;
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                vxm.v[c] = Mliq * (mP.v[c] - mxm.v[c]) * kp.inv_dx;
-                vxp.v[c] = Mliq * (mxp.v[c] - mP.v[c]) * kp.inv_dx;
-                vym.v[c] = Mliq * (mP.v[c] - mym.v[c]) * kp.inv_dx;
-                vyp.v[c] = Mliq * (myp.v[c] - mP.v[c]) * kp.inv_dx;
-            }
-            R div0 = (vxp.v[0] - vxm.v[0]) * kp.inv_dx;
-            R div1 = (vxp.v[1] - vxm.v[1]) * kp.inv_dx;
-            div0 = div0 + (vyp.v[0] - vym.v[0]) * kp.inv_dx;
-            div1 = div1 + (vyp.v[1] - vym.v[1]) * kp.inv_dx;
-            div0 = div0 + (Vz_hi.v[0] - Vz_lo.v[0]) * kp.inv_dx;
-            div1 = div1 + (Vz_hi.v[1] - Vz_lo.v[1]) * kp.inv_dx;
-            Ph<R> liquid;
-            liquid.v[0] = liquid.v[1] = liquid.v[2] = R(0);
-            liquid.v[3] = R(1);
-            const Mu<R> out = mu_cell_coded(kp, tab + q, 3, 3, liquid, liquid, mP, div0, div1);
+            const Mu<R> out = quiet_mu_cell(kp, tab + q, mP, Mq[t1 - 1], Mq[t1 + 1], Mq[t1 - SX], Mq[t1 + SX], Vz_lo,
+                                            Vz_hi);
             if (valid) {
                 st_mu(mu_out + plane_off(q, nz, zbase, plane) + col_own, out);
                 bad = bad | !isfinite(out.v[0] + out.v[1]);
@@ -1391,7 +1593,12 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
             Vz_lo = Vz_hi;
             continue;
         }
-        __syncthreads();  // S3 reads phi^{n+1}(q+1) written by other threads in S2
+        {
+            // S3 reads phi^{n+1}(q+1) written by other threads in S2; the barrier also gives the
+            // liquid-map entry of that plane
+            const int liq_q1 = __syncthreads_and(phi_quiet || own_liq);
+            if (tmap_out && tid == 0 && q + 1 < z1) tmap_out[(size_t)splane(q + 1) * ntl + tile] = liq_q1 ? 1 : 0;
+        }
         // S3: mu face fluxes of plane q, the z flux (q | q+1)
         mu_faces(q, false);
         const Mu<R> Vz_hi = mu_zface(q);
@@ -1426,43 +1633,23 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
         Vz_lo = Vz_hi;
     }
 
-    // FP64 per-CTA partials (fixed order: lanes by a shuffle tree, then warps in order)
-    liq_def += (double)solid_cells;
-    double badv = bad ? 1.0 : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        liq_def += __shfl_down_sync(0xffffffffu, liq_def, o);
-        badv += __shfl_down_sync(0xffffffffu, badv, o);
-    }
-    const int w = tid >> 5, lane = tid & 31;
-    if (lane == 0) {
-        red[w][0] = liq_def;
-        red[w][1] = badv;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double a = 0.0, b = 0.0;
-        for (int q = 0; q < NT / 32; q++) {
-            a += red[q][0];
-            b += red[q][1];
-        }
-        part->liq_deficit = a;
-        part->nonfinite = b;
-    }
+    epilogue(liq_def + (double)solid_cells, bad);
 }
 
 template <typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) fused_step_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
+__global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) fused_step_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
                                                            const Mu<R> *__restrict__ mu,
                                                            Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out,
                                                            const DevState *__restrict__ st,
                                                            const PlaneT<R> *__restrict__ tab,
-                                                           Partial *__restrict__ partials)
+                                                           Partial *__restrict__ partials,
+                                                           const unsigned char *__restrict__ tmap_in,
+                                                           unsigned char *__restrict__ tmap_out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     fused_tile<R, TX, TY>(kp, phi, mu, phi_out, mu_out, st, tab, partials + bid, blockIdx.x, blockIdx.y, blockIdx.z,
-                          smem_raw);
+                          smem_raw, tmap_in, tmap_out);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1472,7 +1659,7 @@ __global__ void __launch_bounds__(TX *TY) fused_step_kernel(const KParams<R> kp,
 // same tile body as the single-domain kernel.
 // ---------------------------------------------------------------------------------------
 template <typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) batched_fused_kernel(const BatchDomain<R> *__restrict__ doms,
+__global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) batched_fused_kernel(const BatchDomain<R> *__restrict__ doms,
                                                               const BatchItem *__restrict__ items, int nitems,
                                                               unsigned *__restrict__ counter, int parity)
 {
@@ -1496,7 +1683,8 @@ __global__ void __launch_bounds__(TX *TY) batched_fused_kernel(const BatchDomain
         const int a = parity, b = parity ^ 1;
         Partial *part = d->parts + ((size_t)w.bz * d->gy + w.by) * d->gx + w.bx;
         fused_tile<R, TX, TY>(s_kp, (const Ph<R> *)d->phi[a], (const Mu<R> *)d->mu[a], (Ph<R> *)d->phi[b],
-                              (Mu<R> *)d->mu[b], d->st, d->tab, part, w.bx, w.by, w.bz, smem_raw);
+                              (Mu<R> *)d->mu[b], d->st, d->tab, part, w.bx, w.by, w.bz, smem_raw, d->tmap[a],
+                              d->tmap[b]);
     }
 }
 
@@ -1589,7 +1777,8 @@ template <typename R>
 __device__ __forceinline__ void post_body(const KParams<R> &kp, const DevState *__restrict__ st,
                                           Ph<R> *__restrict__ phi, Mu<R> *__restrict__ mu,
                                           PlaneT<R> *__restrict__ tab, Ph<R> *__restrict__ phi_lo,
-                                          Mu<R> *__restrict__ mu_lo, size_t tid, size_t nth)
+                                          Mu<R> *__restrict__ mu_lo, size_t tid, size_t nth,
+                                          unsigned char *__restrict__ tmap)
 {
     const double t = st->t, off = st->off;
     const int s = st->shift, zbase = st->zbase;
@@ -1599,6 +1788,15 @@ __device__ __forceinline__ void post_body(const KParams<R> &kp, const DevState *
             make_plane(kp, (double)e + off, t, tab + e);
         else
             make_plane(kp, ((double)(e - nz) + off) + 0.5, t, tab + e);
+    }
+    if (s > 0 && tmap) {
+        // the entering planes are pure liquid, and so is their liquid-map entry
+        const size_t ntl = (size_t)kp.tgx * kp.tgy;
+        for (size_t q = tid; q < (size_t)s * ntl; q += nth) {
+            int sp = nz - s + (int)(q / ntl) + zbase;
+            if (sp >= nz) sp -= nz;
+            tmap[(size_t)sp * ntl + q % ntl] = 1;
+        }
     }
     if (s > 0) {
         const size_t plane = (size_t)kp.nx * kp.ny;
@@ -1626,10 +1824,10 @@ template <typename R>
 __global__ void __launch_bounds__(256) post_kernel(const KParams<R> kp, const DevState *__restrict__ st,
                                                   Ph<R> *__restrict__ phi, Mu<R> *__restrict__ mu,
                                                   PlaneT<R> *__restrict__ tab, Ph<R> *__restrict__ phi_lo,
-                                                  Mu<R> *__restrict__ mu_lo)
+                                                  Mu<R> *__restrict__ mu_lo, unsigned char *__restrict__ tmap)
 {
     post_body(kp, st, phi, mu, tab, phi_lo, mu_lo, (size_t)blockIdx.x * blockDim.x + threadIdx.x,
-              (size_t)gridDim.x * blockDim.x);
+              (size_t)gridDim.x * blockDim.x, tmap);
 }
 
 // grid (blocks per domain, domains); the new source fields of each domain are phi/mu[parity ^ 1]
@@ -1638,7 +1836,8 @@ __global__ void __launch_bounds__(256) batched_post_kernel(const BatchDomain<R> 
 {
     const BatchDomain<R> *d = doms + blockIdx.y;
     post_body(d->kp, d->st, (Ph<R> *)d->phi[parity ^ 1], (Mu<R> *)d->mu[parity ^ 1], d->tab, (Ph<R> *)nullptr,
-              (Mu<R> *)nullptr, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+              (Mu<R> *)nullptr, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x,
+              d->tmap[parity ^ 1]);
 }
 
 // Voronoi nuclei (reading R13): cells with k < H take the phase of the nearest seed
@@ -1811,6 +2010,27 @@ __global__ void __launch_bounds__(256) unpack_kernel(const KParams<R> kp, const 
     }
 }
 
+// Liquid map of a field: one byte per (storage plane, fused-step tile), 1 when every cell of the
+// tile in that plane is exactly pure liquid.  Grid (tiles, groups of 32 planes).
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) classify_kernel(const KParams<R> kp, const DevState *__restrict__ st,
+                                                         const Ph<R> *__restrict__ phi,
+                                                         unsigned char *__restrict__ tmap)
+{
+    const int tile = blockIdx.x, bx = tile % kp.tgx, by = tile / kp.tgx;
+    const int i = bx * TX + (int)threadIdx.x % TX, j = by * TY + (int)threadIdx.x / TX;
+    const bool valid = i < kp.nx && j < kp.ny;
+    const size_t plane = (size_t)kp.nx * kp.ny;
+    const int zbase = st->zbase;
+    const int k0 = blockIdx.y * 32, k1 = min(k0 + 32, kp.nz);
+    for (int k = k0; k < k1; k++) {
+        const size_t off = plane_off(k, kp.nz, zbase, plane);
+        const bool liq = !valid || code_of(ldg_ph(phi + off + (size_t)j * kp.nx + i)) == 3;
+        const int all = __syncthreads_and(liq);
+        if (threadIdx.x == 0) tmap[off / plane * kp.tgx * kp.tgy + tile] = all ? 1 : 0;
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------
@@ -1885,10 +2105,21 @@ static size_t fused_smem_bytes()
 }
 
 template <typename R>
+cudaError_t launch_classify(const KParams<R> &kp, const DevState *st, const void *phi, unsigned char *tmap,
+                            cudaStream_t s)
+{
+    if (kp.tgx * kTX < kp.nx || kp.tgy * kTY < kp.ny) return cudaErrorInvalidValue;
+    dim3 grid(kp.tgx * kp.tgy, (kp.nz + 31) / 32);
+    classify_kernel<R, kTX, kTY><<<grid, kTX * kTY, 0, s>>>(kp, st, (const Ph<R> *)phi, tmap);
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const void *phi, const void *mu,
                               void *phi_out, void *mu_out, const DevState *st, const PlaneT<R> *tab, Partial *parts,
-                              cudaStream_t s)
+                              cudaStream_t s, const unsigned char *tmap_in, unsigned char *tmap_out)
 {
+    if ((tmap_in || tmap_out) && (kp.tgx != g.gx || kp.tgy != g.gy)) return cudaErrorInvalidValue;
     static bool attr = false;
     const size_t sm = fused_smem_bytes<R>();
     if (!attr) {
@@ -1899,7 +2130,8 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
     }
     dim3 grid(g.gx, g.gy, g.gz);
     fused_step_kernel<R, kTX, kTY><<<grid, kTX * kTY, sm, s>>>(kp, (const Ph<R> *)phi, (const Mu<R> *)mu,
-                                                               (Ph<R> *)phi_out, (Mu<R> *)mu_out, st, tab, parts);
+                                                               (Ph<R> *)phi_out, (Mu<R> *)mu_out, st, tab, parts,
+                                                               tmap_in, tmap_out);
     return cudaGetLastError();
 }
 
@@ -1986,12 +2218,12 @@ cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *p
 
 template <typename R>
 cudaError_t launch_post(const KParams<R> &kp, const DevState *st, void *phi, void *mu, PlaneT<R> *tab,
-                        cudaStream_t s, void *phi_lo, void *mu_lo)
+                        cudaStream_t s, void *phi_lo, void *mu_lo, unsigned char *tmap)
 {
     // enough threads to fill one full plane per thread-sweep when the window moves
     const size_t work = (size_t)kp.nx * kp.ny;
     post_kernel<R><<<grid1d(work > (size_t)2 * kp.nz ? work : (size_t)2 * kp.nz), 256, 0, s>>>(
-        kp, st, (Ph<R> *)phi, (Mu<R> *)mu, tab, (Ph<R> *)phi_lo, (Mu<R> *)mu_lo);
+        kp, st, (Ph<R> *)phi, (Mu<R> *)mu, tab, (Ph<R> *)phi_lo, (Mu<R> *)mu_lo, tmap);
     return cudaGetLastError();
 }
 
@@ -2041,13 +2273,15 @@ cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, v
                                             Partial *, cudaStream_t);                                            \
     template cudaError_t launch_fused_step<R>(const KParams<R> &, const Geometry &, const void *, const void *, \
                                               void *, void *, const DevState *, const PlaneT<R> *, Partial *,     \
-                                              cudaStream_t);                                                      \
+                                              cudaStream_t, const unsigned char *, unsigned char *);              \
+    template cudaError_t launch_classify<R>(const KParams<R> &, const DevState *, const void *, unsigned char *, \
+                                            cudaStream_t);                                                       \
     template cudaError_t launch_batched_step<R>(const BatchDomain<R> *, int, const BatchItem *, int, unsigned *, \
                                                 int, int, int, cudaStream_t);                                    \
     template int fused_ctas_per_sm<R>();                                                                         \
     template cudaError_t launch_finalize<R>(const KParams<R> &, DevState *, const Partial *, int, cudaStream_t); \
     template cudaError_t launch_post<R>(const KParams<R> &, const DevState *, void *, void *, PlaneT<R> *,       \
-                                        cudaStream_t, void *, void *);                                           \
+                                        cudaStream_t, void *, void *, unsigned char *);                          \
     template cudaError_t launch_init<R>(const KParams<R> &, void *, void *, const double *, int, int,            \
                                         cudaStream_t);                                                           \
     template cudaError_t launch_reduce<R>(const KParams<R> &, const DevState *, const void *, const void *,      \

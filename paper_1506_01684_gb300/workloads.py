@@ -16,8 +16,11 @@ Symmetric parameter set (Section 2 model, readings R1/R3/R12):
     (1/3, 1/3); TE = 1; s = 1 for solids, 0 for the liquid; kT = 0 for solids,
     (0.1, 0.1) for the liquid; D = 1 in the liquid, 0 in the solids.
   * frozen gradient T = T0 + G (z - v t) with G = 1e-3, v = 1e-2 and
-    T0 = TE - G H so that the eutectic isotherm starts at the top of the
-    H = 8 seed layers.
+    T0 = TE - G H - DT0: the top of the H = 8 seed layers starts DT0 = 0.15
+    below TE (the eutectic isotherm lies DT0/G = 150 cells above the seeds).
+    With DT0 = 0 the seeds, thinner than the diffuse interface (about 10 cells
+    at eps = 4), melt back completely within about 2000 steps; at 0.15 they
+    survive and the front advances.
 """
 from __future__ import annotations
 
@@ -26,6 +29,7 @@ import copy
 import numpy as np
 
 SEED_LAYERS = 8
+INITIAL_UNDERCOOLING = 0.15
 
 
 def symmetric_params(G: float = 1e-3, v: float = 1e-2, n_grains: int = 12,
@@ -40,7 +44,7 @@ def symmetric_params(G: float = 1e-3, v: float = 1e-2, n_grains: int = 12,
         "kT": [[0.0, 0.0], [0.0, 0.0], [0.0, 0.0], [0.1, 0.1]],
         "s": [1.0, 1.0, 1.0, 0.0],
         "D": [0.0, 0.0, 0.0, 1.0],
-        "TE": TE, "T0": TE - G * H, "G": G, "v": v,
+        "TE": TE, "T0": TE - G * H - INITIAL_UNDERCOOLING, "G": G, "v": v,
         "seed_layers": H, "n_grains": n_grains,
         "window_trigger_z": window_trigger_z,
     }
@@ -138,12 +142,52 @@ def planar_front(nx: int, ny: int, nz: int, z0: float, width: float, solid: int 
     return phi
 
 
-def interface_block(n: int, seed: int = 0):
-    """Region micro-benchmarks of the paper's performance section (liquid, solid, interface)
-    at n^3: returns dict name -> (phi, mu) initial data or None when the library's own
-    initial condition (Voronoi) is used."""
+def _voronoi_labels(points, seeds, box):
+    """Index of the nearest seed for every point (periodic in x and y over box[:2], open in z;
+    ties to the lowest index), through scipy's k-d tree."""
+    from scipy.spatial import cKDTree
+
+    bx, by, bz = box
+    tree = cKDTree(seeds, boxsize=[bx, by, 4.0 * bz])
+    _, idx = tree.query(points, k=1)
+    return idx
+
+
+REGION_KINDS = ("liquid", "solid", "interface")
+
+
+def region_fields(kind: str, nx: int, ny: int, nz: int, seed: int = 0):
+    """Initial fields of the three block compositions of the paper's performance section
+    (Section 4: liquid, solid and interface blocks), shape (4, nz, ny, nx) and (2, nz, ny, nx):
+      * liquid: pure liquid, mu uniform in [-1e-3, 1e-3];
+      * solid: 3D Voronoi grains of the three solid phases, about 48 cells across (bulk
+        dominated), mu as above;
+      * interface: the solidification front crossing the block -- columnar grains (x-y Voronoi,
+        about 12 cells across, phases drawn uniformly from the three solids) below z = nz/2,
+        liquid above, mu as above.
+    Interfaces start sharp; a few steps give them their diffuse profile.  numpy PCG64 stream
+    seeded with ``seed``."""
     rng = np.random.default_rng(seed)
-    liquid_phi = np.zeros((4, n, n, n))
-    liquid_phi[3] = 1.0
-    liquid_mu = rng.uniform(-1e-3, 1e-3, size=(2, n, n, n))
-    return {"liquid": (liquid_phi, liquid_mu)}
+    mu = rng.uniform(-1e-3, 1e-3, size=(2, nz, ny, nx))
+    lab = np.full((nz, ny, nx), 3, dtype=np.int64)
+    if kind == "solid":
+        ng = max(4, int(nx * ny * nz / 48.0 ** 3))
+        seeds = rng.uniform(0, 1, size=(ng, 3)) * [nx, ny, nz]
+        phase = rng.integers(0, 3, size=ng)
+        k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        pts = np.stack([i.ravel() + 0.5, j.ravel() + 0.5, k.ravel() + 0.5], axis=1)
+        lab = phase[_voronoi_labels(pts, seeds, (nx, ny, nz))].reshape(nz, ny, nx)
+    elif kind == "interface":
+        ng = max(3, int(nx * ny / 12.0 ** 2))
+        seeds = np.concatenate([rng.uniform(0, 1, size=(ng, 2)) * [nx, ny], np.zeros((ng, 1))], axis=1)
+        phase = rng.integers(0, 3, size=ng)
+        j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+        pts = np.stack([i.ravel() + 0.5, j.ravel() + 0.5, np.zeros(i.size)], axis=1)
+        cols = phase[_voronoi_labels(pts, seeds, (nx, ny, 1))].reshape(ny, nx)
+        lab[: nz // 2] = cols[None]
+    elif kind != "liquid":
+        raise ValueError(kind)
+    phi = np.zeros((4, nz, ny, nx))
+    for a in range(4):
+        phi[a][lab == a] = 1.0
+    return phi, mu

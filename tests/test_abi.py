@@ -36,7 +36,7 @@ def test_host_only_entry_points():
     # calls that touch no device: defaults, error strings, argument checks
     p = pf.pf_default_params()
     assert p.version == pf.PF_PARAMS_VERSION and p.eps == 4.0 and p.gamma3[2] == 15.0
-    assert abs(p.T0 - (1.0 - 8e-3)) < 1e-15
+    assert abs(p.T0 - (1.0 - 8e-3 - 0.15)) < 1e-15
     assert pf.pf_strerror(pf.PF_E_UNSTABLE).startswith("non-finite")
     L = pf.lib()
     h = ctypes.c_void_p()

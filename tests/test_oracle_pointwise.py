@@ -190,8 +190,8 @@ def test_splitmix64_matches_published_vector():
 
 
 def test_default_dt_is_half_the_explicit_limit():
-    # 32x32x64, G = 1e-3, T0 = TE - 8 G: T_max = T0 + 63 G = 1.055, gamma_max = 1, D_max = 1
+    # 32x32x64, G = 1e-3, T0 = TE - 8 G - 0.15: T_max = T0 + 63 G = 0.905, gamma_max = 1, D_max = 1
     dt = oracle.default_dt(P, 64)
-    Tmax = 1.0 - 8e-3 + 63e-3
+    Tmax = 1.0 - 8e-3 - 0.15 + 63e-3
     assert dt == pytest.approx(0.5 * min(1.0 / (12 * Tmax), 1.0 / 6.0), rel=1e-15)
-    assert dt == pytest.approx(0.0395, abs=1e-4)
+    assert dt == pytest.approx(0.0460, abs=1e-4)
