@@ -38,14 +38,16 @@ SEED = 0
 WORKLOAD = "single domain 256x256x1024, 64 grains, window trigger z=512, symmetric parameter set"
 METRIC = "phi+mu step MLUP/s (FP32 stencil; FP64 GPU path and error reported beside it)"
 
-# algorithmic bytes per cell and launch (FP32): the mu-sweep reads phi^n, phi^{n+1} (16 B each)
-# and mu^n (8 B) and writes mu^{n+1} (8 B); the phi-sweep reads phi^n and mu^n and writes phi^{n+1}
-# and the fused step reads phi^n and mu^n and writes phi^{n+1} and mu^{n+1}
-BYTES_PER_CELL = {"mu_sweep": 48, "phi_sweep": 40, "fused_step": 48}
+# Algorithmic bytes per kernel and launch come from the library (pf_step_bytes): the mu-sweep
+# reads phi^n, phi^{n+1} (16 B each) and mu^n (8 B) and writes mu^{n+1} (8 B); the phi-sweep
+# reads phi^n and mu^n and writes phi^{n+1}.  The fused step's general planes move 48 B a cell
+# (phi^n, mu^n in, phi^{n+1}, mu^{n+1} out); its pure-liquid planes (the lean kernel) 16 B (mu^n
+# in, mu^{n+1} out; phi^{n+1} = e_l is stored only where the destination does not hold it
+# already) -- tallied by the kernels themselves.
 # DRAM bytes per cell per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of
 # the kernel as it is now, on 128x128x512 with the same workload recipe, scaled by cells (the capture
 # file and its command are in profiles/); remove an entry when its kernel changes
-TRAFFIC_BYTES_PER_CELL = {"fused_step": 44.72}  # profiles/fused_step_fp32_128x128x512.md
+TRAFFIC_BYTES_PER_CELL = {}
 
 
 def _env_int(name, default):
@@ -512,6 +514,11 @@ def main():
     clk = clocks.stop()
     prof = pf.pf_profile_read(sim.h)
     sim.sync()
+    # algorithmic bytes per kernel of the last timed step as the kernels tallied them (the front
+    # moves less than a plane over the timed steps, so every timed launch moves about the same bytes)
+    kbytes = sim.step_bytes()
+    step_bytes = sum(kbytes.values())
+    bytes_per_cell = {k: v / cells for k, v in kbytes.items()}
     ms_max = max_over_ranks(ms, dist, "cuda")
     value = whole_job_mlups(world, cells, args.steps, ms_max)
     launches = sum(n for _, n in prof.values())
@@ -522,17 +529,17 @@ def main():
     dom_ms = prof[dom][0] / max(prof[dom][1], 1)
     kern = {k: {"ms_avg": v[0] / max(v[1], 1), "launches": v[1], "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)}
             for k, v in prof.items()}
-    achieved = BYTES_PER_CELL.get(dom, 0) * cells / (dom_ms / 1e3) / 1e9
+    achieved = bytes_per_cell.get(dom, 0) * cells / (dom_ms / 1e3) / 1e9
     traffic = None
     if dom in TRAFFIC_BYTES_PER_CELL and NX * NY * NZ >= 8 << 20:
         traffic = TRAFFIC_BYTES_PER_CELL[dom] * cells
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
-            "bytes_per_cell": BYTES_PER_CELL.get(dom)}
+            "bytes_per_cell": bytes_per_cell.get(dom)}
     for k in kern:
-        if k in BYTES_PER_CELL:
-            kern[k]["gbs"] = BYTES_PER_CELL[k] * cells / (kern[k]["ms_avg"] / 1e3) / 1e9
-    design_bytes = 48 if "fused_step" in prof else 88
+        if k in bytes_per_cell:
+            kern[k]["gbs"] = bytes_per_cell[k] * cells / (kern[k]["ms_avg"] / 1e3) / 1e9
+    design_bytes = step_bytes / cells
     fused_bound = hbm * 1e9 / (48 * cells) * cells / 1e6  # MLUP/s at 48 B/cell (fused FP32 minimum)
     unfused_bound = hbm * 1e9 / (88 * cells) * cells / 1e6
 
@@ -608,7 +615,8 @@ def main():
         "roofline": roof,
         "kernels": kern,
         "bounds_mlups": {"fused_48B": fused_bound, "unfused_88B": unfused_bound,
-                         "this_design_bytes_per_cell": design_bytes},
+                         "this_design_bytes_per_cell": design_bytes,
+                         "this_design": hbm * 1e9 / design_bytes / 1e6 if design_bytes else None},
         "variant": "fused" if "fused_step" in prof else "unfused",
         "frac_of_unfused_bound": value / unfused_bound, "frac_of_fused_bound": value / fused_bound,
         "fp64": fp64, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,

@@ -144,6 +144,8 @@ int pf_stats(pf_sim *sim, double *t, double *window_offset, double solute[2], do
 /* Number of window shifts (planes moved) since pf_init.  Synchronising. */
 int pf_window_shifts(pf_sim *sim, int *planes);
 
+
+
 /* Kernel classes of the per-kernel timers. */
 enum {
     PF_K_PHI = 0,      /* phi-sweep (Eq. 1-2 and the projection) */
@@ -151,6 +153,7 @@ enum {
     PF_K_FINALIZE = 2, /* FP64 reduction of the partials, clock, window decision */
     PF_K_POST = 3,     /* plane-table rebuild and fill of planes entering the window */
     PF_K_FUSED = 4,    /* fused phi+mu step (both sweeps in one pass) */
+    PF_K_LEAN = 5,     /* the fused step's pure-liquid planes (Section 3.3 shortcuts), a kernel of their own */
     PF_K_COUNT = 8
 };
 
@@ -170,6 +173,20 @@ int pf_profile(pf_sim *sim, int enable);
 /* Device milliseconds and launch counts per kernel class (arrays of PF_K_COUNT) accumulated
  * since the last read; resets the accumulators.  Synchronising. */
 int pf_profile_read(pf_sim *sim, double ms[], int launches[]);
+
+/* Algorithmic HBM bytes per kernel class (array of PF_K_COUNT) of the last step pf_step ran on
+ * this simulation (batch steps excluded): the compulsory loads and stores of each kernel.
+ *   PF_K_PHI / PF_K_MU (two sweeps): 10 and 12 words a cell (18 and 16 with the compensated low
+ *     words), from the cell count;
+ *   PF_K_FUSED: 12 words a cell on the planes of the general path, as tallied by the kernel;
+ *   PF_K_LEAN: on the pure-liquid planes (the paper's shortcuts, Section 3.3) 4 words a cell --
+ *     mu^n in, mu^{n+1} out; phi^{n+1} = phi^n = e_l is known from the liquid map -- plus 4 words
+ *     where phi^{n+1} is stored because the destination buffer does not hold pure liquid there
+ *     already; tallied by the kernel (with the fused kernel alone these planes count under
+ *     PF_K_FUSED).
+ * All zero before the first step.  Synchronising (reads the per-CTA partials back); meant for
+ * measurement outside timed regions. */
+int pf_step_bytes(pf_sim *sim, double bytes[]);
 
 /*
  * Batched launch: many independent domains of uneven size stepped together.  Each step is one

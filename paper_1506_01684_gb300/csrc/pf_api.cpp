@@ -1,6 +1,8 @@
 // pf_api.cpp -- host runtime behind the C ABI of include/pf.h: device buffers, the per-step
 // launch sequence of Algorithm 1 (phi-sweep, mu-sweep, FP64 reductions, window), the
 // Voronoi seeds, and the field/diagnostic transfers.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>
@@ -104,6 +106,11 @@ struct pf_sim {
     // new field, rebuilt by the classify kernel where tmap_ok says the map is stale
     DevBuf tmap[2];
     bool tmap_ok[2] = {false, false};
+    // TMA tensor maps of the two mu buffers for the lean kernel (the fused step's pure-liquid
+    // planes); lean_ok when both could be encoded (FP32 rows must be 16-byte multiples: nx even)
+    CUtensorMap mu_map[2];
+    bool lean_ok = false;
+    int lean_nsub = 1;  // lean CTAs per z chunk of the fused grid
     DevBuf state;          // DevState
     DevBuf parts;          // Partial[geo.nparts()]
     DevBuf tab;            // PlaneT<R>[2 nz]
@@ -124,12 +131,49 @@ struct pf_sim {
     int graph_variant = -1;
     long long direct_steps = 0;
     bool use_graphs = true;
+    int last_nparts = 0;  // partial sums written by the last step's kernels
+    int last_kind = -1;   // 0: two sweeps, 1: fused kernel alone, 2: fused kernel + lean kernel
     size_t ncell() const { return (size_t)nx * ny * nz; }
     size_t wbytes() const { return p.precision == PF_FP64 ? 8 : 4; }
     bool comp() const { return p.precision == PF_FP32_COMP; }
     void *lo_phi(int b) const { return comp() ? philo[b].p : nullptr; }
     void *lo_mu(int b) const { return comp() ? mulo[b].p : nullptr; }
 };
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of one mu buffer for the lean kernel: 3D (2 nx words, ny rows, nz storage planes),
+// box of (TX + 4) cells x (TY + 2) rows x 1 plane, zero fill outside (the kernel copies the
+// periodic images there itself).  False when the layout does not allow it.
+static bool encode_mu_map(CUtensorMap *m, void *base, int nx, int ny, int nz, size_t w, int tx, int ty)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !base || ((uintptr_t)base & 15) || ((size_t)2 * nx * w) % 16 != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)2 * nx * w, (cuuint64_t)2 * nx * ny * w};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * (tx + 4)), (cuuint32_t)(ty + 2), 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = enc(m, w == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
+                           dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 namespace pf {
 Geometry make_geometry(int nx, int ny, int nz, int zchunk_hint)
@@ -310,6 +354,23 @@ static bool use_fused(const pf_sim *s)
     return s->p.precision == PF_FP32;  // AUTO: fused for FP32 (measured faster), the two sweeps for FP64
 }
 
+// The fused step trusts the liquid maps of both field buffers: the source's to find the
+// pure-liquid planes, the destination's (which describes the field two steps back) to skip the
+// phi stores of planes that stay pure liquid.  Rebuild whichever map is stale.
+template <typename R>
+static cudaError_t ensure_maps(pf_sim *s, cudaStream_t stream)
+{
+    const KParams<R> kp = make_kparams<R>(s);
+    for (int b = 0; b < 2; b++) {
+        if (s->tmap_ok[b]) continue;
+        cudaError_t e = launch_classify<R>(kp, (const DevState *)s->state.p, s->phi[b].p,
+                                           (unsigned char *)s->tmap[b].p, stream);
+        if (e != cudaSuccess) return e;
+        s->tmap_ok[b] = true;
+    }
+    return cudaSuccess;
+}
+
 template <typename R>
 static int do_step_direct(pf_sim *s, int n)
 {
@@ -319,21 +380,27 @@ static int do_step_direct(pf_sim *s, int n)
     DevState *st = (DevState *)s->state.p;
     PlaneT<R> *tab = (PlaneT<R> *)s->tab.p;
     Partial *parts = (Partial *)s->parts.p;
-    const int nparts = fused ? s->geo_fused.nparts() : s->geo.nparts();
+    const bool lean = fused && s->lean_ok;
+    const int np_fused = s->geo_fused.nparts();
+    const int nparts = fused ? np_fused * (lean ? 1 + s->lean_nsub : 1) : s->geo.nparts();
+    s->last_nparts = nparts;
+    s->last_kind = fused ? (lean ? 2 : 1) : 0;
     for (int q = 0; q < n; q++) {
         const int a = s->cur, b = 1 - s->cur;
         cudaError_t e;
         if (fused) {
-            e = cudaSuccess;
-            if (!s->tmap_ok[a]) {
-                e = launch_classify<R>(kp, st, s->phi[a].p, (unsigned char *)s->tmap[a].p, s->stream);
-                s->tmap_ok[a] = e == cudaSuccess;
-            }
+            e = ensure_maps<R>(s, s->stream);
             if (e == cudaSuccess)
                 e = timed(s, PF_K_FUSED, [&] {
                     return launch_fused_step<R>(kp, s->geo_fused, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p,
                                                 st, tab, parts, s->stream, (const unsigned char *)s->tmap[a].p,
-                                                (unsigned char *)s->tmap[b].p);
+                                                (unsigned char *)s->tmap[b].p, !lean);
+                });
+            if (e == cudaSuccess && lean)
+                e = timed(s, PF_K_LEAN, [&] {
+                    return launch_lean_step<R>(kp, s->geo_fused, s->lean_nsub, &s->mu_map[a], s->mu[a].p,
+                                               s->phi[b].p, s->mu[b].p, st, tab, parts + np_fused, s->stream,
+                                               (const unsigned char *)s->tmap[a].p, (unsigned char *)s->tmap[b].p);
                 });
         } else if (s->comp()) {
             const KParams<float> &kf = reinterpret_cast<const KParams<float> &>(kp);
@@ -394,13 +461,10 @@ static int do_step(pf_sim *s, int n)
         n -= 1;
     }
     const int want = use_fused(s) ? 1 : 0;
-    if (want && !s->tmap_ok[0]) {
-        // the graph's fused steps take the liquid map of buffer 0 as valid
-        const KParams<R> kp = make_kparams<R>(s);
-        cudaError_t e = launch_classify<R>(kp, (const DevState *)s->state.p, s->phi[0].p,
-                                           (unsigned char *)s->tmap[0].p, s->stream);
+    if (want) {
+        // the graph's fused steps take the liquid maps of both buffers as valid
+        cudaError_t e = ensure_maps<R>(s, s->stream);
         if (e != cudaSuccess) return latch(s, cuda_status(e));
-        s->tmap_ok[0] = true;
     }
     if (!s->graph || s->graph_variant != want) {
         if (s->graph) {
@@ -691,9 +755,19 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
     for (int b = 0; b < 2 && r == PF_OK; b++)
         r = dev_alloc(s->tmap[b], (size_t)nz * s->geo_fused.gx * s->geo_fused.gy, s->stream);
     if (r == PF_OK) r = dev_alloc(s->state, sizeof(DevState), s->stream);
+    // lean CTAs: about 64 planes each
+    s->lean_nsub = std::max(1, (s->geo_fused.zchunk + 63) / 64);
     if (r == PF_OK)
-        r = dev_alloc(s->parts, (size_t)std::max(s->geo.nparts(), s->geo_fused.nparts()) * sizeof(Partial),
+        r = dev_alloc(s->parts,
+                      (size_t)std::max(s->geo.nparts(), s->geo_fused.nparts() * (1 + s->lean_nsub)) * sizeof(Partial),
                       s->stream);
+    if (r == PF_OK && !s->comp()) {
+        // the compensated state never takes the fused step
+        s->lean_ok = true;
+        for (int b = 0; b < 2; b++)
+            s->lean_ok = s->lean_ok && encode_mu_map(&s->mu_map[b], s->mu[b].p, nx, ny, nz, w, s->geo_fused.tx,
+                                                     s->geo_fused.ty);
+    }
     if (r == PF_OK) r = dev_alloc(s->tab, tabsz, s->stream);
     if (r == PF_OK) r = dev_alloc(s->red, (size_t)nz * 8 * sizeof(double), s->stream);
     if (r != PF_OK) {
@@ -736,10 +810,10 @@ int pf_sync(pf_sim *s)
     if (!s) return PF_E_INVAL;
     DevState ds;
     int r = read_state(s, &ds);
-    if (r == PF_OK && ds.nonfinite) latch(s, PF_E_UNSTABLE);
+    if (r == PF_OK && ds.nonfinite) latch(s, ds.nonfinite == 2 ? PF_E_TIMEOUT : PF_E_UNSTABLE);
     r = s->latched;
     s->latched = PF_OK;
-    if (r == PF_E_UNSTABLE) {
+    if (r == PF_E_UNSTABLE || r == PF_E_TIMEOUT) {
         // clear the sticky device flag with the latched error
         ds.nonfinite = 0;
         cudaMemcpyAsync(s->state.p, &ds, sizeof ds, cudaMemcpyHostToDevice, s->stream);
@@ -797,6 +871,29 @@ int pf_window_shifts(pf_sim *s, int *planes)
     int r = read_state(s, &ds);
     if (r != PF_OK) return r;
     *planes = ds.nshift_total;
+    return PF_OK;
+}
+
+int pf_step_bytes(pf_sim *s, double bytes[])
+{
+    if (!s || !bytes) return PF_E_INVAL;
+    for (int c = 0; c < PF_K_COUNT; c++) bytes[c] = 0.0;
+    if (s->last_kind < 0) return PF_OK;
+    const double cells = (double)s->ncell(), w = (double)s->wbytes();
+    if (s->last_kind == 0) {
+        // phi-sweep: phi^n, mu^n in, phi^{n+1} out (10 words; 18 with the compensated low words of
+        // phi in and out); mu-sweep: phi^n, phi^{n+1}, mu^n in, mu^{n+1} out (12 words; 16)
+        bytes[PF_K_PHI] = cells * w * (s->comp() ? 18.0 : 10.0);
+        bytes[PF_K_MU] = cells * w * (s->comp() ? 16.0 : 12.0);
+        return PF_OK;
+    }
+    std::vector<Partial> h((size_t)s->last_nparts);
+    cudaError_t e = cudaMemcpyAsync(h.data(), s->parts.p, h.size() * sizeof(Partial), cudaMemcpyDeviceToHost,
+                                    s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return latch(s, cuda_status(e));
+    const size_t np = (size_t)s->geo_fused.nparts();
+    for (size_t q = 0; q < h.size(); q++) bytes[q < np ? PF_K_FUSED : PF_K_LEAN] += h[q].bytes;
     return PF_OK;
 }
 
@@ -973,14 +1070,10 @@ static int batch_step(pf_batch *b, int n)
     }
     for (size_t q = 0; q < b->sims.size(); q++)
         if (b->sims[q]->cur != (b->cur0[q] ^ b->parity)) return PF_E_INVAL;  // stepped on its own
-    for (pf_sim *s : b->sims)
-        if (!s->tmap_ok[s->cur]) {  // fields written since its last fused step: rebuild its liquid map
-            const KParams<R> kp = make_kparams<R>(s);
-            cudaError_t e = launch_classify<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p,
-                                               (unsigned char *)s->tmap[s->cur].p, b->stream);
-            if (e != cudaSuccess) return cuda_status(e);
-            s->tmap_ok[s->cur] = true;
-        }
+    for (pf_sim *s : b->sims) {  // fields written since their last fused step: rebuild the liquid maps
+        cudaError_t e = ensure_maps<R>(s, b->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(b->stream, &cs) != cudaSuccess) {
         cudaGetLastError();
@@ -1240,7 +1333,7 @@ size_t footprint_of(int nx, int ny, int nz)
 {
     const size_t n = (size_t)nx * ny * nz;
     const Geometry g = make_geometry(nx, ny, nz, 0);
-    return 2 * n * (16 + 8) + (size_t)2 * nz * 64 + (size_t)g.nparts() * sizeof(Partial) + (size_t)nz * 64 +
+    return 2 * n * (16 + 8) + (size_t)2 * nz * 64 + (size_t)2 * g.nparts() * sizeof(Partial) + (size_t)nz * 64 +
            (size_t)2 * nz * g.gx * g.gy + 4096;
 }
 }  // namespace

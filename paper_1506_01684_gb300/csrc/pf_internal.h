@@ -19,7 +19,7 @@ struct DevState {
     double h_int;      // interface height measured after the last step
     int zbase;         // storage plane of logical plane 0 (moving-window ring buffer)
     int shift;         // planes shifted by the last finalize (0: none); read by post_kernel
-    int nonfinite;     // sticky: a non-finite value was seen
+    int nonfinite;     // sticky: 1 a non-finite value was seen, 2 a bounded device wait gave up
     int nshift_total;  // planes shifted since init
 };
 
@@ -27,6 +27,9 @@ struct DevState {
 struct Partial {
     double liq_deficit;  // sum over the CTA's cells of (1 - phi_l^{n+1})
     double nonfinite;    // > 0 when a cell of the CTA produced a non-finite value
+    double bytes;        // algorithmic HBM bytes of the step for the CTA's cells (compulsory
+                         // loads and stores of the design that ran; read back for the roofline)
+    double timeout;      // > 0 when a bounded wait of the CTA gave up
 };
 
 // Temperature-dependent constants of one x-y plane (cell centres) or one z-face level,
@@ -113,7 +116,15 @@ template <typename R>
 cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const void *phi, const void *mu,
                               void *phi_out, void *mu_out, const DevState *st, const PlaneT<R> *tab, Partial *parts,
                               cudaStream_t s, const unsigned char *tmap_in = nullptr,
-                              unsigned char *tmap_out = nullptr);
+                              unsigned char *tmap_out = nullptr, bool lean_here = true);
+// The pure-liquid planes of the fused step (lean_step_kernel), launched beside the fused kernel
+// run with lean_here = 0: grid (tgx, tgy, gz * nsub), one CTA per tile and sub-chunk of a z chunk.
+// mu_map: TMA tensor map of the source mu buffer (3D: 2 nx words, ny, nz); parts: gx*gy*gz*nsub
+// partials.  Returns cudaErrorInvalidValue when the map layout does not fit the kernel.
+template <typename R>
+cudaError_t launch_lean_step(const KParams<R> &kp, const Geometry &g, int nsub, const void *mu_map, const void *mu,
+                             void *phi_out, void *mu_out, const DevState *st, const PlaneT<R> *tab, Partial *parts,
+                             cudaStream_t s, const unsigned char *tmap_in, unsigned char *tmap_out);
 // liquid map of a field (for states not produced by a fused step)
 template <typename R>
 cudaError_t launch_classify(const KParams<R> &kp, const DevState *st, const void *phi, unsigned char *tmap,

@@ -1019,6 +1019,11 @@ __global__ void __launch_bounds__(TX *TY) mu_sweep_kernel(const KParams<R> kp, c
         const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         partials[bid].liq_deficit = a;
         partials[bid].nonfinite = b;
+        // this sweep: phi^n, phi^{n+1}, mu^n in, mu^{n+1} out (12 words a cell); the compensated
+        // state adds the low words of mu in and out
+        const double cells = (double)max(0, min(TX, nx - i0)) * (double)max(0, min(TY, ny - j0)) * (double)(z1 - z0);
+        partials[bid].bytes = cells * (double)sizeof(R) * (COMP ? 16.0 : 12.0);
+        partials[bid].timeout = 0.0;
     }
 }
 
@@ -1119,6 +1124,69 @@ __device__ __forceinline__ Mu<R> quiet_mu_cell(const KParams<R> &kp, const Plane
     return mu_cell_coded(kp, tc, 3, 3, liquid, liquid, mP, div0, div1);
 }
 
+// Lean / general split of the z chunk [z0, z1) of tile (bx, by).  Plane q is lean when phi^n is
+// pure liquid (liquid map of the source field) on the tile's 2-ring region over the planes
+// q-2 .. q+2: then phi^{n+1}(q) = phi^n(q) = e_l and every mu face of the plane takes the quiet
+// form (constant mobility, no anti-trapping current).  With kmin / kmax the lowest / highest plane
+// of z0-2 .. z1+1 that is not pure liquid, the lean planes are [z0, lo_end) and [hi_beg, z1); the
+// general path runs on [lo_end, hi_beg).  CTA-wide: every one of the NTH threads calls it (one
+// barrier); kred is NTH/32 pairs of shared ints.
+template <int TX, int TY, int NTH>
+__device__ __forceinline__ void lean_split(const unsigned char *__restrict__ tmap_in, int tgx, int tgy, int nx, int ny,
+                                           int nz, int zbase, int bx, int by, int z0, int z1, int (*kred)[2],
+                                           int &lo_end, int &hi_beg)
+{
+    const int tid = threadIdx.x;
+    const int i0 = bx * TX, j0 = by * TY;
+    const int ntl = tgx * tgy;
+    // tiles that hold the 2-ring region: own, and those of the columns i0-2, i0-1, i0+w, i0+w+1
+    // (rows alike) -- with a narrow last tile these can lie two tiles away
+    const int w = min(TX, nx - i0), hgt = min(TY, ny - j0);
+    const int xa = wrapi(i0 - 2, nx) / TX, xb = wrapi(i0 - 1, nx) / TX, xc = wrapi(i0 + w, nx) / TX,
+              xd = wrapi(i0 + w + 1, nx) / TX;
+    const int ya = wrapi(j0 - 2, ny) / TY, yb = wrapi(j0 - 1, ny) / TY, yc = wrapi(j0 + hgt, ny) / TY,
+              yd = wrapi(j0 + hgt + 1, ny) / TY;
+    // one entry per distinct tile: a candidate is skipped when an earlier one names the same tile
+    const bool ux[5] = {true, xa != bx, xb != bx && xb != xa, xc != bx && xc != xa && xc != xb,
+                        xd != bx && xd != xa && xd != xb && xd != xc};
+    const bool uy[5] = {true, ya != by, yb != by && yb != ya, yc != by && yc != ya && yc != yb,
+                        yd != by && yd != ya && yd != yb && yd != yc};
+    int kmin = INT_MAX, kmax = INT_MIN;
+    for (int k = z0 - 2 + tid; k < z1 + 2; k += NTH) {
+        const int kc = k < 0 ? 0 : (k >= nz ? nz - 1 : k);
+        const int sp = kc + zbase >= nz ? kc + zbase - nz : kc + zbase;
+        const unsigned char *m = tmap_in + (size_t)sp * ntl;
+        bool ok = true;
+#pragma unroll
+        for (int r = 0; r < 5; r++) {
+            const int yy = r == 0 ? by : (r == 1 ? ya : (r == 2 ? yb : (r == 3 ? yc : yd)));
+#pragma unroll
+            for (int c = 0; c < 5; c++) {
+                const int xx = c == 0 ? bx : (c == 1 ? xa : (c == 2 ? xb : (c == 3 ? xc : xd)));
+                if (uy[r] && ux[c]) ok = ok & (m[yy * tgx + xx] == 1);
+            }
+        }
+        if (!ok) {
+            kmin = min(kmin, k);
+            kmax = max(kmax, k);
+        }
+    }
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    if ((tid & 31) == 0) {
+        kred[tid >> 5][0] = kmin;
+        kred[tid >> 5][1] = kmax;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NTH / 32; q++) {
+        kmin = min(kmin, kred[q][0]);
+        kmax = max(kmax, kred[q][1]);
+    }
+    lo_end = kmin == INT_MAX ? z1 : max(z0, min(z1, kmin - 2));
+    hi_beg = kmin == INT_MAX ? z1 : min(z1, max(lo_end, kmax + 3));
+}
+
 template <typename R, int TX, int TY>
 __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__restrict__ phi,
                                            const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
@@ -1126,7 +1194,7 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
                                            const PlaneT<R> *__restrict__ tab, Partial *__restrict__ part, int bx,
                                            int by, int bz, unsigned char *__restrict__ smem_raw,
                                            const unsigned char *__restrict__ tmap_in,
-                                           unsigned char *__restrict__ tmap_out)
+                                           unsigned char *__restrict__ tmap_out, bool lean_here = true)
 {
     constexpr int NT = TX * TY;
     constexpr int SX = TX + 2, SY = TY + 2, SN = SX * SY, NR = SN - NT;  // tile + 1-ring
@@ -1168,7 +1236,7 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
     };
 
     // FP64 per-CTA partials (fixed order: lanes by a shuffle tree, then warps in order)
-    auto epilogue = [&](double liq_def, bool bad) {
+    auto epilogue = [&](double liq_def, bool bad, double bytes) {
         double badv = bad ? 1.0 : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -1189,86 +1257,56 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
             }
             part->liq_deficit = a;
             part->nonfinite = b;
+            part->bytes = bytes;
+            part->timeout = 0.0;
         }
     };
+    // the tile's cells per plane (a ragged tile at the domain edge holds fewer)
+    const double tile_cells = (double)min(TX, nx - i0) * (double)min(TY, ny - j0);
+    double lean_bytes = 0.0;
 
-    // ---- lean segments.  Plane q of the chunk is lean when phi^n is pure liquid on the tile's
-    // 2-ring region over the planes q-2 .. q+2 (read from the liquid map of the source field):
-    // then phi^{n+1}(q) = phi^n(q) and every mu face of the plane takes the quiet form, so the
-    // plane needs no shared memory and no barrier.  With kmin / kmax the lowest / highest plane
-    // of z0-2 .. z1+1 that is not pure liquid, the lean planes are [z0, kmin-2) and
-    // [kmax+3, z1); the planes between run the general path below.
+    // ---- lean segments (see lean_split): they need no shared memory and no barrier.  With
+    // lean_here = false they belong to lean_step_kernel, launched beside this one, and this CTA
+    // runs only the general planes between them.
     bool bad = false;
     if (tmap_in) {
-        // tiles that hold the 2-ring region: own, and those of the columns i0-2, i0-1, i0+w, i0+w+1
-        // (rows alike) -- with a narrow last tile these can lie two tiles away
-        const int w = min(TX, nx - i0), hgt = min(TY, ny - j0);
-        const int xa = wrapi(i0 - 2, nx) / TX, xb = wrapi(i0 - 1, nx) / TX, xc = wrapi(i0 + w, nx) / TX,
-                  xd = wrapi(i0 + w + 1, nx) / TX;
-        const int ya = wrapi(j0 - 2, ny) / TY, yb = wrapi(j0 - 1, ny) / TY, yc = wrapi(j0 + hgt, ny) / TY,
-                  yd = wrapi(j0 + hgt + 1, ny) / TY;
-        // one entry per distinct tile: a candidate is skipped when an earlier one names the same tile
-        const bool ux[5] = {true, xa != bx, xb != bx && xb != xa, xc != bx && xc != xa && xc != xb,
-                            xd != bx && xd != xa && xd != xb && xd != xc};
-        const bool uy[5] = {true, ya != by, yb != by && yb != ya, yc != by && yc != ya && yc != yb,
-                            yd != by && yd != ya && yd != yb && yd != yc};
-        int kmin = INT_MAX, kmax = INT_MIN;
-        for (int k = z0 - 2 + tid; k < z1 + 2; k += NT) {
-            const unsigned char *m = tmap_in + (size_t)splane(k) * ntl;
-            bool ok = true;
-#pragma unroll
-            for (int r = 0; r < 5; r++) {
-                const int yy = r == 0 ? by : (r == 1 ? ya : (r == 2 ? yb : (r == 3 ? yc : yd)));
-#pragma unroll
-                for (int c = 0; c < 5; c++) {
-                    const int xx = c == 0 ? bx : (c == 1 ? xa : (c == 2 ? xb : (c == 3 ? xc : xd)));
-                    if (uy[r] && ux[c]) ok = ok & (m[yy * kp.tgx + xx] == 1);
-                }
-            }
-            if (!ok) {
-                kmin = min(kmin, k);
-                kmax = max(kmax, k);
-            }
-        }
-        kmin = __reduce_min_sync(0xffffffffu, kmin);
-        kmax = __reduce_max_sync(0xffffffffu, kmax);
-        if ((tid & 31) == 0) {
-            kred[tid >> 5][0] = kmin;
-            kred[tid >> 5][1] = kmax;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < NT / 32; q++) {
-            kmin = min(kmin, kred[q][0]);
-            kmax = max(kmax, kred[q][1]);
-        }
-        const int lo_end = kmin == INT_MAX ? z1 : max(z0, min(z1, kmin - 2));
-        const int hi_beg = kmin == INT_MAX ? z1 : min(z1, max(lo_end, kmax + 3));
-
+        int lo_end, hi_beg;
+        lean_split<TX, TY, NT>(tmap_in, kp.tgx, kp.tgy, nx, ny, nz, zbase, bx, by, z0, z1, kred, lo_end, hi_beg);
         const int i = i0 + tx, j = j0 + ty;
         const int cxm = wrapi(j, ny) * nx + wrapi(i - 1, nx), cxp = wrapi(j, ny) * nx + wrapi(i + 1, nx);
         const int cym = wrapi(j - 1, ny) * nx + wrapi(i, nx), cyp = wrapi(j + 1, ny) * nx + wrapi(i, nx);
-        // one lean segment [qa, qb).  Register slots hold LD planes in flight (phi, mu and its four
-        // in-plane neighbours); plane q is computed from slot q mod LD, whose loads for plane q+LD
-        // are issued right after.  Loads past the segment read clamped planes and are not used.
+        // one lean segment [qa, qb).  phi^n is pure liquid there (the map says so), hence
+        // phi^{n+1} = e_l without reading phi^n; it is stored only where the destination's own map
+        // does not already show a pure-liquid tile plane (the destination holds phi^{n-1}, and a
+        // plane that stayed liquid needs no store).  Register slots hold LD planes of mu in flight
+        // (the cell and its four in-plane neighbours); plane q is computed from slot q mod LD,
+        // whose loads for plane q+LD are issued right after.  Loads past the segment read clamped
+        // planes and are not used.
+        // A tile row is one warp, and every lane holds the periodic image of its column (lanes
+        // past a ragged edge included), so the x neighbours are the adjacent lanes' cells; only
+        // lane 0 (x - 1) and lane TX - 1 (x + 1) load theirs.
+        static_assert(TX == 32, "a tile row must be one warp");
+        const bool xedge = tx == 0 || tx == TX - 1;
+        const int cxe = tx == 0 ? cxm : cxp;
         auto lean = [&](int qa, int qb) {
-            constexpr int LD = 4;
-            Ph<R> pv[LD];
-            Mu<R> mo[LD], mxm[LD], mxp[LD], mym[LD], myp[LD];
+            constexpr int LD = 8;
+            Mu<R> mo[LD], mxe[LD], mym[LD], myp[LD];
             auto load = [&](int u, int k) {
                 const size_t o = (size_t)splane(k) * plane;
-                pv[u] = ldg_ph(phi + o + col_own);
                 mo[u] = ldg_mu(mu + o + col_own);
-                mxm[u] = ldg_mu(mu + o + cxm);
-                mxp[u] = ldg_mu(mu + o + cxp);
+                if (xedge) mxe[u] = ldg_mu(mu + o + cxe);
                 mym[u] = ldg_mu(mu + o + cym);
                 myp[u] = ldg_mu(mu + o + cyp);
             };
 #pragma unroll
             for (int u = 0; u < LD; u++) load(u, qa + u);
+            Ph<R> liquid;
+            liquid.v[0] = liquid.v[1] = liquid.v[2] = R(0);
+            liquid.v[3] = R(1);
             Mu<R> Vz_lo;
             Vz_lo.v[0] = Vz_lo.v[1] = R(0);
             if (qa > 0) Vz_lo = quiet_zflux(kp, ldg_mu(mu + (size_t)splane(qa - 1) * plane + col_own), mo[0]);
+            int phi_stores = 0;
             for (int q0 = qa; q0 < qb; q0 += LD) {
 #pragma unroll
                 for (int u = 0; u < LD; u++) {
@@ -1279,11 +1317,20 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
                         Mu<R> Vz_hi;
                         Vz_hi.v[0] = Vz_hi.v[1] = R(0);
                         if (q < nz - 1) Vz_hi = quiet_zflux(kp, mo[u], m_next);
-                        const Mu<R> out =
-                            quiet_mu_cell(kp, tab + q, mo[u], mxm[u], mxp[u], mym[u], myp[u], Vz_lo, Vz_hi);
+                        Mu<R> xm, xp;
+#pragma unroll
+                        for (int c = 0; c < 2; c++) {
+                            xm.v[c] = __shfl_up_sync(0xffffffffu, mo[u].v[c], 1);
+                            xp.v[c] = __shfl_down_sync(0xffffffffu, mo[u].v[c], 1);
+                        }
+                        if (tx == 0) xm = mxe[u];
+                        if (tx == TX - 1) xp = mxe[u];
+                        const Mu<R> out = quiet_mu_cell(kp, tab + q, mo[u], xm, xp, mym[u], myp[u], Vz_lo, Vz_hi);
                         const size_t o = (size_t)splane(q) * plane;
+                        const bool store_phi = !tmap_out || tmap_out[(size_t)splane(q) * ntl + tile] != 1;
+                        phi_stores += store_phi ? 1 : 0;
                         if (valid) {
-                            st_ph(phi_out + o + col_own, pv[u]);
+                            if (store_phi) st_ph(phi_out + o + col_own, liquid);
                             st_mu(mu_out + o + col_own, out);
                             bad = bad | !isfinite(out.v[0] + out.v[1]);
                         }
@@ -1292,16 +1339,21 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
                     }
                 }
             }
+            // every thread has read the destination's map entries of the segment before any is
+            // replaced by the new field's
+            __syncthreads();
             if (tmap_out)
                 for (int q = qa + tid; q < qb; q += NT) tmap_out[(size_t)splane(q) * ntl + tile] = 1;
+            // mu^n in, mu^{n+1} out (4 words a cell), plus phi^{n+1} where it was stored
+            lean_bytes += tile_cells * (double)sizeof(R) * (4.0 * (qb - qa) + 4.0 * phi_stores);
         };
-        if (lo_end > z0) lean(z0, lo_end);
-        if (z1 > hi_beg) lean(hi_beg, z1);
+        if (lean_here && lo_end > z0) lean(z0, lo_end);
+        if (lean_here && z1 > hi_beg) lean(hi_beg, z1);
         // the general path runs on the planes in between
         z0 = lo_end;
         z1 = hi_beg;
         if (z0 >= z1) {
-            epilogue(0.0, bad);
+            epilogue(0.0, bad, lean_bytes);
             return;
         }
     }
@@ -1633,7 +1685,8 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
         Vz_lo = Vz_hi;
     }
 
-    epilogue(liq_def + (double)solid_cells, bad);
+    // general planes: phi^n, mu^n in, phi^{n+1}, mu^{n+1} out (12 words a cell)
+    epilogue(liq_def + (double)solid_cells, bad, lean_bytes + tile_cells * (double)sizeof(R) * 12.0 * (z1 - z0));
 }
 
 template <typename R, int TX, int TY>
@@ -1644,12 +1697,12 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) fused_step_ker
                                                            const PlaneT<R> *__restrict__ tab,
                                                            Partial *__restrict__ partials,
                                                            const unsigned char *__restrict__ tmap_in,
-                                                           unsigned char *__restrict__ tmap_out)
+                                                           unsigned char *__restrict__ tmap_out, int lean_here)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     fused_tile<R, TX, TY>(kp, phi, mu, phi_out, mu_out, st, tab, partials + bid, blockIdx.x, blockIdx.y, blockIdx.z,
-                          smem_raw, tmap_in, tmap_out);
+                          smem_raw, tmap_in, tmap_out, lean_here != 0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1688,6 +1741,10 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) batched_fused_
     }
 }
 
+}  // namespace pf
+#include "pf_lean.cuh"
+namespace pf {
+
 // ---------------------------------------------------------------------------------------
 // per-step bookkeeping kernels
 // ---------------------------------------------------------------------------------------
@@ -1719,11 +1776,17 @@ __device__ __forceinline__ void finalize_body(const KParams<R> &kp, DevState *__
                                               const Partial *__restrict__ parts, int nparts)
 {
     __shared__ double sa[256], sb[256];
+    __shared__ int s_to;
+    if (threadIdx.x == 0) s_to = 0;
+    __syncthreads();
     double a = 0.0, b = 0.0;
+    bool to = false;
     for (int q = threadIdx.x; q < nparts; q += 256) {
         a += parts[q].liq_deficit;
         b += parts[q].nonfinite;
+        to = to || parts[q].timeout > 0.0;
     }
+    if (to) atomicOr(&s_to, 1);
     sa[threadIdx.x] = a;
     sb[threadIdx.x] = b;
     __syncthreads();
@@ -1736,7 +1799,8 @@ __device__ __forceinline__ void finalize_body(const KParams<R> &kp, DevState *__
     }
     if (threadIdx.x == 0) {
         st->t = st->t + kp.dt64;
-        if (sb[0] > 0.0) st->nonfinite = 1;
+        if (sb[0] > 0.0 && st->nonfinite == 0) st->nonfinite = 1;
+        if (s_to) st->nonfinite = 2;
         const double h = sa[0] / ((double)kp.nx * (double)kp.ny);
         st->h_int = h;
         int s = 0;
@@ -2117,7 +2181,7 @@ cudaError_t launch_classify(const KParams<R> &kp, const DevState *st, const void
 template <typename R>
 cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const void *phi, const void *mu,
                               void *phi_out, void *mu_out, const DevState *st, const PlaneT<R> *tab, Partial *parts,
-                              cudaStream_t s, const unsigned char *tmap_in, unsigned char *tmap_out)
+                              cudaStream_t s, const unsigned char *tmap_in, unsigned char *tmap_out, bool lean_here)
 {
     if ((tmap_in || tmap_out) && (kp.tgx != g.gx || kp.tgy != g.gy)) return cudaErrorInvalidValue;
     static bool attr = false;
@@ -2131,7 +2195,32 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
     dim3 grid(g.gx, g.gy, g.gz);
     fused_step_kernel<R, kTX, kTY><<<grid, kTX * kTY, sm, s>>>(kp, (const Ph<R> *)phi, (const Mu<R> *)mu,
                                                                (Ph<R> *)phi_out, (Mu<R> *)mu_out, st, tab, parts,
-                                                               tmap_in, tmap_out);
+                                                               tmap_in, tmap_out, lean_here ? 1 : 0);
+    return cudaGetLastError();
+}
+
+constexpr int kLeanStages = 6;
+
+template <typename R>
+cudaError_t launch_lean_step(const KParams<R> &kp, const Geometry &g, int nsub, const void *mu_map, const void *mu,
+                             void *phi_out, void *mu_out, const DevState *st, const PlaneT<R> *tab, Partial *parts,
+                             cudaStream_t s, const unsigned char *tmap_in, unsigned char *tmap_out)
+{
+    using L = LeanLayout<R, kTX, kTY>;
+    if (!mu_map || !tmap_in || !tmap_out || nsub < 1 || kp.tgx != g.gx || kp.tgy != g.gy) return cudaErrorInvalidValue;
+    if (sizeof(R) == 4 && (kp.nx & 1)) return cudaErrorInvalidValue;  // rows must be 16-byte multiples
+    static bool attr = false;
+    const size_t sm = L::smem_bytes(kLeanStages);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(lean_step_kernel<R, kTX, kTY, kLeanStages>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(g.gx, g.gy, g.gz * nsub);
+    lean_step_kernel<R, kTX, kTY, kLeanStages><<<grid, kTX * kTY + 32, sm, s>>>(
+        kp, *reinterpret_cast<const CUtensorMap *>(mu_map), (const Mu<R> *)mu, (Ph<R> *)phi_out, (Mu<R> *)mu_out, st,
+        tab, parts, tmap_in, tmap_out, nsub);
     return cudaGetLastError();
 }
 
@@ -2273,9 +2362,12 @@ cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, v
                                             Partial *, cudaStream_t);                                            \
     template cudaError_t launch_fused_step<R>(const KParams<R> &, const Geometry &, const void *, const void *, \
                                               void *, void *, const DevState *, const PlaneT<R> *, Partial *,     \
-                                              cudaStream_t, const unsigned char *, unsigned char *);              \
+                                              cudaStream_t, const unsigned char *, unsigned char *, bool);        \
     template cudaError_t launch_classify<R>(const KParams<R> &, const DevState *, const void *, unsigned char *, \
                                             cudaStream_t);                                                       \
+    template cudaError_t launch_lean_step<R>(const KParams<R> &, const Geometry &, int, const void *, const void *, \
+                                             void *, void *, const DevState *, const PlaneT<R> *, Partial *,      \
+                                             cudaStream_t, const unsigned char *, unsigned char *);                \
     template cudaError_t launch_batched_step<R>(const BatchDomain<R> *, int, const BatchItem *, int, unsigned *, \
                                                 int, int, int, cudaStream_t);                                    \
     template int fused_ctas_per_sm<R>();                                                                         \

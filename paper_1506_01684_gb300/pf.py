@@ -81,6 +81,7 @@ SIGNATURES = {
     "pf_phase_fractions": (_I, [_VP, _DP]),
     "pf_stats": (_I, [_VP, _DP, _DP, _DP, _DP]),
     "pf_window_shifts": (_I, [_VP, ctypes.POINTER(_I)]),
+    "pf_step_bytes": (_I, [_VP, _DP]),
     "pf_profile": (_I, [_VP, _I]),
     "pf_set_variant": (_I, [_VP, _I]),
     "pf_profile_read": (_I, [_VP, _DP, ctypes.POINTER(_I)]),
@@ -103,9 +104,9 @@ SIGNATURES = {
     "pf_server_stats": (_I, [_VP, _DP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
 }
 
-PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_FUSED, PF_K_COUNT = 0, 1, 2, 3, 4, 8
+PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_FUSED, PF_K_LEAN, PF_K_COUNT = 0, 1, 2, 3, 4, 5, 8
 KERNEL_NAMES = {PF_K_PHI: "phi_sweep", PF_K_MU: "mu_sweep", PF_K_FINALIZE: "finalize", PF_K_POST: "post",
-                PF_K_FUSED: "fused_step"}
+                PF_K_FUSED: "fused_step", PF_K_LEAN: "lean_step"}
 PF_VARIANT_AUTO, PF_VARIANT_UNFUSED, PF_VARIANT_FUSED = 0, 1, 2
 VARIANTS = {"auto": PF_VARIANT_AUTO, "unfused": PF_VARIANT_UNFUSED, "fused": PF_VARIANT_FUSED}
 
@@ -256,6 +257,13 @@ def pf_window_shifts(sim) -> int:
     n = _I()
     _check(lib().pf_window_shifts(sim, ctypes.byref(n)), "pf_window_shifts")
     return n.value
+
+
+def pf_step_bytes(sim) -> dict:
+    """Algorithmic bytes of the last step per kernel name (kernels that ran only)."""
+    b = np.zeros(PF_K_COUNT)
+    _check(lib().pf_step_bytes(sim, _dp(b)), "pf_step_bytes")
+    return {KERNEL_NAMES[c]: float(b[c]) for c in KERNEL_NAMES if b[c] > 0}
 
 
 def pf_set_variant(sim, variant):
@@ -517,3 +525,6 @@ class Simulation:
 
     def shifts(self):
         return pf_window_shifts(self.h)
+
+    def step_bytes(self):
+        return pf_step_bytes(self.h)
