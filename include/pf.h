@@ -154,6 +154,7 @@ enum {
     PF_K_POST = 3,     /* plane-table rebuild and fill of planes entering the window */
     PF_K_FUSED = 4,    /* fused phi+mu step (both sweeps in one pass) */
     PF_K_LEAN = 5,     /* the fused step's pure-liquid planes (Section 3.3 shortcuts), a kernel of their own */
+    PF_K_PLAN = 6,     /* the fused step's split into pure-liquid and general planes */
     PF_K_COUNT = 8
 };
 

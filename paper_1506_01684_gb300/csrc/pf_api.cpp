@@ -22,6 +22,16 @@
 
 using namespace pf;
 
+// Launch shape of the fused step with the lean kernel: the persistent general-plane CTAs per SM,
+// and whether the general planes run on a second stream beside the lean kernel (1) or before it
+// on the sim's stream (0).
+#ifndef PF_GENERAL_CTAS_PER_SM
+#define PF_GENERAL_CTAS_PER_SM 1
+#endif
+#ifndef PF_OVERLAP_GENERAL
+#define PF_OVERLAP_GENERAL 1
+#endif
+
 // ------------------------------------------------------------------------------------------
 // allocator hooks
 // ------------------------------------------------------------------------------------------
@@ -109,6 +119,12 @@ struct pf_sim {
     // TMA tensor maps of the two mu buffers for the lean kernel (the fused step's pure-liquid
     // planes); lean_ok when both could be encoded (FP32 rows must be 16-byte multiples: nx even)
     CUtensorMap mu_map[2];
+    DevBuf lean_stats;  // LeanStats
+    DevBuf splits;      // int2 per (tile, chunk) of the fused grid: the lean / general split
+    DevBuf glist;       // int per (tile, chunk): the items with general planes
+    int general_ctas = 0;  // persistent CTAs of the general kernel
+    cudaStream_t aux = nullptr;  // the fused step's general planes, concurrent with the lean kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool lean_ok = false;
     int lean_nsub = 1;  // lean CTAs per z chunk of the fused grid
     DevBuf state;          // DevState
@@ -332,17 +348,33 @@ static cudaEvent_t pool_event(pf_sim *s)
     return e;
 }
 
-// Launch f() on the sim's stream, bracketed by timing events when profiling is on.
+// Launch f() on stream st (default: the sim's stream), bracketed by timing events when profiling
+// is on.
 template <typename F>
-static cudaError_t timed(pf_sim *s, int cls, F &&f)
+static cudaError_t timed(pf_sim *s, int cls, F &&f, cudaStream_t st = nullptr)
 {
+    if (!st) st = s->stream;
     if (!s->prof) return f();
     cudaEvent_t a = pool_event(s), b = pool_event(s);
     if (!a || !b) return cudaErrorMemoryAllocation;
-    cudaError_t e = cudaEventRecord(a, s->stream);
+    cudaError_t e = cudaEventRecord(a, st);
     if (e == cudaSuccess) e = f();
-    if (e == cudaSuccess) e = cudaEventRecord(b, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
     s->recs.push_back({cls, a, b});
+    return e;
+}
+
+// The second stream of the fused step: its general planes run there, beside the lean kernel on the
+// sim's stream (fork after the previous step's post kernel, join before finalize).  Created on
+// first use, with the highest priority so that the general CTAs are placed first.
+static cudaError_t ensure_aux(pf_sim *s)
+{
+    if (s->aux) return cudaSuccess;
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->aux, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
     return e;
 }
 
@@ -382,7 +414,7 @@ static int do_step_direct(pf_sim *s, int n)
     Partial *parts = (Partial *)s->parts.p;
     const bool lean = fused && s->lean_ok;
     const int np_fused = s->geo_fused.nparts();
-    const int nparts = fused ? np_fused * (lean ? 1 + s->lean_nsub : 1) : s->geo.nparts();
+    const int nparts = fused ? np_fused : s->geo.nparts();
     s->last_nparts = nparts;
     s->last_kind = fused ? (lean ? 2 : 1) : 0;
     for (int q = 0; q < n; q++) {
@@ -390,18 +422,49 @@ static int do_step_direct(pf_sim *s, int n)
         cudaError_t e;
         if (fused) {
             e = ensure_maps<R>(s, s->stream);
-            if (e == cudaSuccess)
-                e = timed(s, PF_K_FUSED, [&] {
-                    return launch_fused_step<R>(kp, s->geo_fused, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p,
-                                                st, tab, parts, s->stream, (const unsigned char *)s->tmap[a].p,
-                                                (unsigned char *)s->tmap[b].p, !lean);
-                });
-            if (e == cudaSuccess && lean)
-                e = timed(s, PF_K_LEAN, [&] {
-                    return launch_lean_step<R>(kp, s->geo_fused, s->lean_nsub, &s->mu_map[a], s->mu[a].p,
-                                               s->phi[b].p, s->mu[b].p, st, tab, parts + np_fused, s->stream,
-                                               (const unsigned char *)s->tmap[a].p, (unsigned char *)s->tmap[b].p);
-                });
+            const unsigned char *tin = (const unsigned char *)s->tmap[a].p;
+            unsigned char *tout = (unsigned char *)s->tmap[b].p;
+            LeanStats *ls = (LeanStats *)s->lean_stats.p;
+            if (!lean) {
+                if (e == cudaSuccess)
+                    e = timed(s, PF_K_FUSED, [&] {
+                        return launch_fused_step<R>(kp, s->geo_fused, s->phi[a].p, s->mu[a].p, s->phi[b].p,
+                                                    s->mu[b].p, st, tab, parts, s->stream, tin, tout, true);
+                    });
+            } else {
+                // plan the step (splits, list of items with general planes), then the general planes
+                // on the second stream beside the lean planes (a disjoint set of planes, map entries
+                // and partials) on the sim's stream
+                if (e == cudaSuccess)
+                    e = timed(s, PF_K_PLAN, [&] {
+                        return launch_plan<R>(kp, s->geo_fused, st, tin, (int2 *)s->splits.p, (int *)s->glist.p, ls,
+                                              parts, s->stream);
+                    });
+                cudaStream_t gs = s->stream;
+                if (PF_OVERLAP_GENERAL) {
+                    if (e == cudaSuccess) e = ensure_aux(s);
+                    if (e == cudaSuccess) e = cudaEventRecord(s->ev_fork, s->stream);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->aux, s->ev_fork, 0);
+                    gs = s->aux;
+                }
+                if (e == cudaSuccess)
+                    e = timed(
+                        s, PF_K_FUSED,
+                        [&] {
+                            return launch_general_step<R>(kp, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st,
+                                                          tab, parts, tin, tout, (const int2 *)s->splits.p,
+                                                          (const int *)s->glist.p, ls, s->general_ctas, gs);
+                        },
+                        gs);
+                if (e == cudaSuccess)
+                    e = timed(s, PF_K_LEAN, [&] {
+                        return launch_lean_step<R>(kp, s->geo_fused, s->lean_nsub, &s->mu_map[a], s->mu[a].p,
+                                                   s->phi[b].p, s->mu[b].p, st, ls, s->stream, tin, tout,
+                                                   (const int2 *)s->splits.p);
+                    });
+                if (PF_OVERLAP_GENERAL && e == cudaSuccess) e = cudaEventRecord(s->ev_join, s->aux);
+                if (PF_OVERLAP_GENERAL && e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+            }
         } else if (s->comp()) {
             const KParams<float> &kf = reinterpret_cast<const KParams<float> &>(kp);
             const PlaneT<float> *tf = reinterpret_cast<const PlaneT<float> *>(tab);
@@ -425,7 +488,10 @@ static int do_step_direct(pf_sim *s, int n)
                 });
         }
         if (e == cudaSuccess)
-            e = timed(s, PF_K_FINALIZE, [&] { return launch_finalize<R>(kp, st, parts, nparts, s->stream); });
+            e = timed(s, PF_K_FINALIZE, [&] {
+                return launch_finalize<R>(kp, st, parts, nparts, s->stream,
+                                          lean ? (LeanStats *)s->lean_stats.p : nullptr);
+            });
         if (e == cudaSuccess)
             e = timed(s, PF_K_POST, [&] {
                 return launch_post<R>(kp, st, s->phi[b].p, s->mu[b].p, tab, s->stream, s->lo_phi(b), s->lo_mu(b),
@@ -696,6 +762,9 @@ int pf_destroy(pf_sim *s)
     }
     dev_free(s->state, s->stream);
     dev_free(s->parts, s->stream);
+    dev_free(s->lean_stats, s->stream);
+    dev_free(s->splits, s->stream);
+    dev_free(s->glist, s->stream);
     dev_free(s->tab, s->stream);
     dev_free(s->seeds, s->stream);
     dev_free(s->red, s->stream);
@@ -705,6 +774,12 @@ int pf_destroy(pf_sim *s)
     }
     for (auto e : s->pool) cudaEventDestroy(e);
     if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->aux) {
+        cudaStreamSynchronize(s->aux);
+        cudaStreamDestroy(s->aux);
+    }
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
     return PF_OK;
@@ -755,12 +830,28 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
     for (int b = 0; b < 2 && r == PF_OK; b++)
         r = dev_alloc(s->tmap[b], (size_t)nz * s->geo_fused.gx * s->geo_fused.gy, s->stream);
     if (r == PF_OK) r = dev_alloc(s->state, sizeof(DevState), s->stream);
-    // lean CTAs: about 64 planes each
+    // lean CTAs: at most 64 planes each
     s->lean_nsub = std::max(1, (s->geo_fused.zchunk + 63) / 64);
     if (r == PF_OK)
-        r = dev_alloc(s->parts,
-                      (size_t)std::max(s->geo.nparts(), s->geo_fused.nparts() * (1 + s->lean_nsub)) * sizeof(Partial),
+        r = dev_alloc(s->parts, (size_t)std::max(s->geo.nparts(), s->geo_fused.nparts()) * sizeof(Partial),
                       s->stream);
+    if (r == PF_OK) r = dev_alloc(s->lean_stats, sizeof(LeanStats), s->stream);
+    if (r == PF_OK) r = dev_alloc(s->splits, (size_t)s->geo_fused.nparts() * sizeof(int2), s->stream);
+    if (r == PF_OK) r = dev_alloc(s->glist, (size_t)s->geo_fused.nparts() * sizeof(int), s->stream);
+    if (r == PF_OK) {
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // one persistent general CTA per SM by default: the rest of each SM (a general CTA takes half
+        // of its registers) stays open to the lean kernel running beside it
+        const int per_sm = std::min(PF_GENERAL_CTAS_PER_SM, p->precision == PF_FP64 ? general_ctas_per_sm<double>()
+                                                                                    : general_ctas_per_sm<float>());
+        s->general_ctas = std::max(1, std::min(s->geo_fused.nparts(), per_sm * sms));
+    }
+    if (r == PF_OK) {
+        cudaError_t e = cudaMemsetAsync(s->lean_stats.p, 0, sizeof(LeanStats), s->stream);
+        if (e != cudaSuccess) r = cuda_status(e);
+    }
     if (r == PF_OK && !s->comp()) {
         // the compensated state never takes the fused step
         s->lean_ok = true;
@@ -888,12 +979,16 @@ int pf_step_bytes(pf_sim *s, double bytes[])
         return PF_OK;
     }
     std::vector<Partial> h((size_t)s->last_nparts);
+    LeanStats ls;
+    memset(&ls, 0, sizeof ls);
     cudaError_t e = cudaMemcpyAsync(h.data(), s->parts.p, h.size() * sizeof(Partial), cudaMemcpyDeviceToHost,
                                     s->stream);
+    if (e == cudaSuccess && s->last_kind == 2)
+        e = cudaMemcpyAsync(&ls, s->lean_stats.p, sizeof ls, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return latch(s, cuda_status(e));
-    const size_t np = (size_t)s->geo_fused.nparts();
-    for (size_t q = 0; q < h.size(); q++) bytes[q < np ? PF_K_FUSED : PF_K_LEAN] += h[q].bytes;
+    for (const Partial &x : h) bytes[PF_K_FUSED] += x.bytes;
+    bytes[PF_K_LEAN] = (double)ls.last_bytes;
     return PF_OK;
 }
 

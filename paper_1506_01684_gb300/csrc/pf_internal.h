@@ -32,6 +32,16 @@ struct Partial {
     double timeout;      // > 0 when a bounded wait of the CTA gave up
 };
 
+// Per-simulation statistics of the lean kernel (the fused step's pure-liquid planes), summed
+// atomically by its CTAs and folded into the step's state by finalize.
+struct LeanStats {
+    unsigned long long bytes;       // algorithmic bytes of the current step
+    int nonfinite;                  // a non-finite mu^{n+1} was produced
+    int timeout;                    // a bounded wait gave up
+    unsigned long long last_bytes;  // bytes of the last finished step (read by the host)
+    unsigned gcount, gnext;         // (tile, chunk) items with general planes; next one to take
+};
+
 // Temperature-dependent constants of one x-y plane (cell centres) or one z-face level,
 // formed once per plane in FP64 and rounded to the stencil precision (the per-slice
 // precompute of the paper's Section 3.3).  16 words so that it stages with vector loads.
@@ -119,18 +129,34 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
                               unsigned char *tmap_out = nullptr, bool lean_here = true);
 // The pure-liquid planes of the fused step (lean_step_kernel), launched beside the fused kernel
 // run with lean_here = 0: grid (tgx, tgy, gz * nsub), one CTA per tile and sub-chunk of a z chunk.
-// mu_map: TMA tensor map of the source mu buffer (3D: 2 nx words, ny, nz); parts: gx*gy*gz*nsub
-// partials.  Returns cudaErrorInvalidValue when the map layout does not fit the kernel.
+// mu_map: TMA tensor map of the source mu buffer (3D: 2 nx words, ny, nz); stats: the sim's lean
+// statistics (folded in by the next finalize).  Returns cudaErrorInvalidValue when the map layout
+// or the chunking does not fit the kernel.
 template <typename R>
 cudaError_t launch_lean_step(const KParams<R> &kp, const Geometry &g, int nsub, const void *mu_map, const void *mu,
-                             void *phi_out, void *mu_out, const DevState *st, const PlaneT<R> *tab, Partial *parts,
-                             cudaStream_t s, const unsigned char *tmap_in, unsigned char *tmap_out);
+                             void *phi_out, void *mu_out, const DevState *st, LeanStats *stats, cudaStream_t s,
+                             const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits);
+// Plan of a fused step with the lean kernel (plan_kernel): each (tile, chunk) item's split into
+// lean and general planes (splits, gx*gy*gz), the list of items with general planes (glist,
+// count in stats->gcount; finalize resets the counters), zeroed partials for the all-lean items.
+template <typename R>
+cudaError_t launch_plan(const KParams<R> &kp, const Geometry &g, const DevState *st, const unsigned char *tmap_in,
+                        int2 *splits, int *glist, LeanStats *stats, Partial *parts, cudaStream_t s);
+// The general planes of the listed items: ctas persistent CTAs (general_step_kernel).
+template <typename R>
+cudaError_t launch_general_step(const KParams<R> &kp, const void *phi, const void *mu, void *phi_out, void *mu_out,
+                                const DevState *st, const PlaneT<R> *tab, Partial *parts,
+                                const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits,
+                                const int *glist, LeanStats *stats, int ctas, cudaStream_t s);
+template <typename R>
+int general_ctas_per_sm();
 // liquid map of a field (for states not produced by a fused step)
 template <typename R>
 cudaError_t launch_classify(const KParams<R> &kp, const DevState *st, const void *phi, unsigned char *tmap,
                             cudaStream_t s);
 template <typename R>
-cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s);
+cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s,
+                            LeanStats *lean = nullptr);
 // Batched fused step of ndoms domains: counter reset, persistent kernel (ctas CTAs) over the
 // work items, per-domain finalize and post.  parity: index of the source buffers.
 template <typename R>

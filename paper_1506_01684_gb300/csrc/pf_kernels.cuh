@@ -509,8 +509,9 @@ __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const Pla
 #pragma unroll
     for (int b = 0; b < 4; b++) h[b] = pb[b] * pb[b] * inv_S;
     const R M = kp.DinvA[0] * h[0] + kp.DinvA[1] * h[1] + kp.DinvA[2] * h[2] + kp.DinvA[3] * h[3];
-    v.v[0] = M * (mR.v[0] - mL.v[0]) * kp.inv_dx;
-    v.v[1] = M * (mR.v[1] - mL.v[1]) * kp.inv_dx;
+    const R Mdx = M * kp.inv_dx;  // mobility over the face width, formed once per face
+    v.v[0] = Mdx * (mR.v[0] - mL.v[0]);
+    v.v[1] = Mdx * (mR.v[1] - mL.v[1]);
     // anti-trapping current (Eq. 4, g_a = phi_a); terms skipped per reading R9
     if (pb[3] > R(0) && (pb[0] > R(0) || pb[1] > R(0) || pb[2] > R(0))) {
         R gl[3];
@@ -565,8 +566,9 @@ __device__ __forceinline__ Mu<R> face_mu(const KParams<R> &kp, const PlaneT<R> *
     if (same(nL, nR) && onehot(nL)) {
         Mu<R> v;
         const R M = kp.DinvA[0] * nL.v[0] + kp.DinvA[1] * nL.v[1] + kp.DinvA[2] * nL.v[2] + kp.DinvA[3] * nL.v[3];
-        v.v[0] = M * (mR.v[0] - mL.v[0]) * kp.inv_dx;
-        v.v[1] = M * (mR.v[1] - mL.v[1]) * kp.inv_dx;
+        const R Mdx = M * kp.inv_dx;
+        v.v[0] = Mdx * (mR.v[0] - mL.v[0]);
+        v.v[1] = Mdx * (mR.v[1] - mL.v[1]);
         return v;
     }
     return face_mu_general(kp, tf, nL, nR, oL, oR, mL, mR, aLp, aLm, aRp, aRm, bLp, bLm, bRp, bRm);
@@ -1056,8 +1058,9 @@ __device__ __forceinline__ Mu<R> face_mu_coded(const KParams<R> &kp, const Plane
     if (cL == cR && cL < 4) {
         Mu<R> v;
         const R M = pick4(kp.DinvA, cL);
-        v.v[0] = M * (mR.v[0] - mL.v[0]) * kp.inv_dx;
-        v.v[1] = M * (mR.v[1] - mL.v[1]) * kp.inv_dx;
+        const R Mdx = M * kp.inv_dx;
+        v.v[0] = Mdx * (mR.v[0] - mL.v[0]);
+        v.v[1] = Mdx * (mR.v[1] - mL.v[1]);
         return v;
     }
     return face_mu_general(kp, tf, nL, nR, oL, oR, mL, mR, aLp, aLm, aRp, aRm, bLp, bLm, bRp, bRm);
@@ -1084,34 +1087,31 @@ __device__ __forceinline__ Mu<R> mu_cell_coded(const KParams<R> &kp, const Plane
     return mu_cell(kp, tc, nP, oP, m, div0, div1);
 }
 
-// One CTA's work of the fused step: tile (bx, by) of x-y columns, z chunk bz.  Shared by the
-// single-domain kernel (tile = block index) and the batched persistent kernel (tile = work item).
 // Fluxes and mu^{n+1} of a pure-liquid cell whose neighbourhood is pure liquid in phi^n and
 // phi^{n+1}: constant mobility, no anti-trapping current, h = phi -- the short forms of
 // face_mu_coded and mu_cell_coded for equal codes, kept in one place so that every path that
 // takes them evaluates the same expressions.
 template <typename R>
-__device__ __forceinline__ Mu<R> quiet_zflux(const KParams<R> &kp, const Mu<R> &a, const Mu<R> &b)
+__device__ __forceinline__ Mu<R> quiet_flux(const KParams<R> &kp, const Mu<R> &a, const Mu<R> &b)
 {
+    // flux of the face from cell a to cell b
     Mu<R> v;
-    v.v[0] = kp.DinvA[3] * (b.v[0] - a.v[0]) * kp.inv_dx;
-    v.v[1] = kp.DinvA[3] * (b.v[1] - a.v[1]) * kp.inv_dx;
+    const R Mdx = kp.DinvA[3] * kp.inv_dx;
+    v.v[0] = Mdx * (b.v[0] - a.v[0]);
+    v.v[1] = Mdx * (b.v[1] - a.v[1]);
     return v;
 }
 template <typename R>
-__device__ __forceinline__ Mu<R> quiet_mu_cell(const KParams<R> &kp, const PlaneT<R> *__restrict__ tc, const Mu<R> &mP,
-                                               const Mu<R> &mxm, const Mu<R> &mxp, const Mu<R> &mym,
-                                               const Mu<R> &myp, const Mu<R> &Vz_lo, const Mu<R> &Vz_hi)
+__device__ __forceinline__ Mu<R> quiet_zflux(const KParams<R> &kp, const Mu<R> &a, const Mu<R> &b)
 {
-    const R Mliq = kp.DinvA[3];
-    Mu<R> vxm, vxp, vym, vyp;
-#pragma unroll
-    for (int c = 0; c < 2; c++) {
-        vxm.v[c] = Mliq * (mP.v[c] - mxm.v[c]) * kp.inv_dx;
-        vxp.v[c] = Mliq * (mxp.v[c] - mP.v[c]) * kp.inv_dx;
-        vym.v[c] = Mliq * (mP.v[c] - mym.v[c]) * kp.inv_dx;
-        vyp.v[c] = Mliq * (myp.v[c] - mP.v[c]) * kp.inv_dx;
-    }
+    return quiet_flux(kp, a, b);
+}
+// mu^{n+1} of a pure-liquid cell from its six face fluxes
+template <typename R>
+__device__ __forceinline__ Mu<R> quiet_mu_update(const KParams<R> &kp, const Mu<R> &mP, const Mu<R> &vxm,
+                                                 const Mu<R> &vxp, const Mu<R> &vym, const Mu<R> &vyp,
+                                                 const Mu<R> &Vz_lo, const Mu<R> &Vz_hi)
+{
     R div0 = (vxp.v[0] - vxm.v[0]) * kp.inv_dx;
     R div1 = (vxp.v[1] - vxm.v[1]) * kp.inv_dx;
     div0 = div0 + (vyp.v[0] - vym.v[0]) * kp.inv_dx;
@@ -1121,7 +1121,16 @@ __device__ __forceinline__ Mu<R> quiet_mu_cell(const KParams<R> &kp, const Plane
     Ph<R> liquid;
     liquid.v[0] = liquid.v[1] = liquid.v[2] = R(0);
     liquid.v[3] = R(1);
-    return mu_cell_coded(kp, tc, 3, 3, liquid, liquid, mP, div0, div1);
+    return mu_cell_coded(kp, (const PlaneT<R> *)nullptr, 3, 3, liquid, liquid, mP, div0, div1);
+}
+template <typename R>
+__device__ __forceinline__ Mu<R> quiet_mu_cell(const KParams<R> &kp, const PlaneT<R> *__restrict__ tc, const Mu<R> &mP,
+                                               const Mu<R> &mxm, const Mu<R> &mxp, const Mu<R> &mym,
+                                               const Mu<R> &myp, const Mu<R> &Vz_lo, const Mu<R> &Vz_hi)
+{
+    (void)tc;  // a liquid cell needs no temperature-dependent constant
+    return quiet_mu_update(kp, mP, quiet_flux(kp, mxm, mP), quiet_flux(kp, mP, mxp), quiet_flux(kp, mym, mP),
+                           quiet_flux(kp, mP, myp), Vz_lo, Vz_hi);
 }
 
 // Lean / general split of the z chunk [z0, z1) of tile (bx, by).  Plane q is lean when phi^n is
@@ -1131,46 +1140,82 @@ __device__ __forceinline__ Mu<R> quiet_mu_cell(const KParams<R> &kp, const Plane
 // of z0-2 .. z1+1 that is not pure liquid, the lean planes are [z0, lo_end) and [hi_beg, z1); the
 // general path runs on [lo_end, hi_beg).  CTA-wide: every one of the NTH threads calls it (one
 // barrier); kred is NTH/32 pairs of shared ints.
+// The fused-step tiles that hold tile (bx, by)'s 2-ring region: its own, and those of the columns
+// i0-2, i0-1, i0+w, i0+w+1 (rows alike; with a narrow last tile these can lie two tiles away).
+// u* flags mark the first occurrence of each distinct tile.
+template <int TX, int TY>
+struct RingTiles {
+    int xs[5], ys[5];
+    bool ux[5], uy[5];
+    __device__ __forceinline__ RingTiles(int nx, int ny, int bx, int by)
+    {
+        const int i0 = bx * TX, j0 = by * TY;
+        const int w = min(TX, nx - i0), hgt = min(TY, ny - j0);
+        xs[0] = bx;
+        xs[1] = wrapi(i0 - 2, nx) / TX;
+        xs[2] = wrapi(i0 - 1, nx) / TX;
+        xs[3] = wrapi(i0 + w, nx) / TX;
+        xs[4] = wrapi(i0 + w + 1, nx) / TX;
+        ys[0] = by;
+        ys[1] = wrapi(j0 - 2, ny) / TY;
+        ys[2] = wrapi(j0 - 1, ny) / TY;
+        ys[3] = wrapi(j0 + hgt, ny) / TY;
+        ys[4] = wrapi(j0 + hgt + 1, ny) / TY;
+#pragma unroll
+        for (int c = 0; c < 5; c++) {
+            bool ux_ = true, uy_ = true;
+#pragma unroll
+            for (int d = 0; d < c; d++) {
+                ux_ = ux_ && xs[d] != xs[c];
+                uy_ = uy_ && ys[d] != ys[c];
+            }
+            ux[c] = ux_;
+            uy[c] = uy_;
+        }
+    }
+    // whether every cell of the 2-ring region is pure liquid in logical plane k (clamped to the
+    // domain: the zero-gradient mirror) according to the liquid map
+    __device__ __forceinline__ bool liquid(const unsigned char *__restrict__ tmap, int tgx, int ntl, int nz, int zbase,
+                                           int k) const
+    {
+        const int kc = k < 0 ? 0 : (k >= nz ? nz - 1 : k);
+        const int sp = kc + zbase >= nz ? kc + zbase - nz : kc + zbase;
+        const unsigned char *m = tmap + (size_t)sp * ntl;
+        bool ok = true;
+#pragma unroll
+        for (int r = 0; r < 5; r++)
+#pragma unroll
+            for (int c = 0; c < 5; c++)
+                if (uy[r] && ux[c]) ok = ok & (m[ys[r] * tgx + xs[c]] == 1);
+        return ok;
+    }
+};
+
+// Lean / general split of the z chunk [z0, z1) of tile (bx, by).  Plane q is lean when phi^n is
+// pure liquid (liquid map of the source field) on the tile's 2-ring region over the planes
+// q-2 .. q+2: then phi^{n+1}(q) = phi^n(q) = e_l and every mu face of the plane takes the quiet
+// form (constant mobility, no anti-trapping current).  With kmin / kmax the lowest / highest plane
+// of z0-2 .. z1+1 that is not pure liquid, the lean planes are [z0, lo_end) and [hi_beg, z1); the
+// general path runs on [lo_end, hi_beg).
+__device__ __forceinline__ void split_from(int z0, int z1, int kmin, int kmax, int &lo_end, int &hi_beg)
+{
+    lo_end = kmin == INT_MAX ? z1 : max(z0, min(z1, kmin - 2));
+    hi_beg = kmin == INT_MAX ? z1 : min(z1, max(lo_end, kmax + 3));
+}
+// CTA-wide (all NTH threads call it; one barrier); kred is NTH/32 pairs of shared ints.
 template <int TX, int TY, int NTH>
 __device__ __forceinline__ void lean_split(const unsigned char *__restrict__ tmap_in, int tgx, int tgy, int nx, int ny,
                                            int nz, int zbase, int bx, int by, int z0, int z1, int (*kred)[2],
                                            int &lo_end, int &hi_beg)
 {
     const int tid = threadIdx.x;
-    const int i0 = bx * TX, j0 = by * TY;
-    const int ntl = tgx * tgy;
-    // tiles that hold the 2-ring region: own, and those of the columns i0-2, i0-1, i0+w, i0+w+1
-    // (rows alike) -- with a narrow last tile these can lie two tiles away
-    const int w = min(TX, nx - i0), hgt = min(TY, ny - j0);
-    const int xa = wrapi(i0 - 2, nx) / TX, xb = wrapi(i0 - 1, nx) / TX, xc = wrapi(i0 + w, nx) / TX,
-              xd = wrapi(i0 + w + 1, nx) / TX;
-    const int ya = wrapi(j0 - 2, ny) / TY, yb = wrapi(j0 - 1, ny) / TY, yc = wrapi(j0 + hgt, ny) / TY,
-              yd = wrapi(j0 + hgt + 1, ny) / TY;
-    // one entry per distinct tile: a candidate is skipped when an earlier one names the same tile
-    const bool ux[5] = {true, xa != bx, xb != bx && xb != xa, xc != bx && xc != xa && xc != xb,
-                        xd != bx && xd != xa && xd != xb && xd != xc};
-    const bool uy[5] = {true, ya != by, yb != by && yb != ya, yc != by && yc != ya && yc != yb,
-                        yd != by && yd != ya && yd != yb && yd != yc};
+    const RingTiles<TX, TY> rt(nx, ny, bx, by);
     int kmin = INT_MAX, kmax = INT_MIN;
-    for (int k = z0 - 2 + tid; k < z1 + 2; k += NTH) {
-        const int kc = k < 0 ? 0 : (k >= nz ? nz - 1 : k);
-        const int sp = kc + zbase >= nz ? kc + zbase - nz : kc + zbase;
-        const unsigned char *m = tmap_in + (size_t)sp * ntl;
-        bool ok = true;
-#pragma unroll
-        for (int r = 0; r < 5; r++) {
-            const int yy = r == 0 ? by : (r == 1 ? ya : (r == 2 ? yb : (r == 3 ? yc : yd)));
-#pragma unroll
-            for (int c = 0; c < 5; c++) {
-                const int xx = c == 0 ? bx : (c == 1 ? xa : (c == 2 ? xb : (c == 3 ? xc : xd)));
-                if (uy[r] && ux[c]) ok = ok & (m[yy * tgx + xx] == 1);
-            }
-        }
-        if (!ok) {
+    for (int k = z0 - 2 + tid; k < z1 + 2; k += NTH)
+        if (!rt.liquid(tmap_in, tgx, tgx * tgy, nz, zbase, k)) {
             kmin = min(kmin, k);
             kmax = max(kmax, k);
         }
-    }
     kmin = __reduce_min_sync(0xffffffffu, kmin);
     kmax = __reduce_max_sync(0xffffffffu, kmax);
     if ((tid & 31) == 0) {
@@ -1183,10 +1228,42 @@ __device__ __forceinline__ void lean_split(const unsigned char *__restrict__ tma
         kmin = min(kmin, kred[q][0]);
         kmax = max(kmax, kred[q][1]);
     }
-    lo_end = kmin == INT_MAX ? z1 : max(z0, min(z1, kmin - 2));
-    hi_beg = kmin == INT_MAX ? z1 : min(z1, max(lo_end, kmax + 3));
+    split_from(z0, z1, kmin, kmax, lo_end, hi_beg);
 }
 
+// Plan of a fused step with the lean kernel: one CTA per (tile, z chunk) item (item = bz * tiles
+// + tile, the fused grid's CTA order), one thread per plane of the chunk and its 2-plane margins,
+// computes the item's split; items with general planes are appended to glist (count in
+// stats->gcount) for general_step_kernel, the partials of the others are zeroed (their planes are
+// all lean: no liquid deficit, no general-path value).
+template <int TX, int TY>
+__global__ void __launch_bounds__(256) plan_kernel(int nx, int ny, int nz, int tgx, int tgy, int zchunk, int gz,
+                                                   const DevState *__restrict__ st,
+                                                   const unsigned char *__restrict__ tmap_in, int2 *__restrict__ splits,
+                                                   int *__restrict__ glist, LeanStats *__restrict__ stats,
+                                                   Partial *__restrict__ parts)
+{
+    __shared__ int kred[8][2];
+    const int ntl = tgx * tgy;
+    const int item = blockIdx.x;
+    const int bz = item / ntl, tile = item % ntl, bx = tile % tgx, by = tile / tgx;
+    const int z0 = bz * zchunk, z1 = min(z0 + zchunk, nz);
+    int lo_end, hi_beg;
+    lean_split<TX, TY, 256>(tmap_in, tgx, tgy, nx, ny, nz, st->zbase, bx, by, z0, z1, kred, lo_end, hi_beg);
+    if (threadIdx.x == 0) {
+        splits[item] = make_int2(lo_end, hi_beg);
+        if (hi_beg > lo_end) {
+            glist[atomicAdd(&stats->gcount, 1u)] = item;
+        } else {
+            Partial z;
+            z.liq_deficit = z.nonfinite = z.bytes = z.timeout = 0.0;
+            parts[item] = z;
+        }
+    }
+}
+
+// One CTA's work of the fused step: tile (bx, by) of x-y columns, z chunk bz.  Shared by the
+// single-domain kernel (tile = block index) and the batched persistent kernel (tile = work item).
 template <typename R, int TX, int TY>
 __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__restrict__ phi,
                                            const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
@@ -1194,7 +1271,8 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
                                            const PlaneT<R> *__restrict__ tab, Partial *__restrict__ part, int bx,
                                            int by, int bz, unsigned char *__restrict__ smem_raw,
                                            const unsigned char *__restrict__ tmap_in,
-                                           unsigned char *__restrict__ tmap_out, bool lean_here = true)
+                                           unsigned char *__restrict__ tmap_out, bool lean_here = true,
+                                           const int2 *__restrict__ split = nullptr)
 {
     constexpr int NT = TX * TY;
     constexpr int SX = TX + 2, SY = TY + 2, SN = SX * SY, NR = SN - NT;  // tile + 1-ring
@@ -1267,11 +1345,17 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
 
     // ---- lean segments (see lean_split): they need no shared memory and no barrier.  With
     // lean_here = false they belong to lean_step_kernel, launched beside this one, and this CTA
-    // runs only the general planes between them.
+    // runs only the general planes between them (split: the chunk's split, precomputed by
+    // plan_kernel).
     bool bad = false;
     if (tmap_in) {
         int lo_end, hi_beg;
-        lean_split<TX, TY, NT>(tmap_in, kp.tgx, kp.tgy, nx, ny, nz, zbase, bx, by, z0, z1, kred, lo_end, hi_beg);
+        if (split) {
+            lo_end = split->x;
+            hi_beg = split->y;
+        } else {
+            lean_split<TX, TY, NT>(tmap_in, kp.tgx, kp.tgy, nx, ny, nz, zbase, bx, by, z0, z1, kred, lo_end, hi_beg);
+        }
         const int i = i0 + tx, j = j0 + ty;
         const int cxm = wrapi(j, ny) * nx + wrapi(i - 1, nx), cxp = wrapi(j, ny) * nx + wrapi(i + 1, nx);
         const int cym = wrapi(j - 1, ny) * nx + wrapi(i, nx), cyp = wrapi(j + 1, ny) * nx + wrapi(i, nx);
@@ -1705,6 +1789,34 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) fused_step_ker
                           smem_raw, tmap_in, tmap_out, lean_here != 0);
 }
 
+// The general planes of a fused step whose lean planes run in lean_step_kernel: persistent CTAs
+// take the (tile, chunk) items that plan_kernel listed, one at a time, and run the general path on
+// each item's precomputed range.
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) general_step_kernel(
+    const KParams<R> kp, const Ph<R> *__restrict__ phi, const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
+    Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st, const PlaneT<R> *__restrict__ tab,
+    Partial *__restrict__ partials, const unsigned char *__restrict__ tmap_in, unsigned char *__restrict__ tmap_out,
+    const int2 *__restrict__ splits, const int *__restrict__ glist, LeanStats *__restrict__ stats)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    const int ntl = kp.tgx * kp.tgy;
+    for (;;) {
+        __syncthreads();  // the previous item is done with s_item and the shared rings
+        if (threadIdx.x == 0) {
+            const unsigned it = atomicAdd(&stats->gnext, 1u);
+            s_item = it < *(volatile unsigned *)&stats->gcount ? glist[it] : -1;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item < 0) break;
+        const int bz = item / ntl, tile = item % ntl;
+        fused_tile<R, TX, TY>(kp, phi, mu, phi_out, mu_out, st, tab, partials + item, tile % kp.tgx, tile / kp.tgx,
+                              bz, smem_raw, tmap_in, tmap_out, false, splits + item);
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // batched step: many independent domains of uneven size in one persistent launch.  Each CTA
 // pulls (domain, tile, z chunk) work items from a table through an atomic counter (largest
@@ -1773,7 +1885,8 @@ __device__ __forceinline__ void make_plane(const KParams<R> &kp, double zc, doub
 // values, and decide the moving-window shift (reading R11).
 template <typename R>
 __device__ __forceinline__ void finalize_body(const KParams<R> &kp, DevState *__restrict__ st,
-                                              const Partial *__restrict__ parts, int nparts)
+                                              const Partial *__restrict__ parts, int nparts,
+                                              LeanStats *__restrict__ lean = nullptr)
 {
     __shared__ double sa[256], sb[256];
     __shared__ int s_to;
@@ -1799,8 +1912,19 @@ __device__ __forceinline__ void finalize_body(const KParams<R> &kp, DevState *__
     }
     if (threadIdx.x == 0) {
         st->t = st->t + kp.dt64;
-        if (sb[0] > 0.0 && st->nonfinite == 0) st->nonfinite = 1;
-        if (s_to) st->nonfinite = 2;
+        bool bad = sb[0] > 0.0, tmo = s_to != 0;
+        if (lean) {  // the lean kernel's flags and bytes of this step
+            bad = bad || lean->nonfinite != 0;
+            tmo = tmo || lean->timeout != 0;
+            lean->last_bytes = lean->bytes;
+            lean->bytes = 0ull;
+            lean->nonfinite = 0;
+            lean->timeout = 0;
+            lean->gcount = 0u;
+            lean->gnext = 0u;
+        }
+        if (bad && st->nonfinite == 0) st->nonfinite = 1;
+        if (tmo) st->nonfinite = 2;
         const double h = sa[0] / ((double)kp.nx * (double)kp.ny);
         st->h_int = h;
         int s = 0;
@@ -1822,9 +1946,10 @@ __device__ __forceinline__ void finalize_body(const KParams<R> &kp, DevState *__
 
 template <typename R>
 __global__ void __launch_bounds__(256) finalize_kernel(const KParams<R> kp, DevState *__restrict__ st,
-                                                      const Partial *__restrict__ parts, int nparts)
+                                                      const Partial *__restrict__ parts, int nparts,
+                                                      LeanStats *__restrict__ lean)
 {
-    finalize_body(kp, st, parts, nparts);
+    finalize_body(kp, st, parts, nparts, lean);
 }
 
 // one block per domain
@@ -2199,28 +2324,73 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
     return cudaGetLastError();
 }
 
-constexpr int kLeanStages = 6;
+constexpr int kLeanStages = 8, kLeanMaxSub = 64, kLeanRows = 4;
+
+template <typename R>
+cudaError_t launch_plan(const KParams<R> &kp, const Geometry &g, const DevState *st, const unsigned char *tmap_in,
+                        int2 *splits, int *glist, LeanStats *stats, Partial *parts, cudaStream_t s)
+{
+    if (kp.tgx != g.gx || kp.tgy != g.gy) return cudaErrorInvalidValue;
+    const int items = g.gx * g.gy * g.gz;
+    plan_kernel<kTX, kTY><<<items, 256, 0, s>>>(kp.nx, kp.ny, kp.nz, kp.tgx, kp.tgy, kp.zchunk, g.gz, st, tmap_in,
+                                               splits, glist, stats, parts);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_general_step(const KParams<R> &kp, const void *phi, const void *mu, void *phi_out, void *mu_out,
+                                const DevState *st, const PlaneT<R> *tab, Partial *parts,
+                                const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits,
+                                const int *glist, LeanStats *stats, int ctas, cudaStream_t s)
+{
+    static bool attr = false;
+    const size_t sm = fused_smem_bytes<R>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(general_step_kernel<R, kTX, kTY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    general_step_kernel<R, kTX, kTY><<<ctas, kTX * kTY, sm, s>>>(kp, (const Ph<R> *)phi, (const Mu<R> *)mu,
+                                                                (Ph<R> *)phi_out, (Mu<R> *)mu_out, st, tab, parts,
+                                                                tmap_in, tmap_out, splits, glist, stats);
+    return cudaGetLastError();
+}
+
+template <typename R>
+int general_ctas_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, general_step_kernel<R, kTX, kTY>, kTX * kTY,
+                                                      fused_smem_bytes<R>()) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
 
 template <typename R>
 cudaError_t launch_lean_step(const KParams<R> &kp, const Geometry &g, int nsub, const void *mu_map, const void *mu,
-                             void *phi_out, void *mu_out, const DevState *st, const PlaneT<R> *tab, Partial *parts,
-                             cudaStream_t s, const unsigned char *tmap_in, unsigned char *tmap_out)
+                             void *phi_out, void *mu_out, const DevState *st, LeanStats *stats, cudaStream_t s,
+                             const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits)
 {
     using L = LeanLayout<R, kTX, kTY>;
-    if (!mu_map || !tmap_in || !tmap_out || nsub < 1 || kp.tgx != g.gx || kp.tgy != g.gy) return cudaErrorInvalidValue;
+    if (!mu_map || !tmap_in || !tmap_out || !splits || nsub < 1 || kp.tgx != g.gx || kp.tgy != g.gy)
+        return cudaErrorInvalidValue;
+    if ((kp.zchunk + nsub - 1) / nsub > kLeanMaxSub) return cudaErrorInvalidValue;  // planes per lean CTA
     if (sizeof(R) == 4 && (kp.nx & 1)) return cudaErrorInvalidValue;  // rows must be 16-byte multiples
     static bool attr = false;
     const size_t sm = L::smem_bytes(kLeanStages);
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(lean_step_kernel<R, kTX, kTY, kLeanStages>,
+        cudaError_t e = cudaFuncSetAttribute(lean_step_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid(g.gx, g.gy, g.gz * nsub);
-    lean_step_kernel<R, kTX, kTY, kLeanStages><<<grid, kTX * kTY + 32, sm, s>>>(
+    lean_step_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows><<<grid, kTX * kTY / kLeanRows + 32, sm, s>>>(
         kp, *reinterpret_cast<const CUtensorMap *>(mu_map), (const Mu<R> *)mu, (Ph<R> *)phi_out, (Mu<R> *)mu_out, st,
-        tab, parts, tmap_in, tmap_out, nsub);
+        stats, tmap_out, splits, nsub);
     return cudaGetLastError();
 }
 
@@ -2299,9 +2469,10 @@ int fused_ctas_per_sm()
 }
 
 template <typename R>
-cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s)
+cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s,
+                            LeanStats *lean)
 {
-    finalize_kernel<R><<<1, 256, 0, s>>>(kp, st, parts, nparts);
+    finalize_kernel<R><<<1, 256, 0, s>>>(kp, st, parts, nparts, lean);
     return cudaGetLastError();
 }
 
@@ -2366,12 +2537,21 @@ cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, v
     template cudaError_t launch_classify<R>(const KParams<R> &, const DevState *, const void *, unsigned char *, \
                                             cudaStream_t);                                                       \
     template cudaError_t launch_lean_step<R>(const KParams<R> &, const Geometry &, int, const void *, const void *, \
-                                             void *, void *, const DevState *, const PlaneT<R> *, Partial *,      \
-                                             cudaStream_t, const unsigned char *, unsigned char *);                \
+                                             void *, void *, const DevState *, LeanStats *, cudaStream_t,          \
+                                             const unsigned char *, unsigned char *, const int2 *);                \
+    template cudaError_t launch_plan<R>(const KParams<R> &, const Geometry &, const DevState *,                  \
+                                        const unsigned char *, int2 *, int *, LeanStats *, Partial *,            \
+                                        cudaStream_t);                                                           \
+    template cudaError_t launch_general_step<R>(const KParams<R> &, const void *, const void *, void *, void *,  \
+                                                const DevState *, const PlaneT<R> *, Partial *,                  \
+                                                const unsigned char *, unsigned char *, const int2 *, const int *, \
+                                                LeanStats *, int, cudaStream_t);                                 \
+    template int general_ctas_per_sm<R>();                                                                       \
     template cudaError_t launch_batched_step<R>(const BatchDomain<R> *, int, const BatchItem *, int, unsigned *, \
                                                 int, int, int, cudaStream_t);                                    \
     template int fused_ctas_per_sm<R>();                                                                         \
-    template cudaError_t launch_finalize<R>(const KParams<R> &, DevState *, const Partial *, int, cudaStream_t); \
+    template cudaError_t launch_finalize<R>(const KParams<R> &, DevState *, const Partial *, int, cudaStream_t,   \
+                                            LeanStats *);                                                        \
     template cudaError_t launch_post<R>(const KParams<R> &, const DevState *, void *, void *, PlaneT<R> *,       \
                                         cudaStream_t, void *, void *, unsigned char *);                          \
     template cudaError_t launch_init<R>(const KParams<R> &, void *, void *, const double *, int, int,            \

@@ -51,6 +51,18 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
         : "memory");
     return done != 0;
 }
+// As mbar_test, but a thread whose phase is not complete is suspended until it completes or about
+// hint_ns nanoseconds have passed, so a waiting warp takes no issue slots from the others.
+__device__ __forceinline__ bool mbar_test_suspend(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return done != 0;
+}
 // Bounded wait for the completion of the phase with the given parity.  Gives up after about 2^31
 // clock cycles (about a second) and raises *abort, or as soon as another thread has raised it.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
@@ -58,7 +70,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
-        if (mbar_test(bar, parity)) return true;
+        if (mbar_test_suspend(bar, parity, 1000u)) return true;
         if (*abort) return false;
         if (clock64() - t0 > (1LL << 31)) {
             *abort = 1;
@@ -107,22 +119,46 @@ struct LeanLayout {
     static constexpr size_t smem_bytes(int stages) { return (size_t)stages * STAGE_BYTES + 128; }
 };
 
-template <typename R, int TX, int TY, int LD>
-__global__ void __launch_bounds__(TX *TY + 32) lean_step_kernel(
+// shared-memory load of one mu cell at a byte offset (cells are 8- / 16-byte aligned)
+template <typename R>
+__device__ __forceinline__ Mu<R> lds_cell(const unsigned char *p)
+{
+    Mu<R> m;
+    if constexpr (sizeof(R) == 4) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        m.v[0] = v.x;
+        m.v[1] = v.y;
+    } else {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        m.v[0] = v.x;
+        m.v[1] = v.y;
+    }
+    return m;
+}
+
+// Grid (tgx, tgy, gz * nsub): tile (bx, by) of the fused step's grid, z chunk blockIdx.z / nsub,
+// and of that chunk the sub-chunk blockIdx.z % nsub of at most MAXSUB planes.  The CTA updates the
+// chunk's lean planes (its split, from plan_kernel) that fall into its sub-chunk.  TY/ROWS consumer warps own ROWS
+// consecutive tile rows each (lane = tile column), one producer warp feeds them.
+template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS>
+__global__ void __launch_bounds__(TX *TY / ROWS + 32, 6) lean_step_kernel(
     const KParams<R> kp, const __grid_constant__ CUtensorMap mu_map, const Mu<R> *__restrict__ mu,
     Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st,
-    const PlaneT<R> *__restrict__ tab, Partial *__restrict__ parts, const unsigned char *__restrict__ tmap_in,
-    unsigned char *__restrict__ tmap_out, int nsub)
+    LeanStats *__restrict__ stats, unsigned char *__restrict__ tmap_out, const int2 *__restrict__ splits, int nsub)
 {
     using L = LeanLayout<R, TX, TY>;
-    constexpr int NC = TX * TY, NTH = NC + 32;
-    static_assert(TX == 32 && TY <= 32, "one warp per tile row; halo rows fit a warp");
+    static_assert(TY % ROWS == 0, "whole rows per consumer warp");
+    constexpr int NCW = TY / ROWS, NC = 32 * NCW, NTH = NC + 32;
+    constexpr int CB = (int)sizeof(Mu<R>);
+    static_assert(TX == 32 && TY % 2 == 0 && TY <= 32 && (LD & (LD - 1)) == 0, "layout");
+    constexpr int LDLOG = LD == 2 ? 1 : (LD == 4 ? 2 : (LD == 8 ? 3 : 4));
+    static_assert((1 << LDLOG) == LD, "LD: 2, 4, 8 or 16");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *stage_base =  // [LD][STAGE_BYTES], 128-byte aligned
         smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t full[LD], empty[LD];
-    __shared__ int kred[NTH / 32][2];
     __shared__ int s_abort, s_bad;
+    __shared__ unsigned char s_dst_liquid[MAXSUB];  // destination map entries of the sub-chunk's planes
 
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     const int tid = threadIdx.x;
@@ -139,19 +175,31 @@ __global__ void __launch_bounds__(TX *TY + 32) lean_step_kernel(
         const int sp = k + zbase;
         return sp >= nz ? sp - nz : sp;
     };
+    // producer lane l copies periodic images outside the tensor box: x = -1 and x = nx of tile row
+    // l, y = -1 and y = ny of tile column l (only at the domain's edges)
+    auto fixes = [&](int l) {
+        const bool row = l < TY && j0 + l < ny, colv = i0 + l < nx;
+        return (bx == 0 && row) || (i0 + TX >= nx && row) || (by == 0 && colv) || (j0 + TY >= ny && colv);
+    };
 
+    // (the launch guarantees s1 - s0 <= MAXSUB) the destination's map entries, read before any is
+    // replaced
+    for (int q = s0 + tid; q < s1; q += NTH) s_dst_liquid[q - s0] = tmap_out[(size_t)splane(q) * ntl + tile];
     if (tid == 0) {
+        int nfix = 0;
+        for (int l = 0; l < 32; l++) nfix += fixes(l) ? 1 : 0;
         for (int s = 0; s < LD; s++) {
-            mbar_init(&full[s], 1 + 32);  // the producer's expect-tx arrival + one per producer lane
-            mbar_init(&empty[s], TY);     // one per consumer warp
+            mbar_init(&full[s], 1 + nfix);  // the producer's expect-tx arrival + one per copying lane
+            mbar_init(&empty[s], NCW);      // one per consumer warp
         }
         s_abort = 0;
         s_bad = 0;
         fence_proxy_async_shared();
     }
-    // (lean_split's barrier publishes the initialisation)
-    int lo_end, hi_beg;
-    lean_split<TX, TY, NTH>(tmap_in, kp.tgx, kp.tgy, nx, ny, nz, zbase, bx, by, z0, z1, kred, lo_end, hi_beg);
+    // the chunk's split (plan_kernel)
+    const int2 sp2 = splits[(size_t)chunk * ntl + tile];
+    const int lo_end = sp2.x, hi_beg = sp2.y;
+    __syncthreads();  // barrier initialisation and destination map entries
     // this CTA's planes: the lean planes of the chunk that fall into its sub-chunk [s0, s1)
     int qa[2], qb[2];
     qa[0] = s0;
@@ -162,6 +210,7 @@ __global__ void __launch_bounds__(TX *TY + 32) lean_step_kernel(
     if (tid >= NC) {
         // ---------------- producer warp ----------------
         const int lane = tid - NC;
+        const bool fix = fixes(lane);
         unsigned u = 0;  // stage uses issued
         bool ok = true;
         for (int g = 0; g < 2 && ok; g++) {
@@ -169,28 +218,30 @@ __global__ void __launch_bounds__(TX *TY + 32) lean_step_kernel(
             // planes qa-1 (its mu for the z flux below qa) .. qb (for the z flux above qb-1)
             const int la = max(qa[g] - 1, 0), lb = min(qb[g], nz - 1);
             for (int p = la; p <= lb; p++, u++) {
-                const int s = u % LD;
+                const int s = u & (LD - 1);
                 if (u >= LD) {
-                    ok = mbar_wait(&empty[s], ((u / LD) - 1) & 1, &s_abort);
+                    ok = mbar_wait(&empty[s], ((u >> LDLOG) - 1) & 1, &s_abort);
                     ok = __all_sync(0xffffffffu, ok);
                     if (!ok) break;
                 }
-                Mu<R> *stg = reinterpret_cast<Mu<R> *>(stage_base + s * L::STAGE_BYTES);
+                unsigned char *stg = stage_base + s * L::STAGE_BYTES;
                 const int sp = splane(p);
                 if (lane == 0) {
                     mbar_arrive_expect_tx(&full[s], L::BOX_BYTES);
                     tma_load_3d(stg, &mu_map, &full[s], 2 * (i0 - 2), j0 - 1, sp);
                 }
-                const Mu<R> *mp = mu + (size_t)sp * plane;
-                Mu<R> *fix = stg + L::BOX;
-                if (bx == 0 && lane < TY && j0 + lane < ny)
-                    cp_async_bytes<sizeof(Mu<R>)>(fix + lane, mp + (size_t)(j0 + lane) * nx + (nx - 1));
-                if (i0 + TX >= nx && lane < TY && j0 + lane < ny)
-                    cp_async_bytes<sizeof(Mu<R>)>(fix + 32 + lane, mp + (size_t)(j0 + lane) * nx);
-                if (by == 0 && i0 + lane < nx)
-                    cp_async_bytes<sizeof(Mu<R>)>(fix + 64 + lane, mp + (size_t)(ny - 1) * nx + i0 + lane);
-                if (j0 + TY >= ny && i0 + lane < nx) cp_async_bytes<sizeof(Mu<R>)>(fix + 96 + lane, mp + i0 + lane);
-                cp_async_arrive_noinc(&full[s]);
+                if (fix) {
+                    const Mu<R> *mp = mu + (size_t)sp * plane;
+                    Mu<R> *fx = reinterpret_cast<Mu<R> *>(stg + L::BOX_BYTES);
+                    if (bx == 0 && lane < TY && j0 + lane < ny)
+                        cp_async_bytes<CB>(fx + lane, mp + (size_t)(j0 + lane) * nx + (nx - 1));
+                    if (i0 + TX >= nx && lane < TY && j0 + lane < ny)
+                        cp_async_bytes<CB>(fx + 32 + lane, mp + (size_t)(j0 + lane) * nx);
+                    if (by == 0 && i0 + lane < nx)
+                        cp_async_bytes<CB>(fx + 64 + lane, mp + (size_t)(ny - 1) * nx + i0 + lane);
+                    if (j0 + TY >= ny && i0 + lane < nx) cp_async_bytes<CB>(fx + 96 + lane, mp + i0 + lane);
+                    cp_async_arrive_noinc(&full[s]);
+                }
             }
         }
         cp_async_wait_all();
@@ -198,98 +249,145 @@ __global__ void __launch_bounds__(TX *TY + 32) lean_step_kernel(
             // drain: the tensor copies of the last LD uses may still be landing in shared memory
             for (unsigned v = u > (unsigned)LD ? u - LD : 0; v < u; v++) {
                 const long long t0 = clock64();
-                while (!mbar_test(&full[v % LD], (v / LD) & 1) && clock64() - t0 < (1LL << 31)) {
+                while (!mbar_test(&full[v & (LD - 1)], (v >> LDLOG) & 1) && clock64() - t0 < (1LL << 31)) {
                 }
             }
         }
         return;
     }
 
-    // ---------------- consumer warps: thread (tx, ty) owns column (i0 + tx, j0 + ty) ----------------
-    const int tx = tid % TX, ty = tid / TX, lane = tid & 31;
-    const int i = i0 + tx, j = j0 + ty;
-    const bool valid = i < nx && j < ny;
-    const size_t col = valid ? (size_t)j * nx + i : 0;
-    const int own = (ty + 1) * L::BW + tx + 2;
+    // ---------------- consumer warps: lane = tile column, warp w = tile rows w*ROWS .. w*ROWS+ROWS-1 ----------------
+    const int lane = tid & 31, w = tid >> 5;
+    const int i = i0 + lane, jr0 = j0 + w * ROWS;
+    // byte offsets within a stage: own cells (row r at own0 + r * BW cells), their x neighbours,
+    // the cell below row 0 and the cell above each row; a neighbour across the domain edge is its
+    // periodic image in the stage's wrapped-cell rows
+    const int own0 = ((w * ROWS + 1) * L::BW + lane + 2) * CB;
+    const int fixx0 = L::BOX_BYTES, fixx1 = fixx0 + 32 * CB, fixy0 = fixx1 + 32 * CB, fixy1 = fixy0 + 32 * CB;
+    int oxm[ROWS], oxp[ROWS], oyu[ROWS];
+    bool vr[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; r++) {
+        const int own = own0 + r * L::BW * CB, tyr = w * ROWS + r, j = jr0 + r;
+        vr[r] = i < nx && j < ny;
+        oxm[r] = i == 0 ? fixx0 + tyr * CB : own - CB;
+        oxp[r] = i == nx - 1 ? fixx1 + tyr * CB : own + CB;
+        oyu[r] = j == ny - 1 ? fixy1 + lane * CB : own + L::BW * CB;
+    }
+    const int oyb = jr0 == 0 ? fixy0 + lane * CB : own0 - L::BW * CB;
+    const size_t col0 = (size_t)jr0 * nx + (size_t)min(i, nx - 1);
     Ph<R> liquid;
     liquid.v[0] = liquid.v[1] = liquid.v[2] = R(0);
     liquid.v[3] = R(1);
-    bool bad = false, ok = true;
+    bool ok = true;
+    R acc = R(0);  // sum of the updated values: non-finite iff one of them is
     int phi_stores = 0, planes = 0;
     unsigned u = 0;  // stage uses consumed
     for (int g = 0; g < 2 && ok; g++) {
         if (qb[g] <= qa[g]) continue;
         const int la = max(qa[g] - 1, 0), lb = min(qb[g], nz - 1);
-        const unsigned ub = u;
-        auto stg = [&](int p) {
-            return reinterpret_cast<const Mu<R> *>(stage_base + ((ub + (unsigned)(p - la)) % LD) * L::STAGE_BYTES);
+        // use v holds plane la + (v - u): stage v mod LD, phase parity (v / LD) mod 2
+        auto stg = [&](unsigned v) { return (const unsigned char *)stage_base + (v & (LD - 1)) * L::STAGE_BYTES; };
+        auto wait_use = [&](unsigned v) {
+            return __all_sync(0xffffffffu, mbar_wait(&full[v & (LD - 1)], (v >> LDLOG) & 1, &s_abort));
         };
-        auto wait_plane = [&](int p) {
-            const unsigned v = ub + (unsigned)(p - la);
-            return __all_sync(0xffffffffu, mbar_wait(&full[v % LD], (v / LD) & 1, &s_abort));
-        };
-        auto release = [&](int p) {
+        auto release = [&](unsigned v) {
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[(ub + (unsigned)(p - la)) % LD]);
+            if (lane == 0) mbar_arrive(&empty[v & (LD - 1)]);
         };
-        Mu<R> Vz_lo;
-        Vz_lo.v[0] = Vz_lo.v[1] = R(0);
-        ok = wait_plane(la);
-        if (ok && qa[g] > 0) {  // la = qa - 1: only the z flux below qa
-            ok = wait_plane(qa[g]);
+        unsigned v = u;  // use of the plane being updated
+        Mu<R> m[ROWS], zlo[ROWS];  // mu^n of the cells, the fluxes of their lower z faces
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) zlo[r].v[0] = zlo[r].v[1] = R(0);
+        ok = wait_use(v);
+        if (ok && qa[g] > 0) {  // plane qa - 1: only the z fluxes below qa
+            ok = wait_use(v + 1);
             if (ok) {
-                Vz_lo = quiet_zflux(kp, stg(la)[own], stg(qa[g])[own]);
-                release(la);
+                const unsigned char *S0 = stg(v), *S1 = stg(v + 1);
+#pragma unroll
+                for (int r = 0; r < ROWS; r++)
+                    zlo[r] = quiet_flux(kp, lds_cell<R>(S0 + own0 + r * L::BW * CB),
+                                        lds_cell<R>(S1 + own0 + r * L::BW * CB));
+                release(v);
+                v++;
             }
         }
-        for (int q = qa[g]; q < qb[g] && ok; q++) {
-            const Mu<R> *B = stg(q);
-            const Mu<R> *F = B + L::BOX;
-            const Mu<R> mP = B[own];
-            Mu<R> Vz_hi;
-            Vz_hi.v[0] = Vz_hi.v[1] = R(0);
-            if (q < nz - 1) {
-                ok = wait_plane(q + 1);
-                if (!ok) break;
-                Vz_hi = quiet_zflux(kp, mP, stg(q + 1)[own]);
+        if (ok) {
+#pragma unroll
+            for (int r = 0; r < ROWS; r++) m[r] = lds_cell<R>(stg(v) + own0 + r * L::BW * CB);
+        }
+        for (int q = qa[g]; q < qb[g] && ok; q++, v++) {
+            const unsigned char *S = stg(v);
+            Mu<R> mn[ROWS], zhi[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS; r++) {
+                mn[r] = m[r];
+                zhi[r].v[0] = zhi[r].v[1] = R(0);
             }
-            const Mu<R> xm = i == 0 ? F[ty] : B[own - 1];
-            const Mu<R> xp = i == nx - 1 ? F[32 + ty] : B[own + 1];
-            const Mu<R> ym = j == 0 ? F[64 + tx] : B[own - L::BW];
-            const Mu<R> yp = j == ny - 1 ? F[96 + tx] : B[own + L::BW];
-            const Mu<R> out = quiet_mu_cell(kp, tab + q, mP, xm, xp, ym, yp, Vz_lo, Vz_hi);
-            release(q);
-            const int sp = splane(q);
-            const bool store_phi = tmap_out[(size_t)sp * ntl + tile] != 1;
+            if (q < nz - 1) {
+                ok = wait_use(v + 1);
+                if (!ok) break;
+                const unsigned char *N = stg(v + 1);
+#pragma unroll
+                for (int r = 0; r < ROWS; r++) {
+                    mn[r] = lds_cell<R>(N + own0 + r * L::BW * CB);
+                    zhi[r] = quiet_flux(kp, m[r], mn[r]);
+                }
+            }
+            Mu<R> xm[ROWS], xp[ROWS], yu[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS; r++) {
+                xm[r] = lds_cell<R>(S + oxm[r]);
+                xp[r] = lds_cell<R>(S + oxp[r]);
+                yu[r] = lds_cell<R>(S + oyu[r]);
+            }
+            const Mu<R> yb = lds_cell<R>(S + oyb);
+            release(v);
+            // the y face between rows r and r+1 is evaluated once, from the same operands both
+            // cells would use
+            Mu<R> fy_lo = quiet_flux(kp, yb, m[0]);
+            Mu<R> out[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS; r++) {
+                const Mu<R> fy_hi = quiet_flux(kp, m[r], yu[r]);
+                out[r] = quiet_mu_update(kp, m[r], quiet_flux(kp, xm[r], m[r]), quiet_flux(kp, m[r], xp[r]), fy_lo,
+                                         fy_hi, zlo[r], zhi[r]);
+                fy_lo = fy_hi;
+            }
+            const bool store_phi = s_dst_liquid[q - s0] != 1;
             phi_stores += store_phi ? 1 : 0;
             planes++;
-            if (valid) {
-                if (store_phi) st_ph(phi_out + (size_t)sp * plane + col, liquid);
-                st_mu(mu_out + (size_t)sp * plane + col, out);
-                bad = bad | !isfinite(out.v[0] + out.v[1]);
+            const size_t o = (size_t)splane(q) * plane + col0;
+#pragma unroll
+            for (int r = 0; r < ROWS; r++) {
+                if (vr[r]) {
+                    if (store_phi) st_ph(phi_out + o + (size_t)r * nx, liquid);
+                    st_mu(mu_out + o + (size_t)r * nx, out[r]);
+                    acc += out[r].v[0] + out[r].v[1];
+                }
+                zlo[r] = zhi[r];
+                m[r] = mn[r];
             }
-            Vz_lo = Vz_hi;
         }
-        if (ok && lb == qb[g]) release(lb);  // waited for the z flux of plane qb-1, not updated here
-        u = ub + (unsigned)(lb - la + 1);
+        if (ok && lb == qb[g]) release(v);  // plane qb: waited for the z flux of plane qb-1 only
+        u += (unsigned)(lb - la + 1);
     }
+    const bool bad = !isfinite(acc);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&s_bad, 1);
-    // every consumer has read the destination's map entries before any is replaced by the new
-    // field's (the lean planes of the new field are pure liquid)
-    consumer_sync<NC>();
-    // (after a timeout the planes' content is not known: 0, "not known to be pure liquid", is
-    // always a safe entry)
+    consumer_sync<NC>();  // every consumer warp has posted its flags
+    // the new field's map entries of the lean planes: pure liquid (the old entries were read at the
+    // start).  After a timeout the planes' content is not known: 0, "not known to be pure liquid",
+    // is always a safe entry.
     const unsigned char mark = s_abort ? 0 : 1;
     for (int g = 0; g < 2; g++)
         for (int q = qa[g] + tid; q < qb[g]; q += NC) tmap_out[(size_t)splane(q) * ntl + tile] = mark;
     if (tid == 0) {
-        Partial *part = parts + ((size_t)blockIdx.z * gridDim.y + by) * gridDim.x + bx;
-        const double tile_cells = (double)min(TX, nx - i0) * (double)min(TY, ny - j0);
-        part->liq_deficit = 0.0;
-        part->nonfinite = s_bad ? 1.0 : 0.0;
+        const unsigned long long tile_cells = (unsigned long long)min(TX, nx - i0) * (unsigned long long)min(TY, ny - j0);
         // mu^n in, mu^{n+1} out (4 words a cell), plus phi^{n+1} where it was stored
-        part->bytes = tile_cells * (double)sizeof(R) * 4.0 * (double)(planes + phi_stores);
-        part->timeout = s_abort ? 1.0 : 0.0;
+        const unsigned long long b = tile_cells * sizeof(R) * 4ull * (unsigned long long)(planes + phi_stores);
+        if (b) atomicAdd(&stats->bytes, b);
+        if (s_bad) atomicOr(&stats->nonfinite, 1);
+        if (s_abort) atomicOr(&stats->timeout, 1);
     }
 }
 
