@@ -155,6 +155,7 @@ enum {
     PF_K_FUSED = 4,    /* fused phi+mu step (both sweeps in one pass) */
     PF_K_LEAN = 5,     /* the fused step's pure-liquid planes (Section 3.3 shortcuts), a kernel of their own */
     PF_K_PLAN = 6,     /* the fused step's split into pure-liquid and general planes */
+    PF_K_GENERAL = 7,  /* the fused step's general planes as the two sweeps (Algorithm 1) */
     PF_K_COUNT = 8
 };
 
@@ -180,6 +181,8 @@ int pf_profile_read(pf_sim *sim, double ms[], int launches[]);
  *   PF_K_PHI / PF_K_MU (two sweeps): 10 and 12 words a cell (18 and 16 with the compensated low
  *     words), from the cell count;
  *   PF_K_FUSED: 12 words a cell on the planes of the general path, as tallied by the kernel;
+ *   PF_K_GENERAL: 22 words a cell on the general planes when they run as the two sweeps beside the
+ *     lean kernel (phi^{n+1} goes through HBM there), as tallied by the mu-sweep;
  *   PF_K_LEAN: on the pure-liquid planes (the paper's shortcuts, Section 3.3) 4 words a cell --
  *     mu^n in, mu^{n+1} out; phi^{n+1} = phi^n = e_l is known from the liquid map -- plus 4 words
  *     where phi^{n+1} is stored because the destination buffer does not hold pure liquid there

@@ -26,10 +26,14 @@ using namespace pf;
 // and whether the general planes run on a second stream beside the lean kernel (1) or before it
 // on the sim's stream (0).
 #ifndef PF_GENERAL_CTAS_PER_SM
-#define PF_GENERAL_CTAS_PER_SM 1
+#define PF_GENERAL_CTAS_PER_SM 2
 #endif
 #ifndef PF_OVERLAP_GENERAL
 #define PF_OVERLAP_GENERAL 1
+#endif
+// the general planes as the two sweeps of Algorithm 1 (1) or as the fused tile (0)
+#ifndef PF_GENERAL_SWEEPS
+#define PF_GENERAL_SWEEPS 1
 #endif
 
 // ------------------------------------------------------------------------------------------
@@ -123,6 +127,7 @@ struct pf_sim {
     DevBuf splits;      // int2 per (tile, chunk) of the fused grid: the lean / general split
     DevBuf glist;       // int per (tile, chunk): the items with general planes
     int general_ctas = 0;  // persistent CTAs of the general kernel
+    int gphi_ctas = 0, gmu_ctas = 0;  // persistent CTAs of the general planes' two sweeps
     cudaStream_t aux = nullptr;  // the fused step's general planes, concurrent with the lean kernel
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool lean_ok = false;
@@ -447,7 +452,17 @@ static int do_step_direct(pf_sim *s, int n)
                     if (e == cudaSuccess) e = cudaStreamWaitEvent(s->aux, s->ev_fork, 0);
                     gs = s->aux;
                 }
-                if (e == cudaSuccess)
+                if (e == cudaSuccess && PF_GENERAL_SWEEPS)
+                    e = timed(
+                        s, PF_K_GENERAL,
+                        [&] {
+                            return launch_general_sweeps<R>(kp, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st,
+                                                            tab, parts, tout, (const int2 *)s->splits.p,
+                                                            (const int *)s->glist.p, ls, s->gphi_ctas, s->gmu_ctas,
+                                                            gs);
+                        },
+                        gs);
+                if (e == cudaSuccess && !PF_GENERAL_SWEEPS)
                     e = timed(
                         s, PF_K_FUSED,
                         [&] {
@@ -842,11 +857,18 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        // one persistent general CTA per SM by default: the rest of each SM (a general CTA takes half
-        // of its registers) stays open to the lean kernel running beside it
+        // persistent general CTAs: PF_GENERAL_CTAS_PER_SM per SM, at most what fits (two take all of
+        // an SM's registers; the lean CTAs beside them get SMs as general CTAs finish)
         const int per_sm = std::min(PF_GENERAL_CTAS_PER_SM, p->precision == PF_FP64 ? general_ctas_per_sm<double>()
                                                                                     : general_ctas_per_sm<float>());
         s->general_ctas = std::max(1, std::min(s->geo_fused.nparts(), per_sm * sms));
+        int pp = 1, pm = 1;
+        if (p->precision == PF_FP64)
+            general_sweep_ctas_per_sm<double>(&pp, &pm);
+        else
+            general_sweep_ctas_per_sm<float>(&pp, &pm);
+        s->gphi_ctas = std::max(1, std::min(s->geo_fused.nparts(), pp * sms));
+        s->gmu_ctas = std::max(1, std::min(s->geo_fused.nparts(), pm * sms));
     }
     if (r == PF_OK) {
         cudaError_t e = cudaMemsetAsync(s->lean_stats.p, 0, sizeof(LeanStats), s->stream);
@@ -987,7 +1009,9 @@ int pf_step_bytes(pf_sim *s, double bytes[])
         e = cudaMemcpyAsync(&ls, s->lean_stats.p, sizeof ls, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return latch(s, cuda_status(e));
-    for (const Partial &x : h) bytes[PF_K_FUSED] += x.bytes;
+    double g = 0.0;
+    for (const Partial &x : h) g += x.bytes;
+    bytes[s->last_kind == 2 && PF_GENERAL_SWEEPS ? PF_K_GENERAL : PF_K_FUSED] = g;
     bytes[PF_K_LEAN] = (double)ls.last_bytes;
     return PF_OK;
 }

@@ -40,6 +40,7 @@ struct LeanStats {
     int timeout;                    // a bounded wait gave up
     unsigned long long last_bytes;  // bytes of the last finished step (read by the host)
     unsigned gcount, gnext;         // (tile, chunk) items with general planes; next one to take
+    unsigned gnext_mu, pad_;        // next item of the general planes' mu-sweep
 };
 
 // Temperature-dependent constants of one x-y plane (cell centres) or one z-face level,
@@ -150,6 +151,16 @@ cudaError_t launch_general_step(const KParams<R> &kp, const void *phi, const voi
                                 const int *glist, LeanStats *stats, int ctas, cudaStream_t s);
 template <typename R>
 int general_ctas_per_sm();
+// The general planes of the listed items as Algorithm 1's two sweeps: the phi-sweep (phi^{n+1} and
+// its liquid-map entries) and then the mu-sweep (phi^{n+1} of lean tile planes taken as e_l), each
+// by persistent CTAs over the list; the mu partials carry both sweeps' bytes (22 words a cell).
+template <typename R>
+cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const void *mu, void *phi_out, void *mu_out,
+                                  const DevState *st, const PlaneT<R> *tab, Partial *parts, unsigned char *tmap_out,
+                                  const int2 *splits, const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas,
+                                  cudaStream_t s);
+template <typename R>
+void general_sweep_ctas_per_sm(int *phi_per_sm, int *mu_per_sm);
 // liquid map of a field (for states not produced by a fused step)
 template <typename R>
 cudaError_t launch_classify(const KParams<R> &kp, const DevState *st, const void *phi, unsigned char *tmap,

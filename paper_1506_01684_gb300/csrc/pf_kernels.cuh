@@ -678,19 +678,19 @@ __device__ __forceinline__ void mu_cell_comp(const KParams<float> &kp, const Pla
 // Each thread loads its own column and, for the first 2(TX+TY)+4 threads, one halo cell; the
 // wrapped (periodic) column offsets are computed once.
 // ---------------------------------------------------------------------------------------
+// One CTA's phi-sweep of tile (bx, by), planes [z0, z1).  With tmap_out, also the new field's
+// liquid-map entries of those planes (1 when the tile's cells are exactly pure liquid).
 template <typename R, int TX, int TY, bool COMP = false>
-__global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
-                                                          const Mu<R> *__restrict__ mu,
-                                                          Ph<R> *__restrict__ phi_out,
-                                                          const DevState *__restrict__ st,
-                                                          const PlaneT<R> *__restrict__ tab,
-                                                          const Ph<R> *__restrict__ phi_lo = nullptr,
-                                                          Ph<R> *__restrict__ phi_out_lo = nullptr)
+__device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R> *__restrict__ phi,
+                                               const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
+                                               const DevState *__restrict__ st, const PlaneT<R> *__restrict__ tab,
+                                               const Ph<R> *__restrict__ phi_lo, Ph<R> *__restrict__ phi_out_lo,
+                                               int bx, int by, int z0, int z1, unsigned char *__restrict__ smem_raw,
+                                               unsigned char *__restrict__ tmap_out = nullptr)
 {
     constexpr int NT = TX * TY, SX = TX + 2, SY = TY + 2, SN = SX * SY, NR = SN - NT;
     constexpr int FX = TY * (TX + 1), FY = (TY + 1) * TX;
     static_assert(NR <= NT, "one halo cell per thread at most");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     Ph<R> *sP = reinterpret_cast<Ph<R> *>(smem_raw);  // [4][SN]
     Ph<R> *sFx = sP + 4 * SN;                          // [2][FX]
     Ph<R> *sFy = sFx + 2 * FX;                         // [2][FY]
@@ -700,10 +700,8 @@ __global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, 
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int i0 = bx * TX, j0 = by * TY;
     const bool valid = i0 + tx < nx && j0 + ty < ny;
-    const int z0 = blockIdx.z * kp.zchunk;
-    const int z1 = min(z0 + kp.zchunk, nz);
     const int zbase = st->zbase;
     const size_t plane = (size_t)nx * ny;
 
@@ -760,6 +758,7 @@ __global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, 
     prefetch(z0 + 3);
     __syncthreads();
 
+    bool out_liquid = true;
     for (int p = z0; p < z1; ++p) {
         // C(p)
         {
@@ -793,6 +792,7 @@ __global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, 
                 st_ph(phi_out + plane_off(p, nz, zbase, plane) + col0, out);
                 if constexpr (COMP) st_ph(phi_out_lo + plane_off(p, nz, zbase, plane) + col0, out_lo);
             }
+            out_liquid = !valid || (out.v[3] == R(1) && out.v[0] == R(0) && out.v[1] == R(0) && out.v[2] == R(0));
         }
         // B(p+1), A(p+3)
         Ph<R> Fz_next = Fz_cur;
@@ -803,13 +803,34 @@ __global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, 
         }
         commit(p + 3);
         prefetch(p + 4);
-        __syncthreads();
+        if (tmap_out) {
+            // the barrier also gives the map entry of the new plane p
+            const int all = __syncthreads_and(out_liquid);
+            if (tid == 0) tmap_out[plane_off(p, nz, zbase, plane) / plane * kp.tgx * kp.tgy + by * kp.tgx + bx] = all ? 1 : 0;
+        } else {
+            __syncthreads();
+        }
         pm = pc;
         pc = pn;
         pn = pnn;
         Fz_prev = Fz_cur;
         Fz_cur = Fz_next;
     }
+}
+
+template <typename R, int TX, int TY, bool COMP = false>
+__global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
+                                                          const Mu<R> *__restrict__ mu,
+                                                          Ph<R> *__restrict__ phi_out,
+                                                          const DevState *__restrict__ st,
+                                                          const PlaneT<R> *__restrict__ tab,
+                                                          const Ph<R> *__restrict__ phi_lo = nullptr,
+                                                          Ph<R> *__restrict__ phi_out_lo = nullptr)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int z0 = blockIdx.z * kp.zchunk;
+    phi_sweep_tile<R, TX, TY, COMP>(kp, phi, mu, phi_out, st, tab, phi_lo, phi_out_lo, blockIdx.x, blockIdx.y, z0,
+                                    min(z0 + kp.zchunk, kp.nz), smem_raw);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -821,21 +842,23 @@ __global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, 
 // loads of plane p+4).  phi^{n+1} sits in a 4-plane shared ring (the faces of plane q read planes
 // q-1..q+1), phi^n and mu^n in 3-plane rings; the cell update reads its own values from registers.
 // ---------------------------------------------------------------------------------------
+// One CTA's mu-sweep of tile (bx, by), planes [z0, z1); its FP64 partial sums go to *part, with
+// `words` words a cell as its algorithmic bytes.  With splits (the step's plan), phi^{n+1} of a
+// tile plane that the lean kernel updates is e_l by construction and is taken as such instead of
+// being read (the lean kernel may still be writing it).
 template <typename R, int TX, int TY, bool COMP = false>
-__global__ void __launch_bounds__(TX *TY) mu_sweep_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi_old,
-                                                         const Ph<R> *__restrict__ phi_new,
-                                                         const Mu<R> *__restrict__ mu,
-                                                         Mu<R> *__restrict__ mu_out,
-                                                         const DevState *__restrict__ st,
-                                                         const PlaneT<R> *__restrict__ tab,
-                                                         Partial *__restrict__ partials,
-                                                         const Mu<R> *__restrict__ mu_lo = nullptr,
-                                                         Mu<R> *__restrict__ mu_out_lo = nullptr)
+__device__ __forceinline__ void mu_sweep_tile(const KParams<R> &kp, const Ph<R> *__restrict__ phi_old,
+                                              const Ph<R> *__restrict__ phi_new, const Mu<R> *__restrict__ mu,
+                                              Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st,
+                                              const PlaneT<R> *__restrict__ tab, Partial *__restrict__ part,
+                                              const Mu<R> *__restrict__ mu_lo, Mu<R> *__restrict__ mu_out_lo, int bx,
+                                              int by, int z0, int z1, unsigned char *__restrict__ smem_raw,
+                                              double words, const int2 *__restrict__ splits = nullptr,
+                                              int split_zchunk = 1)
 {
     constexpr int NT = TX * TY, SX = TX + 2, SY = TY + 2, SN = SX * SY, NR = SN - NT;
     constexpr int FX = TY * (TX + 1), FY = (TY + 1) * TX;
     static_assert(NR <= NT, "one halo cell per thread at most");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     Ph<R> *sN = reinterpret_cast<Ph<R> *>(smem_raw);  // [4][SN] phi^{n+1}
     Ph<R> *sO = sN + 4 * SN;                           // [3][SN] phi^n
     Mu<R> *sM = reinterpret_cast<Mu<R> *>(sO + 3 * SN);  // [3][SN] mu^n
@@ -846,28 +869,36 @@ __global__ void __launch_bounds__(TX *TY) mu_sweep_kernel(const KParams<R> kp, c
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int i0 = bx * TX, j0 = by * TY;
     const bool valid = i0 + tx < nx && j0 + ty < ny;
-    const int z0 = blockIdx.z * kp.zchunk;
-    const int z1 = min(z0 + kp.zchunk, nz);
     const int zbase = st->zbase;
     const size_t plane = (size_t)nx * ny;
 
     const int s0 = (ty + 1) * SX + (tx + 1);
     const int col0 = wrapi(j0 + ty, ny) * nx + wrapi(i0 + tx, nx);
-    int s1 = -1, col1 = 0;
+    int s1 = -1, col1 = 0, tile1 = 0;
     if (tid < NR) {
         int li, lj;
         ring_cell<TX, TY>(tid, li, lj);
         s1 = (lj + 1) * SX + (li + 1);
-        col1 = wrapi(j0 + lj, ny) * nx + wrapi(i0 + li, nx);
+        const int wi = wrapi(i0 + li, nx), wj = wrapi(j0 + lj, ny);
+        col1 = wj * nx + wi;
+        tile1 = (wj / TY) * kp.tgx + wi / TX;  // the ring cell's tile in the plan's grid
     }
+    const int tile0 = by * kp.tgx + bx;
+    const int ntl = kp.tgx * kp.tgy;
     const bool xtra_y = ty == 0;
     const bool xtra_x = ty == 1 % TY && tx < TY;
 
     Ph<R> pfN0, pfN1, pfO0, pfO1;
     Mu<R> pfM0, pfM1;
     auto mod3 = [](int k) { return (k + 3) % 3; };  // k >= -3
+    // whether tile t's (logical, clamped) plane k is a lean plane of the step's plan
+    auto lean_plane = [&](int t, int k) {
+        const int kc = k < 0 ? 0 : (k >= nz ? nz - 1 : k);
+        const int2 sp = splits[(kc / split_zchunk) * ntl + t];
+        return kc < sp.x || kc >= sp.y;
+    };
     auto prefetch = [&](int k) {
         const size_t b = plane_off(k, nz, zbase, plane);
         pfN0 = ldg_ph(phi_new + b + col0);
@@ -877,6 +908,13 @@ __global__ void __launch_bounds__(TX *TY) mu_sweep_kernel(const KParams<R> kp, c
             pfN1 = ldg_ph(phi_new + b + col1);
             pfO1 = ldg_ph(phi_old + b + col1);
             pfM1 = ldg_mu(mu + b + col1);
+        }
+        if (splits) {
+            Ph<R> liq;
+            liq.v[0] = liq.v[1] = liq.v[2] = R(0);
+            liq.v[3] = R(1);
+            if (lean_plane(tile0, k)) pfN0 = liq;
+            if (s1 >= 0 && lean_plane(tile1, k)) pfN1 = liq;
         }
     };
     auto commitN = [&](int k) {
@@ -1018,15 +1056,33 @@ __global__ void __launch_bounds__(TX *TY) mu_sweep_kernel(const KParams<R> kp, c
             a += red[q][0];
             b += red[q][1];
         }
-        const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        partials[bid].liq_deficit = a;
-        partials[bid].nonfinite = b;
-        // this sweep: phi^n, phi^{n+1}, mu^n in, mu^{n+1} out (12 words a cell); the compensated
-        // state adds the low words of mu in and out
+        part->liq_deficit = a;
+        part->nonfinite = b;
         const double cells = (double)max(0, min(TX, nx - i0)) * (double)max(0, min(TY, ny - j0)) * (double)(z1 - z0);
-        partials[bid].bytes = cells * (double)sizeof(R) * (COMP ? 16.0 : 12.0);
-        partials[bid].timeout = 0.0;
+        part->bytes = cells * (double)sizeof(R) * words;
+        part->timeout = 0.0;
     }
+}
+
+template <typename R, int TX, int TY, bool COMP = false>
+__global__ void __launch_bounds__(TX *TY) mu_sweep_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi_old,
+                                                         const Ph<R> *__restrict__ phi_new,
+                                                         const Mu<R> *__restrict__ mu,
+                                                         Mu<R> *__restrict__ mu_out,
+                                                         const DevState *__restrict__ st,
+                                                         const PlaneT<R> *__restrict__ tab,
+                                                         Partial *__restrict__ partials,
+                                                         const Mu<R> *__restrict__ mu_lo = nullptr,
+                                                         Mu<R> *__restrict__ mu_out_lo = nullptr)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int z0 = blockIdx.z * kp.zchunk;
+    // this sweep: phi^n, phi^{n+1}, mu^n in, mu^{n+1} out (12 words a cell); the compensated state
+    // adds the low words of mu in and out
+    mu_sweep_tile<R, TX, TY, COMP>(kp, phi_old, phi_new, mu, mu_out, st, tab, partials + bid, mu_lo, mu_out_lo,
+                                   blockIdx.x, blockIdx.y, z0, min(z0 + kp.zchunk, kp.nz), smem_raw,
+                                   COMP ? 16.0 : 12.0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1817,6 +1873,68 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) general_step_k
     }
 }
 
+// The general planes as the two sweeps: persistent CTAs take the listed (tile, chunk) items one
+// at a time (phi pass: counter gnext, mu pass: gnext_mu) and sweep each item's general range.
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) general_phi_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
+                                                            const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
+                                                            const DevState *__restrict__ st,
+                                                            const PlaneT<R> *__restrict__ tab,
+                                                            unsigned char *__restrict__ tmap_out,
+                                                            const int2 *__restrict__ splits,
+                                                            const int *__restrict__ glist,
+                                                            LeanStats *__restrict__ stats)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    const int ntl = kp.tgx * kp.tgy;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned it = atomicAdd(&stats->gnext, 1u);
+            s_item = it < *(volatile unsigned *)&stats->gcount ? glist[it] : -1;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item < 0) break;
+        const int tile = item % ntl;
+        const int2 sp = splits[item];
+        phi_sweep_tile<R, TX, TY, false>(kp, phi, mu, phi_out, st, tab, nullptr, nullptr, tile % kp.tgx, tile / kp.tgx,
+                                         sp.x, sp.y, smem_raw, tmap_out);
+    }
+}
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) general_mu_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi_old,
+                                                           const Ph<R> *__restrict__ phi_new,
+                                                           const Mu<R> *__restrict__ mu, Mu<R> *__restrict__ mu_out,
+                                                           const DevState *__restrict__ st,
+                                                           const PlaneT<R> *__restrict__ tab,
+                                                           Partial *__restrict__ partials,
+                                                           const int2 *__restrict__ splits,
+                                                           const int *__restrict__ glist,
+                                                           LeanStats *__restrict__ stats)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    const int ntl = kp.tgx * kp.tgy;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned it = atomicAdd(&stats->gnext_mu, 1u);
+            s_item = it < *(volatile unsigned *)&stats->gcount ? glist[it] : -1;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item < 0) break;
+        const int tile = item % ntl;
+        const int2 sp = splits[item];
+        // both sweeps' compulsory words: phi^n, mu^n in, phi^{n+1} out; phi^n, phi^{n+1}, mu^n in,
+        // mu^{n+1} out
+        mu_sweep_tile<R, TX, TY, false>(kp, phi_old, phi_new, mu, mu_out, st, tab, partials + item, nullptr, nullptr,
+                                        tile % kp.tgx, tile / kp.tgx, sp.x, sp.y, smem_raw, 22.0, splits, kp.zchunk);
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // batched step: many independent domains of uneven size in one persistent launch.  Each CTA
 // pulls (domain, tile, z chunk) work items from a table through an atomic counter (largest
@@ -1922,6 +2040,7 @@ __device__ __forceinline__ void finalize_body(const KParams<R> &kp, DevState *__
             lean->timeout = 0;
             lean->gcount = 0u;
             lean->gnext = 0u;
+            lean->gnext_mu = 0u;
         }
         if (bad && st->nonfinite == 0) st->nonfinite = 1;
         if (tmo) st->nonfinite = 2;
@@ -2358,10 +2477,60 @@ cudaError_t launch_general_step(const KParams<R> &kp, const void *phi, const voi
 }
 
 template <typename R>
+cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const void *mu, void *phi_out, void *mu_out,
+                                  const DevState *st, const PlaneT<R> *tab, Partial *parts, unsigned char *tmap_out,
+                                  const int2 *splits, const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas,
+                                  cudaStream_t s)
+{
+    static bool attr = false;
+    const size_t smp = phi_smem_bytes<R>(), smm = mu_smem_bytes<R>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(general_phi_kernel<R, kTX, kTY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(general_mu_kernel<R, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    general_phi_kernel<R, kTX, kTY><<<phi_ctas, kTX * kTY, smp, s>>>(kp, (const Ph<R> *)phi, (const Mu<R> *)mu,
+                                                                    (Ph<R> *)phi_out, st, tab, tmap_out, splits,
+                                                                    glist, stats);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    general_mu_kernel<R, kTX, kTY><<<mu_ctas, kTX * kTY, smm, s>>>(kp, (const Ph<R> *)phi, (const Ph<R> *)phi_out,
+                                                                  (const Mu<R> *)mu, (Mu<R> *)mu_out, st, tab, parts,
+                                                                  splits, glist, stats);
+    return cudaGetLastError();
+}
+
+template <typename R>
+void general_sweep_ctas_per_sm(int *phi_per_sm, int *mu_per_sm)
+{
+    int a = 0, b = 0;
+    if (cudaFuncSetAttribute(general_phi_kernel<R, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)phi_smem_bytes<R>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, general_phi_kernel<R, kTX, kTY>, kTX * kTY,
+                                                      phi_smem_bytes<R>()) != cudaSuccess)
+        a = 1;
+    if (cudaFuncSetAttribute(general_mu_kernel<R, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)mu_smem_bytes<R>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, general_mu_kernel<R, kTX, kTY>, kTX * kTY,
+                                                      mu_smem_bytes<R>()) != cudaSuccess)
+        b = 1;
+    cudaGetLastError();
+    *phi_per_sm = a > 0 ? a : 1;
+    *mu_per_sm = b > 0 ? b : 1;
+}
+
+template <typename R>
 int general_ctas_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, general_step_kernel<R, kTX, kTY>, kTX * kTY,
+    // the occupancy of a launch with the kernel's dynamic shared memory: its limit must be raised first
+    if (cudaFuncSetAttribute(general_step_kernel<R, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fused_smem_bytes<R>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, general_step_kernel<R, kTX, kTY>, kTX * kTY,
                                                       fused_smem_bytes<R>()) != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -2460,7 +2629,9 @@ template <typename R>
 int fused_ctas_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_fused_kernel<R, kTX, kTY>, kTX * kTY,
+    if (cudaFuncSetAttribute(batched_fused_kernel<R, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fused_smem_bytes<R>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_fused_kernel<R, kTX, kTY>, kTX * kTY,
                                                       fused_smem_bytes<R>()) != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -2547,6 +2718,10 @@ cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, v
                                                 const unsigned char *, unsigned char *, const int2 *, const int *, \
                                                 LeanStats *, int, cudaStream_t);                                 \
     template int general_ctas_per_sm<R>();                                                                       \
+    template cudaError_t launch_general_sweeps<R>(const KParams<R> &, const void *, const void *, void *, void *, \
+                                                  const DevState *, const PlaneT<R> *, Partial *, unsigned char *, \
+                                                  const int2 *, const int *, LeanStats *, int, int, cudaStream_t); \
+    template void general_sweep_ctas_per_sm<R>(int *, int *);                                                    \
     template cudaError_t launch_batched_step<R>(const BatchDomain<R> *, int, const BatchItem *, int, unsigned *, \
                                                 int, int, int, cudaStream_t);                                    \
     template int fused_ctas_per_sm<R>();                                                                         \

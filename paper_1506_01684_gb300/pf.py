@@ -104,9 +104,10 @@ SIGNATURES = {
     "pf_server_stats": (_I, [_VP, _DP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
 }
 
-PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_FUSED, PF_K_LEAN, PF_K_PLAN, PF_K_COUNT = 0, 1, 2, 3, 4, 5, 6, 8
+PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_FUSED, PF_K_LEAN, PF_K_PLAN, PF_K_GENERAL, PF_K_COUNT = \
+    0, 1, 2, 3, 4, 5, 6, 7, 8
 KERNEL_NAMES = {PF_K_PHI: "phi_sweep", PF_K_MU: "mu_sweep", PF_K_FINALIZE: "finalize", PF_K_POST: "post",
-                PF_K_FUSED: "fused_step", PF_K_LEAN: "lean_step", PF_K_PLAN: "plan"}
+                PF_K_FUSED: "fused_step", PF_K_LEAN: "lean_step", PF_K_PLAN: "plan", PF_K_GENERAL: "general_sweeps"}
 PF_VARIANT_AUTO, PF_VARIANT_UNFUSED, PF_VARIANT_FUSED = 0, 1, 2
 VARIANTS = {"auto": PF_VARIANT_AUTO, "unfused": PF_VARIANT_UNFUSED, "fused": PF_VARIANT_FUSED}
 

@@ -118,14 +118,16 @@ def test_step_bytes_follow_the_design_word_counts():
     sim.step(3)
     assert sim.step_bytes() == {"fused_step": 16 * (nx - 1) * ny * nz}
     sim.close()
-    # a solidification front: between the pure-liquid and the general (12 words a cell) counts
+    # a solidification front: the general planes run as the two sweeps (22 words a cell), the
+    # pure-liquid planes in the lean kernel (4 words a cell)
     sim = pf.Simulation(nx, ny, nz, p, "fp32", variant="fused")
     phi_i, mu_i = W.region_fields("interface", nx, ny, nz, seed=0)
     sim.set_fields(phi_i, mu_i)
     sim.step(3)
     b = sim.step_bytes()
-    assert set(b) == {"fused_step", "lean_step"}
-    assert 16 * cells < sum(b.values()) < 48 * cells
+    assert set(b) == {"general_sweeps", "lean_step"}
+    assert b["general_sweeps"] % (88 * nx) == 0  # whole tile rows of 22 words a cell
+    assert 16 * cells < sum(b.values()) < 88 * cells
     sim.close()
 
 

@@ -63,11 +63,13 @@ def test_results_are_the_same_alone_and_in_the_mix():
         pf.pf_server_destroy(s1)
         assert (fr1 == fr).all() and (slab1 == slab).all()
         assert lat > 0
-        # and the same as the plain simulation API
+        # and the same as the plain simulation API, up to rounding order: served runs take the
+        # batched fused tile, a simulation of even nx the lean kernel and the two sweeps (same
+        # expressions, another order; phi agrees to ~1e-7, so a mean of phi to well below 1e-6)
         sim = pf.Simulation(r["nx"], r["ny"], r["nz"], r["p"], "fp32", variant="fused")
         sim.init(r["seed"])
         sim.step(r["steps"])
-        np.testing.assert_array_equal(sim.fractions(), fr)
+        np.testing.assert_allclose(sim.fractions(), fr, rtol=0, atol=1e-6)
         sim.close()
 
 
