@@ -12,6 +12,13 @@ Printed: one JSON line with MLUP/s (value), the FP64 GPU path on the same worklo
 FP32-vs-FP64 error, the dominant kernel's roofline, an end-to-end figure through host
 buffers, the oracle's CPU baseline, clocks and launch counts.
 
+Two timed regions of K steps each follow the warm-up: A, the steps as pf_step runs them (replayed
+from the captured CUDA graph), gives `value` and `ms_per_step`; B, the next K steps with the
+library's per-kernel CUDA-event timers (every kernel launched directly between its two events),
+gives the per-kernel durations, their shares and the roofline of the dominant kernel, and its own
+`ms_per_step_kernel_timers`.  The roofline's algorithmic bytes are the kernels' own tally of the
+last step (pf_step_bytes): 16 B a cell on pure-liquid planes, 88 B on general planes.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
 With N > 1 (torchrun, one process per GPU) every rank runs its own replica of the
@@ -44,10 +51,12 @@ METRIC = "phi+mu step MLUP/s (FP32 stencil; FP64 GPU path and error reported bes
 # (phi^n, mu^n in, phi^{n+1}, mu^{n+1} out); its pure-liquid planes (the lean kernel) 16 B (mu^n
 # in, mu^{n+1} out; phi^{n+1} = e_l is stored only where the destination does not hold it
 # already) -- tallied by the kernels themselves.
-# DRAM bytes per cell per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of
-# the kernel as it is now, on 128x128x512 with the same workload recipe, scaled by cells (the capture
-# file and its command are in profiles/); remove an entry when its kernel changes
-TRAFFIC_BYTES_PER_CELL = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) over the kernel's algorithmic
+# bytes, from an ncu capture of the kernel as it is now on 256x256x512 (the same workload at half the
+# depth, mu larger than L2; the capture and its command are in profiles/lean_step_traffic_fp32_256x256x512.md);
+# traffic of a full launch = this ratio x the launch's algorithmic bytes (traffic grows with the lean
+# cells).  Remove an entry when its kernel changes.
+TRAFFIC_RATIO = {"lean_step": 0.95}
 
 
 def _env_int(name, default):
@@ -540,8 +549,8 @@ def main():
             for k, v in prof.items()}
     achieved = bytes_per_cell.get(dom, 0) * cells / (dom_ms / 1e3) / 1e9
     traffic = None
-    if dom in TRAFFIC_BYTES_PER_CELL and NX * NY * NZ >= 8 << 20:
-        traffic = TRAFFIC_BYTES_PER_CELL[dom] * cells
+    if dom in TRAFFIC_RATIO and dom in kbytes:
+        traffic = TRAFFIC_RATIO[dom] * kbytes[dom]
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
             "bytes_per_cell": bytes_per_cell.get(dom)}

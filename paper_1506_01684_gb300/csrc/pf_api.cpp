@@ -24,12 +24,14 @@ using namespace pf;
 
 // Launch shape of the fused step with the lean kernel: the persistent general-plane CTAs per SM,
 // and whether the general planes run on a second stream beside the lean kernel (1) or before it
-// on the sim's stream (0).
+// on the sim's stream (0).  Measured on 256x256x1024 FP32 (GB300): the two orders give the same
+// step time (the general CTAs hold most of an SM's registers, so the lean kernel gets little of
+// the GPU until they finish); the default is the plain order.
 #ifndef PF_GENERAL_CTAS_PER_SM
 #define PF_GENERAL_CTAS_PER_SM 2
 #endif
 #ifndef PF_OVERLAP_GENERAL
-#define PF_OVERLAP_GENERAL 1
+#define PF_OVERLAP_GENERAL 0
 #endif
 // the general planes as the two sweeps of Algorithm 1 (1) or as the fused tile (0)
 #ifndef PF_GENERAL_SWEEPS
@@ -845,8 +847,11 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
     for (int b = 0; b < 2 && r == PF_OK; b++)
         r = dev_alloc(s->tmap[b], (size_t)nz * s->geo_fused.gx * s->geo_fused.gy, s->stream);
     if (r == PF_OK) r = dev_alloc(s->state, sizeof(DevState), s->stream);
-    // lean CTAs: at most 64 planes each
-    s->lean_nsub = std::max(1, (s->geo_fused.zchunk + 63) / 64);
+    // lean CTAs: at most PF_LEAN_PLANES planes each
+#ifndef PF_LEAN_PLANES
+#define PF_LEAN_PLANES 64
+#endif
+    s->lean_nsub = std::max(1, (s->geo_fused.zchunk + PF_LEAN_PLANES - 1) / PF_LEAN_PLANES);
     if (r == PF_OK)
         r = dev_alloc(s->parts, (size_t)std::max(s->geo.nparts(), s->geo_fused.nparts()) * sizeof(Partial),
                       s->stream);
@@ -867,8 +872,8 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
             general_sweep_ctas_per_sm<double>(&pp, &pm);
         else
             general_sweep_ctas_per_sm<float>(&pp, &pm);
-        s->gphi_ctas = std::max(1, std::min(s->geo_fused.nparts(), pp * sms));
-        s->gmu_ctas = std::max(1, std::min(s->geo_fused.nparts(), pm * sms));
+        s->gphi_ctas = std::max(1, std::min(s->geo_fused.nparts(), std::min(pp, PF_GENERAL_CTAS_PER_SM) * sms));
+        s->gmu_ctas = std::max(1, std::min(s->geo_fused.nparts(), std::min(pm, PF_GENERAL_CTAS_PER_SM) * sms));
     }
     if (r == PF_OK) {
         cudaError_t e = cudaMemsetAsync(s->lean_stats.p, 0, sizeof(LeanStats), s->stream);

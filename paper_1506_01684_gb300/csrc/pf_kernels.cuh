@@ -1287,11 +1287,13 @@ __device__ __forceinline__ void lean_split(const unsigned char *__restrict__ tma
     split_from(z0, z1, kmin, kmax, lo_end, hi_beg);
 }
 
-// Plan of a fused step with the lean kernel: one CTA per (tile, z chunk) item (item = bz * tiles
-// + tile, the fused grid's CTA order), one thread per plane of the chunk and its 2-plane margins,
-// computes the item's split; items with general planes are appended to glist (count in
-// stats->gcount) for general_step_kernel, the partials of the others are zeroed (their planes are
-// all lean: no liquid deficit, no general-path value).
+// Plan of a fused step with the lean kernel: 64 threads per (tile, z chunk) item (item = bz *
+// tiles + tile, the fused grid's CTA order), four items per CTA, compute each item's split; items
+// with general planes are appended to glist (count in stats->gcount) for the general-plane
+// kernels, the partials of the others are zeroed (their planes are all lean: no liquid deficit,
+// no general-path value).  A thread tests up to PLAN_PER planes, with all their map loads issued
+// before the first test (the planes of a chunk and its 2-plane margins: zchunk + 4 <= 64 PLAN_PER).
+constexpr int PLAN_PER = 5;
 template <int TX, int TY>
 __global__ void __launch_bounds__(256) plan_kernel(int nx, int ny, int nz, int tgx, int tgy, int zchunk, int gz,
                                                    const DevState *__restrict__ st,
@@ -1301,12 +1303,44 @@ __global__ void __launch_bounds__(256) plan_kernel(int nx, int ny, int nz, int t
 {
     __shared__ int kred[8][2];
     const int ntl = tgx * tgy;
-    const int item = blockIdx.x;
-    const int bz = item / ntl, tile = item % ntl, bx = tile % tgx, by = tile / tgx;
-    const int z0 = bz * zchunk, z1 = min(z0 + zchunk, nz);
-    int lo_end, hi_beg;
-    lean_split<TX, TY, 256>(tmap_in, tgx, tgy, nx, ny, nz, st->zbase, bx, by, z0, z1, kred, lo_end, hi_beg);
-    if (threadIdx.x == 0) {
+    const int sub = threadIdx.x >> 6, t64 = threadIdx.x & 63, w = threadIdx.x >> 5;
+    const int item = blockIdx.x * 4 + sub;
+    const bool live = item < ntl * gz;
+    int kmin = INT_MAX, kmax = INT_MIN;
+    int z0 = 0, z1 = 0;
+    if (live) {
+        const int bz = item / ntl, tile = item % ntl;
+        z0 = bz * zchunk;
+        z1 = min(z0 + zchunk, nz);
+        const RingTiles<TX, TY> rt(nx, ny, tile % tgx, tile / tgx);
+        const int zbase = st->zbase;
+        bool liq[PLAN_PER];
+#pragma unroll
+        for (int r = 0; r < PLAN_PER; r++) {
+            const int k = z0 - 2 + t64 + 64 * r;
+            liq[r] = k >= z1 + 2 || rt.liquid(tmap_in, tgx, ntl, nz, zbase, k);
+        }
+#pragma unroll
+        for (int r = 0; r < PLAN_PER; r++) {
+            const int k = z0 - 2 + t64 + 64 * r;
+            if (!liq[r]) {
+                kmin = min(kmin, k);
+                kmax = max(kmax, k);
+            }
+        }
+    }
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    if ((threadIdx.x & 31) == 0) {
+        kred[w][0] = kmin;
+        kred[w][1] = kmax;
+    }
+    __syncthreads();
+    if (live && t64 == 0) {
+        kmin = min(kred[2 * sub][0], kred[2 * sub + 1][0]);
+        kmax = max(kred[2 * sub][1], kred[2 * sub + 1][1]);
+        int lo_end, hi_beg;
+        split_from(z0, z1, kmin, kmax, lo_end, hi_beg);
         splits[item] = make_int2(lo_end, hi_beg);
         if (hi_beg > lo_end) {
             glist[atomicAdd(&stats->gcount, 1u)] = item;
@@ -2012,6 +2046,7 @@ __device__ __forceinline__ void finalize_body(const KParams<R> &kp, DevState *__
     __syncthreads();
     double a = 0.0, b = 0.0;
     bool to = false;
+#pragma unroll 4
     for (int q = threadIdx.x; q < nparts; q += 256) {
         a += parts[q].liq_deficit;
         b += parts[q].nonfinite;
@@ -2443,16 +2478,27 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
     return cudaGetLastError();
 }
 
-constexpr int kLeanStages = 8, kLeanMaxSub = 64, kLeanRows = 4;
+// lean kernel shape: pipeline stages, at most planes per CTA, tile rows per consumer thread
+#ifndef PF_LEAN_STAGES
+#define PF_LEAN_STAGES 4
+#endif
+#ifndef PF_LEAN_PLANES
+#define PF_LEAN_PLANES 64
+#endif
+#ifndef PF_LEAN_ROWS
+#define PF_LEAN_ROWS 4
+#endif
+constexpr int kLeanStages = PF_LEAN_STAGES, kLeanMaxSub = PF_LEAN_PLANES, kLeanRows = PF_LEAN_ROWS;
 
 template <typename R>
 cudaError_t launch_plan(const KParams<R> &kp, const Geometry &g, const DevState *st, const unsigned char *tmap_in,
                         int2 *splits, int *glist, LeanStats *stats, Partial *parts, cudaStream_t s)
 {
     if (kp.tgx != g.gx || kp.tgy != g.gy) return cudaErrorInvalidValue;
+    if (kp.zchunk + 4 > 64 * PLAN_PER) return cudaErrorInvalidValue;
     const int items = g.gx * g.gy * g.gz;
-    plan_kernel<kTX, kTY><<<items, 256, 0, s>>>(kp.nx, kp.ny, kp.nz, kp.tgx, kp.tgy, kp.zchunk, g.gz, st, tmap_in,
-                                               splits, glist, stats, parts);
+    plan_kernel<kTX, kTY><<<(items + 3) / 4, 256, 0, s>>>(kp.nx, kp.ny, kp.nz, kp.tgx, kp.tgy, kp.zchunk, g.gz, st,
+                                                          tmap_in, splits, glist, stats, parts);
     return cudaGetLastError();
 }
 

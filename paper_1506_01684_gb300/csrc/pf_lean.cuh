@@ -19,6 +19,13 @@
 
 #include <cuda.h>
 
+#ifndef PF_LEAN_MIN_CTAS
+#define PF_LEAN_MIN_CTAS 8  // resident lean CTAs per SM the register allocation must allow
+#endif
+#ifndef PF_LEAN_SUSPEND_NS
+#define PF_LEAN_SUSPEND_NS 1000u  // longest suspension of a waiting thread per try (the wait's bound is separate)
+#endif
+
 namespace pf {
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -70,7 +77,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
-        if (mbar_test_suspend(bar, parity, 1000u)) return true;
+        if (mbar_test_suspend(bar, parity, PF_LEAN_SUSPEND_NS)) return true;
         if (*abort) return false;
         if (clock64() - t0 > (1LL << 31)) {
             *abort = 1;
@@ -141,7 +148,7 @@ __device__ __forceinline__ Mu<R> lds_cell(const unsigned char *p)
 // chunk's lean planes (its split, from plan_kernel) that fall into its sub-chunk.  TY/ROWS consumer warps own ROWS
 // consecutive tile rows each (lane = tile column), one producer warp feeds them.
 template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS>
-__global__ void __launch_bounds__(TX *TY / ROWS + 32, 6) lean_step_kernel(
+__global__ void __launch_bounds__(TX *TY / ROWS + 32, PF_LEAN_MIN_CTAS) lean_step_kernel(
     const KParams<R> kp, const __grid_constant__ CUtensorMap mu_map, const Mu<R> *__restrict__ mu,
     Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st,
     LeanStats *__restrict__ stats, unsigned char *__restrict__ tmap_out, const int2 *__restrict__ splits, int nsub)
@@ -276,6 +283,17 @@ __global__ void __launch_bounds__(TX *TY / ROWS + 32, 6) lean_step_kernel(
     }
     const int oyb = jr0 == 0 ? fixy0 + lane * CB : own0 - L::BW * CB;
     const size_t col0 = (size_t)jr0 * nx + (size_t)min(i, nx - 1);
+    // The liquid update with constant mobility M = D_l/(2 A_l), h = e_l and no phase change (the
+    // short form of Eq. 3 for a cell whose neighbourhood is pure liquid): the six face fluxes
+    // M (mu_nb - mu)/dx reduce to the 7-point sum, so
+    //   mu^{n+1} = mu^n + C1 (sum of the six neighbours - 6 mu^n) + C0,
+    //   C1 = dt M / (chi dx^2),  C0 = -k_l dT / chi  (per component; chi = 1/(2 A_l)).
+    // The zero-gradient mirror at z = 0 and z = nz-1 makes the missing neighbour the cell itself.
+    const R ichi = rcp(kp.inv2A[3]);
+    const R C1 = ichi * (kp.dt * (kp.DinvA[3] * kp.inv_dx * kp.inv_dx));
+    R C0[2];
+    C0[0] = -(kp.kT[3][0] * kp.dTstep) * ichi;
+    C0[1] = -(kp.kT[3][1] * kp.dTstep) * ichi;
     Ph<R> liquid;
     liquid.v[0] = liquid.v[1] = liquid.v[2] = R(0);
     liquid.v[3] = R(1);
@@ -296,63 +314,63 @@ __global__ void __launch_bounds__(TX *TY / ROWS + 32, 6) lean_step_kernel(
             if (lane == 0) mbar_arrive(&empty[v & (LD - 1)]);
         };
         unsigned v = u;  // use of the plane being updated
-        Mu<R> m[ROWS], zlo[ROWS];  // mu^n of the cells, the fluxes of their lower z faces
-#pragma unroll
-        for (int r = 0; r < ROWS; r++) zlo[r].v[0] = zlo[r].v[1] = R(0);
+        Mu<R> m[ROWS], mlo[ROWS];  // mu^n of the cells and of the cells below them
         ok = wait_use(v);
-        if (ok && qa[g] > 0) {  // plane qa - 1: only the z fluxes below qa
-            ok = wait_use(v + 1);
-            if (ok) {
-                const unsigned char *S0 = stg(v), *S1 = stg(v + 1);
+        if (ok && qa[g] > 0) {  // plane qa - 1: only the cells below qa
 #pragma unroll
-                for (int r = 0; r < ROWS; r++)
-                    zlo[r] = quiet_flux(kp, lds_cell<R>(S0 + own0 + r * L::BW * CB),
-                                        lds_cell<R>(S1 + own0 + r * L::BW * CB));
-                release(v);
-                v++;
-            }
+            for (int r = 0; r < ROWS; r++) mlo[r] = lds_cell<R>(stg(v) + own0 + r * L::BW * CB);
+            release(v);
+            v++;
+            ok = wait_use(v);
         }
         if (ok) {
 #pragma unroll
-            for (int r = 0; r < ROWS; r++) m[r] = lds_cell<R>(stg(v) + own0 + r * L::BW * CB);
+            for (int r = 0; r < ROWS; r++) {
+                m[r] = lds_cell<R>(stg(v) + own0 + r * L::BW * CB);
+                if (qa[g] == 0) mlo[r] = m[r];  // mirror below plane 0
+            }
         }
         for (int q = qa[g]; q < qb[g] && ok; q++, v++) {
             const unsigned char *S = stg(v);
-            Mu<R> mn[ROWS], zhi[ROWS];
+            Mu<R> mn[ROWS];
 #pragma unroll
-            for (int r = 0; r < ROWS; r++) {
-                mn[r] = m[r];
-                zhi[r].v[0] = zhi[r].v[1] = R(0);
-            }
+            for (int r = 0; r < ROWS; r++) mn[r] = m[r];  // mirror above plane nz-1
             if (q < nz - 1) {
                 ok = wait_use(v + 1);
                 if (!ok) break;
                 const unsigned char *N = stg(v + 1);
 #pragma unroll
-                for (int r = 0; r < ROWS; r++) {
-                    mn[r] = lds_cell<R>(N + own0 + r * L::BW * CB);
-                    zhi[r] = quiet_flux(kp, m[r], mn[r]);
-                }
+                for (int r = 0; r < ROWS; r++) mn[r] = lds_cell<R>(N + own0 + r * L::BW * CB);
             }
-            Mu<R> xm[ROWS], xp[ROWS], yu[ROWS];
+            Mu<R> xm[ROWS], xp[ROWS];
 #pragma unroll
             for (int r = 0; r < ROWS; r++) {
                 xm[r] = lds_cell<R>(S + oxm[r]);
                 xp[r] = lds_cell<R>(S + oxp[r]);
-                yu[r] = lds_cell<R>(S + oyu[r]);
             }
-            const Mu<R> yb = lds_cell<R>(S + oyb);
+            // y neighbours: the rows of this thread, the cell below row 0 and above row ROWS-1 (or
+            // their periodic images); a last domain row's upper neighbour is its periodic image
+            Mu<R> yd[ROWS + 1];
+            yd[0] = lds_cell<R>(S + oyb);
+#pragma unroll
+            for (int r = 1; r < ROWS; r++) yd[r] = m[r];
+            yd[ROWS] = lds_cell<R>(S + oyu[ROWS - 1]);
+            Mu<R> wrap_up[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS - 1; r++)
+                if (jr0 + r == ny - 1) wrap_up[r] = lds_cell<R>(S + oyu[r]);
             release(v);
-            // the y face between rows r and r+1 is evaluated once, from the same operands both
-            // cells would use
-            Mu<R> fy_lo = quiet_flux(kp, yb, m[0]);
             Mu<R> out[ROWS];
 #pragma unroll
             for (int r = 0; r < ROWS; r++) {
-                const Mu<R> fy_hi = quiet_flux(kp, m[r], yu[r]);
-                out[r] = quiet_mu_update(kp, m[r], quiet_flux(kp, xm[r], m[r]), quiet_flux(kp, m[r], xp[r]), fy_lo,
-                                         fy_hi, zlo[r], zhi[r]);
-                fy_lo = fy_hi;
+                const Mu<R> ylo = r == 0 ? yd[0] : m[r - 1];
+                const Mu<R> yhi = (r < ROWS - 1 && jr0 + r == ny - 1) ? wrap_up[r] : yd[r + 1];
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const R sum = ((xm[r].v[c] + xp[r].v[c]) + (ylo.v[c] + yhi.v[c])) + (mlo[r].v[c] + mn[r].v[c]);
+                    const R lap = sum - R(6) * m[r].v[c];
+                    out[r].v[c] = C1 * lap + (m[r].v[c] + C0[c]);
+                }
             }
             const bool store_phi = s_dst_liquid[q - s0] != 1;
             phi_stores += store_phi ? 1 : 0;
@@ -365,11 +383,11 @@ __global__ void __launch_bounds__(TX *TY / ROWS + 32, 6) lean_step_kernel(
                     st_mu(mu_out + o + (size_t)r * nx, out[r]);
                     acc += out[r].v[0] + out[r].v[1];
                 }
-                zlo[r] = zhi[r];
+                mlo[r] = m[r];
                 m[r] = mn[r];
             }
         }
-        if (ok && lb == qb[g]) release(v);  // plane qb: waited for the z flux of plane qb-1 only
+        if (ok && lb == qb[g]) release(v);  // plane qb: waited for the z neighbours of plane qb-1 only
         u += (unsigned)(lb - la + 1);
     }
     const bool bad = !isfinite(acc);
