@@ -30,6 +30,9 @@ using namespace pf;
 #ifndef PF_GENERAL_CTAS_PER_SM
 #define PF_GENERAL_CTAS_PER_SM 2
 #endif
+#ifndef PF_LEAN_PLANES
+#define PF_LEAN_PLANES 64  // at most planes per lean CTA (the kernels' limit, PF_LEAN_PLANES in pf_kernels.cuh)
+#endif
 #ifndef PF_OVERLAP_GENERAL
 #define PF_OVERLAP_GENERAL 0
 #endif
@@ -848,9 +851,6 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
         r = dev_alloc(s->tmap[b], (size_t)nz * s->geo_fused.gx * s->geo_fused.gy, s->stream);
     if (r == PF_OK) r = dev_alloc(s->state, sizeof(DevState), s->stream);
     // lean CTAs: at most PF_LEAN_PLANES planes each
-#ifndef PF_LEAN_PLANES
-#define PF_LEAN_PLANES 64
-#endif
     s->lean_nsub = std::max(1, (s->geo_fused.zchunk + PF_LEAN_PLANES - 1) / PF_LEAN_PLANES);
     if (r == PF_OK)
         r = dev_alloc(s->parts, (size_t)std::max(s->geo.nparts(), s->geo_fused.nparts()) * sizeof(Partial),
@@ -1082,6 +1082,12 @@ struct pf_batch {
     std::vector<int> cur0;
     size_t dom_capacity = 0;
     bool owns_sims = true;
+    // lean path (domains with TMA maps): plan entries (domain, item), lean items (domain, tile x,
+    // tile y, chunk * nsub + sub), the splits of all its domains, the batch-wide general list and its
+    // counters; the other domains run the fused tile over `items`
+    DevBuf plan_entries, lean_items, splits, glist, plan;
+    int nplan = 0, nlean = 0, gphi_ctas = 1, gmu_ctas = 1;
+    bool lean_mode = false;
 };
 
 template <typename R>
@@ -1089,10 +1095,13 @@ static int batch_build(pf_batch *b)
 {
     const int n = (int)b->sims.size();
     std::vector<BatchDomain<R>> d(n);
-    std::vector<size_t> part_off(n);
+    std::vector<size_t> part_off(n), split_off(n);
     std::vector<BatchItem> items;
     std::vector<std::pair<long, int>> order;  // (cost, item) for the largest-first sort
-    size_t part_total = 0;
+    std::vector<int2> plan_entries;
+    std::vector<int4> lean_items;
+    std::vector<std::pair<long, int>> lean_order;  // (domain cells, domain) for the lean items' order
+    size_t part_total = 0, split_total = 0;
     int post = 1;
     for (int q = 0; q < n; q++) {
         pf_sim *s = b->sims[q];
@@ -1106,27 +1115,50 @@ static int batch_build(pf_batch *b)
             d[q].phi[k] = s->phi[k ^ s->cur].p;
             d[q].mu[k] = s->mu[k ^ s->cur].p;
             d[q].tmap[k] = (unsigned char *)s->tmap[k ^ s->cur].p;
+            d[q].mu_map[k] = s->mu_map[k ^ s->cur];
         }
         d[q].st = (DevState *)s->state.p;
         d[q].tab = (PlaneT<R> *)s->tab.p;
         d[q].parts = nullptr;  // set once the partial-sum array exists
+        d[q].splits = nullptr;
+        d[q].lean = nullptr;
         part_off[q] = part_total;
         d[q].gx = g.gx;
         d[q].gy = g.gy;
         d[q].gz = g.gz;
+        d[q].nsub = std::max(1, (g.zchunk + PF_LEAN_PLANES - 1) / PF_LEAN_PLANES);
         part_total += (size_t)g.nparts();
-        for (int bz = 0; bz < g.gz; bz++)
-            for (int by = 0; by < g.gy; by++)
-                for (int bx = 0; bx < g.gx; bx++) {
-                    const int planes = std::min(g.zchunk, s->nz - bz * g.zchunk);
-                    // cost ~ planes + the chunk's two recomputed planes; the chunk at the bottom of
-                    // the window holds the solidification front
-                    const long cost = (long)(planes + 3) * (bz == 0 ? 4 : 1);
-                    order.push_back({cost, (int)items.size()});
-                    items.push_back({q, bx, by, bz});
-                }
+        // the lean path needs the TMA maps and a chunk the batched plan covers
+        const bool lean = s->lean_ok && g.zchunk + 4 <= 64 * 9;
+        if (lean) {
+            split_off[q] = split_total;
+            split_total += (size_t)g.nparts();
+            d[q].lean = (LeanStats *)s->lean_stats.p;
+            for (int it = 0; it < g.nparts(); it++) plan_entries.push_back(make_int2(q, it));
+            lean_order.push_back({(long)s->nx * s->ny * s->nz, q});
+        } else {
+            for (int bz = 0; bz < g.gz; bz++)
+                for (int by = 0; by < g.gy; by++)
+                    for (int bx = 0; bx < g.gx; bx++) {
+                        const int planes = std::min(g.zchunk, s->nz - bz * g.zchunk);
+                        // cost ~ planes + the chunk's two recomputed planes; the chunk at the bottom of
+                        // the window holds the solidification front
+                        const long cost = (long)(planes + 3) * (bz == 0 ? 4 : 1);
+                        order.push_back({cost, (int)items.size()});
+                        items.push_back({q, bx, by, bz});
+                    }
+        }
         const long pw = std::max<long>((long)s->nx * s->ny, 2L * s->nz);
         post = std::max(post, (int)std::min<long>(64, (pw + 255) / 256));
+    }
+    // lean items of the largest domains first
+    std::stable_sort(lean_order.begin(), lean_order.end(),
+                     [](const std::pair<long, int> &x, const std::pair<long, int> &y) { return x.first > y.first; });
+    for (const auto &lo : lean_order) {
+        const int q = lo.second;
+        for (int z = 0; z < d[q].gz * d[q].nsub; z++)
+            for (int by = 0; by < d[q].gy; by++)
+                for (int bx = 0; bx < d[q].gx; bx++) lean_items.push_back(make_int4(q, bx, by, z));
     }
     std::stable_sort(order.begin(), order.end(), [](const std::pair<long, int> &x, const std::pair<long, int> &y) {
         return x.first > y.first;
@@ -1135,8 +1167,17 @@ static int batch_build(pf_batch *b)
     for (size_t q = 0; q < order.size(); q++) sorted[q] = items[order[q].second];
     dev_free(b->items, b->stream);
     dev_free(b->parts, b->stream);
+    dev_free(b->plan_entries, b->stream);
+    dev_free(b->lean_items, b->stream);
+    dev_free(b->splits, b->stream);
+    dev_free(b->glist, b->stream);
     int r = dev_alloc(b->items, std::max<size_t>(1, sorted.size()) * sizeof(BatchItem), b->stream);
     if (r == PF_OK) r = dev_alloc(b->parts, std::max<size_t>(1, part_total) * sizeof(Partial), b->stream);
+    if (r == PF_OK) r = dev_alloc(b->plan_entries, std::max<size_t>(1, plan_entries.size()) * sizeof(int2), b->stream);
+    if (r == PF_OK) r = dev_alloc(b->lean_items, std::max<size_t>(1, lean_items.size()) * sizeof(int4), b->stream);
+    if (r == PF_OK) r = dev_alloc(b->splits, std::max<size_t>(1, split_total) * sizeof(int2), b->stream);
+    if (r == PF_OK) r = dev_alloc(b->glist, std::max<size_t>(1, plan_entries.size()) * sizeof(int2), b->stream);
+    if (r == PF_OK && !b->plan.p) r = dev_alloc(b->plan, sizeof(BatchPlan), b->stream);
     if (r == PF_OK && b->dom_capacity < (size_t)n) {
         dev_free(b->doms, b->stream);
         r = dev_alloc(b->doms, (size_t)n * sizeof(BatchDomain<R>), b->stream);
@@ -1144,9 +1185,20 @@ static int batch_build(pf_batch *b)
     }
     if (r == PF_OK && !b->counter.p) r = dev_alloc(b->counter, 256, b->stream);
     if (r != PF_OK) return r;
-    for (int q = 0; q < n; q++) d[q].parts = (Partial *)b->parts.p + part_off[q];
-    cudaError_t e = cudaMemcpyAsync(b->items.p, sorted.data(), sorted.size() * sizeof(BatchItem),
-                                    cudaMemcpyHostToDevice, b->stream);
+    for (int q = 0; q < n; q++) {
+        d[q].parts = (Partial *)b->parts.p + part_off[q];
+        if (d[q].lean) d[q].splits = (int2 *)b->splits.p + split_off[q];
+    }
+    cudaError_t e = cudaSuccess;
+    if (!sorted.empty())
+        e = cudaMemcpyAsync(b->items.p, sorted.data(), sorted.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess && !plan_entries.empty())
+        e = cudaMemcpyAsync(b->plan_entries.p, plan_entries.data(), plan_entries.size() * sizeof(int2),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !lean_items.empty())
+        e = cudaMemcpyAsync(b->lean_items.p, lean_items.data(), lean_items.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->doms.p, d.data(), (size_t)n * sizeof(BatchDomain<R>), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host vectors go out of scope
@@ -1154,8 +1206,17 @@ static int batch_build(pf_batch *b)
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->ctas = std::max(1, std::min((int)sorted.size(), fused_ctas_per_sm<R>() * sms));
+    b->ctas = std::max(1, std::min((int)std::max<size_t>(1, sorted.size()), fused_ctas_per_sm<R>() * sms));
     b->nitems = (int)sorted.size();
+    b->nplan = (int)plan_entries.size();
+    b->nlean = (int)lean_items.size();
+    b->lean_mode = b->nplan > 0;
+    if (b->lean_mode) {
+        int pp = 1, pm = 1;
+        batched_general_ctas_per_sm<R>(&pp, &pm);
+        b->gphi_ctas = std::max(1, std::min(b->nplan, std::min(pp, PF_GENERAL_CTAS_PER_SM) * sms));
+        b->gmu_ctas = std::max(1, std::min(b->nplan, std::min(pm, PF_GENERAL_CTAS_PER_SM) * sms));
+    }
     b->post_blocks = post;
     b->built = true;
     b->parity = 0;
@@ -1172,14 +1233,22 @@ template <typename R>
 static int batch_step_direct(pf_batch *b, int n)
 {
     for (int q = 0; q < n; q++) {
-        cudaError_t e = launch_batched_step<R>((const BatchDomain<R> *)b->doms.p, (int)b->sims.size(),
-                                               (const BatchItem *)b->items.p, b->nitems, (unsigned *)b->counter.p,
-                                               b->parity, b->ctas, b->post_blocks, b->stream);
+        cudaError_t e;
+        if (b->lean_mode)
+            e = launch_batched_lean_step<R>((const BatchDomain<R> *)b->doms.p, (int)b->sims.size(),
+                                            (const int2 *)b->plan_entries.p, b->nplan, (const int4 *)b->lean_items.p,
+                                            b->nlean, (int2 *)b->glist.p, (BatchPlan *)b->plan.p, b->gphi_ctas,
+                                            b->gmu_ctas, (const BatchItem *)b->items.p, b->nitems,
+                                            (unsigned *)b->counter.p, b->ctas, b->parity, b->post_blocks, b->stream);
+        else
+            e = launch_batched_step<R>((const BatchDomain<R> *)b->doms.p, (int)b->sims.size(),
+                                       (const BatchItem *)b->items.p, b->nitems, (unsigned *)b->counter.p, b->parity,
+                                       b->ctas, b->post_blocks, b->stream);
         if (e != cudaSuccess) return cuda_status(e);
         b->parity ^= 1;
         for (pf_sim *s : b->sims) {
             s->cur = 1 - s->cur;
-            s->tmap_ok[s->cur] = true;  // written by the fused tiles and the window fill
+            s->tmap_ok[s->cur] = true;  // written by the step's kernels and the window fill
         }
     }
     return PF_OK;
@@ -1254,6 +1323,11 @@ int pf_batch_destroy(pf_batch *b)
     dev_free(b->items, b->stream);
     dev_free(b->parts, b->stream);
     dev_free(b->counter, b->stream);
+    dev_free(b->plan_entries, b->stream);
+    dev_free(b->lean_items, b->stream);
+    dev_free(b->splits, b->stream);
+    dev_free(b->glist, b->stream);
+    dev_free(b->plan, b->stream);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return PF_OK;

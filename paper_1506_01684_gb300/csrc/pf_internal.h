@@ -2,6 +2,7 @@
 // CUDA kernels of the phase-field time step.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -80,16 +81,24 @@ struct KParams {
 };
 
 // One domain of a batched step: its parameters, ping-pong field buffers, state, plane table and
-// partial sums, and its fused-step tile grid.
+// partial sums, and its fused-step tile grid; for the lean path also the TMA tensor maps of its mu
+// buffers, its plan (splits per (tile, chunk)) and its lean statistics.
 template <typename R>
-struct BatchDomain {
+struct alignas(64) BatchDomain {
+    CUtensorMap mu_map[2];   // TMA maps of mu[0], mu[1] (lean path)
     KParams<R> kp;
     void *phi[2], *mu[2];
     unsigned char *tmap[2];  // liquid maps of the two field buffers
     DevState *st;
     PlaneT<R> *tab;
     Partial *parts;
-    int gx, gy, gz, pad_;
+    int2 *splits;            // the step's lean / general split per (tile, chunk) (lean path)
+    LeanStats *lean;         // the domain's lean statistics (lean path)
+    int gx, gy, gz, nsub;    // fused-step tile grid; lean CTAs per z chunk
+};
+// The general-plane list of a batched step: (domain, item) pairs and their counters.
+struct BatchPlan {
+    unsigned gcount, gnext, gnext_mu, pad_;
 };
 // One work item of a batched step: a tile of one domain.
 struct BatchItem {
@@ -175,6 +184,17 @@ cudaError_t launch_batched_step(const BatchDomain<R> *doms, int ndoms, const Bat
                                 unsigned *counter, int parity, int ctas, int post_blocks, cudaStream_t s);
 template <typename R>
 int fused_ctas_per_sm();
+// Batched step on the lean path: counters reset, plan over the (domain, item) entries, the general
+// planes' two sweeps (persistent CTAs over the batch-wide list), the lean kernel over its items
+// (domain, tile x, tile y, chunk * nsub + sub); domains without TMA maps run the fused tile over
+// their items (fitems); then per-domain finalize and post.  parity: index of the source buffers.
+template <typename R>
+cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, const int2 *plan_entries, int nplan,
+                                     const int4 *lean_items, int nlean, int2 *glist, BatchPlan *plan,
+                                     int phi_ctas, int mu_ctas, const BatchItem *fitems, int nfitems,
+                                     unsigned *counter, int fctas, int parity, int post_blocks, cudaStream_t s);
+template <typename R>
+void batched_general_ctas_per_sm(int *phi_per_sm, int *mu_per_sm);
 template <typename R>
 cudaError_t launch_post(const KParams<R> &kp, const DevState *st, void *phi, void *mu, PlaneT<R> *tab,
                         cudaStream_t s, void *phi_lo = nullptr, void *mu_lo = nullptr,

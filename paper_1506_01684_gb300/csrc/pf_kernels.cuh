@@ -1287,25 +1287,18 @@ __device__ __forceinline__ void lean_split(const unsigned char *__restrict__ tma
     split_from(z0, z1, kmin, kmax, lo_end, hi_beg);
 }
 
-// Plan of a fused step with the lean kernel: 64 threads per (tile, z chunk) item (item = bz *
-// tiles + tile, the fused grid's CTA order), four items per CTA, compute each item's split; items
-// with general planes are appended to glist (count in stats->gcount) for the general-plane
-// kernels, the partials of the others are zeroed (their planes are all lean: no liquid deficit,
-// no general-path value).  A thread tests up to PLAN_PER planes, with all their map loads issued
-// before the first test (the planes of a chunk and its 2-plane margins: zchunk + 4 <= 64 PLAN_PER).
-constexpr int PLAN_PER = 5;
-template <int TX, int TY>
-__global__ void __launch_bounds__(256) plan_kernel(int nx, int ny, int nz, int tgx, int tgy, int zchunk, int gz,
-                                                   const DevState *__restrict__ st,
-                                                   const unsigned char *__restrict__ tmap_in, int2 *__restrict__ splits,
-                                                   int *__restrict__ glist, LeanStats *__restrict__ stats,
-                                                   Partial *__restrict__ parts)
+// Plan of a fused step with the lean kernel: 64 threads (group sub of the 256-thread CTA) compute
+// the split of the (tile, z chunk) item `item` (item = bz * tiles + tile, the fused grid's CTA
+// order).  A thread tests up to PER planes of the chunk and its 2-plane margins (zchunk + 4 <= 64
+// PER), with all their map loads issued before the first test.  Every thread of the CTA calls it
+// (one barrier); kred is 8 pairs of shared ints.
+template <int TX, int TY, int PER>
+__device__ __forceinline__ void plan_item(int nx, int ny, int nz, int tgx, int tgy, int zchunk, int zbase,
+                                          const unsigned char *__restrict__ tmap_in, int item, bool live,
+                                          int (*kred)[2], int &lo_end, int &hi_beg)
 {
-    __shared__ int kred[8][2];
     const int ntl = tgx * tgy;
     const int sub = threadIdx.x >> 6, t64 = threadIdx.x & 63, w = threadIdx.x >> 5;
-    const int item = blockIdx.x * 4 + sub;
-    const bool live = item < ntl * gz;
     int kmin = INT_MAX, kmax = INT_MIN;
     int z0 = 0, z1 = 0;
     if (live) {
@@ -1313,15 +1306,14 @@ __global__ void __launch_bounds__(256) plan_kernel(int nx, int ny, int nz, int t
         z0 = bz * zchunk;
         z1 = min(z0 + zchunk, nz);
         const RingTiles<TX, TY> rt(nx, ny, tile % tgx, tile / tgx);
-        const int zbase = st->zbase;
-        bool liq[PLAN_PER];
+        bool liq[PER];
 #pragma unroll
-        for (int r = 0; r < PLAN_PER; r++) {
+        for (int r = 0; r < PER; r++) {
             const int k = z0 - 2 + t64 + 64 * r;
             liq[r] = k >= z1 + 2 || rt.liquid(tmap_in, tgx, ntl, nz, zbase, k);
         }
 #pragma unroll
-        for (int r = 0; r < PLAN_PER; r++) {
+        for (int r = 0; r < PER; r++) {
             const int k = z0 - 2 + t64 + 64 * r;
             if (!liq[r]) {
                 kmin = min(kmin, k);
@@ -1336,19 +1328,39 @@ __global__ void __launch_bounds__(256) plan_kernel(int nx, int ny, int nz, int t
         kred[w][1] = kmax;
     }
     __syncthreads();
-    if (live && t64 == 0) {
-        kmin = min(kred[2 * sub][0], kred[2 * sub + 1][0]);
-        kmax = max(kred[2 * sub][1], kred[2 * sub + 1][1]);
-        int lo_end, hi_beg;
-        split_from(z0, z1, kmin, kmax, lo_end, hi_beg);
+    kmin = min(kred[2 * sub][0], kred[2 * sub + 1][0]);
+    kmax = max(kred[2 * sub][1], kred[2 * sub + 1][1]);
+    split_from(z0, z1, kmin, kmax, lo_end, hi_beg);
+}
+__device__ __forceinline__ void zero_partial(Partial *p)
+{
+    Partial z;
+    z.liq_deficit = z.nonfinite = z.bytes = z.timeout = 0.0;
+    *p = z;
+}
+
+// Plan of one domain: four items per CTA; items with general planes are appended to glist (count
+// in stats->gcount) for the general-plane kernels, the partials of the others are zeroed (their
+// planes are all lean: no liquid deficit, no general-path value).
+constexpr int PLAN_PER = 5;
+template <int TX, int TY>
+__global__ void __launch_bounds__(256) plan_kernel(int nx, int ny, int nz, int tgx, int tgy, int zchunk, int gz,
+                                                   const DevState *__restrict__ st,
+                                                   const unsigned char *__restrict__ tmap_in, int2 *__restrict__ splits,
+                                                   int *__restrict__ glist, LeanStats *__restrict__ stats,
+                                                   Partial *__restrict__ parts)
+{
+    __shared__ int kred[8][2];
+    const int item = blockIdx.x * 4 + (threadIdx.x >> 6);
+    const bool live = item < tgx * tgy * gz;
+    int lo_end, hi_beg;
+    plan_item<TX, TY, PLAN_PER>(nx, ny, nz, tgx, tgy, zchunk, st->zbase, tmap_in, item, live, kred, lo_end, hi_beg);
+    if (live && (threadIdx.x & 63) == 0) {
         splits[item] = make_int2(lo_end, hi_beg);
-        if (hi_beg > lo_end) {
+        if (hi_beg > lo_end)
             glist[atomicAdd(&stats->gcount, 1u)] = item;
-        } else {
-            Partial z;
-            z.liq_deficit = z.nonfinite = z.bytes = z.timeout = 0.0;
-            parts[item] = z;
-        }
+        else
+            zero_partial(parts + item);
     }
 }
 
@@ -1909,8 +1921,13 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) general_step_k
 
 // The general planes as the two sweeps: persistent CTAs take the listed (tile, chunk) items one
 // at a time (phi pass: counter gnext, mu pass: gnext_mu) and sweep each item's general range.
+// Registers are budgeted for PF_GENERAL_MIN_CTAS resident CTAs per SM (2: ~100 registers; 3 fits 80
+// registers without spills but ran slower on the 256x256x1024 workload).
+#ifndef PF_GENERAL_MIN_CTAS
+#define PF_GENERAL_MIN_CTAS 2
+#endif
 template <typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) general_phi_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
+__global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_phi_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
                                                             const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
                                                             const DevState *__restrict__ st,
                                                             const PlaneT<R> *__restrict__ tab,
@@ -1938,7 +1955,7 @@ __global__ void __launch_bounds__(TX *TY) general_phi_kernel(const KParams<R> kp
     }
 }
 template <typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) general_mu_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi_old,
+__global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_mu_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi_old,
                                                            const Ph<R> *__restrict__ phi_new,
                                                            const Mu<R> *__restrict__ mu, Mu<R> *__restrict__ mu_out,
                                                            const DevState *__restrict__ st,
@@ -1966,6 +1983,72 @@ __global__ void __launch_bounds__(TX *TY) general_mu_kernel(const KParams<R> kp,
         // mu^{n+1} out
         mu_sweep_tile<R, TX, TY, false>(kp, phi_old, phi_new, mu, mu_out, st, tab, partials + item, nullptr, nullptr,
                                         tile % kp.tgx, tile / kp.tgx, sp.x, sp.y, smem_raw, 22.0, splits, kp.zchunk);
+    }
+}
+
+// Plan of a batched step: four (domain, item) entries of the table per CTA; general items are
+// appended to the batch-wide list.  PLAN_PER_BATCH planes per thread cover z chunks up to 572.
+constexpr int PLAN_PER_BATCH = 9;
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(256) batched_plan_kernel(const BatchDomain<R> *__restrict__ doms,
+                                                           const int2 *__restrict__ entries, int nentries,
+                                                           int parity, int2 *__restrict__ glist,
+                                                           BatchPlan *__restrict__ plan)
+{
+    __shared__ int kred[8][2];
+    const int e = blockIdx.x * 4 + (threadIdx.x >> 6);
+    const bool live = e < nentries;
+    const int2 en = live ? entries[e] : make_int2(0, 0);
+    const BatchDomain<R> *d = doms + en.x;
+    int lo_end, hi_beg;
+    plan_item<TX, TY, PLAN_PER_BATCH>(d->kp.nx, d->kp.ny, d->kp.nz, d->kp.tgx, d->kp.tgy, d->kp.zchunk, d->st->zbase,
+                                      d->tmap[parity], en.y, live, kred, lo_end, hi_beg);
+    if (live && (threadIdx.x & 63) == 0) {
+        d->splits[en.y] = make_int2(lo_end, hi_beg);
+        if (hi_beg > lo_end)
+            glist[atomicAdd(&plan->gcount, 1u)] = en;
+        else
+            zero_partial(d->parts + en.y);
+    }
+}
+
+// The general planes of a batched step as the two sweeps: persistent CTAs over the batch-wide list
+// of (domain, item) entries (pass 0: phi-sweep, counter gnext; pass 1: mu-sweep, counter gnext_mu).
+template <typename R, int TX, int TY, int PASS>
+__global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) batched_general_kernel(
+    const BatchDomain<R> *__restrict__ doms, const int2 *__restrict__ glist, BatchPlan *__restrict__ plan, int parity)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int2 s_en;
+    __shared__ __align__(16) KParams<R> s_kp;
+    for (;;) {
+        __syncthreads();  // the previous entry's readers of s_kp and shared memory are done
+        if (threadIdx.x == 0) {
+            const unsigned it = atomicAdd(PASS == 0 ? &plan->gnext : &plan->gnext_mu, 1u);
+            s_en = it < *(volatile unsigned *)&plan->gcount ? glist[it] : make_int2(-1, 0);
+        }
+        __syncthreads();
+        const int2 en = s_en;
+        if (en.x < 0) break;
+        const BatchDomain<R> *d = doms + en.x;
+        {
+            const int *src = reinterpret_cast<const int *>(&d->kp);
+            int *dst = reinterpret_cast<int *>(&s_kp);
+            for (int q = threadIdx.x; q < (int)(sizeof(KParams<R>) / sizeof(int)); q += TX * TY) dst[q] = src[q];
+        }
+        __syncthreads();
+        const int ntl = s_kp.tgx * s_kp.tgy, tile = en.y % ntl;
+        const int2 sp = d->splits[en.y];
+        const int a = parity, b = parity ^ 1;
+        if (PASS == 0)
+            phi_sweep_tile<R, TX, TY, false>(s_kp, (const Ph<R> *)d->phi[a], (const Mu<R> *)d->mu[a], (Ph<R> *)d->phi[b],
+                                             d->st, d->tab, nullptr, nullptr, tile % s_kp.tgx, tile / s_kp.tgx, sp.x,
+                                             sp.y, smem_raw, d->tmap[b]);
+        else
+            mu_sweep_tile<R, TX, TY, false>(s_kp, (const Ph<R> *)d->phi[a], (const Ph<R> *)d->phi[b],
+                                            (const Mu<R> *)d->mu[a], (Mu<R> *)d->mu[b], d->st, d->tab,
+                                            d->parts + en.y, nullptr, nullptr, tile % s_kp.tgx, tile / s_kp.tgx, sp.x,
+                                            sp.y, smem_raw, 22.0, d->splits, s_kp.zchunk);
     }
 }
 
@@ -2111,7 +2194,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) batched_finalize_kernel(const BatchDomain<R> *__restrict__ doms)
 {
     const BatchDomain<R> *d = doms + blockIdx.x;
-    finalize_body(d->kp, d->st, d->parts, d->gx * d->gy * d->gz);
+    finalize_body(d->kp, d->st, d->parts, d->gx * d->gy * d->gz, d->lean);
 }
 
 // After finalize: rebuild the plane table for the new (t, offset) and fill the planes that
@@ -2671,6 +2754,72 @@ cudaError_t launch_batched_step(const BatchDomain<R> *doms, int ndoms, const Bat
     return cudaGetLastError();
 }
 
+// Batched step on the lean path (domains with TMA maps) and, for the other domains, the fused tile.
+template <typename R>
+cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, const int2 *plan_entries, int nplan,
+                                     const int4 *lean_items, int nlean, int2 *glist, BatchPlan *plan,
+                                     int phi_ctas, int mu_ctas, const BatchItem *fitems, int nfitems,
+                                     unsigned *counter, int fctas, int parity, int post_blocks, cudaStream_t s)
+{
+    using L = LeanLayout<R, kTX, kTY>;
+    static bool attr = false;
+    const size_t smp = phi_smem_bytes<R>(), smm = mu_smem_bytes<R>(), sml = L::smem_bytes(kLeanStages);
+    const size_t smf = fused_smem_bytes<R>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 0>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batched_lean_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sml);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batched_fused_kernel<R, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smf);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaError_t e = cudaMemsetAsync(plan, 0, sizeof(BatchPlan), s);
+    if (e != cudaSuccess) return e;
+    if (nplan > 0) {
+        batched_plan_kernel<R, kTX, kTY><<<(nplan + 3) / 4, 256, 0, s>>>(doms, plan_entries, nplan, parity, glist,
+                                                                          plan);
+        batched_general_kernel<R, kTX, kTY, 0><<<phi_ctas, kTX * kTY, smp, s>>>(doms, glist, plan, parity);
+        batched_general_kernel<R, kTX, kTY, 1><<<mu_ctas, kTX * kTY, smm, s>>>(doms, glist, plan, parity);
+    }
+    if (nlean > 0)
+        batched_lean_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>
+            <<<nlean, kTX * kTY / kLeanRows + 32, sml, s>>>(doms, lean_items, parity);
+    if (nfitems > 0) {
+        e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        batched_fused_kernel<R, kTX, kTY><<<fctas, kTX * kTY, smf, s>>>(doms, fitems, nfitems, counter, parity);
+    }
+    batched_finalize_kernel<R><<<ndoms, 256, 0, s>>>(doms);
+    batched_post_kernel<R><<<dim3(post_blocks, ndoms), 256, 0, s>>>(doms, parity);
+    return cudaGetLastError();
+}
+
+template <typename R>
+void batched_general_ctas_per_sm(int *phi_per_sm, int *mu_per_sm)
+{
+    int a = 0, b = 0;
+    if (cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)phi_smem_bytes<R>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batched_general_kernel<R, kTX, kTY, 0>, kTX * kTY,
+                                                      phi_smem_bytes<R>()) != cudaSuccess)
+        a = 1;
+    if (cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)mu_smem_bytes<R>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_general_kernel<R, kTX, kTY, 1>, kTX * kTY,
+                                                      mu_smem_bytes<R>()) != cudaSuccess)
+        b = 1;
+    cudaGetLastError();
+    *phi_per_sm = a > 0 ? a : 1;
+    *mu_per_sm = b > 0 ? b : 1;
+}
+
 template <typename R>
 int fused_ctas_per_sm()
 {
@@ -2771,6 +2920,10 @@ cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, v
     template cudaError_t launch_batched_step<R>(const BatchDomain<R> *, int, const BatchItem *, int, unsigned *, \
                                                 int, int, int, cudaStream_t);                                    \
     template int fused_ctas_per_sm<R>();                                                                         \
+    template cudaError_t launch_batched_lean_step<R>(const BatchDomain<R> *, int, const int2 *, int, const int4 *, \
+                                                     int, int2 *, BatchPlan *, int, int, const BatchItem *, int,   \
+                                                     unsigned *, int, int, int, cudaStream_t);                      \
+    template void batched_general_ctas_per_sm<R>(int *, int *);                                                  \
     template cudaError_t launch_finalize<R>(const KParams<R> &, DevState *, const Partial *, int, cudaStream_t,   \
                                             LeanStats *);                                                        \
     template cudaError_t launch_post<R>(const KParams<R> &, const DevState *, void *, void *, PlaneT<R> *,       \

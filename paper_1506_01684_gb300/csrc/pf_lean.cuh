@@ -148,10 +148,11 @@ __device__ __forceinline__ Mu<R> lds_cell(const unsigned char *p)
 // chunk's lean planes (its split, from plan_kernel) that fall into its sub-chunk.  TY/ROWS consumer warps own ROWS
 // consecutive tile rows each (lane = tile column), one producer warp feeds them.
 template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS>
-__global__ void __launch_bounds__(TX *TY / ROWS + 32, PF_LEAN_MIN_CTAS) lean_step_kernel(
-    const KParams<R> kp, const __grid_constant__ CUtensorMap mu_map, const Mu<R> *__restrict__ mu,
-    Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st,
-    LeanStats *__restrict__ stats, unsigned char *__restrict__ tmap_out, const int2 *__restrict__ splits, int nsub)
+__device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMap *mu_map, const Mu<R> *__restrict__ mu,
+                                          Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out,
+                                          const DevState *__restrict__ st, LeanStats *__restrict__ stats,
+                                          unsigned char *__restrict__ tmap_out, const int2 *__restrict__ splits,
+                                          int nsub, int bx, int by, int zsub)
 {
     using L = LeanLayout<R, TX, TY>;
     static_assert(TY % ROWS == 0, "whole rows per consumer warp");
@@ -169,9 +170,8 @@ __global__ void __launch_bounds__(TX *TY / ROWS + 32, PF_LEAN_MIN_CTAS) lean_ste
 
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     const int tid = threadIdx.x;
-    const int bx = blockIdx.x, by = blockIdx.y;
     const int i0 = bx * TX, j0 = by * TY;
-    const int chunk = blockIdx.z / nsub, sub = blockIdx.z % nsub;
+    const int chunk = zsub / nsub, sub = zsub % nsub;
     const int z0 = chunk * kp.zchunk, z1 = min(z0 + kp.zchunk, nz);
     const int sublen = (kp.zchunk + nsub - 1) / nsub;
     const int s0 = min(z1, z0 + sub * sublen), s1 = min(z1, s0 + sublen);
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(TX *TY / ROWS + 32, PF_LEAN_MIN_CTAS) lean_ste
                 const int sp = splane(p);
                 if (lane == 0) {
                     mbar_arrive_expect_tx(&full[s], L::BOX_BYTES);
-                    tma_load_3d(stg, &mu_map, &full[s], 2 * (i0 - 2), j0 - 1, sp);
+                    tma_load_3d(stg, mu_map, &full[s], 2 * (i0 - 2), j0 - 1, sp);
                 }
                 if (fix) {
                     const Mu<R> *mp = mu + (size_t)sp * plane;
@@ -407,6 +407,31 @@ __global__ void __launch_bounds__(TX *TY / ROWS + 32, PF_LEAN_MIN_CTAS) lean_ste
         if (s_bad) atomicOr(&stats->nonfinite, 1);
         if (s_abort) atomicOr(&stats->timeout, 1);
     }
+}
+
+// The lean planes of one domain: grid (tgx, tgy, gz * nsub).
+template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS>
+__global__ void __launch_bounds__(TX *TY / ROWS + 32, PF_LEAN_MIN_CTAS) lean_step_kernel(
+    const KParams<R> kp, const __grid_constant__ CUtensorMap mu_map, const Mu<R> *__restrict__ mu,
+    Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st,
+    LeanStats *__restrict__ stats, unsigned char *__restrict__ tmap_out, const int2 *__restrict__ splits, int nsub)
+{
+    lean_tile<R, TX, TY, LD, MAXSUB, ROWS>(kp, &mu_map, mu, phi_out, mu_out, st, stats, tmap_out, splits, nsub,
+                                           blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// One lean work item of a batched step: CTA blockIdx.x takes (domain, tile x, tile y, chunk * nsub +
+// sub) from the table; the domain's tensor maps live in device memory (64-byte aligned).
+template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS>
+__global__ void __launch_bounds__(TX *TY / ROWS + 32, PF_LEAN_MIN_CTAS) batched_lean_kernel(
+    const BatchDomain<R> *__restrict__ doms, const int4 *__restrict__ items, int parity)
+{
+    const int4 w = items[blockIdx.x];
+    const BatchDomain<R> *d = doms + w.x;
+    const int a = parity, b = parity ^ 1;
+    lean_tile<R, TX, TY, LD, MAXSUB, ROWS>(d->kp, d->mu_map + a, (const Mu<R> *)d->mu[a], (Ph<R> *)d->phi[b],
+                                           (Mu<R> *)d->mu[b], d->st, d->lean, d->tmap[b], d->splits, d->nsub, w.y,
+                                           w.z, w.w);
 }
 
 }  // namespace pf
