@@ -133,6 +133,22 @@ int pf_read_fields(pf_sim *sim, double *phi, double *mu, size_t cap_cells);
  * window offset are left unchanged.  Synchronising. */
 int pf_write_fields(pf_sim *sim, const double *phi, const double *mu);
 
+/* Checkpoint (the paper's infrequent field checkpoints, Section 3.2): write the current fields,
+ * simulation time and window offset to the file at path.  Layout: a 64-byte header (magic
+ * "PFCKPT01"; int32 version 1, nx, ny, nz, bytes per value, writer precision, planes shifted since
+ * init, 4 bytes of padding; FP64 time and window offset; 8 bytes of padding; little-endian), then for each logical
+ * plane k = 0 .. nz-1 the six nx*ny arrays (x fastest) phi_0, phi_1, phi_2, phi_3, mu_0, mu_1.
+ * Values are FP32 for an FP32 simulation and FP64 for FP64 and compensated FP32 (the state's own
+ * values, so that nothing is rounded).  PF_E_INVAL if the file cannot be written.  Synchronising. */
+int pf_checkpoint_write(pf_sim *sim, const char *path);
+
+/* Restore a checkpoint written for the same grid (any precision: values are converted to this
+ * simulation's): fields, time, window offset and shift count; the plane table is rebuilt and no
+ * window shift is pending.  A run resumed from a checkpoint of its own precision continues bitwise
+ * as the uninterrupted run.  PF_E_INVAL for a missing, short or foreign file or another grid
+ * (the fields may then be partly overwritten).  Synchronising. */
+int pf_checkpoint_read(pf_sim *sim, const char *path);
+
 /* Mean of each phi_a over all cells, accumulated in FP64 on the device. Synchronising. */
 int pf_phase_fractions(pf_sim *sim, double out[4]);
 

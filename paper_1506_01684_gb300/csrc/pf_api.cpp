@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -706,6 +707,160 @@ static int read_state(pf_sim *s, DevState *ds)
     return e == cudaSuccess ? PF_OK : latch(s, cuda_status(e));
 }
 
+// ------------------------------------------------------------------------------------------
+// checkpoints (the paper's infrequent field checkpoints, Section 3.2)
+// ------------------------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];    // "PFCKPT01"
+    int32_t version;  // 1
+    int32_t nx, ny, nz;
+    int32_t elem;       // bytes per value: 4 (FP32) or 8 (FP64)
+    int32_t precision;  // PF_FP64 / PF_FP32 / PF_FP32_COMP of the writer
+    int32_t nshift;     // planes shifted since init
+    int32_t pad0;
+    double t, off;      // simulation time, window offset
+    int32_t pad[2];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header");
+const char kCkptMagic[8] = {'P', 'F', 'C', 'K', 'P', 'T', '0', '1'};
+}  // namespace
+
+template <typename R>
+static int do_checkpoint_write(pf_sim *s, const char *path)
+{
+    DevState ds;
+    int r = read_state(s, &ds);
+    if (r != PF_OK) return r;
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.nx = s->nx;
+    h.ny = s->ny;
+    h.nz = s->nz;
+    h.elem = s->p.precision == PF_FP32 ? 4 : 8;  // the state's own values, exactly
+    h.precision = s->p.precision;
+    h.nshift = ds.nshift_total;
+    h.t = ds.t;
+    h.off = ds.off;
+    const KParams<R> kp = make_kparams<R>(s);
+    const size_t plane = (size_t)s->nx * s->ny;
+    const int pk = (int)std::max<size_t>(1, std::min<size_t>(s->nz, kChunkCells / plane));
+    DevBuf stg;
+    r = dev_alloc(stg, (size_t)pk * plane * 6 * sizeof(double), s->stream);
+    if (r != PF_OK) return r;
+    FILE *f = fopen(path, "wb");
+    if (!f) {
+        dev_free(stg, s->stream);
+        return PF_E_INVAL;
+    }
+    bool io_ok = fwrite(&h, sizeof h, 1, f) == 1;
+    std::vector<double> hb((size_t)pk * plane * 6);
+    std::vector<float> hf(h.elem == 4 ? plane : 0);
+    double *dphi = (double *)stg.p, *dmu = dphi + (size_t)pk * plane * 4;
+    cudaError_t e = cudaSuccess;
+    for (int k0 = 0; k0 < s->nz && e == cudaSuccess && io_ok; k0 += pk) {
+        const int nk = std::min(pk, s->nz - k0);
+        const size_t m = (size_t)nk * plane;
+        e = launch_pack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, dphi, dmu, k0, nk,
+                           s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
+        // [c][k][y][x] of the chunk: phi components, then mu components
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hb.data(), dphi, m * 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hb.data() + m * 4, dmu, m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        for (int kk = 0; kk < nk && e == cudaSuccess && io_ok; kk++)
+            for (int c = 0; c < 6 && io_ok; c++) {
+                const double *src = hb.data() + (size_t)c * m + (size_t)kk * plane;
+                if (h.elem == 4) {
+                    for (size_t q = 0; q < plane; q++) hf[q] = (float)src[q];
+                    io_ok = fwrite(hf.data(), sizeof(float), plane, f) == plane;
+                } else {
+                    io_ok = fwrite(src, sizeof(double), plane, f) == plane;
+                }
+            }
+    }
+    io_ok = (fclose(f) == 0) && io_ok;
+    dev_free(stg, s->stream);
+    if (e != cudaSuccess) return latch(s, cuda_status(e));
+    return io_ok ? PF_OK : PF_E_INVAL;
+}
+
+template <typename R>
+static int do_checkpoint_read(pf_sim *s, const char *path)
+{
+    FILE *f = fopen(path, "rb");
+    if (!f) return PF_E_INVAL;
+    CkptHeader h;
+    bool io_ok = fread(&h, sizeof h, 1, f) == 1;
+    if (!io_ok || memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1 || h.nx != s->nx || h.ny != s->ny ||
+        h.nz != s->nz || (h.elem != 4 && h.elem != 8)) {
+        fclose(f);
+        return PF_E_INVAL;
+    }
+    const KParams<R> kp = make_kparams<R>(s);
+    const size_t plane = (size_t)s->nx * s->ny;
+    const int pk = (int)std::max<size_t>(1, std::min<size_t>(s->nz, kChunkCells / plane));
+    DevBuf stg;
+    int r = dev_alloc(stg, (size_t)pk * plane * 6 * sizeof(double), s->stream);
+    if (r != PF_OK) {
+        fclose(f);
+        return r;
+    }
+    std::vector<double> hb((size_t)pk * plane * 6);
+    std::vector<float> hf(h.elem == 4 ? plane : 0);
+    double *dphi = (double *)stg.p, *dmu = dphi + (size_t)pk * plane * 4;
+    cudaError_t e = cudaSuccess;
+    s->tmap_ok[0] = s->tmap_ok[1] = false;
+    for (int k0 = 0; k0 < s->nz && e == cudaSuccess && io_ok; k0 += pk) {
+        const int nk = std::min(pk, s->nz - k0);
+        const size_t m = (size_t)nk * plane;
+        for (int kk = 0; kk < nk && io_ok; kk++)
+            for (int c = 0; c < 6 && io_ok; c++) {
+                double *dst = hb.data() + (size_t)c * m + (size_t)kk * plane;
+                if (h.elem == 4) {
+                    io_ok = fread(hf.data(), sizeof(float), plane, f) == plane;
+                    for (size_t q = 0; q < plane && io_ok; q++) dst[q] = (double)hf[q];
+                } else {
+                    io_ok = fread(dst, sizeof(double), plane, f) == plane;
+                }
+            }
+        if (!io_ok) break;
+        e = cudaMemcpyAsync(dphi, hb.data(), m * 4 * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dmu, hb.data() + m * 4, m * 2 * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = launch_unpack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, dphi, dmu, k0,
+                                 nk, s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // the host chunk is reused
+    }
+    fclose(f);
+    if (e == cudaSuccess && io_ok) {
+        // the clock and window of the checkpoint; no shift pending; the plane table for them
+        DevState ds;
+        r = read_state(s, &ds);
+        if (r != PF_OK) {
+            dev_free(stg, s->stream);
+            return r;
+        }
+        ds.t = h.t;
+        ds.off = h.off;
+        ds.shift = 0;
+        ds.nonfinite = 0;
+        ds.nshift_total = h.nshift;
+        e = cudaMemcpyAsync(s->state.p, &ds, sizeof ds, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = launch_post<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p,
+                               (PlaneT<R> *)s->tab.p, s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    }
+    dev_free(stg, s->stream);
+    if (e != cudaSuccess) return latch(s, cuda_status(e));
+    return io_ok ? PF_OK : PF_E_INVAL;
+}
+
 #define PF_DISPATCH(s, fn, ...) ((s)->p.precision == PF_FP64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
 
 // ------------------------------------------------------------------------------------------
@@ -951,6 +1106,18 @@ int pf_write_fields(pf_sim *s, const double *phi, const double *mu)
 {
     if (!s || !phi || !mu) return PF_E_INVAL;
     return PF_DISPATCH(s, do_write, s, phi, mu);
+}
+
+int pf_checkpoint_write(pf_sim *s, const char *path)
+{
+    if (!s || !path) return PF_E_INVAL;
+    return PF_DISPATCH(s, do_checkpoint_write, s, path);
+}
+
+int pf_checkpoint_read(pf_sim *s, const char *path)
+{
+    if (!s || !path) return PF_E_INVAL;
+    return PF_DISPATCH(s, do_checkpoint_read, s, path);
 }
 
 int pf_phase_fractions(pf_sim *s, double out[4])

@@ -82,6 +82,8 @@ SIGNATURES = {
     "pf_stats": (_I, [_VP, _DP, _DP, _DP, _DP]),
     "pf_window_shifts": (_I, [_VP, ctypes.POINTER(_I)]),
     "pf_step_bytes": (_I, [_VP, _DP]),
+    "pf_checkpoint_write": (_I, [_VP, ctypes.c_char_p]),
+    "pf_checkpoint_read": (_I, [_VP, ctypes.c_char_p]),
     "pf_profile": (_I, [_VP, _I]),
     "pf_set_variant": (_I, [_VP, _I]),
     "pf_profile_read": (_I, [_VP, _DP, ctypes.POINTER(_I)]),
@@ -258,6 +260,14 @@ def pf_window_shifts(sim) -> int:
     n = _I()
     _check(lib().pf_window_shifts(sim, ctypes.byref(n)), "pf_window_shifts")
     return n.value
+
+
+def pf_checkpoint_write(sim, path: str):
+    _check(lib().pf_checkpoint_write(sim, os.fsencode(path)), "pf_checkpoint_write")
+
+
+def pf_checkpoint_read(sim, path: str):
+    _check(lib().pf_checkpoint_read(sim, os.fsencode(path)), "pf_checkpoint_read")
 
 
 def pf_step_bytes(sim) -> dict:
@@ -529,3 +539,11 @@ class Simulation:
 
     def step_bytes(self):
         return pf_step_bytes(self.h)
+
+    def checkpoint(self, path):
+        pf_checkpoint_write(self.h, path)
+        return self
+
+    def restore(self, path):
+        pf_checkpoint_read(self.h, path)
+        return self

@@ -1,0 +1,110 @@
+"""Checkpoint and restart (the paper's field checkpoints, Section 3.2) through the C ABI.
+
+A run resumed from a checkpoint of its own precision must continue bitwise as the uninterrupted
+run: same fields, clock, window offset and shift count.  The configuration shifts the moving
+window before the checkpoint, so that the restored window offset and clock decide the plane
+constants of the resumed steps.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1506_01684_gb300 import pf
+from paper_1506_01684_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pf.lib()
+
+
+def _params():
+    p = W.symmetric_params(window_trigger_z=7.0)
+    p["seed_layers"] = 10
+    return p
+
+
+@pytest.mark.parametrize("precision,elem", [("fp32", 4), ("fp64", 8), ("fp32c", 8)])
+@pytest.mark.parametrize("variant", ["auto", "unfused"])
+def test_resumed_run_equals_the_uninterrupted_run_bitwise(tmp_path, precision, elem, variant):
+    nx, ny, nz = 32, 32, 64
+    p = _params()
+    path = str(tmp_path / f"ck_{precision}_{variant}.pfc")
+    a = pf.Simulation(nx, ny, nz, p, precision, variant=variant)
+    a.init(3)
+    a.step(25)
+    a.checkpoint(path)
+    st_ck = a.stats()
+    assert os.path.getsize(path) == 64 + nz * 6 * nx * ny * elem
+    a.step(30)
+    pa, ma = a.fields()
+    sa = a.stats()
+    b = pf.Simulation(nx, ny, nz, p, precision, variant=variant)
+    b.init(99)  # a different state, overwritten by the checkpoint
+    b.step(3)
+    b.restore(path)
+    sb0 = b.stats()
+    assert sb0["t"] == st_ck["t"] and sb0["window_offset"] == st_ck["window_offset"]
+    b.step(30)
+    pb, mb = b.fields()
+    sbb = b.stats()
+    assert st_ck["window_offset"] > 0  # the window had moved: the restored offset sets the plane constants
+    assert (pa == pb).all() and (ma == mb).all()
+    assert sa["t"] == sbb["t"] and sa["window_offset"] == sbb["window_offset"]
+    assert a.shifts() == b.shifts()
+    a.close()
+    b.close()
+
+
+def test_fp32_checkpoint_restores_into_fp64(tmp_path):
+    nx, ny, nz = 24, 16, 20
+    p = W.symmetric_params(n_grains=5)
+    path = str(tmp_path / "ck32.pfc")
+    a = pf.Simulation(nx, ny, nz, p, "fp32")
+    a.init(1)
+    a.step(5)
+    a.checkpoint(path)
+    pa, ma = a.fields()
+    b = pf.Simulation(nx, ny, nz, p, "fp64")
+    b.restore(path)
+    pb, mb = b.fields()
+    assert (pa == pb).all() and (ma == mb).all()  # FP32 values are exact in FP64
+    assert b.stats()["t"] == a.stats()["t"]
+    a.close()
+    b.close()
+
+
+def test_checkpoint_errors(tmp_path):
+    p = W.symmetric_params(n_grains=3)
+    a = pf.Simulation(16, 8, 12, p, "fp32")
+    a.init(0)
+    path = str(tmp_path / "ck.pfc")
+    a.checkpoint(path)
+    # another grid
+    b = pf.Simulation(16, 8, 13, p, "fp32")
+    with pytest.raises(pf.PfError) as e:
+        b.restore(path)
+    assert e.value.status == pf.PF_E_INVAL
+    # missing and truncated files
+    with pytest.raises(pf.PfError):
+        a.restore(str(tmp_path / "missing.pfc"))
+    data = open(path, "rb").read()
+    short = str(tmp_path / "short.pfc")
+    open(short, "wb").write(data[: len(data) // 2])
+    with pytest.raises(pf.PfError):
+        a.restore(short)
+    bad = str(tmp_path / "bad.pfc")
+    open(bad, "wb").write(b"NOTACKPT" + data[8:])
+    with pytest.raises(pf.PfError):
+        a.restore(bad)
+    # an unwritable path
+    with pytest.raises(pf.PfError):
+        a.checkpoint(str(tmp_path / "no_such_dir" / "ck.pfc"))
+    a.close()
+    b.close()
