@@ -175,6 +175,13 @@ enum {
     PF_K_COUNT = 8
 };
 
+/* Test hook for the failure path of the bounded device waits: with on != 0 the producer warp of
+ * the lean kernel (the fused step's pure-liquid planes) issues none of its copies, so its consumers'
+ * waits run out (after about 2^31 clock cycles each), the step ends and pf_sync returns
+ * PF_E_TIMEOUT; the fields of the affected planes are then not updated.  The GPU context stays
+ * usable; on = 0 restores normal steps.  Not for production use. */
+int pf_test_withhold_copies(pf_sim *sim, int on);
+
 /* Kernel variants of pf_step.  UNFUSED runs Algorithm 1 as two kernels (the phi-sweep writes
  * phi^{n+1}, the mu-sweep reads it back: 88 algorithmic bytes per FP32 cell); FUSED computes
  * phi^{n+1} and mu^{n+1} in one pass (each CTA recomputes phi^{n+1} on a one-cell ring around its

@@ -160,6 +160,7 @@ struct pf_sim {
     bool use_graphs = true;
     int last_nparts = 0;  // partial sums written by the last step's kernels
     int last_kind = -1;   // 0: two sweeps, 1: fused kernel alone, 2: fused kernel + lean kernel
+    bool test_withhold = false;  // test hook: the lean kernel's producer issues no copies
     size_t ncell() const { return (size_t)nx * ny * nz; }
     size_t wbytes() const { return p.precision == PF_FP64 ? 8 : 4; }
     bool comp() const { return p.precision == PF_FP32_COMP; }
@@ -238,6 +239,7 @@ static KParams<R> make_kparams(const pf_sim *s)
     k.window = p.window_trigger_z > 0.0 ? 1 : 0;
     k.tgx = s->geo_fused.gx;
     k.tgy = s->geo_fused.gy;
+    k.test_flags = s->test_withhold ? 1 : 0;
     k.dx = (R)p.dx;
     k.inv_dx = (R)(1.0 / p.dx);
     k.inv_2dx = (R)(1.0 / (2.0 * p.dx));
@@ -1185,6 +1187,17 @@ int pf_step_bytes(pf_sim *s, double bytes[])
     for (const Partial &x : h) g += x.bytes;
     bytes[s->last_kind == 2 && PF_GENERAL_SWEEPS ? PF_K_GENERAL : PF_K_FUSED] = g;
     bytes[PF_K_LEAN] = (double)ls.last_bytes;
+    return PF_OK;
+}
+
+int pf_test_withhold_copies(pf_sim *s, int on)
+{
+    if (!s) return PF_E_INVAL;
+    s->test_withhold = on != 0;
+    if (s->graph) {  // captured with the previous parameters
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
     return PF_OK;
 }
 

@@ -61,7 +61,7 @@ struct KParams {
     int zchunk;  // planes per CTA along z
     int window;  // 1: moving window enabled
     int tgx, tgy;  // tile grid of the fused step (liquid map layout)
-    int pad_;
+    int test_flags;  // bit 0: the lean kernel's producer withholds its copies (tests of the bounded waits)
     R dx, inv_dx, inv_2dx, inv_4dx;
     R eps, inv_eps;
     R c_phi;  // dt / (tau eps)

@@ -2563,7 +2563,7 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
 
 // lean kernel shape: pipeline stages, at most planes per CTA, tile rows per consumer thread
 #ifndef PF_LEAN_STAGES
-#define PF_LEAN_STAGES 4
+#define PF_LEAN_STAGES 8
 #endif
 #ifndef PF_LEAN_PLANES
 #define PF_LEAN_PLANES 64

@@ -20,7 +20,7 @@
 #include <cuda.h>
 
 #ifndef PF_LEAN_MIN_CTAS
-#define PF_LEAN_MIN_CTAS 8  // resident lean CTAs per SM the register allocation must allow
+#define PF_LEAN_MIN_CTAS 7  // resident lean CTAs per SM the register allocation must allow
 #endif
 #ifndef PF_LEAN_SUSPEND_NS
 #define PF_LEAN_SUSPEND_NS 1000u  // longest suspension of a waiting thread per try (the wait's bound is separate)
@@ -220,7 +220,8 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
         const bool fix = fixes(lane);
         unsigned u = 0;  // stage uses issued
         bool ok = true;
-        for (int g = 0; g < 2 && ok; g++) {
+        // (test hook: no copies at all, so that the consumers' bounded waits run out)
+        for (int g = 0; g < 2 && ok && !(kp.test_flags & 1); g++) {
             if (qb[g] <= qa[g]) continue;
             // planes qa-1 (its mu for the z flux below qa) .. qb (for the z flux above qb-1)
             const int la = max(qa[g] - 1, 0), lb = min(qb[g], nz - 1);

@@ -82,6 +82,7 @@ SIGNATURES = {
     "pf_stats": (_I, [_VP, _DP, _DP, _DP, _DP]),
     "pf_window_shifts": (_I, [_VP, ctypes.POINTER(_I)]),
     "pf_step_bytes": (_I, [_VP, _DP]),
+    "pf_test_withhold_copies": (_I, [_VP, _I]),
     "pf_checkpoint_write": (_I, [_VP, ctypes.c_char_p]),
     "pf_checkpoint_read": (_I, [_VP, ctypes.c_char_p]),
     "pf_profile": (_I, [_VP, _I]),
@@ -260,6 +261,10 @@ def pf_window_shifts(sim) -> int:
     n = _I()
     _check(lib().pf_window_shifts(sim, ctypes.byref(n)), "pf_window_shifts")
     return n.value
+
+
+def pf_test_withhold_copies(sim, on: bool):
+    _check(lib().pf_test_withhold_copies(sim, 1 if on else 0), "pf_test_withhold_copies")
 
 
 def pf_checkpoint_write(sim, path: str):
