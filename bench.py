@@ -420,6 +420,56 @@ def run_region_study(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mesh_study(args):
+    """Per-phase interface meshes (the paper's isosurface output, Section 3.2) of the benchmark
+    domain after a growth phase: device time of the three mesh kernels (CUDA events around each
+    launch) and the wall time of the whole pf_interface_mesh call (count, scan, totals to the host,
+    emit, copy of the triangles to pageable host memory), for each phase at iso 0.5.  Roofline of the
+    counting kernel (the one that reads the whole field): the layout's algorithmic bytes, every
+    cell's phi (4 words: the AoS cell the phase value sits in) read once."""
+    import time as _t
+
+    from paper_1506_01684_gb300 import pf
+    from paper_1506_01684_gb300 import workloads as W
+
+    p = W.symmetric_params(n_grains=args.grains, window_trigger_z=TRIGGER)
+    sim = pf.Simulation(NX, NY, NZ, p, "fp32")
+    sim.init(SEED)
+    sim.step(args.mesh_steps)
+    sim.sync()
+    peak, peak_kind = _peaks()
+    ncell = NX * NY * NZ
+    phases = {}
+    for a in range(4):
+        for _ in range(args.warmup):
+            tris = sim.interface_mesh(a, 0.5)
+        pf.pf_profile(sim.h, True)
+        pf.pf_profile_read(sim.h)
+        t0 = _t.perf_counter()
+        for _ in range(args.steps):
+            tris = sim.interface_mesh(a, 0.5)
+        wall = (_t.perf_counter() - t0) / args.steps
+        prof = pf.pf_profile_read(sim.h)
+        pf.pf_profile(sim.h, False)
+        ms = {k: prof[k][0] / prof[k][1] for k in ("mesh_count", "mesh_scan", "mesh_emit")}
+        b_c = 16.0 * ncell
+        phases[a] = {"triangles": len(tris), "count_ms": ms["mesh_count"], "scan_ms": ms["mesh_scan"],
+                     "emit_ms": ms["mesh_emit"], "call_ms": wall * 1e3,
+                     "count_gbs": b_c / ms["mesh_count"] / 1e6,
+                     "count_frac_of_" + peak_kind: b_c / ms["mesh_count"] / 1e6 / peak,
+                     "kernel_gcells_per_s": ncell / sum(ms.values()) / 1e6}
+    sim.close()
+    line = {"metric": "interface-mesh extraction (per phase, marching tetrahedra): cells/s of the mesh kernels",
+            "unit": "Gcell/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "f32", "data": "synthetic",
+            "value": min(ph["kernel_gcells_per_s"] for ph in phases.values()),
+            "peak_hbm_gbs": peak, "peak_kind": peak_kind,
+            "config": {"workload": f"{WORKLOAD}, after {args.mesh_steps} steps, iso 0.5",
+                       "timing": "CUDA events around each mesh kernel; wall clock around each call"},
+            "phases": phases}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,7 +479,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="steps of the FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=["batched", "serving", "precision", "regions"],
+    ap.add_argument("--study", default=None, choices=["batched", "serving", "precision", "regions", "mesh"],
                     help="run a secondary study instead of the headline line")
     ap.add_argument("--requests", type=int, default=100, help="serving study: number of requests")
     ap.add_argument("--min-steps", type=int, default=100, help="serving study: fewest steps per request")
@@ -439,6 +489,7 @@ def main():
     ap.add_argument("--study-shape", default="128x128x512", help="precision study: domain")
     ap.add_argument("--study-steps", type=int, default=20000, help="precision study: steps")
     ap.add_argument("--region-shape", default="256x256x256", help="region study: block size")
+    ap.add_argument("--mesh-steps", type=int, default=3000, help="mesh study: growth steps before the meshes")
     ap.add_argument("--variant", default="auto", choices=["auto", "unfused", "fused"],
                     help="kernel variant of the FP32 step (auto: the library's choice)")
     ap.add_argument("--grains", type=int, default=GRAINS,
@@ -477,6 +528,9 @@ def main():
         return
     if args.study == "precision":
         run_precision_study(args)
+        return
+    if args.study == "mesh":
+        run_mesh_study(args)
         return
     if args.study == "regions":
         run_region_study(args)

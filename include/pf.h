@@ -160,6 +160,27 @@ int pf_stats(pf_sim *sim, double *t, double *window_offset, double solute[2], do
 /* Number of window shifts (planes moved) since pf_init.  Synchronising. */
 int pf_window_shifts(pf_sim *sim, int *planes);
 
+/* Interface mesh of one phase (the paper's per-phase isosurface output, Section 3.2): the triangles
+ * of the surface phi_phase = iso of the current fields, by marching tetrahedra over the grid of
+ * cell centres.  A cube has the centres (i + a, j + b, k + c), a, b, c in {0, 1}, as corners and
+ * wraps periodically in x and y (not in z): nx * ny * (nz - 1) cubes, in the order (k ny + j) nx + i.
+ * Each cube is cut into the six tetrahedra of its Kuhn triangulation (corner 0, then the axes added
+ * in the order of a permutation of (x, y, z), permutations in lexicographic order), so shared faces
+ * are cut alike and the surface has no cracks.  A corner is inside when its value is >= iso; a
+ * tetrahedron with one inside (or one outside) corner gives one triangle, with two a quad as two
+ * triangles; vertices are interpolated linearly along the cut edges; each normal (v1 - v0) x (v2 -
+ * v0) points from the inside corners to the outside ones (toward lower phi_phase).  Positions in
+ * units of dx, cell (i, j, k) at (i + 1/2, j + 1/2, k + 1/2 + window offset).
+ *   phase     0..3 (3 = liquid);  iso  the level, rounded to the simulation's precision (the
+ *             compensated FP32 state uses its FP32 words); classification and interpolation run in
+ *             that precision, positions are formed in FP64 and stored as FP32
+ *   tris      HOST buffer of cap_tris * 9 floats (x, y, z of v0, v1, v2 per triangle), written in the
+ *             order cube, tetrahedron, triangle; NULL: count only
+ *   ntris     out: the number of triangles (always set on PF_OK and on a too-small buffer)
+ * PF_E_INVAL for phase out of range, a non-finite iso, ntris == NULL, or cap_tris below the count
+ * (nothing is then written to tris).  Allocates device scratch for the call.  Synchronising. */
+int pf_interface_mesh(pf_sim *sim, int phase, double iso, float *tris, size_t cap_tris, size_t *ntris);
+
 
 
 /* Kernel classes of the per-kernel timers. */
@@ -172,7 +193,10 @@ enum {
     PF_K_LEAN = 5,     /* the fused step's pure-liquid planes (Section 3.3 shortcuts), a kernel of their own */
     PF_K_PLAN = 6,     /* the fused step's split into pure-liquid and general planes */
     PF_K_GENERAL = 7,  /* the fused step's general planes as the two sweeps (Algorithm 1) */
-    PF_K_COUNT = 8
+    PF_K_MESH_COUNT = 8, /* pf_interface_mesh: triangles per segment of cubes */
+    PF_K_MESH_SCAN = 9,  /* pf_interface_mesh: offsets of the segments that have triangles */
+    PF_K_MESH_EMIT = 10, /* pf_interface_mesh: the triangles */
+    PF_K_COUNT = 11
 };
 
 /* Test hook for the failure path of the bounded device waits: with on != 0 the producer warp of

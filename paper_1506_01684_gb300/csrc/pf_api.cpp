@@ -702,6 +702,66 @@ static int do_reduce(pf_sim *s, double out[8])
     return PF_OK;
 }
 
+// interface mesh of one phase: triangles per segment of cubes, a device scan into the offsets of
+// the non-empty segments, the totals to the host, then the triangles of those segments into a
+// device buffer copied to the caller's
+template <typename R>
+static int do_mesh(pf_sim *s, int phase, double iso, float *tris, size_t cap, size_t *ntris)
+{
+    *ntris = 0;
+    if (s->nz < 2) return PF_OK;
+    const KParams<R> kp = make_kparams<R>(s);
+    const size_t nb = ((size_t)s->nx + 255) / 256, nseg = nb * s->ny * (size_t)(s->nz - 1);
+    const size_t npad = (nseg + 15) / 16 * 16;
+    // ne_off (npad u64) | totals (2 u64) | counts (npad u32) | ne_seg (npad u32)
+    DevBuf scratch;
+    int r = dev_alloc(scratch, npad * 8 + 16 + npad * 8, s->stream);
+    if (r != PF_OK) return r;
+    unsigned long long *ne_off = (unsigned long long *)scratch.p, *dtot = ne_off + npad;
+    unsigned *counts = (unsigned *)(dtot + 2), *ne_seg = counts + npad;
+    unsigned long long tot[2] = {0, 0};
+    cudaError_t e = cudaSuccess;
+    if (npad > nseg) e = cudaMemsetAsync(counts + nseg, 0, (npad - nseg) * sizeof(unsigned), s->stream);
+    if (e == cudaSuccess)
+        e = timed(s, PF_K_MESH_COUNT, [&] {
+            return launch_mesh_count<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, phase, iso, counts,
+                                        s->stream);
+        });
+    if (e == cudaSuccess)
+        e = timed(s, PF_K_MESH_SCAN, [&] { return launch_mesh_scan<R>(counts, npad, ne_seg, ne_off, dtot, s->stream); });
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tot, dtot, sizeof tot, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        dev_free(scratch, s->stream);
+        return latch(s, cuda_status(e));
+    }
+    *ntris = (size_t)tot[0];
+    if (!tris || tot[0] == 0) {
+        dev_free(scratch, s->stream);
+        return PF_OK;
+    }
+    if (cap < tot[0]) {
+        dev_free(scratch, s->stream);
+        return PF_E_INVAL;
+    }
+    DevBuf out;
+    r = dev_alloc(out, (size_t)tot[0] * 9 * sizeof(float), s->stream);
+    if (r != PF_OK) {
+        dev_free(scratch, s->stream);
+        return r;
+    }
+    e = timed(s, PF_K_MESH_EMIT, [&] {
+        return launch_mesh_emit<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, phase, iso, ne_seg, ne_off,
+                                   (unsigned)tot[1], tot[0], (float *)out.p, s->stream);
+    });
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tris, out.p, (size_t)tot[0] * 9 * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    dev_free(out, s->stream);
+    dev_free(scratch, s->stream);
+    return e == cudaSuccess ? PF_OK : latch(s, cuda_status(e));
+}
+
 static int read_state(pf_sim *s, DevState *ds)
 {
     cudaError_t e = cudaMemcpyAsync(ds, s->state.p, sizeof *ds, cudaMemcpyDeviceToHost, s->stream);
@@ -1120,6 +1180,12 @@ int pf_checkpoint_read(pf_sim *s, const char *path)
 {
     if (!s || !path) return PF_E_INVAL;
     return PF_DISPATCH(s, do_checkpoint_read, s, path);
+}
+
+int pf_interface_mesh(pf_sim *s, int phase, double iso, float *tris, size_t cap_tris, size_t *ntris)
+{
+    if (!s || !ntris || phase < 0 || phase > 3 || !isfinite(iso)) return PF_E_INVAL;
+    return PF_DISPATCH(s, do_mesh, s, phase, iso, tris, cap_tris, ntris);
 }
 
 int pf_phase_fractions(pf_sim *s, double out[4])

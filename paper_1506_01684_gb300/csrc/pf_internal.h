@@ -214,6 +214,21 @@ template <typename R>
 cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, void *mu, const double *phi_soa,
                           const double *mu_soa, int k0, int nk, cudaStream_t s, void *phi_lo = nullptr,
                           void *mu_lo = nullptr);
+// Interface mesh of phase `phase` (marching tetrahedra over the cell centres), in segments of up to
+// 256 cubes of one row of one layer, ordered (k ny + j) nb + b with nb = ceil(nx / 256): triangles
+// per segment; the offsets and ids of the non-empty segments with the totals (triangles, non-empty
+// segments; one CTA; counts padded with zeros to nseg_pad, a multiple of 16); the triangles of the
+// listed segments (9 floats a triangle).
+template <typename R>
+cudaError_t launch_mesh_count(const KParams<R> &kp, const DevState *st, const void *phi, int phase, double iso,
+                              unsigned *seg_counts, cudaStream_t s);
+template <typename R>
+cudaError_t launch_mesh_scan(const unsigned *seg_counts, size_t nseg_pad, unsigned *ne_seg, unsigned long long *ne_off,
+                             unsigned long long *totals, cudaStream_t s);
+template <typename R>
+cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const void *phi, int phase, double iso,
+                             const unsigned *ne_seg, const unsigned long long *ne_off, unsigned n_ne,
+                             unsigned long long ntris, float *tris, cudaStream_t s);
 
 // Compensated FP32 (state = hi + lo) variants of the two sweeps.
 cudaError_t launch_phi_sweep_comp(const KParams<float> &kp, const Geometry &g, const void *phi, const void *phi_lo,

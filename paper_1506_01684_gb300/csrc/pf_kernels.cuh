@@ -2090,6 +2090,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) batched_fused_
 
 }  // namespace pf
 #include "pf_lean.cuh"
+#include "pf_mesh.cuh"
 namespace pf {
 
 // ---------------------------------------------------------------------------------------
@@ -2891,6 +2892,35 @@ cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, v
     return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_mesh_count(const KParams<R> &kp, const DevState *st, const void *phi, int phase, double iso,
+                              unsigned *seg_counts, cudaStream_t s)
+{
+    const int nb = (kp.nx + MESH_W - 1) / MESH_W;
+    const dim3 grid((unsigned)(nb * kp.ny), (unsigned)((kp.nz - 1 + MESH_KC - 1) / MESH_KC));
+    mesh_count_kernel<R><<<grid, MESH_W, 0, s>>>((const Ph<R> *)phi, st, kp.nx, kp.ny, kp.nz, phase, (R)iso,
+                                                 seg_counts);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_mesh_scan(const unsigned *seg_counts, size_t nseg_pad, unsigned *ne_seg, unsigned long long *ne_off,
+                             unsigned long long *totals, cudaStream_t s)
+{
+    mesh_scan_kernel<<<1, 1024, 0, s>>>(seg_counts, nseg_pad, ne_seg, ne_off, totals);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const void *phi, int phase, double iso,
+                             const unsigned *ne_seg, const unsigned long long *ne_off, unsigned n_ne,
+                             unsigned long long ntris, float *tris, cudaStream_t s)
+{
+    mesh_emit_kernel<R><<<n_ne, MESH_W, 0, s>>>((const Ph<R> *)phi, st, kp.nx, kp.ny, kp.nz, phase, (R)iso, ne_seg,
+                                                ne_off, ntris, tris);
+    return cudaGetLastError();
+}
+
 #define PF_INSTANTIATE(R)                                                                                        \
     template cudaError_t launch_phi_sweep<R>(const KParams<R> &, const Geometry &, const void *, const void *,  \
                                              void *, const DevState *, const PlaneT<R> *, cudaStream_t);        \
@@ -2935,6 +2965,13 @@ cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, v
     template cudaError_t launch_pack<R>(const KParams<R> &, const DevState *, const void *, const void *,        \
                                         double *, double *, int, int, cudaStream_t, const void *, const void *); \
     template cudaError_t launch_unpack<R>(const KParams<R> &, const DevState *, void *, void *, const double *,  \
-                                          const double *, int, int, cudaStream_t, void *, void *);
+                                          const double *, int, int, cudaStream_t, void *, void *);              \
+    template cudaError_t launch_mesh_count<R>(const KParams<R> &, const DevState *, const void *, int, double,    \
+                                              unsigned *, cudaStream_t);                                         \
+    template cudaError_t launch_mesh_scan<R>(const unsigned *, size_t, unsigned *, unsigned long long *,          \
+                                             unsigned long long *, cudaStream_t);                               \
+    template cudaError_t launch_mesh_emit<R>(const KParams<R> &, const DevState *, const void *, int, double,     \
+                                             const unsigned *, const unsigned long long *, unsigned,            \
+                                             unsigned long long, float *, cudaStream_t);
 
 }  // namespace pf

@@ -1,0 +1,400 @@
+// pf_mesh.cuh -- per-phase interface meshes (the paper's isosurface output of each phase,
+// Section 3.2): the isosurface phi_a = iso of the current field by marching tetrahedra over the
+// grid of cell centres.
+//
+// A cube has the cell centres (i + a, j + b, k + c), a, b, c in {0, 1}, as corners (corner n = a +
+// 2b + 4c), wraps periodically in x and y (the position of column nx stays nx) and not in z:
+// nx * ny * (nz - 1) cubes in the order c = (k ny + j) nx + i.  Each cube is cut into the six
+// tetrahedra of its Kuhn triangulation (corner 0, then the three axes added in the order of a
+// permutation, permutations in lexicographic order), which cut shared faces alike, so the surface
+// has no cracks.  A corner is inside when its value is >= iso.  One inside (or outside) corner: one
+// triangle through the edges from that corner to the other three (in increasing corner order); two
+// inside corners a < b and outside c < d: the triangles (ac, ad, bd) and (ac, bd, bc).  A vertex on
+// an edge from inside corner p to outside corner q is p + t (q - p), t = (iso - f_p) / (f_q - f_p).
+// The normal (v1 - v0) x (v2 - v0) of a triangle points from the tetrahedron's inside corners to its
+// outside ones (else v1 and v2 are swapped).  Classification, t and the orientation use the field's
+// precision, the orientation in coordinates local to the cube (exact corner offsets 0 / 1, so that
+// the sign does not depend on how far the cube is from the origin); a position is the cube's base
+// (exact) plus the local vertex, rounded to FP32.  Triangles are written in the order cube,
+// tetrahedron, triangle.
+#pragma once
+
+namespace pf {
+
+__device__ __forceinline__ void kuhn_tet(int q, int (&v)[4])
+{
+    // permutations of (x, y, z) in lexicographic order: 012 021 102 120 201 210
+    const int ax[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    int pos = 0;
+    v[0] = 0;
+#pragma unroll
+    for (int s = 0; s < 3; s++) {
+        pos |= 1 << ax[q][s];
+        v[s + 1] = pos;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ int tet_count(const R (&f)[8], int q, R iso)
+{
+    int v[4];
+    kuhn_tet(q, v);
+    int n = 0;
+#pragma unroll
+    for (int s = 0; s < 4; s++) n += f[v[s]] >= iso ? 1 : 0;
+    return n == 0 || n == 4 ? 0 : (n == 2 ? 2 : 1);
+}
+
+template <typename R>
+__device__ __forceinline__ void corner_values(const Ph<R> *__restrict__ phi, int nx, int ny, int nz, int zbase,
+                                              int phase, int i, int j, int k, R (&f)[8])
+{
+    const size_t plane = (size_t)nx * ny;
+    const int i1 = i + 1 == nx ? 0 : i + 1, j1 = j + 1 == ny ? 0 : j + 1;
+#pragma unroll
+    for (int n = 0; n < 8; n++) {
+        const int ii = (n & 1) ? i1 : i, jj = (n & 2) ? j1 : j, kk = k + ((n >> 2) & 1);
+        f[n] = phi[plane_off(kk, nz, zbase, plane) + (size_t)jj * nx + ii].v[phase];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ int cube_count(const R (&f)[8], R iso)
+{
+    int t = 0;
+#pragma unroll
+    for (int q = 0; q < 6; q++) t += tet_count(f, q, iso);
+    return t;
+}
+
+// the triangles of tetrahedron q of a cube (corner values f, base position bx, by, bz) at out
+// (9 floats each); returns how many
+template <typename R>
+__device__ __forceinline__ int tet_emit(const R (&f)[8], int q, R iso, R bx, R by, R bz, float *__restrict__ out)
+{
+    int v[4];
+    kuhn_tet(q, v);
+    int in[4], ou[4], ni = 0, no = 0;
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        if (f[v[s]] >= iso)
+            in[ni++] = v[s];
+        else
+            ou[no++] = v[s];
+    }
+    if (ni == 0 || ni == 4) return 0;
+    // local vertex on the edge from inside corner a to outside corner b
+    auto vert = [&](int a, int b, R (&p)[3]) {
+        const R t = (iso - f[a]) / (f[b] - f[a]);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const R ca = (R)((a >> d) & 1), cb = (R)((b >> d) & 1);
+            p[d] = ca + t * (cb - ca);
+        }
+    };
+    R tri[2][3][3];
+    int nt;
+    if (ni == 1) {
+        for (int s = 0; s < 3; s++) vert(in[0], ou[s], tri[0][s]);
+        nt = 1;
+    } else if (ni == 3) {
+        for (int s = 0; s < 3; s++) vert(in[s], ou[0], tri[0][s]);
+        nt = 1;
+    } else {
+        R ac[3], ad[3], bd[3], bc[3];
+        vert(in[0], ou[0], ac);
+        vert(in[0], ou[1], ad);
+        vert(in[1], ou[1], bd);
+        vert(in[1], ou[0], bc);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            tri[0][0][d] = ac[d];
+            tri[0][1][d] = ad[d];
+            tri[0][2][d] = bd[d];
+            tri[1][0][d] = ac[d];
+            tri[1][1][d] = bd[d];
+            tri[1][2][d] = bc[d];
+        }
+        nt = 2;
+    }
+    // inside -> outside direction of the tetrahedron (means of the local corner positions)
+    R dir[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        R si = 0, so = 0;
+        for (int s = 0; s < ni; s++) si += (R)((in[s] >> d) & 1);
+        for (int s = 0; s < no; s++) so += (R)((ou[s] >> d) & 1);
+        dir[d] = so / (R)no - si / (R)ni;
+    }
+    const R base[3] = {bx, by, bz};
+    for (int m = 0; m < nt; m++) {
+        R e1[3], e2[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            e1[d] = tri[m][1][d] - tri[m][0][d];
+            e2[d] = tri[m][2][d] - tri[m][0][d];
+        }
+        const R n0 = e1[1] * e2[2] - e1[2] * e2[1], n1 = e1[2] * e2[0] - e1[0] * e2[2],
+                n2 = e1[0] * e2[1] - e1[1] * e2[0];
+        const bool flip = n0 * dir[0] + n1 * dir[1] + n2 * dir[2] < (R)0;
+        float *o = out + 9 * m;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            o[d] = (float)(base[d] + tri[m][0][d]);
+            o[3 + d] = (float)(base[d] + tri[m][flip ? 2 : 1][d]);
+            o[6 + d] = (float)(base[d] + tri[m][flip ? 1 : 2][d]);
+        }
+    }
+    return nt;
+}
+
+// The cubes are counted and emitted in segments: segment (k, j, b) holds the cubes i = 256 b ..
+// 256 b + 255 (< nx) of row j of layer k, so that segments in the order (k ny + j) nb + b keep the
+// cube order.  Pass 1 counts the triangles of each segment (a CTA marches MESH_KC layers of one
+// row piece, one thread per cube, the x + 1 corners taken from the next lane); pass 2 (one CTA)
+// scans the counts into the offsets of the segments that have triangles and lists them; pass 3
+// writes the triangles of the listed segments.
+constexpr int MESH_W = 256;  // cubes of a row per segment (one thread each)
+constexpr int MESH_KC = 32;  // layers per counting CTA
+
+template <typename R>
+__global__ void __launch_bounds__(MESH_W) mesh_count_kernel(const Ph<R> *__restrict__ phi, const DevState *__restrict__ st,
+                                                           int nx, int ny, int nz, int phase, R iso,
+                                                           unsigned *__restrict__ seg_counts)
+{
+    __shared__ unsigned wsum[MESH_KC][MESH_W / 32];
+    const int nb = (nx + MESH_W - 1) / MESH_W;
+    const int b = blockIdx.x % nb, j = blockIdx.x / nb;
+    const int k0 = blockIdx.y * MESH_KC, k1 = min(nz - 1, k0 + MESH_KC);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = b * MESH_W + threadIdx.x;
+    const bool act = i < nx;
+    const int ic = act ? i : nx - 1;
+    const int i1 = ic + 1 == nx ? 0 : ic + 1, j1 = j + 1 == ny ? 0 : j + 1;
+    const bool from_lane = lane < 31 && ic + 1 < nx;  // the next lane holds column i + 1
+    const size_t plane = (size_t)nx * ny;
+    const int zbase = st->zbase;
+    auto ld = [&](int k, int jj, int ii) { return phi[plane_off(k, nz, zbase, plane) + (size_t)jj * nx + ii].v[phase]; };
+    // corner values of layer k: a0 = (i, j), a2 = (i, j+1), a1 = (i+1, j), a3 = (i+1, j+1)
+    R a0 = ld(k0, j, ic), a2 = ld(k0, j1, ic);
+    R a1 = __shfl_down_sync(0xffffffffu, a0, 1), a3 = __shfl_down_sync(0xffffffffu, a2, 1);
+    if (!from_lane) {
+        a1 = ld(k0, j, i1);
+        a3 = ld(k0, j1, i1);
+    }
+    // layer k + 1 is loaded one iteration ahead, so that two layers' loads are in flight
+    R p0 = ld(k0 + 1, j, ic), p2 = ld(k0 + 1, j1, ic), p1 = p0, p3 = p2;
+    if (!from_lane) {
+        p1 = ld(k0 + 1, j, i1);
+        p3 = ld(k0 + 1, j1, i1);
+    }
+    for (int k = k0; k < k1; k++) {
+        const R c0 = p0, c2 = p2;
+        R c1 = __shfl_down_sync(0xffffffffu, c0, 1), c3 = __shfl_down_sync(0xffffffffu, c2, 1);
+        if (!from_lane) {
+            c1 = p1;
+            c3 = p3;
+        }
+        if (k + 2 <= k1) {
+            p0 = ld(k + 2, j, ic);
+            p2 = ld(k + 2, j1, ic);
+            if (!from_lane) {
+                p1 = ld(k + 2, j, i1);
+                p3 = ld(k + 2, j1, i1);
+            }
+        }
+        const R f[8] = {a0, a1, a2, a3, c0, c1, c2, c3};
+        unsigned n = act ? (unsigned)cube_count(f, iso) : 0u;
+        n = __reduce_add_sync(0xffffffffu, n);
+        if (lane == 0) wsum[k - k0][w] = n;
+        a0 = c0;
+        a1 = c1;
+        a2 = c2;
+        a3 = c3;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < k1 - k0) {
+        unsigned sum = 0;
+#pragma unroll
+        for (int q = 0; q < MESH_W / 32; q++) sum += wsum[threadIdx.x][q];
+        seg_counts[((size_t)(k0 + threadIdx.x) * ny + j) * nb + b] = sum;
+    }
+}
+
+// exclusive block-wide sums of two per-thread values (1024 threads); returns the block totals
+__device__ __forceinline__ void block_scan2(unsigned long long &x, unsigned &y, unsigned long long &tx, unsigned &ty,
+                                            unsigned long long *sx, unsigned *sy)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long ix = x;
+    unsigned iy = y;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long px = __shfl_up_sync(0xffffffffu, ix, o);
+        const unsigned py = __shfl_up_sync(0xffffffffu, iy, o);
+        if (lane >= o) {
+            ix += px;
+            iy += py;
+        }
+    }
+    if (lane == 31) {
+        sx[w] = ix;
+        sy[w] = iy;
+    }
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long vx = sx[lane];
+        unsigned vy = sy[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long px = __shfl_up_sync(0xffffffffu, vx, o);
+            const unsigned py = __shfl_up_sync(0xffffffffu, vy, o);
+            if (lane >= o) {
+                vx += px;
+                vy += py;
+            }
+        }
+        sx[lane] = vx;  // inclusive over warps
+        sy[lane] = vy;
+    }
+    __syncthreads();
+    const unsigned long long bx = w ? sx[w - 1] : 0ull;
+    const unsigned by = w ? sy[w - 1] : 0u;
+    x = bx + ix - x;
+    y = by + iy - y;
+    tx = sx[31];
+    ty = sy[31];
+    __syncthreads();
+}
+
+// pass 2: one CTA of 1024 threads over the segment counts (padded with zeros to a multiple of 16):
+// the offsets and ids of the non-empty segments, and the totals (triangles, non-empty segments)
+static __global__ void __launch_bounds__(1024) mesh_scan_kernel(const unsigned *__restrict__ seg_counts, size_t nseg_pad,
+                                                         unsigned *__restrict__ ne_seg,
+                                                         unsigned long long *__restrict__ ne_off,
+                                                         unsigned long long *__restrict__ totals)
+{
+    __shared__ unsigned long long sx[32];
+    __shared__ unsigned sy[32];
+    unsigned long long carry = 0;
+    unsigned ncarry = 0;
+    for (size_t base = 0; base < nseg_pad; base += 1024 * 16) {
+        const size_t first = base + (size_t)threadIdx.x * 16;
+        unsigned v[16];
+        if (first < nseg_pad) {
+            const uint4 *p4 = reinterpret_cast<const uint4 *>(seg_counts + first);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint4 u = p4[q];
+                v[4 * q] = u.x;
+                v[4 * q + 1] = u.y;
+                v[4 * q + 2] = u.z;
+                v[4 * q + 3] = u.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; q++) v[q] = 0;
+        }
+        unsigned long long sum = 0;
+        unsigned ne = 0;
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            sum += v[q];
+            ne += v[q] ? 1u : 0u;
+        }
+        unsigned long long tsum;
+        unsigned tne;
+        block_scan2(sum, ne, tsum, tne, sx, sy);
+        unsigned long long off = carry + sum;
+        unsigned pos = ncarry + ne;
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            if (v[q]) {
+                ne_seg[pos] = (unsigned)(first + q);
+                ne_off[pos] = off;
+                pos++;
+                off += v[q];
+            }
+        }
+        carry += tsum;
+        ncarry += tne;
+    }
+    if (threadIdx.x == 0) {
+        totals[0] = carry;
+        totals[1] = ncarry;
+    }
+}
+
+// pass 3: the triangles of each listed segment, from its offset, in cube order.  The crossed cubes
+// of the segment are gathered into shared memory, then the CTA's threads take one (cube,
+// tetrahedron) pair each, so that the lanes stay busy however sparse the crossed cubes are.
+template <typename R>
+__global__ void __launch_bounds__(MESH_W) mesh_emit_kernel(const Ph<R> *__restrict__ phi, const DevState *__restrict__ st,
+                                                          int nx, int ny, int nz, int phase, R iso,
+                                                          const unsigned *__restrict__ ne_seg,
+                                                          const unsigned long long *__restrict__ ne_off,
+                                                          unsigned long long total, float *__restrict__ out)
+{
+    __shared__ unsigned ws[MESH_W / 32], wc[MESH_W / 32];
+    __shared__ R sf[MESH_W][8];
+    __shared__ unsigned s_first[MESH_W];  // first triangle of the crossed cube, relative to the segment
+    __shared__ int s_i[MESH_W];
+    const int nb = (nx + MESH_W - 1) / MESH_W;
+    const size_t seg = ne_seg[blockIdx.x];
+    const int b = (int)(seg % nb), j = (int)((seg / nb) % ny), k = (int)(seg / ((size_t)nb * ny));
+    const int i = b * MESH_W + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    R f[8];
+    unsigned n = 0;
+    if (i < nx) {
+        corner_values(phi, nx, ny, nz, st->zbase, phase, i, j, k, f);
+        n = (unsigned)cube_count(f, iso);
+    }
+    // exclusive prefixes over the segment of the triangles and of the crossed cubes
+    unsigned x = n, c = n ? 1u : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o), z = __shfl_up_sync(0xffffffffu, c, o);
+        if (lane >= o) {
+            x += y;
+            c += z;
+        }
+    }
+    if (lane == 31) {
+        ws[w] = x;
+        wc[w] = c;
+    }
+    __syncthreads();
+    unsigned before = 0, cbefore = 0, ncross = 0;
+    for (int q = 0; q < MESH_W / 32; q++) {
+        if (q < w) {
+            before += ws[q];
+            cbefore += wc[q];
+        }
+        ncross += wc[q];
+    }
+    if (n) {
+        const unsigned slot = cbefore + c - 1;
+#pragma unroll
+        for (int m = 0; m < 8; m++) sf[slot][m] = f[m];
+        s_first[slot] = before + x - n;
+        s_i[slot] = i;
+    }
+    __syncthreads();
+    const unsigned long long seg_first = ne_off[blockIdx.x];
+    const R by = (R)j + (R)0.5, bz = (R)k + (R)0.5 + (R)st->off;
+    for (unsigned item = threadIdx.x; item < ncross * 6; item += MESH_W) {
+        const unsigned slot = item / 6;
+        const int q = (int)(item - slot * 6);
+        R g[8];
+#pragma unroll
+        for (int m = 0; m < 8; m++) g[m] = sf[slot][m];
+        unsigned first = s_first[slot];
+        for (int p = 0; p < q; p++) first += (unsigned)tet_count(g, p, iso);
+        const unsigned long long at = seg_first + first;
+        if (at + (unsigned long long)tet_count(g, q, iso) <= total)  // the counts of pass 1 and here agree; the bound guards the buffer
+            tet_emit(g, q, iso, (R)s_i[slot] + (R)0.5, by, bz, out + 9ull * at);
+    }
+}
+
+}  // namespace pf

@@ -85,6 +85,8 @@ SIGNATURES = {
     "pf_test_withhold_copies": (_I, [_VP, _I]),
     "pf_checkpoint_write": (_I, [_VP, ctypes.c_char_p]),
     "pf_checkpoint_read": (_I, [_VP, ctypes.c_char_p]),
+    "pf_interface_mesh": (_I, [_VP, _I, _D, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t,
+                               ctypes.POINTER(ctypes.c_size_t)]),
     "pf_profile": (_I, [_VP, _I]),
     "pf_set_variant": (_I, [_VP, _I]),
     "pf_profile_read": (_I, [_VP, _DP, ctypes.POINTER(_I)]),
@@ -107,10 +109,11 @@ SIGNATURES = {
     "pf_server_stats": (_I, [_VP, _DP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
 }
 
-PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_FUSED, PF_K_LEAN, PF_K_PLAN, PF_K_GENERAL, PF_K_COUNT = \
-    0, 1, 2, 3, 4, 5, 6, 7, 8
+PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_FUSED, PF_K_LEAN, PF_K_PLAN, PF_K_GENERAL = 0, 1, 2, 3, 4, 5, 6, 7
+PF_K_MESH_COUNT, PF_K_MESH_SCAN, PF_K_MESH_EMIT, PF_K_COUNT = 8, 9, 10, 11
 KERNEL_NAMES = {PF_K_PHI: "phi_sweep", PF_K_MU: "mu_sweep", PF_K_FINALIZE: "finalize", PF_K_POST: "post",
-                PF_K_FUSED: "fused_step", PF_K_LEAN: "lean_step", PF_K_PLAN: "plan", PF_K_GENERAL: "general_sweeps"}
+                PF_K_FUSED: "fused_step", PF_K_LEAN: "lean_step", PF_K_PLAN: "plan", PF_K_GENERAL: "general_sweeps",
+                PF_K_MESH_COUNT: "mesh_count", PF_K_MESH_SCAN: "mesh_scan", PF_K_MESH_EMIT: "mesh_emit"}
 PF_VARIANT_AUTO, PF_VARIANT_UNFUSED, PF_VARIANT_FUSED = 0, 1, 2
 VARIANTS = {"auto": PF_VARIANT_AUTO, "unfused": PF_VARIANT_UNFUSED, "fused": PF_VARIANT_FUSED}
 
@@ -273,6 +276,20 @@ def pf_checkpoint_write(sim, path: str):
 
 def pf_checkpoint_read(sim, path: str):
     _check(lib().pf_checkpoint_read(sim, os.fsencode(path)), "pf_checkpoint_read")
+
+
+def pf_interface_mesh(sim, phase: int, iso: float = 0.5) -> np.ndarray:
+    """Triangles (T, 3, 3) float32 of the surface phi_phase = iso (count, then fetch)."""
+    n = ctypes.c_size_t()
+    _check(lib().pf_interface_mesh(sim, int(phase), float(iso), None, 0, ctypes.byref(n)), "pf_interface_mesh")
+    out = np.empty((n.value, 3, 3), dtype=np.float32)
+    if n.value:
+        m = ctypes.c_size_t()
+        _check(lib().pf_interface_mesh(sim, int(phase), float(iso),
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n.value,
+                                       ctypes.byref(m)), "pf_interface_mesh")
+        assert m.value == n.value
+    return out
 
 
 def pf_step_bytes(sim) -> dict:
@@ -544,6 +561,9 @@ class Simulation:
 
     def step_bytes(self):
         return pf_step_bytes(self.h)
+
+    def interface_mesh(self, phase, iso=0.5):
+        return pf_interface_mesh(self.h, phase, iso)
 
     def checkpoint(self, path):
         pf_checkpoint_write(self.h, path)
