@@ -47,7 +47,8 @@ class OrcParams(ctypes.Structure):
         ("dx", ctypes.c_double), ("eps", ctypes.c_double), ("tau", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("gamma2", ctypes.c_double * 6), ("gamma3", ctypes.c_double * 4),
-        ("A", ctypes.c_double * 4), ("cE", (ctypes.c_double * 2) * 4),
+        ("A", ctypes.c_double * 4), ("Am", (ctypes.c_double * 3) * 4), ("tau_ab", ctypes.c_double * 6),
+        ("cE", (ctypes.c_double * 2) * 4),
         ("kT", (ctypes.c_double * 2) * 4), ("s", ctypes.c_double * 4),
         ("D", ctypes.c_double * 4),
         ("TE", ctypes.c_double), ("T0", ctypes.c_double), ("G", ctypes.c_double),
@@ -73,6 +74,8 @@ def lib():
             pp = _P(OrcParams)
             sig = {
                 "orc_default_dt": (_D, [pp, _I]),
+                "orc_kmat": (None, [pp, _I, _DP]),
+                "orc_tau": (_D, [pp, _DP]),
                 "orc_temperature": (_D, [pp, _D, _D]),
                 "orc_psi_alpha": (_D, [pp, _I, _DP, _D]),
                 "orc_c_alpha": (None, [pp, _I, _DP, _D, _DP]),
@@ -124,8 +127,13 @@ def make_params(d: dict) -> OrcParams:
         p.gamma2[i] = d["gamma2"][i]
     for i in range(4):
         p.gamma3[i] = d["gamma3"][i]
+    Am = d.get("Am")
+    for q in range(6):
+        p.tau_ab[q] = d["tau_ab"][q] if d.get("tau_ab") is not None else 0.0
     for a in range(4):
         p.A[a] = d["A"][a]
+        for c in range(3):
+            p.Am[a][c] = Am[a][c] if Am is not None else 0.0
         p.s[a] = d["s"][a]
         p.D[a] = d["D"][a]
         for c in range(2):
@@ -153,6 +161,18 @@ def default_dt(d: dict, nz: int) -> float:
 # ---------------------------------------------------------------------------
 # pointwise functions
 # ---------------------------------------------------------------------------
+
+def kmat(d, a):
+    """K_a = dc^a/dmu = (1/2) A_a^{-1} (2x2)."""
+    K = np.zeros((2, 2))
+    lib().orc_kmat(ctypes.byref(make_params(d)), a, _dp(K))
+    return K
+
+
+def tau(d, phi):
+    """Relaxation time at a cell with phase fractions phi (reading R17)."""
+    return lib().orc_tau(ctypes.byref(make_params(d)), _dp(_arr(phi, 4)))
+
 
 def temperature(d, z, t):
     return lib().orc_temperature(ctypes.byref(make_params(d)), z, t)

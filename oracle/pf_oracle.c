@@ -29,9 +29,13 @@
  * Readings where the paper is silent (each is listed with its reason in the
  * project's design notes):
  *   R1  parabolic grand potentials
- *         psi_a(mu,T) = -|mu|^2/(4 A_a) - mu . chat_a(T) + s_a (T - TE),
+ *         psi_a(mu,T) = -(1/2) mu . K_a mu - mu . chat_a(T) + s_a (T - TE),
  *         chat_a(T)   = cE_a + kT_a (T - TE),
- *         c^a(mu,T)   = -d psi_a / d mu = mu/(2 A_a) + chat_a(T).
+ *         c^a(mu,T)   = -d psi_a / d mu = K_a mu + chat_a(T),
+ *       with K_a = (1/2) A_a^{-1} for the curvature A_a of the fitted Gibbs energy
+ *       f_a(c,T) = c . A_a c + B_a(T) . c + C_a(T) (B_a, C_a linear in T): A_a a
+ *       symmetric positive-definite 2x2 matrix (the general form), or A_a times the
+ *       identity (the symmetric set, K_a = I/(2 A_a)).
  *   R2  h_a = phi_a^2 / sum_b phi_b^2.
  *   R3  a = sum_{a<b} gamma_ab |q_ab|^2,  q_ab = phi_a grad phi_b - phi_b grad phi_a;
  *       omega = (16/pi^2) sum_{a<b} gamma_ab phi_a phi_b
@@ -46,11 +50,15 @@
  *       <= 0 or when |grad phi_a|^2 or |grad phi_l|^2 <= 1e-20/dx^2.
  *   R10 dc/dphi dphi/dt -> sum_a c^a(mu^n,T^n) (h_a(phi^{n+1}) - h_a(phi^n)),
  *       dc/dT dT/dt     -> sum_a h_a(phi^{n+1}) kT_a (-G v dt),
- *       susceptibility chi = sum_a h_a(phi^{n+1})/(2 A_a).
+ *       susceptibility chi = sum_a h_a(phi^{n+1}) K_a (a 2x2 matrix; mu^{n+1} =
+ *       mu^n + chi^{-1} (source)), mobility M = sum_a D_a h_a K_a at the face.
  *   R11 moving window: h = sum(1 - phi_l)/(nx ny); when h >= z_trig, shift by
  *       s = min(floor(h - z_trig) + 1, nz - 1) planes; fresh planes get
  *       phi = e_l and the old top plane's mu.
- *   R12 dt <= 0 requests 0.5 * min(tau dx^2/(12 gamma_max T_max), dx^2/(6 D_max)).
+ *   R12 dt <= 0 requests 0.5 * min(tau_min dx^2/(12 gamma_max T_max), dx^2/(6 D_max)).
+ *   R17 relaxation time per phase pair: tau(phi) = sum_{a<b} tau_ab phi_a phi_b /
+ *       sum_{a<b} phi_a phi_b at the cell's phi^n, and tau on a cell where that
+ *       denominator is 0 (a single phase); all tau_ab <= 0: tau everywhere.
  *   R13 Voronoi nuclei from splitmix64.
  *
  * Grid: cell (i,j,k), x fastest; fields are SoA: phi[c][k][j][i] (c = 0..3,
@@ -72,6 +80,8 @@ typedef struct {
     double gamma2[6]; /* pairs (01,02,03,12,13,23) */
     double gamma3[4]; /* triples (012,013,023,123) */
     double A[4];
+    double Am[4][3]; /* A_a as a symmetric matrix (a11, a12, a22); a11 <= 0: A[a] I */
+    double tau_ab[6]; /* pairs (01,02,03,12,13,23); all <= 0: tau everywhere */
     double cE[4][2];
     double kT[4][2];
     double s[4];
@@ -85,11 +95,14 @@ typedef struct {
 /* parameter tables                                                           */
 /* ------------------------------------------------------------------------- */
 
-static double gam2(const orc_params *p, int a, int b)
+/* index of the pair (a, b), a != b, in the order 01 02 03 12 13 23 */
+static int gam2_index(int a, int b)
 {
     static const int I[4][4] = {{-1, 0, 1, 2}, {0, -1, 3, 4}, {1, 3, -1, 5}, {2, 4, 5, -1}};
-    return p->gamma2[I[a][b]];
+    return I[a][b];
 }
+
+static double gam2(const orc_params *p, int a, int b) { return p->gamma2[gam2_index(a, b)]; }
 
 static double gam3(const orc_params *p, int a, int b, int c)
 {
@@ -98,17 +111,59 @@ static double gam3(const orc_params *p, int a, int b, int c)
     return p->gamma3[3 - missing];
 }
 
+/* R1: K_a = dc^a/dmu = (1/2) A_a^{-1} (symmetric 2x2) */
+void orc_kmat(const orc_params *p, int a, double K[2][2])
+{
+    if (p->Am[a][0] > 0.0) {
+        double a11 = p->Am[a][0], a12 = p->Am[a][1], a22 = p->Am[a][2];
+        double det = a11 * a22 - a12 * a12;
+        K[0][0] = 0.5 * a22 / det;
+        K[0][1] = -0.5 * a12 / det;
+        K[1][0] = -0.5 * a12 / det;
+        K[1][1] = 0.5 * a11 / det;
+    } else {
+        K[0][0] = 1.0 / (2.0 * p->A[a]);
+        K[0][1] = 0.0;
+        K[1][0] = 0.0;
+        K[1][1] = 1.0 / (2.0 * p->A[a]);
+    }
+}
+
+static int tau_interpolated(const orc_params *p)
+{
+    for (int q = 0; q < 6; q++)
+        if (p->tau_ab[q] > 0.0) return 1;
+    return 0;
+}
+
+/* R17: relaxation time at a cell with phase fractions phi */
+double orc_tau(const orc_params *p, const double phi[4])
+{
+    if (!tau_interpolated(p)) return p->tau;
+    double num = 0.0, den = 0.0;
+    for (int a = 0; a < NPH; a++)
+        for (int b = a + 1; b < NPH; b++) {
+            double w = phi[a] * phi[b];
+            num += p->tau_ab[gam2_index(a, b)] * w;
+            den += w;
+        }
+    return den > 0.0 ? num / den : p->tau;
+}
+
 /* R12: explicit stability limits of the linearised phi and mu equations. */
 double orc_default_dt(const orc_params *p, int nz)
 {
-    double gmax = 0.0, dmax = 0.0;
+    double gmax = 0.0, dmax = 0.0, tmin = p->tau;
+    if (tau_interpolated(p))
+        for (int q = 0; q < 6; q++)
+            if (p->tau_ab[q] < tmin) tmin = p->tau_ab[q];
     for (int i = 0; i < 6; i++)
         if (p->gamma2[i] > gmax) gmax = p->gamma2[i];
     for (int a = 0; a < NPH; a++)
         if (p->D[a] > dmax) dmax = p->D[a];
     double Ttop = p->T0 + p->G * (double)(nz - 1) * p->dx;
     double Tmax = p->T0 > Ttop ? p->T0 : Ttop;
-    double lim_phi = p->tau * p->dx * p->dx / (12.0 * gmax * Tmax);
+    double lim_phi = tmin * p->dx * p->dx / (12.0 * gmax * Tmax);
     double lim_mu = dmax > 0.0 ? p->dx * p->dx / (6.0 * dmax) : lim_phi;
     double lim = lim_phi < lim_mu ? lim_phi : lim_mu;
     return 0.5 * lim;
@@ -133,18 +188,20 @@ static void chat(const orc_params *p, int a, double T, double out[2])
 /* R1: grand potential of phase a */
 double orc_psi_alpha(const orc_params *p, int a, const double mu[2], double T)
 {
-    double ch[2];
+    double ch[2], K[2][2];
     chat(p, a, T, ch);
-    return -(mu[0] * mu[0] + mu[1] * mu[1]) / (4.0 * p->A[a]) - (mu[0] * ch[0] + mu[1] * ch[1]) +
-           p->s[a] * (T - p->TE);
+    orc_kmat(p, a, K);
+    double muKmu = mu[0] * (K[0][0] * mu[0] + K[0][1] * mu[1]) + mu[1] * (K[1][0] * mu[0] + K[1][1] * mu[1]);
+    return -0.5 * muKmu - (mu[0] * ch[0] + mu[1] * ch[1]) + p->s[a] * (T - p->TE);
 }
 
 /* R1: c^a(mu,T) = -d psi_a/d mu */
 void orc_c_alpha(const orc_params *p, int a, const double mu[2], double T, double out[2])
 {
-    double ch[2];
+    double ch[2], K[2][2];
     chat(p, a, T, ch);
-    for (int i = 0; i < NMU; i++) out[i] = mu[i] / (2.0 * p->A[a]) + ch[i];
+    orc_kmat(p, a, K);
+    for (int i = 0; i < NMU; i++) out[i] = K[i][0] * mu[0] + K[i][1] * mu[1] + ch[i];
 }
 
 /* R2: h_a = phi_a^2 / sum phi_b^2 */
@@ -374,7 +431,8 @@ void orc_phi_sweep(const orc_params *p, int nx, int ny, int nz, double t, double
                 cell_rhs(p, &ph, &m, i, j, k, t, off, rhs);
                 cell4(&ph, i, j, k, phP);
                 double mean = (rhs[0] + rhs[1] + rhs[2] + rhs[3]) / (double)NPH;
-                for (int a = 0; a < NPH; a++) st[a] = phP[a] - p->dt / (p->tau * p->eps) * (rhs[a] - mean);
+                double tau = orc_tau(p, phP);
+                for (int a = 0; a < NPH; a++) st[a] = phP[a] - p->dt / (tau * p->eps) * (rhs[a] - mean);
                 orc_project(st, pr);
                 size_t c0 = ((size_t)k * ny + j) * nx + i;
                 for (int a = 0; a < NPH; a++) {
@@ -410,12 +468,17 @@ static void face_flux(const orc_params *p, const padded *pn, const padded *po, c
     double zf = (double)k + off + (d == 2 ? 0.5 : 0.0);
     double Tf = orc_temperature(p, zf * p->dx, t);
 
-    /* mobility M = sum_a D_a h_a / (2 A_a) (isotropic) */
+    /* mobility M = sum_a D_a h_a K_a (a 2x2 matrix) */
     orc_h(pbar, h);
-    double M = 0.0;
-    for (int a = 0; a < NPH; a++) M += p->D[a] * h[a] / (2.0 * p->A[a]);
+    double M[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int a = 0; a < NPH; a++) {
+        double K[2][2];
+        orc_kmat(p, a, K);
+        for (int r = 0; r < NMU; r++)
+            for (int c = 0; c < NMU; c++) M[r][c] += p->D[a] * h[a] * K[r][c];
+    }
     double flux[2];
-    for (int c = 0; c < NMU; c++) flux[c] = M * (mR[c] - mL[c]) / p->dx;
+    for (int c = 0; c < NMU; c++) flux[c] = (M[c][0] * (mR[0] - mL[0]) + M[c][1] * (mR[1] - mL[1])) / p->dx;
 
     /* face gradient of phi^{n+1}: normal by difference, tangential by the average of
      * the two cells' central differences (the D3C19 stencil) */
@@ -504,8 +567,13 @@ void orc_mu_sweep(const orc_params *p, int nx, int ny, int nz, double t, double 
                 muP[0] = pget(&m, 0, i, j, k);
                 muP[1] = pget(&m, 1, i, j, k);
                 double T = orc_temperature(p, ((double)k + off) * p->dx, t);
-                double chi = 0.0;
-                for (int a = 0; a < NPH; a++) chi += hN[a] / (2.0 * p->A[a]);
+                double chi[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+                for (int a = 0; a < NPH; a++) {
+                    double K[2][2];
+                    orc_kmat(p, a, K);
+                    for (int r = 0; r < NMU; r++)
+                        for (int c = 0; c < NMU; c++) chi[r][c] += hN[a] * K[r][c];
+                }
                 double src[2];
                 for (int c = 0; c < NMU; c++) {
                     double dcdphi = 0.0, dcdT = 0.0;
@@ -518,7 +586,12 @@ void orc_mu_sweep(const orc_params *p, int nx, int ny, int nz, double t, double 
                     src[c] = p->dt * div[c] - dcdphi - dcdT * dT;
                 }
                 size_t c0 = ((size_t)k * ny + j) * nx + i;
-                for (int c = 0; c < NMU; c++) mu_new[c * ncell + c0] = muP[c] + src[c] / chi;
+                /* mu^{n+1} = mu^n + chi^{-1} src, the 2x2 inverse by its adjugate */
+                double det = chi[0][0] * chi[1][1] - chi[0][1] * chi[1][0];
+                double inc[2];
+                inc[0] = (chi[1][1] * src[0] - chi[0][1] * src[1]) / det;
+                inc[1] = (chi[0][0] * src[1] - chi[1][0] * src[0]) / det;
+                for (int c = 0; c < NMU; c++) mu_new[c * ncell + c0] = muP[c] + inc[c];
             }
     free(pn.v);
     free(po.v);

@@ -50,6 +50,19 @@ def symmetric_params(G: float = 1e-3, v: float = 1e-2, n_grains: int = 12,
     }
 
 
+def general_params(G: float = 1e-3, v: float = 1e-2, n_grains: int = 12,
+                   window_trigger_z: float = 0.0, dt: float = 0.0) -> dict:
+    """The symmetric set with general parabolic thermodynamics (the Ag-Al-Cu-shaped variant, whose
+    coefficients the paper does not print): the Gibbs-energy curvature of each phase a symmetric
+    positive-definite 2x2 matrix A_a = [[a11, a12], [a12, a22]] with unequal diagonal entries and a
+    cross term ("Am": a11, a12, a22), and a relaxation time per phase pair ("tau_ab", pairs 01 02 03
+    12 13 23).  Everything else as symmetric_params."""
+    p = symmetric_params(G=G, v=v, n_grains=n_grains, window_trigger_z=window_trigger_z, dt=dt)
+    p["Am"] = [[1.2, 0.3, 0.8], [0.7, -0.2, 1.5], [1.0, 0.4, 1.1], [0.9, 0.15, 1.3]]
+    p["tau_ab"] = [2.0, 1.6, 1.0, 1.8, 0.8, 1.2]
+    return p
+
+
 def with_(p: dict, **kw) -> dict:
     q = copy.deepcopy(p)
     q.update(kw)
