@@ -690,7 +690,8 @@ def main():
         "bounds_mlups": {"fused_48B": fused_bound, "unfused_88B": unfused_bound,
                          "this_design_bytes_per_cell": design_bytes,
                          "this_design": hbm * 1e9 / design_bytes / 1e6 if design_bytes else None},
-        "variant": "fused" if "fused_step" in prof else "unfused",
+        "variant": ("lean kernel + general sweeps" if "lean_step" in prof
+                    else ("fused" if "fused_step" in prof else "unfused")),
         "frac_of_unfused_bound": value / unfused_bound, "frac_of_fused_bound": value / fused_bound,
         "fp64": fp64, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
         "window": {"h_int": st32["h_int"], "offset": st32["window_offset"]},

@@ -52,14 +52,19 @@ enum {
     PF_FP32_COMP = 2 /* FP32 arithmetic, state kept as FP32 high + FP32 low words (compensated) */
 };
 
-#define PF_PARAMS_VERSION 1
+#define PF_PARAMS_VERSION 2
 
 /*
  * Physical and numerical parameters, always FP64 (the library converts them to the
- * kernel precision).  Readings of the paper where it prints no value:
- *   psi_a(mu,T) = -|mu|^2/(4 A_a) - mu . chat_a(T) + s_a (T - TE),
- *   chat_a(T) = cE_a + kT_a (T - TE),  c^a = mu/(2 A_a) + chat_a(T),
- *   h_a = phi_a^2 / sum phi_b^2,  g_a = phi_a,  M = sum_a D_a h_a / (2 A_a),
+ * kernel precision).  Readings of the paper where it prints no value (parabolic Gibbs
+ * energies f_a(c,T) = c . A_a c + B_a(T) . c + C_a(T) as grand potentials, Section 2):
+ *   psi_a(mu,T) = -(1/2) mu . K_a mu - mu . chat_a(T) + s_a (T - TE),  K_a = (1/2) A_a^{-1},
+ *   chat_a(T) = cE_a + kT_a (T - TE),  c^a = K_a mu + chat_a(T),
+ *   A_a = A[a] times the identity, or the symmetric matrix Am[a] when Am[a][0] > 0,
+ *   chi = sum_a h_a K_a,  mu^{n+1} = mu^n + chi^{-1} (source)  (2x2),
+ *   h_a = phi_a^2 / sum phi_b^2,  g_a = phi_a,  M = sum_a D_a h_a K_a,
+ *   tau(phi) = sum_{a<b} tau_ab phi_a phi_b / sum_{a<b} phi_a phi_b at phi^n (tau on a
+ *     single-phase cell) when tau_ab is set, else tau,
  *   a = sum_{a<b} gamma2_ab |phi_a grad phi_b - phi_b grad phi_a|^2,
  *   omega = (16/pi^2) sum gamma2_ab phi_a phi_b + sum gamma3_abd phi_a phi_b phi_d.
  */
@@ -73,6 +78,11 @@ typedef struct pf_params {
     double T0, G, v;            /* frozen temperature T = T0 + G (z - v t) */
     int seed_layers, n_grains;  /* Voronoi nuclei in the bottom seed_layers planes */
     double window_trigger_z;    /* > 0: shift the window when the interface height reaches it */
+    /* general parabolic thermodynamics (version 2) */
+    double Am[4][3];            /* A_a as a symmetric positive-definite matrix (a11, a12, a22);
+                                   Am[a][0] <= 0: A[a] times the identity */
+    double tau_ab[6];           /* relaxation time per phase pair (01 02 03 12 13 23): all > 0, or
+                                   all <= 0 for tau everywhere; dt's phi limit takes the smallest */
 } pf_params;
 
 typedef struct pf_sim pf_sim;
@@ -138,8 +148,11 @@ int pf_write_fields(pf_sim *sim, const double *phi, const double *mu);
  * "PFCKPT01"; int32 version 1, nx, ny, nz, bytes per value, writer precision, planes shifted since
  * init, 4 bytes of padding; FP64 time and window offset; 8 bytes of padding; little-endian), then for each logical
  * plane k = 0 .. nz-1 the six nx*ny arrays (x fastest) phi_0, phi_1, phi_2, phi_3, mu_0, mu_1.
- * Values are FP32 for an FP32 simulation and FP64 for FP64 and compensated FP32 (the state's own
- * values, so that nothing is rounded).  PF_E_INVAL if the file cannot be written.  Synchronising. */
+ * Values are the state's own words, so that nothing is rounded: FP32 for an FP32 simulation, FP64
+ * for FP64, and for compensated FP32 (writer precision PF_FP32_COMP, 4 bytes per value) the six
+ * arrays of high words followed by the six arrays of low words in each plane (a pair's value is
+ * high + low; pairs whose low word lies far below the high word's last bit are not one FP64 value).
+ * PF_E_INVAL if the file cannot be written.  Synchronising. */
 int pf_checkpoint_write(pf_sim *sim, const char *path);
 
 /* Restore a checkpoint written for the same grid (any precision: values are converted to this

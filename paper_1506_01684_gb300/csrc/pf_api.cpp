@@ -226,6 +226,8 @@ Geometry make_geometry(int nx, int ny, int nz, int zchunk_hint)
 }
 }  // namespace pf
 
+static bool tau_pairs(const pf_params &p);
+
 template <typename R>
 static KParams<R> make_kparams(const pf_sim *s)
 {
@@ -263,6 +265,44 @@ static KParams<R> make_kparams(const pf_sim *s)
         k.kT64[a][1] = p.kT[a][1];
         k.s64[a] = p.s[a];
         k.A64[a] = p.A[a];
+    }
+    // K_a = (1/2) A_a^{-1} in FP64 (the identity form when Am[a] is not set)
+    k.gen = 0;
+    for (int a = 0; a < 4; a++) {
+        double K11, K12, K22;
+        if (p.Am[a][0] > 0.0) {
+            k.gen = 1;
+            const double a11 = p.Am[a][0], a12 = p.Am[a][1], a22 = p.Am[a][2];
+            const double det = a11 * a22 - a12 * a12;
+            K11 = 0.5 * a22 / det;
+            K12 = -0.5 * a12 / det;
+            K22 = 0.5 * a11 / det;
+        } else {
+            K11 = K22 = 1.0 / (2.0 * p.A[a]);
+            K12 = 0.0;
+        }
+        const double Kd[3] = {K11, K12, K22};
+        for (int e = 0; e < 3; e++) {
+            k.K64[a][e] = Kd[e];
+            k.K[a][e] = (R)Kd[e];
+            k.DK[a][e] = (R)(p.D[a] * Kd[e]);
+        }
+        k.psiK[a][0] = (R)(0.5 * K11);
+        k.psiK[a][1] = (R)K12;
+        k.psiK[a][2] = (R)(0.5 * K22);
+    }
+    k.gen_tau = tau_pairs(p) ? 1 : 0;
+    for (int q = 0; q < 6; q++) k.tau_ab[q] = (R)(k.gen_tau ? p.tau_ab[q] : p.tau);
+    k.dt_eps = (R)(p.dt / p.eps);
+    {
+        // pure liquid: chi = K_l, M = D_l K_l, so chi^{-1} M = D_l and the source of the
+        // temperature drift is -K_l^{-1} kT_l dT
+        const double K11 = k.K64[3][0], K12 = k.K64[3][1], K22 = k.K64[3][2];
+        const double det = K11 * K22 - K12 * K12, dT = -p.G * p.v * p.dt;
+        const double s0 = p.kT[3][0] * dT, s1 = p.kT[3][1] * dT;
+        k.liqC1 = (R)(p.dt * p.D[3] / (p.dx * p.dx));
+        k.liqC0[0] = (R)(-(K22 * s0 - K12 * s1) / det);
+        k.liqC0[1] = (R)(-(K11 * s1 - K12 * s0) / det);
     }
     const double pi = 3.14159265358979323846;
     k.at_pref = (R)(pi * p.eps / 4.0);
@@ -319,14 +359,23 @@ static int latch(pf_sim *s, int st)
     return st;
 }
 
+static bool tau_pairs(const pf_params &p)
+{
+    for (int q = 0; q < 6; q++)
+        if (p.tau_ab[q] > 0.0) return true;
+    return false;
+}
+
 static double default_dt(const pf_params &p, int nz)
 {
-    double gmax = 0.0, dmax = 0.0;
+    double gmax = 0.0, dmax = 0.0, tmin = p.tau;
+    if (tau_pairs(p))
+        for (int q = 0; q < 6; q++) tmin = p.tau_ab[q] < tmin ? p.tau_ab[q] : tmin;
     for (int i = 0; i < 6; i++) gmax = p.gamma2[i] > gmax ? p.gamma2[i] : gmax;
     for (int a = 0; a < 4; a++) dmax = p.D[a] > dmax ? p.D[a] : dmax;
     const double Ttop = p.T0 + p.G * (double)(nz - 1) * p.dx;
     const double Tmax = p.T0 > Ttop ? p.T0 : Ttop;
-    const double lim_phi = p.tau * p.dx * p.dx / (12.0 * gmax * Tmax);
+    const double lim_phi = tmin * p.dx * p.dx / (12.0 * gmax * Tmax);
     const double lim_mu = dmax > 0.0 ? p.dx * p.dx / (6.0 * dmax) : lim_phi;
     return 0.5 * (lim_phi < lim_mu ? lim_phi : lim_mu);
 }
@@ -336,8 +385,14 @@ static int check_params(const pf_params *p)
     if (!p || p->version != PF_PARAMS_VERSION) return PF_E_INVAL;
     if (p->precision != PF_FP64 && p->precision != PF_FP32 && p->precision != PF_FP32_COMP) return PF_E_INVAL;
     if (!(p->dx > 0) || !(p->eps > 0) || !(p->tau > 0)) return PF_E_INVAL;
-    for (int a = 0; a < 4; a++)
+    for (int a = 0; a < 4; a++) {
         if (!(p->A[a] > 0) || p->D[a] < 0) return PF_E_INVAL;
+        const double a11 = p->Am[a][0], a12 = p->Am[a][1], a22 = p->Am[a][2];
+        if (a11 > 0 && !(a22 > 0 && a11 * a22 - a12 * a12 > 0 && isfinite(a12))) return PF_E_INVAL;
+    }
+    if (tau_pairs(*p))
+        for (int q = 0; q < 6; q++)
+            if (!(p->tau_ab[q] > 0) || !isfinite(p->tau_ab[q])) return PF_E_INVAL;
     double gmax = 0;
     for (int i = 0; i < 6; i++) gmax = std::max(gmax, p->gamma2[i]);
     if (!(gmax > 0)) return PF_E_INVAL;
@@ -801,7 +856,10 @@ static int do_checkpoint_write(pf_sim *s, const char *path)
     h.nx = s->nx;
     h.ny = s->ny;
     h.nz = s->nz;
-    h.elem = s->p.precision == PF_FP32 ? 4 : 8;  // the state's own values, exactly
+    // the state's own values, exactly: FP32 words for FP32, FP64 for FP64, and for the compensated
+    // state its two FP32 words (a high/low pair need not be one FP64 value)
+    const bool pairs = s->comp();
+    h.elem = s->p.precision == PF_FP64 ? 8 : 4;
     h.precision = s->p.precision;
     h.nshift = ds.nshift_total;
     h.t = ds.t;
@@ -818,31 +876,37 @@ static int do_checkpoint_write(pf_sim *s, const char *path)
         return PF_E_INVAL;
     }
     bool io_ok = fwrite(&h, sizeof h, 1, f) == 1;
-    std::vector<double> hb((size_t)pk * plane * 6);
+    const int nwords = pairs ? 2 : 1;  // word 0: the values (high words); word 1: the low words
+    std::vector<double> hb((size_t)nwords * pk * plane * 6);
     std::vector<float> hf(h.elem == 4 ? plane : 0);
     double *dphi = (double *)stg.p, *dmu = dphi + (size_t)pk * plane * 4;
     cudaError_t e = cudaSuccess;
     for (int k0 = 0; k0 < s->nz && e == cudaSuccess && io_ok; k0 += pk) {
         const int nk = std::min(pk, s->nz - k0);
         const size_t m = (size_t)nk * plane;
-        e = launch_pack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, dphi, dmu, k0, nk,
-                           s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
-        // [c][k][y][x] of the chunk: phi components, then mu components
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(hb.data(), dphi, m * 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(hb.data() + m * 4, dmu, m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        for (int w = 0; w < nwords && e == cudaSuccess; w++) {
+            // each word array alone (the low words packed as if they were the fields): exact in FP64
+            double *hw = hb.data() + (size_t)w * m * 6;
+            e = launch_pack<R>(kp, (const DevState *)s->state.p, w ? s->philo[s->cur].p : s->phi[s->cur].p,
+                               w ? s->mulo[s->cur].p : s->mu[s->cur].p, dphi, dmu, k0, nk, s->stream,
+                               pairs ? nullptr : s->lo_phi(s->cur), pairs ? nullptr : s->lo_mu(s->cur));
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hw, dphi, m * 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hw + m * 4, dmu, m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        }
         for (int kk = 0; kk < nk && e == cudaSuccess && io_ok; kk++)
-            for (int c = 0; c < 6 && io_ok; c++) {
-                const double *src = hb.data() + (size_t)c * m + (size_t)kk * plane;
-                if (h.elem == 4) {
-                    for (size_t q = 0; q < plane; q++) hf[q] = (float)src[q];
-                    io_ok = fwrite(hf.data(), sizeof(float), plane, f) == plane;
-                } else {
-                    io_ok = fwrite(src, sizeof(double), plane, f) == plane;
+            for (int w = 0; w < nwords && io_ok; w++)
+                for (int c = 0; c < 6 && io_ok; c++) {
+                    const double *src = hb.data() + (size_t)w * m * 6 + (size_t)c * m + (size_t)kk * plane;
+                    if (h.elem == 4) {
+                        for (size_t q = 0; q < plane; q++) hf[q] = (float)src[q];
+                        io_ok = fwrite(hf.data(), sizeof(float), plane, f) == plane;
+                    } else {
+                        io_ok = fwrite(src, sizeof(double), plane, f) == plane;
+                    }
                 }
-            }
     }
     io_ok = (fclose(f) == 0) && io_ok;
     dev_free(stg, s->stream);
@@ -871,7 +935,10 @@ static int do_checkpoint_read(pf_sim *s, const char *path)
         fclose(f);
         return r;
     }
-    std::vector<double> hb((size_t)pk * plane * 6);
+    // a compensated writer stored both FP32 words of each value (high arrays, then low arrays, per plane)
+    const bool file_pairs = h.precision == PF_FP32_COMP && h.elem == 4;
+    const int nwords = file_pairs ? 2 : 1;
+    std::vector<double> hb((size_t)nwords * pk * plane * 6);
     std::vector<float> hf(h.elem == 4 ? plane : 0);
     double *dphi = (double *)stg.p, *dmu = dphi + (size_t)pk * plane * 4;
     cudaError_t e = cudaSuccess;
@@ -880,23 +947,37 @@ static int do_checkpoint_read(pf_sim *s, const char *path)
         const int nk = std::min(pk, s->nz - k0);
         const size_t m = (size_t)nk * plane;
         for (int kk = 0; kk < nk && io_ok; kk++)
-            for (int c = 0; c < 6 && io_ok; c++) {
-                double *dst = hb.data() + (size_t)c * m + (size_t)kk * plane;
-                if (h.elem == 4) {
-                    io_ok = fread(hf.data(), sizeof(float), plane, f) == plane;
-                    for (size_t q = 0; q < plane && io_ok; q++) dst[q] = (double)hf[q];
-                } else {
-                    io_ok = fread(dst, sizeof(double), plane, f) == plane;
+            for (int w = 0; w < nwords && io_ok; w++)
+                for (int c = 0; c < 6 && io_ok; c++) {
+                    double *dst = hb.data() + (size_t)w * m * 6 + (size_t)c * m + (size_t)kk * plane;
+                    if (h.elem == 4) {
+                        io_ok = fread(hf.data(), sizeof(float), plane, f) == plane;
+                        for (size_t q = 0; q < plane && io_ok; q++) dst[q] = (double)hf[q];
+                    } else {
+                        io_ok = fread(dst, sizeof(double), plane, f) == plane;
+                    }
                 }
-            }
         if (!io_ok) break;
-        e = cudaMemcpyAsync(dphi, hb.data(), m * 4 * sizeof(double), cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dmu, hb.data() + m * 4, m * 2 * sizeof(double), cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess)
-            e = launch_unpack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, dphi, dmu, k0,
-                                 nk, s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // the host chunk is reused
+        if (file_pairs && !s->comp())  // into another precision: the value of each pair, rounded once
+            for (size_t q = 0; q < m * 6; q++) hb[q] += hb[m * 6 + q];
+        // a compensated reader of pairs takes both words as they are; otherwise the values
+        const int nw = file_pairs && s->comp() ? 2 : 1;
+        for (int w = 0; w < nw && e == cudaSuccess; w++) {
+            const double *hw = hb.data() + (size_t)w * m * 6;
+            e = cudaMemcpyAsync(dphi, hw, m * 4 * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(dmu, hw + m * 4, m * 2 * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+            if (e == cudaSuccess) {
+                if (nw == 2)
+                    e = launch_unpack<R>(kp, (const DevState *)s->state.p, w ? s->philo[s->cur].p : s->phi[s->cur].p,
+                                         w ? s->mulo[s->cur].p : s->mu[s->cur].p, dphi, dmu, k0, nk, s->stream,
+                                         nullptr, nullptr);
+                else
+                    e = launch_unpack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, dphi,
+                                         dmu, k0, nk, s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // the host chunk is reused
+        }
     }
     fclose(f);
     if (e == cudaSuccess && io_ok) {

@@ -78,6 +78,16 @@ struct KParams {
     // FP64 data for the plane table, the reductions and the clock
     double T0, G, v, TE, dx64, dt64, eps64, window_trigger_z;
     double cE[4][2], kT64[4][2], s64[4], A64[4];
+    // general parabolic thermodynamics (matrix curvatures A_a, pair relaxation times)
+    int gen;          // 1: K_a = (1/2) A_a^{-1} is a full 2x2 matrix; 0: K_a = inv2A[a] times the identity
+    int gen_tau;      // 1: tau interpolated over the phase pairs at the cell's phi^n
+    R K[4][3];        // K_a: (K11, K12, K22)
+    R DK[4][3];       // D_a K_a
+    R psiK[4][3];     // (K11/2, K12, K22/2): (1/2) mu . K_a mu = psiK0 mu0^2 + psiK1 mu0 mu1 + psiK2 mu1^2
+    R tau_ab[6];      // pairs 01 02 03 12 13 23
+    R dt_eps;         // dt / eps
+    R liqC1, liqC0[2];  // pure-liquid update mu + C1 (7-point Laplacian sum) + C0 with matrix curvatures
+    double K64[4][3];   // K_a in FP64 (reductions)
 };
 
 // One domain of a batched step: its parameters, ping-pong field buffers, state, plane table and

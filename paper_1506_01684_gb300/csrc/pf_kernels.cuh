@@ -138,6 +138,65 @@ __device__ __forceinline__ R pick4(const R (&v)[4], int c)
     return c == 0 ? v[0] : (c == 1 ? v[1] : (c == 2 ? v[2] : v[3]));
 }
 
+// General parabolic thermodynamics (matrix curvatures): a symmetric 2x2 matrix [[s0, s1], [s1, s2]]
+template <typename R>
+struct Sym2 {
+    R s0, s1, s2;
+};
+// sum_a w_a M_a over the four phases of a table of symmetric matrices
+template <typename R>
+__device__ __forceinline__ Sym2<R> sym_sum(const R (&M)[4][3], const R *w)
+{
+    Sym2<R> o;
+    o.s0 = M[0][0] * w[0] + M[1][0] * w[1] + M[2][0] * w[2] + M[3][0] * w[3];
+    o.s1 = M[0][1] * w[0] + M[1][1] * w[1] + M[2][1] * w[2] + M[3][1] * w[3];
+    o.s2 = M[0][2] * w[0] + M[1][2] * w[1] + M[2][2] * w[2] + M[3][2] * w[3];
+    return o;
+}
+// the matrix of phase c (an exactly one-hot cell)
+template <typename R>
+__device__ __forceinline__ Sym2<R> sym_pick(const R (&M)[4][3], int c)
+{
+    const R t0[4] = {M[0][0], M[1][0], M[2][0], M[3][0]};
+    const R t1[4] = {M[0][1], M[1][1], M[2][1], M[3][1]};
+    const R t2[4] = {M[0][2], M[1][2], M[2][2], M[3][2]};
+    return Sym2<R>{pick4(t0, c), pick4(t1, c), pick4(t2, c)};
+}
+// S^{-1} (x0, x1) by the adjugate
+template <typename R>
+__device__ __forceinline__ void sym_solve(const Sym2<R> &S, R x0, R x1, R &y0, R &y1)
+{
+    const R idet = R(1) / (S.s0 * S.s2 - S.s1 * S.s1);
+    y0 = (S.s2 * x0 - S.s1 * x1) * idet;
+    y1 = (S.s0 * x1 - S.s1 * x0) * idet;
+}
+// c^a(mu) = K_a mu + chat_a
+template <typename R>
+__device__ __forceinline__ void c_alpha(const KParams<R> &kp, int a, R m0, R m1, R ch0, R ch1, R &c0, R &c1)
+{
+    if (kp.gen) {
+        c0 = kp.K[a][0] * m0 + kp.K[a][1] * m1 + ch0;
+        c1 = kp.K[a][1] * m0 + kp.K[a][2] * m1 + ch1;
+    } else {
+        c0 = m0 * kp.inv2A[a] + ch0;
+        c1 = m1 * kp.inv2A[a] + ch1;
+    }
+}
+// dt / (tau(phi) eps) at a cell with phase fractions p (phi^n): the pair-weighted relaxation time,
+// tau on a single-phase cell
+template <typename R>
+__device__ __forceinline__ R phi_coef(const KParams<R> &kp, const R *p)
+{
+    if (!kp.gen_tau) return kp.c_phi;
+    const R w01 = p[0] * p[1], w02 = p[0] * p[2], w03 = p[0] * p[3];
+    const R w12 = p[1] * p[2], w13 = p[1] * p[3], w23 = p[2] * p[3];
+    const R den = w01 + w02 + w03 + w12 + w13 + w23;
+    if (!(den > R(0))) return kp.c_phi;
+    const R num = kp.tau_ab[0] * w01 + kp.tau_ab[1] * w02 + kp.tau_ab[2] * w03 + kp.tau_ab[3] * w12 +
+                  kp.tau_ab[4] * w13 + kp.tau_ab[5] * w23;
+    return kp.dt_eps * den / num;
+}
+
 // ---------------------------------------------------------------------------------------
 // phi-sweep pieces (Eq. 1, Eq. 2)
 // ---------------------------------------------------------------------------------------
@@ -269,7 +328,11 @@ __device__ __forceinline__ void phi_rhs(const KParams<R> &kp, const PlaneT<R> &p
     R psi[4], hpsi = R(0);
 #pragma unroll
     for (int a = 0; a < 4; a++) {
-        psi[a] = -mu2 * kp.inv4A[a] - (m.v[0] * pc.chat[a][0] + m.v[1] * pc.chat[a][1]) + pc.sT[a];
+        // -(1/2) mu . K_a mu: |mu|^2 / (4 A_a) for the identity form
+        const R quad = kp.gen ? kp.psiK[a][0] * m.v[0] * m.v[0] + kp.psiK[a][1] * m.v[0] * m.v[1] +
+                                    kp.psiK[a][2] * m.v[1] * m.v[1]
+                              : mu2 * kp.inv4A[a];
+        psi[a] = -quad - (m.v[0] * pc.chat[a][0] + m.v[1] * pc.chat[a][1]) + pc.sT[a];
         hpsi = hpsi + p[a] * p[a] * inv_S * psi[a];
     }
 #pragma unroll
@@ -293,8 +356,9 @@ __device__ __forceinline__ Ph<R> phi_cell(const KParams<R> &kp, const PlaneT<R> 
     const R *p = P.v;
     R mean = (rhs[0] + rhs[1] + rhs[2] + rhs[3]) * R(0.25);
     Ph<R> st;
+    const R cp = phi_coef(kp, p);
 #pragma unroll
-    for (int a = 0; a < 4; a++) st.v[a] = p[a] - kp.c_phi * (rhs[a] - mean);
+    for (int a = 0; a < 4; a++) st.v[a] = p[a] - cp * (rhs[a] - mean);
     return project_simplex(st);
 }
 
@@ -318,15 +382,19 @@ __device__ __forceinline__ DF fast_two_sum(float a, float b)  // |a| >= |b|
     const float s = a + b;
     return DF{s, b - (s - a)};
 }
+// The sums renormalise with a full two-sum: after cancellation the low part can exceed the high
+// one, where the fast form would leave a pair whose high word is not the rounded value of the pair.
+// Every stored pair is canonical (h = fl(h + l)), so its FP64 value splits back into the same two
+// words (checkpoints and host reads of the compensated state round-trip exactly).
 __device__ __forceinline__ DF df_add_f(DF a, float b)
 {
     DF s = two_sum(a.h, b);
-    return fast_two_sum(s.h, s.l + a.l);
+    return two_sum(s.h, s.l + a.l);
 }
 __device__ __forceinline__ DF df_add(DF a, DF b)
 {
     DF s = two_sum(a.h, b.h);
-    return fast_two_sum(s.h, s.l + (a.l + b.l));
+    return two_sum(s.h, s.l + (a.l + b.l));
 }
 __device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.h, -b.l}); }
 __device__ __forceinline__ bool df_pos(DF a) { return a.h > 0.f || (a.h == 0.f && a.l > 0.f); }
@@ -389,8 +457,9 @@ __device__ __forceinline__ void phi_cell_comp(const KParams<float> &kp, const Pl
     phi_rhs(kp, pc, P, xm, xp, ym, yp, zm, zp, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, m, rhs);
     const float mean = (rhs[0] + rhs[1] + rhs[2] + rhs[3]) * 0.25f;
     DF u[4], o[4];
+    const float cp = phi_coef(kp, P.v);
 #pragma unroll
-    for (int a = 0; a < 4; a++) u[a] = df_add_f(DF{P.v[a], Plo.v[a]}, -(kp.c_phi * (rhs[a] - mean)));
+    for (int a = 0; a < 4; a++) u[a] = df_add_f(DF{P.v[a], Plo.v[a]}, -(cp * (rhs[a] - mean)));
     project_simplex_df(u, o);
 #pragma unroll
     for (int a = 0; a < 4; a++) {
@@ -508,10 +577,18 @@ __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const Pla
     R h[4];
 #pragma unroll
     for (int b = 0; b < 4; b++) h[b] = pb[b] * pb[b] * inv_S;
-    const R M = kp.DinvA[0] * h[0] + kp.DinvA[1] * h[1] + kp.DinvA[2] * h[2] + kp.DinvA[3] * h[3];
-    const R Mdx = M * kp.inv_dx;  // mobility over the face width, formed once per face
-    v.v[0] = Mdx * (mR.v[0] - mL.v[0]);
-    v.v[1] = Mdx * (mR.v[1] - mL.v[1]);
+    if (kp.gen) {
+        // M = sum_a D_a h_a K_a (a 2x2 matrix)
+        const Sym2<R> M = sym_sum(kp.DK, h);
+        const R d0 = mR.v[0] - mL.v[0], d1 = mR.v[1] - mL.v[1];
+        v.v[0] = (M.s0 * d0 + M.s1 * d1) * kp.inv_dx;
+        v.v[1] = (M.s1 * d0 + M.s2 * d1) * kp.inv_dx;
+    } else {
+        const R M = kp.DinvA[0] * h[0] + kp.DinvA[1] * h[1] + kp.DinvA[2] * h[2] + kp.DinvA[3] * h[3];
+        const R Mdx = M * kp.inv_dx;  // mobility over the face width, formed once per face
+        v.v[0] = Mdx * (mR.v[0] - mL.v[0]);
+        v.v[1] = Mdx * (mR.v[1] - mL.v[1]);
+    }
     // anti-trapping current (Eq. 4, g_a = phi_a); terms skipped per reading R9
     if (pb[3] > R(0) && (pb[0] > R(0) || pb[1] > R(0) || pb[2] > R(0))) {
         R gl[3];
@@ -524,8 +601,8 @@ __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const Pla
             const R nl = sqrt(gl2);
             const R mb0 = R(0.5) * (mL.v[0] + mR.v[0]);
             const R mb1 = R(0.5) * (mL.v[1] + mR.v[1]);
-            const R cl0 = mb0 * kp.inv2A[3] + ch.c[3][0];
-            const R cl1 = mb1 * kp.inv2A[3] + ch.c[3][1];
+            R cl0, cl1;
+            c_alpha(kp, 3, mb0, mb1, ch.c[3][0], ch.c[3][1], cl0, cl1);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 if (!(pb[a] > R(0))) continue;
@@ -539,8 +616,10 @@ __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const Pla
                 const R ndot = (ga[0] * gl[0] + ga[1] * gl[1] + ga[2] * gl[2]) / (na * nl);
                 const R pdot = R(0.5) * ((nL.v[a] - oL.v[a]) + (nR.v[a] - oR.v[a])) * kp.inv_dt;
                 const R pref = kp.at_pref * (pb[a] * h[3] / sqrt(pb[a] * pb[3])) * pdot * ndot;
-                const R dc0 = cl0 - (mb0 * kp.inv2A[a] + ch.c[a][0]);
-                const R dc1 = cl1 - (mb1 * kp.inv2A[a] + ch.c[a][1]);
+                R ca0, ca1;
+                c_alpha(kp, a, mb0, mb1, ch.c[a][0], ch.c[a][1], ca0, ca1);
+                const R dc0 = cl0 - ca0;
+                const R dc1 = cl1 - ca1;
                 const R nd = ga[0] / na;  // normal component: the face direction is component 0
                 v.v[0] = v.v[0] - pref * dc0 * nd;
                 v.v[1] = v.v[1] - pref * dc1 * nd;
@@ -565,6 +644,13 @@ __device__ __forceinline__ Mu<R> face_mu(const KParams<R> &kp, const PlaneT<R> *
 {
     if (same(nL, nR) && onehot(nL)) {
         Mu<R> v;
+        if (kp.gen) {
+            const Sym2<R> M = sym_sum(kp.DK, nL.v);
+            const R d0 = mR.v[0] - mL.v[0], d1 = mR.v[1] - mL.v[1];
+            v.v[0] = (M.s0 * d0 + M.s1 * d1) * kp.inv_dx;
+            v.v[1] = (M.s1 * d0 + M.s2 * d1) * kp.inv_dx;
+            return v;
+        }
         const R M = kp.DinvA[0] * nL.v[0] + kp.DinvA[1] * nL.v[1] + kp.DinvA[2] * nL.v[2] + kp.DinvA[3] * nL.v[3];
         const R Mdx = M * kp.inv_dx;
         v.v[0] = Mdx * (mR.v[0] - mL.v[0]);
@@ -600,8 +686,10 @@ __device__ __forceinline__ Mu<R> mu_cell(const KParams<R> &kp, const PlaneT<R> *
 #pragma unroll
         for (int a = 0; a < 4; a++) {
             const R dh = hN[a] - hO[a];
-            dphi0 = dphi0 + (m.v[0] * kp.inv2A[a] + ch.c[a][0]) * dh;
-            dphi1 = dphi1 + (m.v[1] * kp.inv2A[a] + ch.c[a][1]) * dh;
+            R ca0, ca1;
+            c_alpha(kp, a, m.v[0], m.v[1], ch.c[a][0], ch.c[a][1], ca0, ca1);
+            dphi0 = dphi0 + ca0 * dh;
+            dphi1 = dphi1 + ca1 * dh;
         }
     }
     R chi = R(0), dT0 = R(0), dT1 = R(0);
@@ -613,8 +701,16 @@ __device__ __forceinline__ Mu<R> mu_cell(const KParams<R> &kp, const PlaneT<R> *
     }
     const R src0 = kp.dt * div0 - dphi0 - dT0 * kp.dTstep;
     const R src1 = kp.dt * div1 - dphi1 - dT1 * kp.dTstep;
-    const R ichi = rcp(chi);
     Mu<R> o;
+    if (kp.gen) {
+        // chi = sum_a h_a K_a (2x2): mu^{n+1} = mu^n + chi^{-1} src
+        R i0, i1;
+        sym_solve(sym_sum(kp.K, hN), src0, src1, i0, i1);
+        o.v[0] = m.v[0] + i0;
+        o.v[1] = m.v[1] + i1;
+        return o;
+    }
+    const R ichi = rcp(chi);
     o.v[0] = m.v[0] + src0 * ichi;
     o.v[1] = m.v[1] + src1 * ichi;
     return o;
@@ -645,8 +741,10 @@ __device__ __forceinline__ void mu_cell_comp(const KParams<float> &kp, const Pla
 #pragma unroll
         for (int a = 0; a < 4; a++) {
             const float dh = hN[a] - hO[a];
-            dphi0 = dphi0 + (m.v[0] * kp.inv2A[a] + ch.c[a][0]) * dh;
-            dphi1 = dphi1 + (m.v[1] * kp.inv2A[a] + ch.c[a][1]) * dh;
+            float ca0, ca1;
+            c_alpha(kp, a, m.v[0], m.v[1], ch.c[a][0], ch.c[a][1], ca0, ca1);
+            dphi0 = dphi0 + ca0 * dh;
+            dphi1 = dphi1 + ca1 * dh;
         }
     }
     float chi = 0.f, dT0 = 0.f, dT1 = 0.f;
@@ -658,9 +756,16 @@ __device__ __forceinline__ void mu_cell_comp(const KParams<float> &kp, const Pla
     }
     const float src0 = kp.dt * div0 - dphi0 - dT0 * kp.dTstep;
     const float src1 = kp.dt * div1 - dphi1 - dT1 * kp.dTstep;
-    const float ichi = rcp(chi);
-    const DF r0 = df_add_f(DF{m.v[0], mlo.v[0]}, src0 * ichi);
-    const DF r1 = df_add_f(DF{m.v[1], mlo.v[1]}, src1 * ichi);
+    float i0, i1;
+    if (kp.gen) {
+        sym_solve(sym_sum(kp.K, hN), src0, src1, i0, i1);
+    } else {
+        const float ichi = rcp(chi);
+        i0 = src0 * ichi;
+        i1 = src1 * ichi;
+    }
+    const DF r0 = df_add_f(DF{m.v[0], mlo.v[0]}, i0);
+    const DF r1 = df_add_f(DF{m.v[1], mlo.v[1]}, i1);
     out.v[0] = r0.h;
     out.v[1] = r1.h;
     out_lo.v[0] = r0.l;
@@ -1113,6 +1218,13 @@ __device__ __forceinline__ Mu<R> face_mu_coded(const KParams<R> &kp, const Plane
 {
     if (cL == cR && cL < 4) {
         Mu<R> v;
+        if (kp.gen) {
+            const Sym2<R> M = sym_pick(kp.DK, cL);
+            const R d0 = mR.v[0] - mL.v[0], d1 = mR.v[1] - mL.v[1];
+            v.v[0] = (M.s0 * d0 + M.s1 * d1) * kp.inv_dx;
+            v.v[1] = (M.s1 * d0 + M.s2 * d1) * kp.inv_dx;
+            return v;
+        }
         const R M = pick4(kp.DinvA, cL);
         const R Mdx = M * kp.inv_dx;
         v.v[0] = Mdx * (mR.v[0] - mL.v[0]);
@@ -1134,8 +1246,15 @@ __device__ __forceinline__ Mu<R> mu_cell_coded(const KParams<R> &kp, const Plane
         const R kT1[4] = {kp.kT[0][1], kp.kT[1][1], kp.kT[2][1], kp.kT[3][1]};
         const R src0 = kp.dt * div0 - R(0) - pick4(kT0, cN) * kp.dTstep;
         const R src1 = kp.dt * div1 - R(0) - pick4(kT1, cN) * kp.dTstep;
-        const R ichi = rcp(chi);
         Mu<R> o;
+        if (kp.gen) {
+            R i0, i1;
+            sym_solve(sym_pick(kp.K, cN), src0, src1, i0, i1);
+            o.v[0] = m.v[0] + i0;
+            o.v[1] = m.v[1] + i1;
+            return o;
+        }
+        const R ichi = rcp(chi);
         o.v[0] = m.v[0] + src0 * ichi;
         o.v[1] = m.v[1] + src1 * ichi;
         return o;
@@ -1152,6 +1271,12 @@ __device__ __forceinline__ Mu<R> quiet_flux(const KParams<R> &kp, const Mu<R> &a
 {
     // flux of the face from cell a to cell b
     Mu<R> v;
+    if (kp.gen) {
+        const R d0 = b.v[0] - a.v[0], d1 = b.v[1] - a.v[1];
+        v.v[0] = (kp.DK[3][0] * d0 + kp.DK[3][1] * d1) * kp.inv_dx;
+        v.v[1] = (kp.DK[3][1] * d0 + kp.DK[3][2] * d1) * kp.inv_dx;
+        return v;
+    }
     const R Mdx = kp.DinvA[3] * kp.inv_dx;
     v.v[0] = Mdx * (b.v[0] - a.v[0]);
     v.v[1] = Mdx * (b.v[1] - a.v[1]);
@@ -2323,9 +2448,8 @@ __global__ void __launch_bounds__(256) reduce_kernel(const KParams<R> kp, const 
     const size_t plane = (size_t)kp.nx * kp.ny;
     const size_t base = plane_off(k, kp.nz, st->zbase, plane);
     const double T = kp.T0 + kp.G * (((double)k + st->off) * kp.dx64 - kp.v * st->t);
-    double i2A[4], ch[4][2];  // per-plane constants: 1/(2 A_a), cE_a + kT_a (T - TE)
+    double ch[4][2];  // per-plane constants: cE_a + kT_a (T - TE)
     for (int a = 0; a < 4; a++) {
-        i2A[a] = 1.0 / (2.0 * kp.A64[a]);
         ch[a][0] = kp.cE[a][0] + kp.kT64[a][0] * (T - kp.TE);
         ch[a][1] = kp.cE[a][1] + kp.kT64[a][1] * (T - kp.TE);
     }
@@ -2352,8 +2476,9 @@ __global__ void __launch_bounds__(256) reduce_kernel(const KParams<R> kp, const 
             bad = bad || !isfinite(ph[a]);
             acc[a] += ph[a];
             const double h = ph[a] * ph[a] * iS;
-            c0 += h * (m0 * i2A[a] + ch[a][0]);
-            c1 += h * (m1 * i2A[a] + ch[a][1]);
+            // c^a = K_a mu + chat_a (K_a = I/(2 A_a) for the identity form)
+            c0 += h * (kp.K64[a][0] * m0 + kp.K64[a][1] * m1 + ch[a][0]);
+            c1 += h * (kp.K64[a][1] * m0 + kp.K64[a][2] * m1 + ch[a][1]);
         }
         acc[4] += c0;
         acc[5] += c1;

@@ -290,11 +290,13 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
     //   mu^{n+1} = mu^n + C1 (sum of the six neighbours - 6 mu^n) + C0,
     //   C1 = dt M / (chi dx^2),  C0 = -k_l dT / chi  (per component; chi = 1/(2 A_l)).
     // The zero-gradient mirror at z = 0 and z = nz-1 makes the missing neighbour the cell itself.
+    // with matrix curvatures chi = K_l, M = D_l K_l: C1 = dt D_l / dx^2, C0 = -K_l^{-1} k_l dT
+    // (formed on the host in FP64)
     const R ichi = rcp(kp.inv2A[3]);
-    const R C1 = ichi * (kp.dt * (kp.DinvA[3] * kp.inv_dx * kp.inv_dx));
+    const R C1 = kp.gen ? kp.liqC1 : ichi * (kp.dt * (kp.DinvA[3] * kp.inv_dx * kp.inv_dx));
     R C0[2];
-    C0[0] = -(kp.kT[3][0] * kp.dTstep) * ichi;
-    C0[1] = -(kp.kT[3][1] * kp.dTstep) * ichi;
+    C0[0] = kp.gen ? kp.liqC0[0] : -(kp.kT[3][0] * kp.dTstep) * ichi;
+    C0[1] = kp.gen ? kp.liqC0[1] : -(kp.kT[3][1] * kp.dTstep) * ichi;
     Ph<R> liquid;
     liquid.v[0] = liquid.v[1] = liquid.v[2] = R(0);
     liquid.v[3] = R(1);

@@ -30,7 +30,7 @@ PF_E_PENDING = 1
 PF_FP64 = 0
 PF_FP32 = 1
 PF_FP32_COMP = 2
-PF_PARAMS_VERSION = 1
+PF_PARAMS_VERSION = 2
 
 PRECISIONS = {"fp64": PF_FP64, "fp32": PF_FP32, "fp32c": PF_FP32_COMP}
 
@@ -52,6 +52,7 @@ class pf_params(ctypes.Structure):
         ("TE", ctypes.c_double), ("T0", ctypes.c_double), ("G", ctypes.c_double), ("v", ctypes.c_double),
         ("seed_layers", ctypes.c_int), ("n_grains", ctypes.c_int),
         ("window_trigger_z", ctypes.c_double),
+        ("Am", (ctypes.c_double * 3) * 4), ("tau_ab", ctypes.c_double * 6),
     ]
 
 
@@ -188,6 +189,12 @@ def params_from_dict(d: dict, precision: int = PF_FP64) -> pf_params:
     p.TE, p.T0, p.G, p.v = d["TE"], d["T0"], d["G"], d["v"]
     p.seed_layers, p.n_grains = int(d["seed_layers"]), int(d["n_grains"])
     p.window_trigger_z = d["window_trigger_z"]
+    Am, tau_ab = d.get("Am"), d.get("tau_ab")
+    for a in range(4):
+        for c in range(3):
+            p.Am[a][c] = Am[a][c] if Am is not None else 0.0
+    for q in range(6):
+        p.tau_ab[q] = tau_ab[q] if tau_ab is not None else 0.0
     return p
 
 

@@ -7,6 +7,7 @@ import re
 import pytest
 
 from paper_1506_01684_gb300 import build, pf
+from paper_1506_01684_gb300 import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -46,6 +47,12 @@ def test_host_only_entry_points():
     assert L.pf_create(4, 4, 4, ctypes.byref(bad), None, ctypes.byref(h)) == pf.PF_E_INVAL
     assert L.pf_step(None, 1) == pf.PF_E_INVAL
     assert L.pf_default_params(None) == pf.PF_E_INVAL
+    # general thermodynamics: curvature matrices must be positive definite, pair times all set or none
+    for change in ({"Am": [[1.0, 2.0, 1.0]] + [[0.0, 0.0, 0.0]] * 3},
+                   {"Am": [[1.0, 0.1, -1.0]] + [[0.0, 0.0, 0.0]] * 3},
+                   {"tau_ab": [1.0, 1.0, 0.0, 1.0, 1.0, 1.0]}):
+        q = pf.params_from_dict(dict(W.symmetric_params(), **change))
+        assert L.pf_create(8, 8, 8, ctypes.byref(q), None, ctypes.byref(h)) == pf.PF_E_INVAL
 
 
 def test_default_params_match_the_workload_parameter_set():

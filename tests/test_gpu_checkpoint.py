@@ -30,6 +30,7 @@ def _params():
     return p
 
 
+# bytes per value slot: the compensated state stores its two FP32 words
 @pytest.mark.parametrize("precision,elem", [("fp32", 4), ("fp64", 8), ("fp32c", 8)])
 @pytest.mark.parametrize("variant", ["auto", "unfused"])
 def test_resumed_run_equals_the_uninterrupted_run_bitwise(tmp_path, precision, elem, variant):
@@ -78,6 +79,31 @@ def test_fp32_checkpoint_restores_into_fp64(tmp_path):
     assert b.stats()["t"] == a.stats()["t"]
     a.close()
     b.close()
+
+
+def test_compensated_checkpoint_holds_both_words(tmp_path):
+    # the pairs' words go to the file as they are: a compensated reader gets the same pairs (the
+    # next steps agree bitwise), an FP64 reader the value of each pair
+    nx, ny, nz = 24, 16, 20
+    p = W.symmetric_params(n_grains=5)
+    path = str(tmp_path / "ckc.pfc")
+    a = pf.Simulation(nx, ny, nz, p, "fp32c")
+    a.init(1)
+    a.step(40)
+    a.checkpoint(path)
+    pa, ma = a.fields()
+    b = pf.Simulation(nx, ny, nz, p, "fp64")
+    b.restore(path)
+    pb, mb = b.fields()
+    assert (pa == pb).all() and (ma == mb).all()
+    c = pf.Simulation(nx, ny, nz, p, "fp32c")
+    c.restore(path)
+    a.step(20)
+    c.step(20)
+    (pa2, ma2), (pc2, mc2) = a.fields(), c.fields()
+    assert (pa2 == pc2).all() and (ma2 == mc2).all()
+    for s in (a, b, c):
+        s.close()
 
 
 def test_checkpoint_errors(tmp_path):

@@ -67,7 +67,10 @@ def test_noalloc_step_matches_pf_step_on_two_calls_in_a_row(torch, precision, to
         phi_n, mu_n = _soa(dst_phi), _soa(dst_mu)
         assert np.abs(phi_n - phi_r).max() <= tol
         assert np.abs(mu_n - mu_r).max() / max(np.abs(mu_r).max(), 1e-8) <= tol
-        assert h == pytest.approx(ref.stats()["h_int"], rel=1e-12)
+        # h = sum (1 - phi_l) / (nx ny) from each path's own fields: the two differ by at most nz
+        # times the largest phi_l difference (FP32: the two kernel paths may round differently)
+        h_ref = ref.stats()["h_int"]
+        assert abs(h - h_ref) <= nz * np.abs(phi_n[3] - phi_r[3]).max() + 1e-12 * abs(h_ref)
         # next call: the new state is the input
         src_phi, dst_phi = dst_phi, src_phi
         src_mu, dst_mu = dst_mu, src_mu
