@@ -170,11 +170,14 @@ __device__ __forceinline__ void sym_solve(const Sym2<R> &S, R x0, R x1, R &y0, R
     y0 = (S.s2 * x0 - S.s1 * x1) * idet;
     y1 = (S.s0 * x1 - S.s1 * x0) * idet;
 }
+// SYM (a template flag of the cell functions below): compiled for the symmetric set only (identity
+// curvatures, one relaxation time), the general branches left out; the host launches such an
+// instantiation only when kp.gen and kp.gen_tau are both 0.
 // c^a(mu) = K_a mu + chat_a
-template <typename R>
+template <typename R, bool SYM = false>
 __device__ __forceinline__ void c_alpha(const KParams<R> &kp, int a, R m0, R m1, R ch0, R ch1, R &c0, R &c1)
 {
-    if (kp.gen) {
+    if (!SYM && kp.gen) {
         c0 = kp.K[a][0] * m0 + kp.K[a][1] * m1 + ch0;
         c1 = kp.K[a][1] * m0 + kp.K[a][2] * m1 + ch1;
     } else {
@@ -184,10 +187,10 @@ __device__ __forceinline__ void c_alpha(const KParams<R> &kp, int a, R m0, R m1,
 }
 // dt / (tau(phi) eps) at a cell with phase fractions p (phi^n): the pair-weighted relaxation time,
 // tau on a single-phase cell
-template <typename R>
+template <typename R, bool SYM = false>
 __device__ __forceinline__ R phi_coef(const KParams<R> &kp, const R *p)
 {
-    if (!kp.gen_tau) return kp.c_phi;
+    if (SYM || !kp.gen_tau) return kp.c_phi;
     const R w01 = p[0] * p[1], w02 = p[0] * p[2], w03 = p[0] * p[3];
     const R w12 = p[1] * p[2], w13 = p[1] * p[3], w23 = p[2] * p[3];
     const R den = w01 + w02 + w03 + w12 + w13 + w23;
@@ -275,7 +278,7 @@ __device__ __forceinline__ Ph<R> project_simplex(const Ph<R> &u)
 
 // rhs_a of Eq. 2 at one cell.
 //   xm/xp, ym/yp, zm/zp: the six neighbours; F*: the six face terms (minus/plus side).
-template <typename R>
+template <typename R, bool SYM = false>
 __device__ __forceinline__ void phi_rhs(const KParams<R> &kp, const PlaneT<R> &pc, const Ph<R> &P, const Ph<R> &xm,
                                         const Ph<R> &xp, const Ph<R> &ym, const Ph<R> &yp, const Ph<R> &zm,
                                         const Ph<R> &zp, const Ph<R> &Fxm, const Ph<R> &Fxp, const Ph<R> &Fym,
@@ -329,7 +332,7 @@ __device__ __forceinline__ void phi_rhs(const KParams<R> &kp, const PlaneT<R> &p
 #pragma unroll
     for (int a = 0; a < 4; a++) {
         // -(1/2) mu . K_a mu: |mu|^2 / (4 A_a) for the identity form
-        const R quad = kp.gen ? kp.psiK[a][0] * m.v[0] * m.v[0] + kp.psiK[a][1] * m.v[0] * m.v[1] +
+        const R quad = (!SYM && kp.gen) ? kp.psiK[a][0] * m.v[0] * m.v[0] + kp.psiK[a][1] * m.v[0] * m.v[1] +
                                     kp.psiK[a][2] * m.v[1] * m.v[1]
                               : mu2 * kp.inv4A[a];
         psi[a] = -quad - (m.v[0] * pc.chat[a][0] + m.v[1] * pc.chat[a][1]) + pc.sT[a];
@@ -343,7 +346,7 @@ __device__ __forceinline__ void phi_rhs(const KParams<R> &kp, const PlaneT<R> &p
 }
 
 // Full cell update of the phi-sweep at one cell: phi^{n+1} = Proj(phi^n - dt/(tau eps)(rhs - mean rhs)).
-template <typename R>
+template <typename R, bool SYM = false>
 __device__ __forceinline__ Ph<R> phi_cell(const KParams<R> &kp, const PlaneT<R> &pc, const Ph<R> &P,
                                           const Ph<R> &xm, const Ph<R> &xp, const Ph<R> &ym,
                                           const Ph<R> &yp, const Ph<R> &zm, const Ph<R> &zp,
@@ -352,11 +355,11 @@ __device__ __forceinline__ Ph<R> phi_cell(const KParams<R> &kp, const PlaneT<R> 
                                           const Mu<R> &m)
 {
     R rhs[4];
-    phi_rhs(kp, pc, P, xm, xp, ym, yp, zm, zp, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, m, rhs);
+    phi_rhs<R, SYM>(kp, pc, P, xm, xp, ym, yp, zm, zp, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, m, rhs);
     const R *p = P.v;
     R mean = (rhs[0] + rhs[1] + rhs[2] + rhs[3]) * R(0.25);
     Ph<R> st;
-    const R cp = phi_coef(kp, p);
+    const R cp = phi_coef<R, SYM>(kp, p);
 #pragma unroll
     for (int a = 0; a < 4; a++) st.v[a] = p[a] - cp * (rhs[a] - mean);
     return project_simplex(st);
@@ -560,7 +563,7 @@ __device__ __forceinline__ void ring_cell(int r, int &li, int &lj)
 // tf: plane-table entry of the face's temperature (read only where the anti-trapping current is
 // evaluated).  A face between two equal one-hot cells takes the exact short form (h = phi there,
 // no anti-trapping current).
-template <typename R>
+template <typename R, bool SYM = false>
 __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const PlaneT<R> *__restrict__ tf,
                                                  const Ph<R> &nL, const Ph<R> &nR, const Ph<R> &oL, const Ph<R> &oR,
                                                  const Mu<R> &mL, const Mu<R> &mR, const Ph<R> &aLp,
@@ -577,7 +580,7 @@ __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const Pla
     R h[4];
 #pragma unroll
     for (int b = 0; b < 4; b++) h[b] = pb[b] * pb[b] * inv_S;
-    if (kp.gen) {
+    if (!SYM && kp.gen) {
         // M = sum_a D_a h_a K_a (a 2x2 matrix)
         const Sym2<R> M = sym_sum(kp.DK, h);
         const R d0 = mR.v[0] - mL.v[0], d1 = mR.v[1] - mL.v[1];
@@ -602,7 +605,7 @@ __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const Pla
             const R mb0 = R(0.5) * (mL.v[0] + mR.v[0]);
             const R mb1 = R(0.5) * (mL.v[1] + mR.v[1]);
             R cl0, cl1;
-            c_alpha(kp, 3, mb0, mb1, ch.c[3][0], ch.c[3][1], cl0, cl1);
+            c_alpha<R, SYM>(kp, 3, mb0, mb1, ch.c[3][0], ch.c[3][1], cl0, cl1);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 if (!(pb[a] > R(0))) continue;
@@ -617,7 +620,7 @@ __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const Pla
                 const R pdot = R(0.5) * ((nL.v[a] - oL.v[a]) + (nR.v[a] - oR.v[a])) * kp.inv_dt;
                 const R pref = kp.at_pref * (pb[a] * h[3] / sqrt(pb[a] * pb[3])) * pdot * ndot;
                 R ca0, ca1;
-                c_alpha(kp, a, mb0, mb1, ch.c[a][0], ch.c[a][1], ca0, ca1);
+                c_alpha<R, SYM>(kp, a, mb0, mb1, ch.c[a][0], ch.c[a][1], ca0, ca1);
                 const R dc0 = cl0 - ca0;
                 const R dc1 = cl1 - ca1;
                 const R nd = ga[0] / na;  // normal component: the face direction is component 0
@@ -635,7 +638,7 @@ __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const Pla
 // tf: plane-table entry of the face's temperature (read only where the anti-trapping current is
 // evaluated).  A face between two equal one-hot cells takes the exact short form (h = phi there,
 // no anti-trapping current).
-template <typename R>
+template <typename R, bool SYM = false>
 __device__ __forceinline__ Mu<R> face_mu(const KParams<R> &kp, const PlaneT<R> *__restrict__ tf, const Ph<R> &nL,
                                          const Ph<R> &nR, const Ph<R> &oL, const Ph<R> &oR, const Mu<R> &mL,
                                          const Mu<R> &mR, const Ph<R> &aLp, const Ph<R> &aLm,
@@ -644,7 +647,7 @@ __device__ __forceinline__ Mu<R> face_mu(const KParams<R> &kp, const PlaneT<R> *
 {
     if (same(nL, nR) && onehot(nL)) {
         Mu<R> v;
-        if (kp.gen) {
+        if (!SYM && kp.gen) {
             const Sym2<R> M = sym_sum(kp.DK, nL.v);
             const R d0 = mR.v[0] - mL.v[0], d1 = mR.v[1] - mL.v[1];
             v.v[0] = (M.s0 * d0 + M.s1 * d1) * kp.inv_dx;
@@ -657,14 +660,14 @@ __device__ __forceinline__ Mu<R> face_mu(const KParams<R> &kp, const PlaneT<R> *
         v.v[1] = Mdx * (mR.v[1] - mL.v[1]);
         return v;
     }
-    return face_mu_general(kp, tf, nL, nR, oL, oR, mL, mR, aLp, aLm, aRp, aRm, bLp, bLm, bRp, bRm);
+    return face_mu_general<R, SYM>(kp, tf, nL, nR, oL, oR, mL, mR, aLp, aLm, aRp, aRm, bLp, bLm, bRp, bRm);
 }
 
 // mu update at one cell (Eq. 3, reading R10):
 //   mu^{n+1} = mu^n + [dt div v - sum_a c^a(mu^n,T)(h_a(new) - h_a(old)) - sum_a h_a(new) kT_a dT] / chi
 // A cell whose phi did not change and is one-hot takes the exact short form (h = phi, no
 // phase-change source).
-template <typename R>
+template <typename R, bool SYM = false>
 __device__ __forceinline__ Mu<R> mu_cell(const KParams<R> &kp, const PlaneT<R> *__restrict__ tc, const Ph<R> &nP,
                                          const Ph<R> &oP, const Mu<R> &m, R div0, R div1)
 {
@@ -687,7 +690,7 @@ __device__ __forceinline__ Mu<R> mu_cell(const KParams<R> &kp, const PlaneT<R> *
         for (int a = 0; a < 4; a++) {
             const R dh = hN[a] - hO[a];
             R ca0, ca1;
-            c_alpha(kp, a, m.v[0], m.v[1], ch.c[a][0], ch.c[a][1], ca0, ca1);
+            c_alpha<R, SYM>(kp, a, m.v[0], m.v[1], ch.c[a][0], ch.c[a][1], ca0, ca1);
             dphi0 = dphi0 + ca0 * dh;
             dphi1 = dphi1 + ca1 * dh;
         }
@@ -702,7 +705,7 @@ __device__ __forceinline__ Mu<R> mu_cell(const KParams<R> &kp, const PlaneT<R> *
     const R src0 = kp.dt * div0 - dphi0 - dT0 * kp.dTstep;
     const R src1 = kp.dt * div1 - dphi1 - dT1 * kp.dTstep;
     Mu<R> o;
-    if (kp.gen) {
+    if (!SYM && kp.gen) {
         // chi = sum_a h_a K_a (2x2): mu^{n+1} = mu^n + chi^{-1} src
         R i0, i1;
         sym_solve(sym_sum(kp.K, hN), src0, src1, i0, i1);
@@ -785,7 +788,7 @@ __device__ __forceinline__ void mu_cell_comp(const KParams<float> &kp, const Pla
 // ---------------------------------------------------------------------------------------
 // One CTA's phi-sweep of tile (bx, by), planes [z0, z1).  With tmap_out, also the new field's
 // liquid-map entries of those planes (1 when the tile's cells are exactly pure liquid).
-template <typename R, int TX, int TY, bool COMP = false>
+template <typename R, int TX, int TY, bool COMP = false, bool SYM = false>
 __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R> *__restrict__ phi,
                                                const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
                                                const DevState *__restrict__ st, const PlaneT<R> *__restrict__ tab,
@@ -888,7 +891,7 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
                                   fx[ty * (TX + 1) + tx + 1], fy[ty * TX + tx], fy[(ty + 1) * TX + tx], Fz_prev, Fz_cur,
                                   sMu[(p & 3) * NT + tid], out, out_lo);
                 } else {
-                    out = phi_cell(kp, T, pc, xm, xp, ym, yp, pm, pn, fx[ty * (TX + 1) + tx],
+                    out = phi_cell<R, SYM>(kp, T, pc, xm, xp, ym, yp, pm, pn, fx[ty * (TX + 1) + tx],
                                    fx[ty * (TX + 1) + tx + 1], fy[ty * TX + tx], fy[(ty + 1) * TX + tx], Fz_prev, Fz_cur,
                                    sMu[(p & 3) * NT + tid]);
                 }
@@ -951,7 +954,7 @@ __global__ void __launch_bounds__(TX *TY) phi_sweep_kernel(const KParams<R> kp, 
 // `words` words a cell as its algorithmic bytes.  With splits (the step's plan), phi^{n+1} of a
 // tile plane that the lean kernel updates is e_l by construction and is taken as such instead of
 // being read (the lean kernel may still be writing it).
-template <typename R, int TX, int TY, bool COMP = false>
+template <typename R, int TX, int TY, bool COMP = false, bool SYM = false>
 __device__ __forceinline__ void mu_sweep_tile(const KParams<R> &kp, const Ph<R> *__restrict__ phi_old,
                                               const Ph<R> *__restrict__ phi_new, const Mu<R> *__restrict__ mu,
                                               Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st,
@@ -1042,13 +1045,13 @@ __device__ __forceinline__ void mu_sweep_tile(const KParams<R> &kp, const Ph<R> 
 
     // x face (li | li+1) and y face (lj | lj+1) of plane q
     auto xface = [&](int q, int li, int lj) -> Mu<R> {
-        return face_mu(kp, tab + q, N(q, li, lj), N(q, li + 1, lj), O(q, li, lj), O(q, li + 1, lj), Mm(q, li, lj),
+        return face_mu<R, SYM>(kp, tab + q, N(q, li, lj), N(q, li + 1, lj), O(q, li, lj), O(q, li + 1, lj), Mm(q, li, lj),
                        Mm(q, li + 1, lj), N(q, li, lj + 1), N(q, li, lj - 1), N(q, li + 1, lj + 1),
                        N(q, li + 1, lj - 1), N(q + 1, li, lj), N(q - 1, li, lj), N(q + 1, li + 1, lj),
                        N(q - 1, li + 1, lj));
     };
     auto yface = [&](int q, int li, int lj) -> Mu<R> {
-        return face_mu(kp, tab + q, N(q, li, lj), N(q, li, lj + 1), O(q, li, lj), O(q, li, lj + 1), Mm(q, li, lj),
+        return face_mu<R, SYM>(kp, tab + q, N(q, li, lj), N(q, li, lj + 1), O(q, li, lj), O(q, li, lj + 1), Mm(q, li, lj),
                        Mm(q, li, lj + 1), N(q, li + 1, lj), N(q, li - 1, lj), N(q, li + 1, lj + 1),
                        N(q, li - 1, lj + 1), N(q + 1, li, lj), N(q - 1, li, lj), N(q + 1, li, lj + 1),
                        N(q - 1, li, lj + 1));
@@ -1060,7 +1063,7 @@ __device__ __forceinline__ void mu_sweep_tile(const KParams<R> &kp, const Ph<R> 
             v.v[0] = v.v[1] = R(0);
             return v;
         }
-        return face_mu(kp, tab + nz + q, N(q, tx, ty), N(q + 1, tx, ty), O(q, tx, ty), O(q + 1, tx, ty),
+        return face_mu<R, SYM>(kp, tab + nz + q, N(q, tx, ty), N(q + 1, tx, ty), O(q, tx, ty), O(q + 1, tx, ty),
                        Mm(q, tx, ty), Mm(q + 1, tx, ty), N(q, tx + 1, ty), N(q, tx - 1, ty), N(q + 1, tx + 1, ty),
                        N(q + 1, tx - 1, ty), N(q, tx, ty + 1), N(q, tx, ty - 1), N(q + 1, tx, ty + 1),
                        N(q + 1, tx, ty - 1));
@@ -1117,7 +1120,7 @@ __device__ __forceinline__ void mu_sweep_tile(const KParams<R> &kp, const Ph<R> 
                 mu_cell_comp(kp, tab + p, ownN, ownO, ownM, mlo, div0, div1, out, out_lo);
                 if (valid) st_mu(mu_out_lo + plane_off(p, nz, zbase, plane) + col0, out_lo);
             } else {
-                out = mu_cell(kp, tab + p, ownN, ownO, ownM, div0, div1);
+                out = mu_cell<R, SYM>(kp, tab + p, ownN, ownO, ownM, div0, div1);
             }
             if (valid) {
                 st_mu(mu_out + plane_off(p, nz, zbase, plane) + col0, out);
@@ -2051,7 +2054,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) general_step_k
 #ifndef PF_GENERAL_MIN_CTAS
 #define PF_GENERAL_MIN_CTAS 2
 #endif
-template <typename R, int TX, int TY>
+template <typename R, int TX, int TY, bool SYM>
 __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_phi_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
                                                             const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
                                                             const DevState *__restrict__ st,
@@ -2075,11 +2078,11 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_phi_kerne
         if (item < 0) break;
         const int tile = item % ntl;
         const int2 sp = splits[item];
-        phi_sweep_tile<R, TX, TY, false>(kp, phi, mu, phi_out, st, tab, nullptr, nullptr, tile % kp.tgx, tile / kp.tgx,
-                                         sp.x, sp.y, smem_raw, tmap_out);
+        phi_sweep_tile<R, TX, TY, false, SYM>(kp, phi, mu, phi_out, st, tab, nullptr, nullptr, tile % kp.tgx,
+                                              tile / kp.tgx, sp.x, sp.y, smem_raw, tmap_out);
     }
 }
-template <typename R, int TX, int TY>
+template <typename R, int TX, int TY, bool SYM>
 __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_mu_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi_old,
                                                            const Ph<R> *__restrict__ phi_new,
                                                            const Mu<R> *__restrict__ mu, Mu<R> *__restrict__ mu_out,
@@ -2106,8 +2109,9 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_mu_kernel
         const int2 sp = splits[item];
         // both sweeps' compulsory words: phi^n, mu^n in, phi^{n+1} out; phi^n, phi^{n+1}, mu^n in,
         // mu^{n+1} out
-        mu_sweep_tile<R, TX, TY, false>(kp, phi_old, phi_new, mu, mu_out, st, tab, partials + item, nullptr, nullptr,
-                                        tile % kp.tgx, tile / kp.tgx, sp.x, sp.y, smem_raw, 22.0, splits, kp.zchunk);
+        mu_sweep_tile<R, TX, TY, false, SYM>(kp, phi_old, phi_new, mu, mu_out, st, tab, partials + item, nullptr,
+                                             nullptr, tile % kp.tgx, tile / kp.tgx, sp.x, sp.y, smem_raw, 22.0, splits,
+                                             kp.zchunk);
     }
 }
 
@@ -2740,22 +2744,28 @@ cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const v
     static bool attr = false;
     const size_t smp = phi_smem_bytes<R>(), smm = mu_smem_bytes<R>();
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(general_phi_kernel<R, kTX, kTY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(general_mu_kernel<R, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smm);
+        cudaError_t e = cudaSuccess;
+        for (int sym = 0; sym < 2 && e == cudaSuccess; sym++) {
+            e = cudaFuncSetAttribute(sym ? general_phi_kernel<R, kTX, kTY, true> : general_phi_kernel<R, kTX, kTY, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(sym ? general_mu_kernel<R, kTX, kTY, true> : general_mu_kernel<R, kTX, kTY, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm);
+        }
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    general_phi_kernel<R, kTX, kTY><<<phi_ctas, kTX * kTY, smp, s>>>(kp, (const Ph<R> *)phi, (const Mu<R> *)mu,
-                                                                    (Ph<R> *)phi_out, st, tab, tmap_out, splits,
-                                                                    glist, stats);
+    // the symmetric set (identity curvatures, one relaxation time) runs the instantiation compiled
+    // without the general branches
+    const bool sym = !kp.gen && !kp.gen_tau;
+    auto kphi = sym ? general_phi_kernel<R, kTX, kTY, true> : general_phi_kernel<R, kTX, kTY, false>;
+    auto kmu = sym ? general_mu_kernel<R, kTX, kTY, true> : general_mu_kernel<R, kTX, kTY, false>;
+    kphi<<<phi_ctas, kTX * kTY, smp, s>>>(kp, (const Ph<R> *)phi, (const Mu<R> *)mu, (Ph<R> *)phi_out, st, tab,
+                                          tmap_out, splits, glist, stats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    general_mu_kernel<R, kTX, kTY><<<mu_ctas, kTX * kTY, smm, s>>>(kp, (const Ph<R> *)phi, (const Ph<R> *)phi_out,
-                                                                  (const Mu<R> *)mu, (Mu<R> *)mu_out, st, tab, parts,
-                                                                  splits, glist, stats);
+    kmu<<<mu_ctas, kTX * kTY, smm, s>>>(kp, (const Ph<R> *)phi, (const Ph<R> *)phi_out, (const Mu<R> *)mu,
+                                        (Mu<R> *)mu_out, st, tab, parts, splits, glist, stats);
     return cudaGetLastError();
 }
 
@@ -2763,14 +2773,15 @@ template <typename R>
 void general_sweep_ctas_per_sm(int *phi_per_sm, int *mu_per_sm)
 {
     int a = 0, b = 0;
-    if (cudaFuncSetAttribute(general_phi_kernel<R, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // the instantiation with the general branches (it needs at least the symmetric one's registers)
+    if (cudaFuncSetAttribute(general_phi_kernel<R, kTX, kTY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)phi_smem_bytes<R>()) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, general_phi_kernel<R, kTX, kTY>, kTX * kTY,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, general_phi_kernel<R, kTX, kTY, false>, kTX * kTY,
                                                       phi_smem_bytes<R>()) != cudaSuccess)
         a = 1;
-    if (cudaFuncSetAttribute(general_mu_kernel<R, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(general_mu_kernel<R, kTX, kTY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)mu_smem_bytes<R>()) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, general_mu_kernel<R, kTX, kTY>, kTX * kTY,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, general_mu_kernel<R, kTX, kTY, false>, kTX * kTY,
                                                       mu_smem_bytes<R>()) != cudaSuccess)
         b = 1;
     cudaGetLastError();
