@@ -1415,6 +1415,7 @@ struct pf_batch {
     DevBuf plan_entries, lean_items, splits, glist, plan;
     int nplan = 0, nlean = 0, gphi_ctas = 1, gmu_ctas = 1;
     bool lean_mode = false;
+    bool sym = true;  // every domain has the symmetric set (no matrix curvature, no pair times)
 };
 
 template <typename R>
@@ -1438,6 +1439,8 @@ static int batch_build(pf_batch *b)
         KParams<R> kp = make_kparams<R>(s);
         kp.zchunk = g.zchunk;
         d[q].kp = kp;
+        if (q == 0) b->sym = true;
+        b->sym = b->sym && !kp.gen && !kp.gen_tau;
         for (int k = 0; k < 2; k++) {
             d[q].phi[k] = s->phi[k ^ s->cur].p;
             d[q].mu[k] = s->mu[k ^ s->cur].p;
@@ -1566,7 +1569,8 @@ static int batch_step_direct(pf_batch *b, int n)
                                             (const int2 *)b->plan_entries.p, b->nplan, (const int4 *)b->lean_items.p,
                                             b->nlean, (int2 *)b->glist.p, (BatchPlan *)b->plan.p, b->gphi_ctas,
                                             b->gmu_ctas, (const BatchItem *)b->items.p, b->nitems,
-                                            (unsigned *)b->counter.p, b->ctas, b->parity, b->post_blocks, b->stream);
+                                            (unsigned *)b->counter.p, b->ctas, b->parity, b->post_blocks, b->stream,
+                                            b->sym);
         else
             e = launch_batched_step<R>((const BatchDomain<R> *)b->doms.p, (int)b->sims.size(),
                                        (const BatchItem *)b->items.p, b->nitems, (unsigned *)b->counter.p, b->parity,

@@ -202,7 +202,8 @@ template <typename R>
 cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, const int2 *plan_entries, int nplan,
                                      const int4 *lean_items, int nlean, int2 *glist, BatchPlan *plan,
                                      int phi_ctas, int mu_ctas, const BatchItem *fitems, int nfitems,
-                                     unsigned *counter, int fctas, int parity, int post_blocks, cudaStream_t s);
+                                     unsigned *counter, int fctas, int parity, int post_blocks, cudaStream_t s,
+                                     bool sym);  // sym: every domain has the symmetric parameter set
 template <typename R>
 void batched_general_ctas_per_sm(int *phi_per_sm, int *mu_per_sm);
 template <typename R>

@@ -82,6 +82,10 @@ __device__ __forceinline__ int wrapi(int x, int n)
     return x < 0 ? x + n : x;
 }
 
+// Liquid map layout: tile-major, the storage planes of one fused-step tile contiguous, so that the
+// threads of a warp testing consecutive planes of one tile read consecutive bytes.
+__device__ __forceinline__ size_t map_idx(int sp, int tile, int nz) { return (size_t)tile * nz + sp; }
+
 // storage plane of logical plane k, with the zero-gradient mirror applied first
 __device__ __forceinline__ size_t plane_off(int k, int nz, int zbase, size_t plane)
 {
@@ -914,7 +918,7 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
         if (tmap_out) {
             // the barrier also gives the map entry of the new plane p
             const int all = __syncthreads_and(out_liquid);
-            if (tid == 0) tmap_out[plane_off(p, nz, zbase, plane) / plane * kp.tgx * kp.tgy + by * kp.tgx + bx] = all ? 1 : 0;
+            if (tid == 0) tmap_out[map_idx((int)(plane_off(p, nz, zbase, plane) / plane), by * kp.tgx + bx, nz)] = all ? 1 : 0;
         } else {
             __syncthreads();
         }
@@ -1364,13 +1368,13 @@ struct RingTiles {
     {
         const int kc = k < 0 ? 0 : (k >= nz ? nz - 1 : k);
         const int sp = kc + zbase >= nz ? kc + zbase - nz : kc + zbase;
-        const unsigned char *m = tmap + (size_t)sp * ntl;
+        (void)ntl;
         bool ok = true;
 #pragma unroll
         for (int r = 0; r < 5; r++)
 #pragma unroll
             for (int c = 0; c < 5; c++)
-                if (uy[r] && ux[c]) ok = ok & (m[ys[r] * tgx + xs[c]] == 1);
+                if (uy[r] && ux[c]) ok = ok & (tmap[map_idx(sp, ys[r] * tgx + xs[c], nz)] == 1);
         return ok;
     }
 };
@@ -1641,7 +1645,7 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
                         if (tx == TX - 1) xp = mxe[u];
                         const Mu<R> out = quiet_mu_cell(kp, tab + q, mo[u], xm, xp, mym[u], myp[u], Vz_lo, Vz_hi);
                         const size_t o = (size_t)splane(q) * plane;
-                        const bool store_phi = !tmap_out || tmap_out[(size_t)splane(q) * ntl + tile] != 1;
+                        const bool store_phi = !tmap_out || tmap_out[map_idx(splane(q), tile, nz)] != 1;
                         phi_stores += store_phi ? 1 : 0;
                         if (valid) {
                             if (store_phi) st_ph(phi_out + o + col_own, liquid);
@@ -1657,7 +1661,7 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
             // replaced by the new field's
             __syncthreads();
             if (tmap_out)
-                for (int q = qa + tid; q < qb; q += NT) tmap_out[(size_t)splane(q) * ntl + tile] = 1;
+                for (int q = qa + tid; q < qb; q += NT) tmap_out[map_idx(splane(q), tile, nz)] = 1;
             // mu^n in, mu^{n+1} out (4 words a cell), plus phi^{n+1} where it was stored
             lean_bytes += tile_cells * (double)sizeof(R) * (4.0 * (qb - qa) + 4.0 * phi_stores);
         };
@@ -1905,7 +1909,7 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
     {
         // the barrier also gives the liquid-map entry of phi^{n+1}(z0)
         const int liq_z0 = __syncthreads_and(own_liq);
-        if (tmap_out && tid == 0) tmap_out[(size_t)splane(z0) * ntl + tile] = liq_z0 ? 1 : 0;
+        if (tmap_out && tid == 0) tmap_out[map_idx(splane(z0), tile, nz)] = liq_z0 ? 1 : 0;
     }
     if (z0 == 0) {
         copy_plane(-1, 0);  // the mirror plane below the domain
@@ -1946,7 +1950,7 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
             // so each cell evaluates its four in-plane faces from mu^n directly (both cells of a face
             // evaluate the same expression: the result is that of the staged faces) -- no barrier
             // (phi^{n+1}(q+1) = phi^n(q+1) is pure liquid on the tile: its liquid-map entry is 1)
-            if (tmap_out && tid == 0 && q + 1 < z1) tmap_out[(size_t)splane(q + 1) * ntl + tile] = 1;
+            if (tmap_out && tid == 0 && q + 1 < z1) tmap_out[map_idx(splane(q + 1), tile, nz)] = 1;
             const Mu<R> *Mq = sM + mod3(q) * SN;
             const Mu<R> mP = Mq[t1];
             const Mu<R> Vz_hi = mu_zflux_quiet(q);
@@ -1963,7 +1967,7 @@ __device__ __forceinline__ void fused_tile(const KParams<R> &kp, const Ph<R> *__
             // S3 reads phi^{n+1}(q+1) written by other threads in S2; the barrier also gives the
             // liquid-map entry of that plane
             const int liq_q1 = __syncthreads_and(phi_quiet || own_liq);
-            if (tmap_out && tid == 0 && q + 1 < z1) tmap_out[(size_t)splane(q + 1) * ntl + tile] = liq_q1 ? 1 : 0;
+            if (tmap_out && tid == 0 && q + 1 < z1) tmap_out[map_idx(splane(q + 1), tile, nz)] = liq_q1 ? 1 : 0;
         }
         // S3: mu face fluxes of plane q, the z flux (q | q+1)
         mu_faces(q, false);
@@ -2143,7 +2147,9 @@ __global__ void __launch_bounds__(256) batched_plan_kernel(const BatchDomain<R> 
 
 // The general planes of a batched step as the two sweeps: persistent CTAs over the batch-wide list
 // of (domain, item) entries (pass 0: phi-sweep, counter gnext; pass 1: mu-sweep, counter gnext_mu).
-template <typename R, int TX, int TY, int PASS>
+// SYM: every domain of the batch has the symmetric set (the instantiation without the general-
+// thermodynamics branches, as the single-domain general kernels).
+template <typename R, int TX, int TY, int PASS, bool SYM>
 __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) batched_general_kernel(
     const BatchDomain<R> *__restrict__ doms, const int2 *__restrict__ glist, BatchPlan *__restrict__ plan, int parity)
 {
@@ -2170,11 +2176,11 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) batched_general_k
         const int2 sp = d->splits[en.y];
         const int a = parity, b = parity ^ 1;
         if (PASS == 0)
-            phi_sweep_tile<R, TX, TY, false>(s_kp, (const Ph<R> *)d->phi[a], (const Mu<R> *)d->mu[a], (Ph<R> *)d->phi[b],
+            phi_sweep_tile<R, TX, TY, false, SYM>(s_kp, (const Ph<R> *)d->phi[a], (const Mu<R> *)d->mu[a], (Ph<R> *)d->phi[b],
                                              d->st, d->tab, nullptr, nullptr, tile % s_kp.tgx, tile / s_kp.tgx, sp.x,
                                              sp.y, smem_raw, d->tmap[b]);
         else
-            mu_sweep_tile<R, TX, TY, false>(s_kp, (const Ph<R> *)d->phi[a], (const Ph<R> *)d->phi[b],
+            mu_sweep_tile<R, TX, TY, false, SYM>(s_kp, (const Ph<R> *)d->phi[a], (const Ph<R> *)d->phi[b],
                                             (const Mu<R> *)d->mu[a], (Mu<R> *)d->mu[b], d->st, d->tab,
                                             d->parts + en.y, nullptr, nullptr, tile % s_kp.tgx, tile / s_kp.tgx, sp.x,
                                             sp.y, smem_raw, 22.0, d->splits, s_kp.zchunk);
@@ -2351,7 +2357,7 @@ __device__ __forceinline__ void post_body(const KParams<R> &kp, const DevState *
         for (size_t q = tid; q < (size_t)s * ntl; q += nth) {
             int sp = nz - s + (int)(q / ntl) + zbase;
             if (sp >= nz) sp -= nz;
-            tmap[(size_t)sp * ntl + q % ntl] = 1;
+            tmap[map_idx(sp, (int)(q % ntl), nz)] = 1;
         }
     }
     if (s > 0) {
@@ -2583,7 +2589,7 @@ __global__ void __launch_bounds__(TX *TY) classify_kernel(const KParams<R> kp, c
         const size_t off = plane_off(k, kp.nz, zbase, plane);
         const bool liq = !valid || code_of(ldg_ph(phi + off + (size_t)j * kp.nx + i)) == 3;
         const int all = __syncthreads_and(liq);
-        if (threadIdx.x == 0) tmap[off / plane * kp.tgx * kp.tgy + tile] = all ? 1 : 0;
+        if (threadIdx.x == 0) tmap[map_idx((int)(off / plane), tile, kp.nz)] = all ? 1 : 0;
     }
 }
 
@@ -2896,17 +2902,24 @@ template <typename R>
 cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, const int2 *plan_entries, int nplan,
                                      const int4 *lean_items, int nlean, int2 *glist, BatchPlan *plan,
                                      int phi_ctas, int mu_ctas, const BatchItem *fitems, int nfitems,
-                                     unsigned *counter, int fctas, int parity, int post_blocks, cudaStream_t s)
+                                     unsigned *counter, int fctas, int parity, int post_blocks, cudaStream_t s,
+                                     bool sym)
 {
     using L = LeanLayout<R, kTX, kTY>;
     static bool attr = false;
     const size_t smp = phi_smem_bytes<R>(), smm = mu_smem_bytes<R>(), sml = L::smem_bytes(kLeanStages);
     const size_t smf = fused_smem_bytes<R>();
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 0>,
+        cudaError_t e = cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 0, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 1>,
+            e = cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 1, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 0, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 1, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(batched_lean_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>,
@@ -2922,8 +2935,13 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
     if (nplan > 0) {
         batched_plan_kernel<R, kTX, kTY><<<(nplan + 3) / 4, 256, 0, s>>>(doms, plan_entries, nplan, parity, glist,
                                                                           plan);
-        batched_general_kernel<R, kTX, kTY, 0><<<phi_ctas, kTX * kTY, smp, s>>>(doms, glist, plan, parity);
-        batched_general_kernel<R, kTX, kTY, 1><<<mu_ctas, kTX * kTY, smm, s>>>(doms, glist, plan, parity);
+        if (sym) {
+            batched_general_kernel<R, kTX, kTY, 0, true><<<phi_ctas, kTX * kTY, smp, s>>>(doms, glist, plan, parity);
+            batched_general_kernel<R, kTX, kTY, 1, true><<<mu_ctas, kTX * kTY, smm, s>>>(doms, glist, plan, parity);
+        } else {
+            batched_general_kernel<R, kTX, kTY, 0, false><<<phi_ctas, kTX * kTY, smp, s>>>(doms, glist, plan, parity);
+            batched_general_kernel<R, kTX, kTY, 1, false><<<mu_ctas, kTX * kTY, smm, s>>>(doms, glist, plan, parity);
+        }
     }
     if (nlean > 0)
         batched_lean_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>
@@ -2942,14 +2960,14 @@ template <typename R>
 void batched_general_ctas_per_sm(int *phi_per_sm, int *mu_per_sm)
 {
     int a = 0, b = 0;
-    if (cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)phi_smem_bytes<R>()) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batched_general_kernel<R, kTX, kTY, 0>, kTX * kTY,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batched_general_kernel<R, kTX, kTY, 0, false>, kTX * kTY,
                                                       phi_smem_bytes<R>()) != cudaSuccess)
         a = 1;
-    if (cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)mu_smem_bytes<R>()) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_general_kernel<R, kTX, kTY, 1>, kTX * kTY,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_general_kernel<R, kTX, kTY, 1, false>, kTX * kTY,
                                                       mu_smem_bytes<R>()) != cudaSuccess)
         b = 1;
     cudaGetLastError();
@@ -3088,7 +3106,7 @@ cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const voi
     template int fused_ctas_per_sm<R>();                                                                         \
     template cudaError_t launch_batched_lean_step<R>(const BatchDomain<R> *, int, const int2 *, int, const int4 *, \
                                                      int, int2 *, BatchPlan *, int, int, const BatchItem *, int,   \
-                                                     unsigned *, int, int, int, cudaStream_t);                      \
+                                                     unsigned *, int, int, int, cudaStream_t, bool);                \
     template void batched_general_ctas_per_sm<R>(int *, int *);                                                  \
     template cudaError_t launch_finalize<R>(const KParams<R> &, DevState *, const Partial *, int, cudaStream_t,   \
                                             LeanStats *);                                                        \

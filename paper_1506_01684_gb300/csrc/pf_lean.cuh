@@ -191,7 +191,7 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
 
     // (the launch guarantees s1 - s0 <= MAXSUB) the destination's map entries, read before any is
     // replaced
-    for (int q = s0 + tid; q < s1; q += NTH) s_dst_liquid[q - s0] = tmap_out[(size_t)splane(q) * ntl + tile];
+    for (int q = s0 + tid; q < s1; q += NTH) s_dst_liquid[q - s0] = tmap_out[map_idx(splane(q), tile, nz)];
     if (tid == 0) {
         int nfix = 0;
         for (int l = 0; l < 32; l++) nfix += fixes(l) ? 1 : 0;
@@ -401,7 +401,7 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
     // is always a safe entry.
     const unsigned char mark = s_abort ? 0 : 1;
     for (int g = 0; g < 2; g++)
-        for (int q = qa[g] + tid; q < qb[g]; q += NC) tmap_out[(size_t)splane(q) * ntl + tile] = mark;
+        for (int q = qa[g] + tid; q < qb[g]; q += NC) tmap_out[map_idx(splane(q), tile, nz)] = mark;
     if (tid == 0) {
         const unsigned long long tile_cells = (unsigned long long)min(TX, nx - i0) * (unsigned long long)min(TY, ny - j0);
         // mu^n in, mu^{n+1} out (4 words a cell), plus phi^{n+1} where it was stored
