@@ -20,13 +20,19 @@
 #include <cuda.h>
 
 #ifndef PF_LEAN_MIN_CTAS
-#define PF_LEAN_MIN_CTAS 7  // resident lean CTAs per SM the register allocation must allow
+#define PF_LEAN_MIN_CTAS 6  // resident lean CTAs per SM the register allocation must allow
 #endif
 #ifndef PF_LEAN_SUSPEND_NS
 #define PF_LEAN_SUSPEND_NS 1000u  // longest suspension of a waiting thread per try (the wait's bound is separate)
 #endif
 
+#ifndef PF_LEAN_UNROLL
+#define PF_LEAN_UNROLL 2  // planes of the consumers' z-march per unrolled loop body
+#endif
+
 namespace pf {
+
+constexpr int kLeanUnroll = PF_LEAN_UNROLL;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -333,6 +339,7 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
                 if (qa[g] == 0) mlo[r] = m[r];  // mirror below plane 0
             }
         }
+#pragma unroll kLeanUnroll
         for (int q = qa[g]; q < qb[g] && ok; q++, v++) {
             const unsigned char *S = stg(v);
             Mu<R> mn[ROWS];
