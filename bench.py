@@ -56,7 +56,7 @@ METRIC = "phi+mu step MLUP/s (FP32 stencil; FP64 GPU path and error reported bes
 # depth, mu larger than L2; the capture and its command are in profiles/lean_step_traffic_fp32_256x256x512.md);
 # traffic of a full launch = this ratio x the launch's algorithmic bytes (traffic grows with the lean
 # cells).  Remove an entry when its kernel changes.
-TRAFFIC_RATIO = {"lean_step": 0.93}
+TRAFFIC_RATIO = {"lean_step": 0.94}
 
 
 def _env_int(name, default):
