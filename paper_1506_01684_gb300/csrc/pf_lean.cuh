@@ -10,8 +10,10 @@
 // copy per plane (the tile plus a one-cell halo, columns i0-2 .. i0+TX+1 so that the box starts on
 // a 16-byte boundary, rows j0-1 .. j0+TY) into a ring of LD stages, plus asynchronous copies of
 // the periodic images that fall outside the tensor (the wrapped column / row at the domain edge);
-// both complete on the stage's "full" mbarrier.  Eight consumer warps (one thread per column)
-// wait on it, update the plane, and release the stage through its "empty" mbarrier.  Nothing of
+// both complete on the stage's "full" mbarrier.  TY / ROWS consumer warps wait on it, update the
+// plane and release the stage through its "empty" mbarrier; a consumer thread holds ROWS cells of
+// one column (FP64), or two adjacent columns of ROWS / 2 rows so that each 16-byte shared load and
+// global store carries two cells (FP32).  Nothing of
 // the plane sits in registers while it is in flight, so the occupancy is not bounded by the
 // prefetch depth.  Every wait is bounded: a wait that gives up raises a CTA-wide abort flag, the
 // producer drains the copies it issued, and the CTA reports a timeout in its partial.
@@ -20,14 +22,18 @@
 #include <cuda.h>
 
 #ifndef PF_LEAN_MIN_CTAS
-#define PF_LEAN_MIN_CTAS 6  // resident lean CTAs per SM the register allocation must allow
+#define PF_LEAN_MIN_CTAS 7  // resident FP32 lean CTAs per SM the register allocation must allow (FP64: 3,
+                            // as many as its shared memory admits)
 #endif
 #ifndef PF_LEAN_SUSPEND_NS
 #define PF_LEAN_SUSPEND_NS 1000u  // longest suspension of a waiting thread per try (the wait's bound is separate)
 #endif
 
+#ifndef PF_LEAN_PAIRS
+#define PF_LEAN_PAIRS 1  // FP32 consumers take two adjacent columns a thread (16-byte loads and stores)
+#endif
 #ifndef PF_LEAN_UNROLL
-#define PF_LEAN_UNROLL 2  // planes of the consumers' z-march per unrolled loop body
+#define PF_LEAN_UNROLL 1  // planes of the consumers' z-march per unrolled loop body
 #endif
 
 namespace pf {
@@ -164,6 +170,8 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
     static_assert(TY % ROWS == 0, "whole rows per consumer warp");
     constexpr int NCW = TY / ROWS, NC = 32 * NCW, NTH = NC + 32;
     constexpr int CB = (int)sizeof(Mu<R>);
+    constexpr bool PAIR = PF_LEAN_PAIRS != 0 && sizeof(R) == 4;
+    constexpr int UNR = sizeof(R) == 4 ? kLeanUnroll : 1;  // FP64 values take twice the registers
     static_assert(TX == 32 && TY % 2 == 0 && TY <= 32 && (LD & (LD - 1)) == 0, "layout");
     constexpr int LDLOG = LD == 2 ? 1 : (LD == 4 ? 2 : (LD == 8 ? 3 : 4));
     static_assert((1 << LDLOG) == LD, "LD: 2, 4, 8 or 16");
@@ -270,26 +278,10 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
         return;
     }
 
-    // ---------------- consumer warps: lane = tile column, warp w = tile rows w*ROWS .. w*ROWS+ROWS-1 ----------------
+    // ---------------- consumer warps ----------------
     const int lane = tid & 31, w = tid >> 5;
-    const int i = i0 + lane, jr0 = j0 + w * ROWS;
-    // byte offsets within a stage: own cells (row r at own0 + r * BW cells), their x neighbours,
-    // the cell below row 0 and the cell above each row; a neighbour across the domain edge is its
-    // periodic image in the stage's wrapped-cell rows
-    const int own0 = ((w * ROWS + 1) * L::BW + lane + 2) * CB;
+    // byte offsets of the periodic images of the stage (x = -1, x = nx, y = -1, y = ny)
     const int fixx0 = L::BOX_BYTES, fixx1 = fixx0 + 32 * CB, fixy0 = fixx1 + 32 * CB, fixy1 = fixy0 + 32 * CB;
-    int oxm[ROWS], oxp[ROWS], oyu[ROWS];
-    bool vr[ROWS];
-#pragma unroll
-    for (int r = 0; r < ROWS; r++) {
-        const int own = own0 + r * L::BW * CB, tyr = w * ROWS + r, j = jr0 + r;
-        vr[r] = i < nx && j < ny;
-        oxm[r] = i == 0 ? fixx0 + tyr * CB : own - CB;
-        oxp[r] = i == nx - 1 ? fixx1 + tyr * CB : own + CB;
-        oyu[r] = j == ny - 1 ? fixy1 + lane * CB : own + L::BW * CB;
-    }
-    const int oyb = jr0 == 0 ? fixy0 + lane * CB : own0 - L::BW * CB;
-    const size_t col0 = (size_t)jr0 * nx + (size_t)min(i, nx - 1);
     // The liquid update with constant mobility M = D_l/(2 A_l), h = e_l and no phase change (the
     // short form of Eq. 3 for a cell whose neighbourhood is pure liquid): the six face fluxes
     // M (mu_nb - mu)/dx reduce to the 7-point sum, so
@@ -310,95 +302,232 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
     R acc = R(0);  // sum of the updated values: non-finite iff one of them is
     int phi_stores = 0, planes = 0;
     unsigned u = 0;  // stage uses consumed
-    for (int g = 0; g < 2 && ok; g++) {
-        if (qb[g] <= qa[g]) continue;
-        const int la = max(qa[g] - 1, 0), lb = min(qb[g], nz - 1);
-        // use v holds plane la + (v - u): stage v mod LD, phase parity (v / LD) mod 2
-        auto stg = [&](unsigned v) { return (const unsigned char *)stage_base + (v & (LD - 1)) * L::STAGE_BYTES; };
-        auto wait_use = [&](unsigned v) {
-            return __all_sync(0xffffffffu, mbar_wait(&full[v & (LD - 1)], (v >> LDLOG) & 1, &s_abort));
-        };
-        auto release = [&](unsigned v) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[v & (LD - 1)]);
-        };
-        unsigned v = u;  // use of the plane being updated
-        Mu<R> m[ROWS], mlo[ROWS];  // mu^n of the cells and of the cells below them
-        ok = wait_use(v);
-        if (ok && qa[g] > 0) {  // plane qa - 1: only the cells below qa
+    if constexpr (PAIR) {
+        // Two adjacent columns per thread: 16-byte shared loads and global stores carry both cells'
+        // mu.  Lane l holds tile columns 2 (l & 15) and 2 (l & 15) + 1 of the tile rows
+        // w ROWS + (l >> 4) PR + k, k < PR; every sum is formed in the order of the one-column form.
+        constexpr int PR = ROWS / 2;
+        static_assert(ROWS % 2 == 0, "row pairs");
+        const int c2 = lane & 15, rs = lane >> 4;
+        const int ca = 2 * c2, ia = i0 + ca, ib = ia + 1;
+        const int trow0 = w * ROWS + rs * PR, jr = j0 + trow0;
+        const int own0 = ((trow0 + 1) * L::BW + ca + 2) * CB;
+        int oxm[PR], oxp[PR], oyw[PR];
+        bool vr[PR], top[PR];
 #pragma unroll
-            for (int r = 0; r < ROWS; r++) mlo[r] = lds_cell<R>(stg(v) + own0 + r * L::BW * CB);
-            release(v);
-            v++;
+        for (int k = 0; k < PR; k++) {
+            const int own = own0 + k * L::BW * CB, tyr = trow0 + k, j = jr + k;
+            vr[k] = ia < nx && j < ny;  // nx is even on this path: ia < nx implies ib < nx
+            oxm[k] = ia == 0 ? fixx0 + tyr * CB : own - CB;
+            oxp[k] = ib == nx - 1 ? fixx1 + tyr * CB : own + 2 * CB;
+            top[k] = j == ny - 1;
+            oyw[k] = top[k] ? fixy1 + ca * CB : own + L::BW * CB;  // the pair above row k
+        }
+        const int oyb = jr == 0 ? fixy0 + ca * CB : own0 - L::BW * CB;  // the pair below row 0
+        const size_t col0 = (size_t)jr * nx + (size_t)min(ia, nx - 2);
+        auto lds_pair = [](const unsigned char *p) { return *reinterpret_cast<const float4 *>(p); };
+        auto lds_one = [](const unsigned char *p) { return *reinterpret_cast<const float2 *>(p); };
+        for (int g = 0; g < 2 && ok; g++) {
+            if (qb[g] <= qa[g]) continue;
+            const int la = max(qa[g] - 1, 0), lb = min(qb[g], nz - 1);
+            auto stg = [&](unsigned v) { return (const unsigned char *)stage_base + (v & (LD - 1)) * L::STAGE_BYTES; };
+            auto wait_use = [&](unsigned v) {
+                return __all_sync(0xffffffffu, mbar_wait(&full[v & (LD - 1)], (v >> LDLOG) & 1, &s_abort));
+            };
+            auto release = [&](unsigned v) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[v & (LD - 1)]);
+            };
+            unsigned v = u;
+            float4 m[PR], mlo[PR];
             ok = wait_use(v);
-        }
-        if (ok) {
+            if (ok && qa[g] > 0) {  // plane qa - 1: only the cells below qa
 #pragma unroll
-            for (int r = 0; r < ROWS; r++) {
-                m[r] = lds_cell<R>(stg(v) + own0 + r * L::BW * CB);
-                if (qa[g] == 0) mlo[r] = m[r];  // mirror below plane 0
+                for (int k = 0; k < PR; k++) mlo[k] = lds_pair(stg(v) + own0 + k * L::BW * CB);
+                release(v);
+                v++;
+                ok = wait_use(v);
             }
-        }
-#pragma unroll kLeanUnroll
-        for (int q = qa[g]; q < qb[g] && ok; q++, v++) {
-            const unsigned char *S = stg(v);
-            Mu<R> mn[ROWS];
+            if (ok) {
 #pragma unroll
-            for (int r = 0; r < ROWS; r++) mn[r] = m[r];  // mirror above plane nz-1
-            if (q < nz - 1) {
-                ok = wait_use(v + 1);
-                if (!ok) break;
-                const unsigned char *N = stg(v + 1);
-#pragma unroll
-                for (int r = 0; r < ROWS; r++) mn[r] = lds_cell<R>(N + own0 + r * L::BW * CB);
-            }
-            Mu<R> xm[ROWS], xp[ROWS];
-#pragma unroll
-            for (int r = 0; r < ROWS; r++) {
-                xm[r] = lds_cell<R>(S + oxm[r]);
-                xp[r] = lds_cell<R>(S + oxp[r]);
-            }
-            // y neighbours: the rows of this thread, the cell below row 0 and above row ROWS-1 (or
-            // their periodic images); a last domain row's upper neighbour is its periodic image
-            Mu<R> yd[ROWS + 1];
-            yd[0] = lds_cell<R>(S + oyb);
-#pragma unroll
-            for (int r = 1; r < ROWS; r++) yd[r] = m[r];
-            yd[ROWS] = lds_cell<R>(S + oyu[ROWS - 1]);
-            Mu<R> wrap_up[ROWS];
-#pragma unroll
-            for (int r = 0; r < ROWS - 1; r++)
-                if (jr0 + r == ny - 1) wrap_up[r] = lds_cell<R>(S + oyu[r]);
-            release(v);
-            Mu<R> out[ROWS];
-#pragma unroll
-            for (int r = 0; r < ROWS; r++) {
-                const Mu<R> ylo = r == 0 ? yd[0] : m[r - 1];
-                const Mu<R> yhi = (r < ROWS - 1 && jr0 + r == ny - 1) ? wrap_up[r] : yd[r + 1];
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    const R sum = ((xm[r].v[c] + xp[r].v[c]) + (ylo.v[c] + yhi.v[c])) + (mlo[r].v[c] + mn[r].v[c]);
-                    const R lap = sum - R(6) * m[r].v[c];
-                    out[r].v[c] = C1 * lap + (m[r].v[c] + C0[c]);
+                for (int k = 0; k < PR; k++) {
+                    m[k] = lds_pair(stg(v) + own0 + k * L::BW * CB);
+                    if (qa[g] == 0) mlo[k] = m[k];  // mirror below plane 0
                 }
             }
-            const bool store_phi = s_dst_liquid[q - s0] != 1;
-            phi_stores += store_phi ? 1 : 0;
-            planes++;
-            const size_t o = (size_t)splane(q) * plane + col0;
+#pragma unroll UNR
+            for (int q = qa[g]; q < qb[g] && ok; q++, v++) {
+                const unsigned char *S = stg(v);
+                float4 mn[PR];
 #pragma unroll
-            for (int r = 0; r < ROWS; r++) {
-                if (vr[r]) {
-                    if (store_phi) st_ph(phi_out + o + (size_t)r * nx, liquid);
-                    st_mu(mu_out + o + (size_t)r * nx, out[r]);
-                    acc += out[r].v[0] + out[r].v[1];
+                for (int k = 0; k < PR; k++) mn[k] = m[k];  // mirror above plane nz-1
+                if (q < nz - 1) {
+                    ok = wait_use(v + 1);
+                    if (!ok) break;
+                    const unsigned char *N = stg(v + 1);
+#pragma unroll
+                    for (int k = 0; k < PR; k++) mn[k] = lds_pair(N + own0 + k * L::BW * CB);
                 }
-                mlo[r] = m[r];
-                m[r] = mn[r];
+                float2 xm[PR], xp[PR];
+                float4 yhi[PR];
+#pragma unroll
+                for (int k = 0; k < PR; k++) {
+                    xm[k] = lds_one(S + oxm[k]);
+                    xp[k] = lds_one(S + oxp[k]);
+                }
+                const float4 ylo0 = lds_pair(S + oyb);
+#pragma unroll
+                for (int k = 0; k < PR; k++) {
+                    if (k == PR - 1)
+                        yhi[k] = lds_pair(S + oyw[k]);
+                    else
+                        yhi[k] = top[k] ? lds_pair(S + oyw[k]) : m[k + 1];
+                }
+                release(v);
+                float4 out[PR];
+#pragma unroll
+                for (int k = 0; k < PR; k++) {
+                    const float4 c = m[k], yl = k == 0 ? ylo0 : m[k - 1], yh = yhi[k], lo = mlo[k], hi = mn[k];
+                    // cell a: x neighbours xm and cell b; cell b: cell a and xp
+                    const float sa0 = ((xm[k].x + c.z) + (yl.x + yh.x)) + (lo.x + hi.x);
+                    const float sa1 = ((xm[k].y + c.w) + (yl.y + yh.y)) + (lo.y + hi.y);
+                    const float sb0 = ((c.x + xp[k].x) + (yl.z + yh.z)) + (lo.z + hi.z);
+                    const float sb1 = ((c.y + xp[k].y) + (yl.w + yh.w)) + (lo.w + hi.w);
+                    out[k].x = C1 * (sa0 - 6.f * c.x) + (c.x + C0[0]);
+                    out[k].y = C1 * (sa1 - 6.f * c.y) + (c.y + C0[1]);
+                    out[k].z = C1 * (sb0 - 6.f * c.z) + (c.z + C0[0]);
+                    out[k].w = C1 * (sb1 - 6.f * c.w) + (c.w + C0[1]);
+                }
+                const bool store_phi = s_dst_liquid[q - s0] != 1;
+                phi_stores += store_phi ? 1 : 0;
+                planes++;
+                const size_t o = (size_t)splane(q) * plane + col0;
+#pragma unroll
+                for (int k = 0; k < PR; k++) {
+                    if (vr[k]) {
+                        if (store_phi) {
+                            st_ph(phi_out + o + (size_t)k * nx, liquid);
+                            st_ph(phi_out + o + (size_t)k * nx + 1, liquid);
+                        }
+                        *reinterpret_cast<float4 *>(mu_out + o + (size_t)k * nx) = out[k];
+                        acc += (out[k].x + out[k].y) + (out[k].z + out[k].w);
+                    }
+                    mlo[k] = m[k];
+                    m[k] = mn[k];
+                }
             }
+            if (ok && lb == qb[g]) release(v);  // plane qb: waited for the z neighbours of plane qb-1 only
+            u += (unsigned)(lb - la + 1);
         }
-        if (ok && lb == qb[g]) release(v);  // plane qb: waited for the z neighbours of plane qb-1 only
-        u += (unsigned)(lb - la + 1);
+    } else {
+        // one column per thread: lane = tile column, warp w = tile rows w*ROWS .. w*ROWS+ROWS-1
+        const int i = i0 + lane, jr0 = j0 + w * ROWS;
+        // byte offsets within a stage: own cells (row r at own0 + r * BW cells), their x neighbours,
+        // the cell below row 0 and the cell above each row; a neighbour across the domain edge is its
+        // periodic image in the stage's wrapped-cell rows
+        const int own0 = ((w * ROWS + 1) * L::BW + lane + 2) * CB;
+        int oxm[ROWS], oxp[ROWS], oyu[ROWS];
+        bool vr[ROWS];
+    #pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            const int own = own0 + r * L::BW * CB, tyr = w * ROWS + r, j = jr0 + r;
+            vr[r] = i < nx && j < ny;
+            oxm[r] = i == 0 ? fixx0 + tyr * CB : own - CB;
+            oxp[r] = i == nx - 1 ? fixx1 + tyr * CB : own + CB;
+            oyu[r] = j == ny - 1 ? fixy1 + lane * CB : own + L::BW * CB;
+        }
+        const int oyb = jr0 == 0 ? fixy0 + lane * CB : own0 - L::BW * CB;
+        const size_t col0 = (size_t)jr0 * nx + (size_t)min(i, nx - 1);
+        for (int g = 0; g < 2 && ok; g++) {
+            if (qb[g] <= qa[g]) continue;
+            const int la = max(qa[g] - 1, 0), lb = min(qb[g], nz - 1);
+            // use v holds plane la + (v - u): stage v mod LD, phase parity (v / LD) mod 2
+            auto stg = [&](unsigned v) { return (const unsigned char *)stage_base + (v & (LD - 1)) * L::STAGE_BYTES; };
+            auto wait_use = [&](unsigned v) {
+                return __all_sync(0xffffffffu, mbar_wait(&full[v & (LD - 1)], (v >> LDLOG) & 1, &s_abort));
+            };
+            auto release = [&](unsigned v) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[v & (LD - 1)]);
+            };
+            unsigned v = u;  // use of the plane being updated
+            Mu<R> m[ROWS], mlo[ROWS];  // mu^n of the cells and of the cells below them
+            ok = wait_use(v);
+            if (ok && qa[g] > 0) {  // plane qa - 1: only the cells below qa
+    #pragma unroll
+                for (int r = 0; r < ROWS; r++) mlo[r] = lds_cell<R>(stg(v) + own0 + r * L::BW * CB);
+                release(v);
+                v++;
+                ok = wait_use(v);
+            }
+            if (ok) {
+    #pragma unroll
+                for (int r = 0; r < ROWS; r++) {
+                    m[r] = lds_cell<R>(stg(v) + own0 + r * L::BW * CB);
+                    if (qa[g] == 0) mlo[r] = m[r];  // mirror below plane 0
+                }
+            }
+    #pragma unroll UNR
+            for (int q = qa[g]; q < qb[g] && ok; q++, v++) {
+                const unsigned char *S = stg(v);
+                Mu<R> mn[ROWS];
+    #pragma unroll
+                for (int r = 0; r < ROWS; r++) mn[r] = m[r];  // mirror above plane nz-1
+                if (q < nz - 1) {
+                    ok = wait_use(v + 1);
+                    if (!ok) break;
+                    const unsigned char *N = stg(v + 1);
+    #pragma unroll
+                    for (int r = 0; r < ROWS; r++) mn[r] = lds_cell<R>(N + own0 + r * L::BW * CB);
+                }
+                Mu<R> xm[ROWS], xp[ROWS];
+    #pragma unroll
+                for (int r = 0; r < ROWS; r++) {
+                    xm[r] = lds_cell<R>(S + oxm[r]);
+                    xp[r] = lds_cell<R>(S + oxp[r]);
+                }
+                // y neighbours: the rows of this thread, the cell below row 0 and above row ROWS-1 (or
+                // their periodic images); a last domain row's upper neighbour is its periodic image
+                Mu<R> yd[ROWS + 1];
+                yd[0] = lds_cell<R>(S + oyb);
+    #pragma unroll
+                for (int r = 1; r < ROWS; r++) yd[r] = m[r];
+                yd[ROWS] = lds_cell<R>(S + oyu[ROWS - 1]);
+                Mu<R> wrap_up[ROWS];
+    #pragma unroll
+                for (int r = 0; r < ROWS - 1; r++)
+                    if (jr0 + r == ny - 1) wrap_up[r] = lds_cell<R>(S + oyu[r]);
+                release(v);
+                Mu<R> out[ROWS];
+    #pragma unroll
+                for (int r = 0; r < ROWS; r++) {
+                    const Mu<R> ylo = r == 0 ? yd[0] : m[r - 1];
+                    const Mu<R> yhi = (r < ROWS - 1 && jr0 + r == ny - 1) ? wrap_up[r] : yd[r + 1];
+    #pragma unroll
+                    for (int c = 0; c < 2; c++) {
+                        const R sum = ((xm[r].v[c] + xp[r].v[c]) + (ylo.v[c] + yhi.v[c])) + (mlo[r].v[c] + mn[r].v[c]);
+                        const R lap = sum - R(6) * m[r].v[c];
+                        out[r].v[c] = C1 * lap + (m[r].v[c] + C0[c]);
+                    }
+                }
+                const bool store_phi = s_dst_liquid[q - s0] != 1;
+                phi_stores += store_phi ? 1 : 0;
+                planes++;
+                const size_t o = (size_t)splane(q) * plane + col0;
+    #pragma unroll
+                for (int r = 0; r < ROWS; r++) {
+                    if (vr[r]) {
+                        if (store_phi) st_ph(phi_out + o + (size_t)r * nx, liquid);
+                        st_mu(mu_out + o + (size_t)r * nx, out[r]);
+                        acc += out[r].v[0] + out[r].v[1];
+                    }
+                    mlo[r] = m[r];
+                    m[r] = mn[r];
+                }
+            }
+            if (ok && lb == qb[g]) release(v);  // plane qb: waited for the z neighbours of plane qb-1 only
+            u += (unsigned)(lb - la + 1);
+        }
     }
     const bool bad = !isfinite(acc);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&s_bad, 1);
@@ -421,7 +550,7 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
 
 // The lean planes of one domain: grid (tgx, tgy, gz * nsub).
 template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS>
-__global__ void __launch_bounds__(TX *TY / ROWS + 32, PF_LEAN_MIN_CTAS) lean_step_kernel(
+__global__ void __launch_bounds__(TX *TY / ROWS + 32, sizeof(R) == 4 ? PF_LEAN_MIN_CTAS : 3) lean_step_kernel(
     const KParams<R> kp, const __grid_constant__ CUtensorMap mu_map, const Mu<R> *__restrict__ mu,
     Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st,
     LeanStats *__restrict__ stats, unsigned char *__restrict__ tmap_out, const int2 *__restrict__ splits, int nsub)
@@ -433,7 +562,7 @@ __global__ void __launch_bounds__(TX *TY / ROWS + 32, PF_LEAN_MIN_CTAS) lean_ste
 // One lean work item of a batched step: CTA blockIdx.x takes (domain, tile x, tile y, chunk * nsub +
 // sub) from the table; the domain's tensor maps live in device memory (64-byte aligned).
 template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS>
-__global__ void __launch_bounds__(TX *TY / ROWS + 32, PF_LEAN_MIN_CTAS) batched_lean_kernel(
+__global__ void __launch_bounds__(TX *TY / ROWS + 32, sizeof(R) == 4 ? PF_LEAN_MIN_CTAS : 3) batched_lean_kernel(
     const BatchDomain<R> *__restrict__ doms, const int4 *__restrict__ items, int parity)
 {
     const int4 w = items[blockIdx.x];
