@@ -143,6 +143,13 @@ int pf_read_fields(pf_sim *sim, double *phi, double *mu, size_t cap_cells);
  * window offset are left unchanged.  Synchronising. */
 int pf_write_fields(pf_sim *sim, const double *phi, const double *mu);
 
+/* As pf_read_fields / pf_write_fields with FP32 host buffers (same SoA layout, half the bytes to
+ * move): exact for an FP32 simulation; an FP64 or compensated state is rounded once to FP32 on
+ * read (the compensated pair's value), and written values are exact in every precision (the
+ * compensated low words become 0).  Errors as the FP64 forms.  Synchronising. */
+int pf_read_fields_f32(pf_sim *sim, float *phi, float *mu, size_t cap_cells);
+int pf_write_fields_f32(pf_sim *sim, const float *phi, const float *mu);
+
 /* Checkpoint (the paper's infrequent field checkpoints, Section 3.2): write the current fields,
  * simulation time and window offset to the file at path.  Layout: a 64-byte header (magic
  * "PFCKPT01"; int32 version 1, nx, ny, nz, bytes per value, writer precision, planes shifted since

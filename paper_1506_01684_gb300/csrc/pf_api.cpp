@@ -681,16 +681,18 @@ static int do_init(pf_sim *s, uint64_t seed, int ng)
 
 static const size_t kChunkCells = (size_t)1 << 22;  // staging chunk for host transfers
 
-template <typename R>
-static int do_read(pf_sim *s, double *phi, double *mu)
+// host SoA fields of element type H (double or float) <-> the device state, through a staging buffer
+// of a chunk of planes
+template <typename R, typename H>
+static int do_read(pf_sim *s, H *phi, H *mu)
 {
     const KParams<R> kp = make_kparams<R>(s);
     const size_t plane = (size_t)s->nx * s->ny, n = s->ncell();
     int pk = (int)std::max<size_t>(1, std::min<size_t>(s->nz, kChunkCells / plane));
     DevBuf stg;
-    int r = dev_alloc(stg, (size_t)pk * plane * 6 * sizeof(double), s->stream);
+    int r = dev_alloc(stg, (size_t)pk * plane * 6 * sizeof(H), s->stream);
     if (r != PF_OK) return r;
-    double *dphi = (double *)stg.p, *dmu = dphi + (size_t)pk * plane * 4;
+    H *dphi = (H *)stg.p, *dmu = dphi + (size_t)pk * plane * 4;
     cudaError_t e = cudaSuccess;
     for (int k0 = 0; k0 < s->nz && e == cudaSuccess; k0 += pk) {
         const int nk = std::min(pk, s->nz - k0);
@@ -698,10 +700,10 @@ static int do_read(pf_sim *s, double *phi, double *mu)
         e = launch_pack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, phi ? dphi : nullptr,
                            mu ? dmu : nullptr, k0, nk, s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
         for (int c = 0; c < 4 && phi && e == cudaSuccess; c++)
-            e = cudaMemcpyAsync(phi + (size_t)c * n + (size_t)k0 * plane, dphi + (size_t)c * m, m * sizeof(double),
+            e = cudaMemcpyAsync(phi + (size_t)c * n + (size_t)k0 * plane, dphi + (size_t)c * m, m * sizeof(H),
                                 cudaMemcpyDeviceToHost, s->stream);
         for (int c = 0; c < 2 && mu && e == cudaSuccess; c++)
-            e = cudaMemcpyAsync(mu + (size_t)c * n + (size_t)k0 * plane, dmu + (size_t)c * m, m * sizeof(double),
+            e = cudaMemcpyAsync(mu + (size_t)c * n + (size_t)k0 * plane, dmu + (size_t)c * m, m * sizeof(H),
                                 cudaMemcpyDeviceToHost, s->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -709,26 +711,26 @@ static int do_read(pf_sim *s, double *phi, double *mu)
     return e == cudaSuccess ? PF_OK : latch(s, cuda_status(e));
 }
 
-template <typename R>
-static int do_write(pf_sim *s, const double *phi, const double *mu)
+template <typename R, typename H>
+static int do_write(pf_sim *s, const H *phi, const H *mu)
 {
     const KParams<R> kp = make_kparams<R>(s);
     const size_t plane = (size_t)s->nx * s->ny, n = s->ncell();
     int pk = (int)std::max<size_t>(1, std::min<size_t>(s->nz, kChunkCells / plane));
     DevBuf stg;
-    int r = dev_alloc(stg, (size_t)pk * plane * 6 * sizeof(double), s->stream);
+    int r = dev_alloc(stg, (size_t)pk * plane * 6 * sizeof(H), s->stream);
     if (r != PF_OK) return r;
-    double *dphi = (double *)stg.p, *dmu = dphi + (size_t)pk * plane * 4;
+    H *dphi = (H *)stg.p, *dmu = dphi + (size_t)pk * plane * 4;
     cudaError_t e = cudaSuccess;
     s->tmap_ok[0] = s->tmap_ok[1] = false;
     for (int k0 = 0; k0 < s->nz && e == cudaSuccess; k0 += pk) {
         const int nk = std::min(pk, s->nz - k0);
         const size_t m = (size_t)nk * plane;
         for (int c = 0; c < 4 && e == cudaSuccess; c++)
-            e = cudaMemcpyAsync(dphi + (size_t)c * m, phi + (size_t)c * n + (size_t)k0 * plane, m * sizeof(double),
+            e = cudaMemcpyAsync(dphi + (size_t)c * m, phi + (size_t)c * n + (size_t)k0 * plane, m * sizeof(H),
                                 cudaMemcpyHostToDevice, s->stream);
         for (int c = 0; c < 2 && e == cudaSuccess; c++)
-            e = cudaMemcpyAsync(dmu + (size_t)c * m, mu + (size_t)c * n + (size_t)k0 * plane, m * sizeof(double),
+            e = cudaMemcpyAsync(dmu + (size_t)c * m, mu + (size_t)c * n + (size_t)k0 * plane, m * sizeof(H),
                                 cudaMemcpyHostToDevice, s->stream);
         if (e == cudaSuccess)
             e = launch_unpack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, dphi, dmu, k0,
@@ -1246,6 +1248,19 @@ int pf_read_fields(pf_sim *s, double *phi, double *mu, size_t cap_cells)
 }
 
 int pf_write_fields(pf_sim *s, const double *phi, const double *mu)
+{
+    if (!s || !phi || !mu) return PF_E_INVAL;
+    return PF_DISPATCH(s, do_write, s, phi, mu);
+}
+
+int pf_read_fields_f32(pf_sim *s, float *phi, float *mu, size_t cap_cells)
+{
+    if (!s || cap_cells < s->ncell()) return PF_E_INVAL;
+    if (!phi && !mu) return PF_OK;
+    return PF_DISPATCH(s, do_read, s, phi, mu);
+}
+
+int pf_write_fields_f32(pf_sim *s, const float *phi, const float *mu)
 {
     if (!s || !phi || !mu) return PF_E_INVAL;
     return PF_DISPATCH(s, do_write, s, phi, mu);
@@ -1892,7 +1907,7 @@ static int read_phi_plane(pf_sim *s, int k, std::vector<float> &out)
     if (r != PF_OK) return r;
     const KParams<float> kp = make_kparams<float>(s);
     cudaError_t e = launch_pack<float>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p,
-                                       (double *)stg.p, nullptr, k, 1, s->stream);
+                                       (double *)stg.p, (double *)nullptr, k, 1, s->stream);
     std::vector<double> h(plane * 4);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h.data(), stg.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);

@@ -217,13 +217,14 @@ template <typename R>
 cudaError_t launch_reduce(const KParams<R> &kp, const DevState *st, const void *phi, const void *mu,
                           double *plane_sums /* nz x 8 */, cudaStream_t s, const void *phi_lo = nullptr,
                           const void *mu_lo = nullptr);
-template <typename R>
-cudaError_t launch_pack(const KParams<R> &kp, const DevState *st, const void *phi, const void *mu, double *phi_soa,
-                        double *mu_soa, int k0, int nk, cudaStream_t s, const void *phi_lo = nullptr,
+// AoS fields <-> SoA staging of host element type H (double or float) for logical planes [k0, k0 + nk)
+template <typename R, typename H>
+cudaError_t launch_pack(const KParams<R> &kp, const DevState *st, const void *phi, const void *mu, H *phi_soa,
+                        H *mu_soa, int k0, int nk, cudaStream_t s, const void *phi_lo = nullptr,
                         const void *mu_lo = nullptr);
-template <typename R>
-cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, void *mu, const double *phi_soa,
-                          const double *mu_soa, int k0, int nk, cudaStream_t s, void *phi_lo = nullptr,
+template <typename R, typename H>
+cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, void *mu, const H *phi_soa,
+                          const H *mu_soa, int k0, int nk, cudaStream_t s, void *phi_lo = nullptr,
                           void *mu_lo = nullptr);
 // Interface mesh of phase `phase` (marching tetrahedra over the cell centres), in segments of up to
 // 256 cubes of one row of one layer, ordered (k ny + j) nb + b with nb = ceil(nx / 256): triangles

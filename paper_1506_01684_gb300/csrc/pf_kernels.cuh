@@ -2505,13 +2505,14 @@ __global__ void __launch_bounds__(256) reduce_kernel(const KParams<R> kp, const 
     if (threadIdx.x < 8) out[(size_t)k * 8 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// AoS device fields (ring-buffered) <-> FP64 SoA staging for logical planes [k0, k0 + nk).
-template <typename R>
+// AoS device fields (ring-buffered) <-> SoA staging of the host element type H (double or float) for
+// logical planes [k0, k0 + nk).  A compensated state packs the value of its pair (high + low, then
+// rounded once to H) and unpacks into a canonical pair.
+template <typename R, typename H>
 __global__ void __launch_bounds__(256) pack_kernel(const KParams<R> kp, const DevState *__restrict__ st,
                                                   const Ph<R> *__restrict__ phi, const Mu<R> *__restrict__ mu,
-                                                  double *__restrict__ phi_soa, double *__restrict__ mu_soa,
-                                                  int k0, int nk, const Ph<R> *__restrict__ phi_lo,
-                                                  const Mu<R> *__restrict__ mu_lo)
+                                                  H *__restrict__ phi_soa, H *__restrict__ mu_soa, int k0, int nk,
+                                                  const Ph<R> *__restrict__ phi_lo, const Mu<R> *__restrict__ mu_lo)
 {
     const size_t plane = (size_t)kp.nx * kp.ny, n = plane * nk;
     const int zbase = st->zbase;
@@ -2521,31 +2522,34 @@ __global__ void __launch_bounds__(256) pack_kernel(const KParams<R> kp, const De
         const size_t g = plane_off(k0 + kk, kp.nz, zbase, plane) + c;
         if (phi_soa) {
             const Ph<R> p = ldg_ph(phi + g);
-            for (int a = 0; a < 4; a++) phi_soa[(size_t)a * n + q] = (double)p.v[a];
+            double v[4];
+            for (int a = 0; a < 4; a++) v[a] = (double)p.v[a];
             if (phi_lo) {
                 const Ph<R> l = ldg_ph(phi_lo + g);
-                for (int a = 0; a < 4; a++) phi_soa[(size_t)a * n + q] += (double)l.v[a];
+                for (int a = 0; a < 4; a++) v[a] += (double)l.v[a];
             }
+            for (int a = 0; a < 4; a++) phi_soa[(size_t)a * n + q] = (H)v[a];
         }
         if (mu_soa) {
             const Mu<R> m = ldg_mu(mu + g);
-            mu_soa[q] = (double)m.v[0];
-            mu_soa[n + q] = (double)m.v[1];
+            double v0 = (double)m.v[0], v1 = (double)m.v[1];
             if (mu_lo) {
                 const Mu<R> l = ldg_mu(mu_lo + g);
-                mu_soa[q] += (double)l.v[0];
-                mu_soa[n + q] += (double)l.v[1];
+                v0 += (double)l.v[0];
+                v1 += (double)l.v[1];
             }
+            mu_soa[q] = (H)v0;
+            mu_soa[n + q] = (H)v1;
         }
     }
 }
 
-template <typename R>
+template <typename R, typename H>
 __global__ void __launch_bounds__(256) unpack_kernel(const KParams<R> kp, const DevState *__restrict__ st,
                                                     Ph<R> *__restrict__ phi, Mu<R> *__restrict__ mu,
-                                                    const double *__restrict__ phi_soa,
-                                                    const double *__restrict__ mu_soa, int k0, int nk,
-                                                    Ph<R> *__restrict__ phi_lo, Mu<R> *__restrict__ mu_lo)
+                                                    const H *__restrict__ phi_soa, const H *__restrict__ mu_soa,
+                                                    int k0, int nk, Ph<R> *__restrict__ phi_lo,
+                                                    Mu<R> *__restrict__ mu_lo)
 {
     const size_t plane = (size_t)kp.nx * kp.ny, n = plane * nk;
     const int zbase = st->zbase;
@@ -2555,7 +2559,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(const KParams<R> kp, const 
         const size_t g = plane_off(k0 + kk, kp.nz, zbase, plane) + c;
         Ph<R> p, pl;
         for (int a = 0; a < 4; a++) {
-            const double x = phi_soa[(size_t)a * n + q];
+            const double x = (double)phi_soa[(size_t)a * n + q];
             p.v[a] = (R)x;
             pl.v[a] = (R)(x - (double)p.v[a]);
         }
@@ -2563,7 +2567,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(const KParams<R> kp, const 
         if (phi_lo) st_ph(phi_lo + g, pl);
         Mu<R> m, ml;
         for (int c = 0; c < 2; c++) {
-            const double x = mu_soa[(size_t)c * n + q];
+            const double x = (double)mu_soa[(size_t)c * n + q];
             m.v[c] = (R)x;
             ml.v[c] = (R)(x - (double)m.v[c]);
         }
@@ -3026,23 +3030,23 @@ cudaError_t launch_reduce(const KParams<R> &kp, const DevState *st, const void *
     return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_pack(const KParams<R> &kp, const DevState *st, const void *phi, const void *mu, double *phi_soa,
-                        double *mu_soa, int k0, int nk, cudaStream_t s, const void *phi_lo, const void *mu_lo)
+template <typename R, typename H>
+cudaError_t launch_pack(const KParams<R> &kp, const DevState *st, const void *phi, const void *mu, H *phi_soa,
+                        H *mu_soa, int k0, int nk, cudaStream_t s, const void *phi_lo, const void *mu_lo)
 {
     const size_t n = (size_t)kp.nx * kp.ny * nk;
-    pack_kernel<R><<<grid1d(n), 256, 0, s>>>(kp, st, (const Ph<R> *)phi, (const Mu<R> *)mu, phi_soa, mu_soa, k0, nk,
-                                             (const Ph<R> *)phi_lo, (const Mu<R> *)mu_lo);
+    pack_kernel<R, H><<<grid1d(n), 256, 0, s>>>(kp, st, (const Ph<R> *)phi, (const Mu<R> *)mu, phi_soa, mu_soa, k0,
+                                                nk, (const Ph<R> *)phi_lo, (const Mu<R> *)mu_lo);
     return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, void *mu, const double *phi_soa,
-                          const double *mu_soa, int k0, int nk, cudaStream_t s, void *phi_lo, void *mu_lo)
+template <typename R, typename H>
+cudaError_t launch_unpack(const KParams<R> &kp, const DevState *st, void *phi, void *mu, const H *phi_soa,
+                          const H *mu_soa, int k0, int nk, cudaStream_t s, void *phi_lo, void *mu_lo)
 {
     const size_t n = (size_t)kp.nx * kp.ny * nk;
-    unpack_kernel<R><<<grid1d(n), 256, 0, s>>>(kp, st, (Ph<R> *)phi, (Mu<R> *)mu, phi_soa, mu_soa, k0, nk,
-                                               (Ph<R> *)phi_lo, (Mu<R> *)mu_lo);
+    unpack_kernel<R, H><<<grid1d(n), 256, 0, s>>>(kp, st, (Ph<R> *)phi, (Mu<R> *)mu, phi_soa, mu_soa, k0, nk,
+                                                  (Ph<R> *)phi_lo, (Mu<R> *)mu_lo);
     return cudaGetLastError();
 }
 
@@ -3116,10 +3120,18 @@ cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const voi
                                         cudaStream_t);                                                           \
     template cudaError_t launch_reduce<R>(const KParams<R> &, const DevState *, const void *, const void *,      \
                                           double *, cudaStream_t, const void *, const void *);                   \
-    template cudaError_t launch_pack<R>(const KParams<R> &, const DevState *, const void *, const void *,        \
-                                        double *, double *, int, int, cudaStream_t, const void *, const void *); \
-    template cudaError_t launch_unpack<R>(const KParams<R> &, const DevState *, void *, void *, const double *,  \
-                                          const double *, int, int, cudaStream_t, void *, void *);              \
+    template cudaError_t launch_pack<R, double>(const KParams<R> &, const DevState *, const void *, const void *, \
+                                                double *, double *, int, int, cudaStream_t, const void *,        \
+                                                const void *);                                                   \
+    template cudaError_t launch_pack<R, float>(const KParams<R> &, const DevState *, const void *, const void *,  \
+                                               float *, float *, int, int, cudaStream_t, const void *,           \
+                                               const void *);                                                    \
+    template cudaError_t launch_unpack<R, double>(const KParams<R> &, const DevState *, void *, void *,           \
+                                                  const double *, const double *, int, int, cudaStream_t, void *, \
+                                                  void *);                                                       \
+    template cudaError_t launch_unpack<R, float>(const KParams<R> &, const DevState *, void *, void *,            \
+                                                 const float *, const float *, int, int, cudaStream_t, void *,    \
+                                                 void *);                                                        \
     template cudaError_t launch_mesh_count<R>(const KParams<R> &, const DevState *, const void *, int, double,    \
                                               unsigned *, cudaStream_t);                                         \
     template cudaError_t launch_mesh_scan<R>(const unsigned *, size_t, unsigned *, unsigned long long *,          \

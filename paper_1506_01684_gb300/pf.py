@@ -79,6 +79,8 @@ SIGNATURES = {
     "pf_sync": (_I, [_VP]),
     "pf_read_fields": (_I, [_VP, _DP, _DP, ctypes.c_size_t]),
     "pf_write_fields": (_I, [_VP, _DP, _DP]),
+    "pf_read_fields_f32": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+    "pf_write_fields_f32": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     "pf_phase_fractions": (_I, [_VP, _DP]),
     "pf_stats": (_I, [_VP, _DP, _DP, _DP, _DP]),
     "pf_window_shifts": (_I, [_VP, ctypes.POINTER(_I)]),
@@ -252,6 +254,24 @@ def pf_read_fields(sim, phi: np.ndarray | None, mu: np.ndarray | None):
 
 def pf_write_fields(sim, phi: np.ndarray, mu: np.ndarray):
     return _check(lib().pf_write_fields(sim, _dp(phi), _dp(mu)), "pf_write_fields")
+
+
+def _fp(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def pf_read_fields_f32(sim, phi: np.ndarray | None, mu: np.ndarray | None):
+    n = None
+    for a in (phi, mu):
+        if a is not None:
+            n = a.shape[-1] * a.shape[-2] * a.shape[-3]
+    return _check(lib().pf_read_fields_f32(sim, _fp(phi) if phi is not None else None,
+                                           _fp(mu) if mu is not None else None, n or 0), "pf_read_fields_f32")
+
+
+def pf_write_fields_f32(sim, phi: np.ndarray, mu: np.ndarray):
+    return _check(lib().pf_write_fields_f32(sim, _fp(phi), _fp(mu)), "pf_write_fields_f32")
 
 
 def pf_phase_fractions(sim) -> np.ndarray:
@@ -555,6 +575,17 @@ class Simulation:
     def set_fields(self, phi, mu):
         pf_write_fields(self.h, np.ascontiguousarray(phi, dtype=np.float64),
                         np.ascontiguousarray(mu, dtype=np.float64))
+        return self
+
+    def fields_f32(self):
+        phi = np.empty((4, self.nz, self.ny, self.nx), dtype=np.float32)
+        mu = np.empty((2, self.nz, self.ny, self.nx), dtype=np.float32)
+        pf_read_fields_f32(self.h, phi, mu)
+        return phi, mu
+
+    def set_fields_f32(self, phi, mu):
+        pf_write_fields_f32(self.h, np.ascontiguousarray(phi, dtype=np.float32),
+                            np.ascontiguousarray(mu, dtype=np.float32))
         return self
 
     def fractions(self):
