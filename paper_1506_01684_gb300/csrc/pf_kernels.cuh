@@ -14,6 +14,7 @@
 // staggered-value buffering of Section 3.3).
 #pragma once
 
+#include <atomic>
 #include <climits>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -2627,7 +2628,7 @@ template <typename R>
 cudaError_t launch_phi_sweep(const KParams<R> &kp, const Geometry &g, const void *phi, const void *mu,
                              void *phi_out, const DevState *st, const PlaneT<R> *tab, cudaStream_t s)
 {
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
     const size_t sm = phi_smem_bytes<R>();
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(phi_sweep_kernel<R, kTX, kTY>,
@@ -2646,7 +2647,7 @@ cudaError_t launch_mu_sweep(const KParams<R> &kp, const Geometry &g, const void 
                             const void *mu, void *mu_out, const DevState *st, const PlaneT<R> *tab,
                             Partial *parts, cudaStream_t s)
 {
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
     const size_t sm = mu_smem_bytes<R>();
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(mu_sweep_kernel<R, kTX, kTY>,
@@ -2686,7 +2687,7 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
                               cudaStream_t s, const unsigned char *tmap_in, unsigned char *tmap_out, bool lean_here)
 {
     if ((tmap_in || tmap_out) && (kp.tgx != g.gx || kp.tgy != g.gy)) return cudaErrorInvalidValue;
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
     const size_t sm = fused_smem_bytes<R>();
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<R, kTX, kTY>,
@@ -2731,7 +2732,7 @@ cudaError_t launch_general_step(const KParams<R> &kp, const void *phi, const voi
                                 const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits,
                                 const int *glist, LeanStats *stats, int ctas, cudaStream_t s)
 {
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
     const size_t sm = fused_smem_bytes<R>();
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(general_step_kernel<R, kTX, kTY>,
@@ -2751,7 +2752,7 @@ cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const v
                                   const int2 *splits, const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas,
                                   cudaStream_t s)
 {
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
     const size_t smp = phi_smem_bytes<R>(), smm = mu_smem_bytes<R>();
     if (!attr) {
         cudaError_t e = cudaSuccess;
@@ -2824,7 +2825,7 @@ cudaError_t launch_lean_step(const KParams<R> &kp, const Geometry &g, int nsub, 
         return cudaErrorInvalidValue;
     if ((kp.zchunk + nsub - 1) / nsub > kLeanMaxSub) return cudaErrorInvalidValue;  // planes per lean CTA
     if (sizeof(R) == 4 && (kp.nx & 1)) return cudaErrorInvalidValue;  // rows must be 16-byte multiples
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
     const size_t sm = L::smem_bytes(kLeanStages);
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(lean_step_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>,
@@ -2845,7 +2846,7 @@ cudaError_t launch_phi_sweep_comp(const KParams<float> &kp, const Geometry &g, c
                                   const void *mu, void *phi_out, void *phi_out_lo, const DevState *st,
                                   const PlaneT<float> *tab, cudaStream_t s)
 {
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
     const size_t sm = phi_smem_bytes<float>() + sizeof(Ph<float>) * 4 * kTX * kTY;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(phi_sweep_kernel<float, kTX, kTY, true>,
@@ -2865,7 +2866,7 @@ cudaError_t launch_mu_sweep_comp(const KParams<float> &kp, const Geometry &g, co
                                  void *mu_out_lo, const DevState *st, const PlaneT<float> *tab, Partial *parts,
                                  cudaStream_t s)
 {
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
     const size_t sm = mu_smem_bytes<float>();
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(mu_sweep_kernel<float, kTX, kTY, true>,
@@ -2885,7 +2886,7 @@ template <typename R>
 cudaError_t launch_batched_step(const BatchDomain<R> *doms, int ndoms, const BatchItem *items, int nitems,
                                 unsigned *counter, int parity, int ctas, int post_blocks, cudaStream_t s)
 {
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
     const size_t sm = fused_smem_bytes<R>();
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(batched_fused_kernel<R, kTX, kTY>,
@@ -2910,7 +2911,7 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
                                      bool sym)
 {
     using L = LeanLayout<R, kTX, kTY>;
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
     const size_t smp = phi_smem_bytes<R>(), smm = mu_smem_bytes<R>(), sml = L::smem_bytes(kLeanStages);
     const size_t smf = fused_smem_bytes<R>();
     if (!attr) {
