@@ -94,7 +94,7 @@ struct KParams {
 // partial sums, and its fused-step tile grid; for the lean path also the TMA tensor maps of its mu
 // buffers, its plan (splits per (tile, chunk)) and its lean statistics.
 template <typename R>
-struct alignas(64) BatchDomain {
+struct alignas(128) BatchDomain {  // the alignment of its tensor maps
     CUtensorMap mu_map[2];   // TMA maps of mu[0], mu[1] (lean path)
     KParams<R> kp;
     void *phi[2], *mu[2];
