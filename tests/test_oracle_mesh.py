@@ -103,6 +103,11 @@ def test_sphere_is_closed_outward_and_approaches_the_sphere():
     assert (counts == 2).all()  # closed, no cracks
     E = len(counts)
     assert len(verts) - E + len(idx) == 2  # a sphere's Euler characteristic
+    # consistently oriented: every directed edge once, its reverse in the neighbouring triangle
+    directed = np.concatenate([idx[:, [0, 1]], idx[:, [1, 2]], idx[:, [2, 0]]])
+    dset = {tuple(e) for e in directed}
+    assert len(dset) == len(directed)
+    assert all((b, a) in dset for a, b in dset)
     vol = M.mesh_volume(tris)
     assert vol > 0  # normals outward (towards lower phi)
     assert abs(vol / (4.0 / 3.0 * np.pi * R ** 3) - 1) < 0.02
