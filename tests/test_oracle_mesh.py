@@ -134,3 +134,23 @@ def test_cube_counts_and_single_cubes_agree_with_the_whole_mesh():
     # layers that are all inside or all outside give nothing; a single layer has no cubes
     assert M.cube_counts(np.ones((4, 3, 3)), 0.5).sum() == 0
     assert M.cube_counts(f[:1], 0.5).shape == (0, ny, nx) and len(M.interface_mesh(f[:1], 0.5)) == 0
+
+
+def test_vertical_cylinder_is_an_open_tube_ending_on_the_first_and_last_planes():
+    # no cubes across z: a phase column through the whole domain meshes to a tube whose boundary
+    # edges (each in one triangle only) lie on the first and last cell-centre planes, Euler
+    # characteristic 0, area approaching the cylinder's
+    n, nz, R, w, off = 30, 9, 7.0, 3.0, 11.0
+    c = n / 2.0
+    zz, yy, xx = np.meshgrid(np.arange(nz) + 0.5, np.arange(n) + 0.5, np.arange(n) + 0.5, indexing="ij")
+    r = np.sqrt((xx - c) ** 2 + (yy - c) ** 2)
+    f = np.clip(0.5 - (r - R) / w, 0.0, 1.0)
+    tris = M.interface_mesh(f, 0.5, off=off)
+    verts, idx = M.weld(tris)
+    edges = np.sort(np.concatenate([idx[:, [0, 1]], idx[:, [1, 2]], idx[:, [2, 0]]]), axis=1)
+    uniq, counts = np.unique(edges, axis=0, return_counts=True)
+    assert set(counts.tolist()) == {1, 2}
+    bz = verts[uniq[counts == 1]][:, :, 2]
+    assert np.all((np.abs(bz - (off + 0.5)) < 1e-9) | (np.abs(bz - (off + nz - 0.5)) < 1e-9))
+    assert len(verts) - len(uniq) + len(idx) == 0
+    assert abs(M.mesh_area(tris) / (2 * np.pi * R * (nz - 1)) - 1) < 0.05
