@@ -160,3 +160,28 @@ def test_isotropic_matrices_and_equal_pair_times_reduce_to_the_scalar_form():
     b.step(20)
     assert np.abs(a.phi - b.phi).max() <= 1e-13
     assert np.abs(a.mu - b.mu).max() <= 1e-13 * max(np.abs(a.mu).max(), 1e-8)
+
+
+def _relaxed_profile_error(p, eps=4.0, nz=48, steps=4000):
+    # a flat two-phase alpha / liquid front at TE, mu = 0: the stationary profile is the obstacle sine
+    # 1/2 (1 - sin(4 z / (pi eps))) whatever the curvatures and relaxation times (all grand potentials
+    # vanish at mu = 0, T = TE); returns the largest deviation from it and the state
+    p = dict(p, eps=eps, T0=p["TE"])
+    st = oracle.State(p, 1, 1, nz)
+    st.phi = W.planar_front(1, 1, nz, nz / 2 + 0.3, 0.6 * math.pi ** 2 * eps / 4)
+    st.mu = np.zeros((2, nz, 1, 1))
+    st.step(steps)
+    prof = st.phi[0, :, 0, 0]
+    k = np.where((prof[:-1] >= 0.5) & (prof[1:] < 0.5))[0][0]
+    zc = k + (prof[k] - 0.5) / (prof[k] - prof[k + 1])
+    s = 4 * (np.arange(nz) - zc) / (math.pi * eps)
+    ref = np.where(s <= -math.pi / 2, 1.0, np.where(s >= math.pi / 2, 0.0, 0.5 * (1 - np.sin(np.clip(s, -7, 7)))))
+    return np.abs(prof - ref).max(), st
+
+
+def test_general_thermodynamics_keep_the_two_phase_equilibrium_profile():
+    e_sym, _ = _relaxed_profile_error(W.symmetric_params(G=0.0))
+    for p in (W.general_params(G=0.0), dict(W.general_params(G=0.0), tau_ab=[2.0, 1.6, 2.0, 1.8, 0.8, 1.2])):
+        e, st = _relaxed_profile_error(p)
+        assert e < 1.1 * e_sym and e < 0.007, (e, e_sym)
+        assert (st.phi[1] == 0).all() and (st.phi[2] == 0).all()  # the front stays two-phase
