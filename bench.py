@@ -12,14 +12,19 @@ Printed: one JSON line with MLUP/s (value), the FP64 GPU path on the same worklo
 FP32-vs-FP64 error, the dominant kernel's roofline, an end-to-end figure through host
 buffers, the oracle's CPU baseline, clocks and launch counts.
 
-Two timed regions of K steps each follow the warm-up: A, the steps as pf_step runs them (replayed
+The timed steps start from the configuration's own state: 2000 untimed steps (--pre-steps) take the
+Voronoi start's sharp fronts to the diffuse, growing interface of the single-large-domain run, and
+the line reports that state (interface height, fraction of cells on general planes).  Two timed
+regions of K steps each follow the warm-up: A, the steps as pf_step runs them (replayed
 from the captured CUDA graph), gives `value` and `ms_per_step`; B, the next K steps with the
 library's per-kernel CUDA-event timers (every kernel launched directly between its two events),
 gives the per-kernel durations, their shares and the roofline of the dominant kernel, and its own
 `ms_per_step_kernel_timers`.  The roofline's algorithmic bytes are the kernels' own tally of the
-last step (pf_step_bytes): 16 B a cell on pure-liquid planes, 88 B on general planes.
+last step (pf_step_bytes): 16 B a cell on pure-liquid planes, 88 B on general planes.  The general
+planes' sweeps are bound by the FP32 units, so a second roofline (`roofline_general`) sets their
+FP32 operation rate against the FP32 peak derived from the SM count and the sampled clock.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--pre-steps P] [--impl gb300|reference]
 
 With N > 1 (torchrun, one process per GPU) every rank runs its own replica of the
 workload (the path has no exchange step on one domain per GPU: replicas only, weak
@@ -42,6 +47,7 @@ NX, NY, NZ = 256, 256, 1024
 GRAINS = 64
 TRIGGER = 512.0
 SEED = 0
+PRE_STEPS = 2000  # the single-large-domain configuration runs 2000 steps
 WORKLOAD = "single domain 256x256x1024, 64 grains, window trigger z=512, symmetric parameter set"
 METRIC = "phi+mu step MLUP/s (FP32 stencil; FP64 GPU path and error reported beside it)"
 
@@ -57,6 +63,40 @@ METRIC = "phi+mu step MLUP/s (FP32 stencil; FP64 GPU path and error reported bes
 # traffic of a full launch = this ratio x the launch's algorithmic bytes (traffic grows with the lean
 # cells).  Remove an entry when its kernel changes.
 TRAFFIC_RATIO = {"lean_step": 0.94}
+
+
+# The general planes' two sweeps (the interface cells) are bound by the FP32 units, not HBM: per general
+# cell, the FP32 operations (FADD, FMUL = 1, FFMA = 2) and the thread instructions of both sweeps, halo
+# and prologue work included, from the SASS counters of an ncu capture of the kernels as they are now
+# (summed over general_phi_kernel and general_mu_kernel, divided by the general cells the launch
+# processed).  None: not measured for the current kernels.  Remove the entries when the kernels change.
+GENERAL_FLOPS_PER_CELL = None
+GENERAL_INSTS_PER_CELL = None
+
+
+def alu_roofline(k, general_cells, clk):
+    """Roofline of the general planes' sweeps against the FP32 units: FP32 operations per second over
+    SMs x 128 FP32 lanes x 2 (a fused multiply-add) x the median SM clock sampled in the timed region,
+    and thread instructions per second over SMs x 4 schedulers x 32 lanes x that clock."""
+    import torch
+    if not k or general_cells <= 0:
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    secs = k["ms_avg"] / 1e3
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    out = {"bound": "alu", "kernel": "general_sweeps", "unit": "TFLOP/s", "peak": peak,
+           "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x 2 (FMA) x {mhz:.0f} MHz (median sampled)",
+           "general_cells_per_launch": general_cells, "general_gcells_per_s": general_cells / secs / 1e9,
+           "achieved": None, "frac": None}
+    if GENERAL_FLOPS_PER_CELL:
+        a = GENERAL_FLOPS_PER_CELL * general_cells / secs / 1e12
+        out.update(achieved=a, frac=a / peak, flops_per_cell=GENERAL_FLOPS_PER_CELL)
+    if GENERAL_INSTS_PER_CELL:
+        issue_peak = sms * 4 * 32 * mhz * 1e6
+        out.update(insts_per_cell=GENERAL_INSTS_PER_CELL,
+                   issue_frac=GENERAL_INSTS_PER_CELL * general_cells / secs / issue_peak)
+    return out
 
 
 def _env_int(name, default):
@@ -82,11 +122,11 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, path: str | None = None):
+        import tempfile
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv") \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/pf_clocks_{os.getpid()}.csv"
+        self.path = path or os.path.join(tempfile.gettempdir(), f"pf_clocks_{os.getpid()}_{device}.csv")
 
     def start(self):
         try:
@@ -163,6 +203,29 @@ def cpu_baseline(min_seconds: float = 10.0, max_steps: int = 40):
     return {"value": cells * n / dt / 1e6, "unit": "MLUP/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{NX}x{NY}x{nzs} bottom slab of the workload (64 grains, seed 0), {n} FP64 steps, "
                       f"{dt:.1f} s"}
+
+
+def gpu_on_cpu_sample(stream, steps: int = 200):
+    """The GPU path (FP32, the library's variant choice) on the CPU baseline's sample: the same
+    256x256x16 bottom slab, grains and seed, so the oracle's rate has a like-for-like GPU figure."""
+    import torch
+
+    from paper_1506_01684_gb300 import pf
+    from paper_1506_01684_gb300 import workloads as W
+
+    nzs = 16
+    sim = pf.Simulation(NX, NY, nzs, W.symmetric_params(n_grains=GRAINS), "fp32", stream=stream)
+    sim.init(SEED)
+    sim.step(5)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sim.close()
+    return NX * NY * nzs * steps / (ms / 1e3) / 1e6
 
 
 def run_reference(args, rank):
@@ -496,6 +559,11 @@ def main():
                     help="Voronoi grains (0: pure liquid, a bulk-only diagnostic)")
     ap.add_argument("--shape", default=None,
                     help="NXxNYxNZ: a smaller domain of the same workload (profiling captures)")
+    ap.add_argument("--pre-steps", type=int, default=PRE_STEPS,
+                    help="untimed steps before the warm-up: the timed steps start from the state the "
+                         "single-large-domain configuration reaches after its 2000 steps (0: the sharp initial state)")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.shape:
@@ -557,9 +625,14 @@ def main():
     sim = pf.Simulation(NX, NY, NZ, params, "fp32", stream=stream, variant=args.variant)
     sim.init(SEED)
     sol0 = sim.stats()["solute"]
+    # the configuration's state: pre-steps advance the front from its sharp Voronoi start to the
+    # diffuse, growing interface the configuration's 2000 steps reach (untimed)
+    if args.pre_steps > 0:
+        sim.step(args.pre_steps)
     sim.step(args.warmup)
     sim.sync()
-    clocks = ClockSampler(torch.cuda.current_device())
+    st_pre = sim.stats()
+    clocks = ClockSampler(torch.cuda.current_device(), args.clocks_csv)
     clocks.start()
     time.sleep(0.3)
     # timed region A (the value): K steps as pf_step runs them, replayed from the captured graph
@@ -614,10 +687,14 @@ def main():
     design_bytes = step_bytes / cells
     fused_bound = hbm * 1e9 / (48 * cells) * cells / 1e6  # MLUP/s at 48 B/cell (fused FP32 minimum)
     unfused_bound = hbm * 1e9 / (88 * cells) * cells / 1e6
+    design_bound = hbm * 1e9 / design_bytes / 1e6 if design_bytes else None
+    # cells of the general planes (88 algorithmic bytes each in FP32: both sweeps' words)
+    general_cells = kbytes.get("general_sweeps", 0.0) / 88.0
+    roof_alu = alu_roofline(kern.get("general_sweeps"), general_cells, clk)
 
     phi32, mu32 = sim.fields()
     st32 = sim.stats()
-    steps_done = args.warmup + 2 * args.steps
+    steps_done = args.pre_steps + args.warmup + 2 * args.steps
 
     # ---------------- FP64 GPU path on the same workload ----------------
     n64 = args.fp64_steps if args.fp64_steps is not None else steps_done
@@ -681,6 +758,9 @@ def main():
                "what": "pf_write_fields_f32 (pinned FP32 host state) + pf_step(K) + pf_read_fields_f32, wall "
                        "clock, median of three runs after an untimed one"}
     sim.close()
+    if cpu is not None:
+        cpu["gpu_same_sample_mlups"] = gpu_on_cpu_sample(stream)
+        cpu["gpu_same_sample_what"] = "the FP32 GPU step on the same 256x256x16 slab, 200 steps, CUDA events"
 
     if rank != 0:
         return
@@ -693,9 +773,13 @@ def main():
                    "parallelism": f"replicas x{world}", "l2": "inputs (1.6 GB of fields) larger than L2"},
         "roofline": roof,
         "kernels": kern,
+        "roofline_general": roof_alu,
         "bounds_mlups": {"fused_48B": fused_bound, "unfused_88B": unfused_bound,
-                         "this_design_bytes_per_cell": design_bytes,
-                         "this_design": hbm * 1e9 / design_bytes / 1e6 if design_bytes else None},
+                         "this_design_bytes_per_cell": design_bytes, "this_design": design_bound},
+        "frac_of_design_bound": value / design_bound if design_bound else None,
+        "state": {"steps_before_timing": args.pre_steps + args.warmup, "h_int": st_pre["h_int"],
+                  "general_cell_fraction": general_cells / cells,
+                  "what": "the timed steps start after the configuration's 2000 steps (pre-steps) and the warm-up"},
         "variant": ("lean kernel + general sweeps" if "lean_step" in prof
                     else ("fused" if "fused_step" in prof else "unfused")),
         "frac_of_unfused_bound": value / unfused_bound, "frac_of_fused_bound": value / fused_bound,

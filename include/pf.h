@@ -88,17 +88,22 @@ typedef struct pf_params {
 typedef struct pf_sim pf_sim;
 typedef struct pf_server pf_server;
 
-/* Human-readable text for a status code (static storage). */
+/* Human-readable text for a status code (static storage).  The paper has no counterpart: status codes
+ * are the library's error convention. */
 const char *pf_strerror(int status);
 
-/* Fill *p with the symmetric parameter set: dx = 1, eps = 4, tau = 1, dt = 0 (auto),
+/* Parameters of the model of Section 2 (Eq. 1-4) with the fitted parabolic Gibbs energies of Section 3.3;
+ * the paper prints no coefficient values (it takes them from its Al-Ag-Cu reference system), so the
+ * defaults are a symmetric stand-in.
+ * Fill *p with the symmetric parameter set: dx = 1, eps = 4, tau = 1, dt = 0 (auto),
  * gamma2 = 1, gamma3 = 15, A = 1, cE = alpha(0.8,0.1) beta(0.1,0.8) gamma(0.1,0.1)
  * liquid(1/3,1/3), kT = 0 solids / (0.1,0.1) liquid, s = 1 solids / 0 liquid,
  * D = 0 solids / 1 liquid, TE = 1, G = 1e-3, v = 1e-2, T0 = TE - 8 G - 0.15, seed_layers = 8,
  * n_grains = 12, window off, precision PF_FP64.  Returns PF_E_INVAL for p == NULL. */
 int pf_default_params(pf_params *p);
 
-/* Optional allocator hooks for every device buffer the library allocates (fields and
+/* The paper has no counterpart (allocation of the fields is the library's own concern).
+ * Optional allocator hooks for every device buffer the library allocates (fields and
  * scratch).  alloc(bytes, stream, ctx) returns a device pointer or NULL; free(ptr, bytes,
  * stream, ctx) releases it.  Passing NULLs restores cudaMalloc/cudaFree.  Set before
  * pf_create; buffers are released with the hook that allocated them. */
@@ -106,7 +111,9 @@ typedef void *(*pf_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*pf_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 int pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void *ctx);
 
-/* Create a simulation of nx*ny*nz cells on the current CUDA device.  Allocates the
+/* The domain of Section 2, discretised into equidistant regular cells, with the two lattices per
+ * variable of Section 2.1 (source and destination fields, swapped after each step, Algorithm 1).
+ * Create a simulation of nx*ny*nz cells on the current CUDA device.  Allocates the
  * double-buffered phi and mu fields (phi: 4 words/cell, mu: 2 words/cell, words of the
  * chosen precision; twice that for PF_FP32_COMP) and a small device state.  Copies *p;
  * dt <= 0 is replaced by the default limit.  The fields start as pure liquid, mu = 0,
@@ -114,10 +121,12 @@ int pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void *ctx);
  * Errors: PF_E_INVAL (sizes < 1, bad params/version), PF_E_NOMEM, PF_E_CUDA. */
 int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim **out);
 
-/* Release every device buffer and handle of sim (waits for its pending work). */
+/* Release every device buffer and handle of sim (waits for its pending work).  No counterpart in the
+ * paper: the inverse of pf_create. */
 int pf_destroy(pf_sim *sim);
 
-/* The effective parameters (dt resolved), copied into *out. */
+/* The effective parameters, copied into *out, with dt resolved: the explicit Euler scheme of Section 2
+ * needs a time step below the stability limits of Eq. 1 and Eq. 3, which the paper does not print. */
 int pf_get_params(const pf_sim *sim, pf_params *out);
 
 /* Initial condition (paper Section 2.1, simulation setting): cells with k < seed_layers
@@ -132,10 +141,14 @@ int pf_init(pf_sim *sim, uint64_t seed);
 int pf_step(pf_sim *sim, int nsteps);
 
 /* Wait for the sim's stream; returns and clears the latched error (PF_E_UNSTABLE when a
- * non-finite value appeared in any completed step). */
+ * non-finite value appeared in any completed step).  No counterpart in the paper (its kernels run
+ * synchronously on the CPU): the library's steps run asynchronously on the device, and this is
+ * where their errors surface. */
 int pf_sync(pf_sim *sim);
 
-/* Copy the current fields to host FP64 SoA buffers (phi: 4*nx*ny*nz, mu: 2*nx*ny*nz
+/* The simulation state of Section 3.2: four phi values and two mu values per cell (phi on the Gibbs
+ * simplex, Section 2; mu of Eq. 3).
+ * Copy the current fields to host FP64 SoA buffers (phi: 4*nx*ny*nz, mu: 2*nx*ny*nz
  * doubles; either may be NULL).  cap_cells must be >= nx*ny*nz.  Synchronising. */
 int pf_read_fields(pf_sim *sim, double *phi, double *mu, size_t cap_cells);
 
@@ -143,7 +156,8 @@ int pf_read_fields(pf_sim *sim, double *phi, double *mu, size_t cap_cells);
  * window offset are left unchanged.  Synchronising. */
 int pf_write_fields(pf_sim *sim, const double *phi, const double *mu);
 
-/* As pf_read_fields / pf_write_fields with FP32 host buffers (same SoA layout, half the bytes to
+/* As pf_read_fields / pf_write_fields with FP32 host buffers (the single precision the paper uses for
+ * the state on disk, Section 3.2) (same SoA layout, half the bytes to
  * move): exact for an FP32 simulation; an FP64 or compensated state is rounded once to FP32 on
  * read (the compensated pair's value), and written values are exact in every precision (the
  * compensated low words become 0).  Errors as the FP64 forms.  Synchronising. */
@@ -169,15 +183,25 @@ int pf_checkpoint_write(pf_sim *sim, const char *path);
  * (the fields may then be partly overwritten).  Synchronising. */
 int pf_checkpoint_read(pf_sim *sim, const char *path);
 
-/* Mean of each phi_a over all cells, accumulated in FP64 on the device. Synchronising. */
+/* Phase fractions: phi_a is the fraction of phase a in each cell (Section 2), so its mean over the cells
+ * is the phase's volume fraction in the domain (the quantity the Voronoi nuclei of Section 2.1 are drawn
+ * for, and the share of each phase in the microstructures of Section 5.2).  The paper prints no
+ * reduction; this one accumulates in FP64 on the device so that the sum of many FP32 values keeps its
+ * accuracy.  Mean of each phi_a over all cells.  Synchronising. */
 int pf_phase_fractions(pf_sim *sim, double out[4]);
 
-/* FP64 diagnostics: simulation time t, window offset (planes), solute totals
+/* FP64 diagnostics.  The time t enters the frozen temperature T = T0 + G (z - v t) (Section 3.3); the
+ * window offset is the moving window's displacement (Section 3.3); the solute totals are the sums of
+ * the concentration c = sum_a h_a c^a(mu, T) whose evolution Eq. 3 states in terms of mu (a closed box
+ * keeps them constant); the interface height is the quantity the moving window follows (Section 3.3
+ * names the technique but not its trigger: here h_int >= window_trigger_z).  The paper prints no
+ * reduction; these accumulate in FP64 on the device.
+ * Simulation time t, window offset (planes), solute totals
  * sum_cells c_i with c = sum_a h_a c^a(mu, T), and interface height
  * sum(1 - phi_liquid)/(nx ny).  Any output pointer may be NULL.  Synchronising. */
 int pf_stats(pf_sim *sim, double *t, double *window_offset, double solute[2], double *h_int);
 
-/* Number of window shifts (planes moved) since pf_init.  Synchronising. */
+/* Planes the moving window (Section 3.3) has moved since pf_init.  Synchronising. */
 int pf_window_shifts(pf_sim *sim, int *planes);
 
 /* Interface mesh of one phase (the paper's per-phase isosurface output, Section 3.2): the triangles
@@ -219,14 +243,15 @@ enum {
     PF_K_COUNT = 11
 };
 
-/* Test hook for the failure path of the bounded device waits: with on != 0 the producer warp of
+/* No counterpart in the paper.  Test hook for the failure path of the bounded device waits: with on != 0 the producer warp of
  * the lean kernel (the fused step's pure-liquid planes) issues none of its copies, so its consumers'
  * waits run out (after about 2^31 clock cycles each), the step ends and pf_sync returns
  * PF_E_TIMEOUT; the fields of the affected planes are then not updated.  The GPU context stays
  * usable; on = 0 restores normal steps.  Not for production use. */
 int pf_test_withhold_copies(pf_sim *sim, int on);
 
-/* Kernel variants of pf_step.  UNFUSED runs Algorithm 1 as two kernels (the phi-sweep writes
+/* Kernel variants of pf_step (Algorithm 1's two kernels, or one pass that computes both).  UNFUSED runs
+ * Algorithm 1 as two kernels (the phi-sweep writes
  * phi^{n+1}, the mu-sweep reads it back: 88 algorithmic bytes per FP32 cell); FUSED computes
  * phi^{n+1} and mu^{n+1} in one pass (each CTA recomputes phi^{n+1} on a one-cell ring around its
  * tile: 48 bytes per FP32 cell).  Both give the same result up to rounding order.  AUTO (the
@@ -243,7 +268,8 @@ int pf_profile(pf_sim *sim, int enable);
  * since the last read; resets the accumulators.  Synchronising. */
 int pf_profile_read(pf_sim *sim, double ms[], int launches[]);
 
-/* Algorithmic HBM bytes per kernel class (array of PF_K_COUNT) of the last step pf_step ran on
+/* The paper's memory model of a kernel (Section 5.1.1: bytes a cell update must move) applied to
+ * these kernels.  Algorithmic HBM bytes per kernel class (array of PF_K_COUNT) of the last step pf_step ran on
  * this simulation (batch steps excluded): the compulsory loads and stores of each kernel.
  *   PF_K_PHI / PF_K_MU (two sweeps): 10 and 12 words a cell (18 and 16 with the compensated low
  *     words), from the cell count;
@@ -260,6 +286,9 @@ int pf_profile_read(pf_sim *sim, double ms[], int launches[]);
 int pf_step_bytes(pf_sim *sim, double bytes[]);
 
 /*
+ * Batched launch.  No counterpart in the paper, whose domain is split into equally sized blocks
+ * (Section 3.1) of one simulation; here many independent simulations, each a domain of its own, share
+ * every launch.
  * Batched launch: many independent domains of uneven size stepped together.  Each step is one
  * persistent fused kernel whose CTAs pull (domain, tile, z chunk) work items -- largest first --
  * from a device table through an atomic counter, followed by a per-domain FP64 finalize and a
@@ -292,6 +321,8 @@ int pf_batch_set_zchunk(pf_batch *b, int zchunk);
 int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms);
 
 /*
+ * Serving.  No counterpart in the paper: a request loop of the library that runs many independent
+ * solidification simulations (each the setting of Section 2.1) on one GPU.
  * Serving: solidification runs submitted as they arrive, run with continuous batching.  A
  * scheduler thread admits queued requests as device memory frees up (admission by HBM footprint
  * of their double-buffered fields against the server's budget; the oldest waiting request keeps
@@ -302,7 +333,8 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms);
  * kernel computes each domain exactly as it would alone.  FP32 only.
  */
 /* Create a server with a device-memory budget (bytes, 0: 90% of the free memory) and at most
- * max_active concurrently running requests (0: 256); chunk = steps per scheduling round (0: 64). */
+ * max_active concurrently running requests (0: 256); chunk = steps per scheduling round (0: 64).
+ * The last two are scheduling knobs of the continuous batching; 0 takes the defaults. */
 int pf_server_create(size_t hbm_budget_bytes, int max_active, int chunk, pf_server **out);
 /* Stop the scheduler (running requests are cancelled) and release everything. */
 int pf_server_destroy(pf_server *srv);
@@ -330,12 +362,12 @@ int pf_server_stats(pf_server *srv, double *mlups, int *running, int *queued, si
  * cudaMalloc would take memory the owner has already promised elsewhere), and code that must
  * not pay cudaMalloc/cudaFree's implicit device-wide synchronisation in the middle of its work.
  *
- * One explicit step (Algorithm 1: phi-sweep, then mu-sweep) on caller-owned device fields,
- * asynchronously on `stream` (a cudaStream_t; NULL = the legacy default stream).  The call
- * allocates nothing: it calls no cudaMalloc/cudaFree and no allocating library routine.  Its
- * scratch (a 64-byte step state, the per-plane temperature table and the per-CTA FP64 partial
- * sums) lives in one file-scope device array of PF_NOALLOC_SCRATCH_BYTES, which every GPU that
- * loads this library holds until the process exits.
+ * One explicit step (phi-sweep, then mu-sweep) on caller-owned device fields, asynchronously on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream).  The call allocates nothing: it
+ * calls no cudaMalloc/cudaFree and no allocating library routine.  Its scratch (the step state,
+ * the per-plane temperature table and the per-CTA FP64 partial sums) lives in one file-scope
+ * device array of PF_NOALLOC_SCRATCH_BYTES, which every GPU that loads this library holds until
+ * the process exits.
  *
  *   phi_src, mu_src : the state at time t (device, read only), precision p->precision
  *                     (PF_FP32: float, PF_FP64: double; PF_FP32_COMP is rejected).
@@ -351,16 +383,22 @@ int pf_server_stats(pf_server *srv, double *mlups, int *running, int *queued, si
  *                     stores the interface height sum(1 - phi_l)/(nx ny) of the new state;
  *                     then a non-finite value in the new state returns PF_E_UNSTABLE.
  *
- * Errors: PF_E_INVAL for null or misaligned fields, sizes < 1, bad parameters, PF_FP32_COMP, or a grid that
- * needs more scratch than PF_NOALLOC_SCRATCH_BYTES (needed bytes: 256 + 32 w nz rounded up to
- * 256, plus 16 per CTA of the sweeps = ceil(nx/32) ceil(ny/8) ceil(nz/zchunk); w = 4 or 8;
- * e.g. 256x256x1024 in FP32 needs about 0.2 MB); PF_E_CUDA if a launch fails.
+ * Scratch a grid needs, in bytes: 256 (the step state's slot) + 2 nz x 16 w rounded up to a
+ * multiple of 256 (the plane table; w = 4 in FP32, 8 in FP64) + 32 x C (one FP64 partial-sum record
+ * per CTA of the sweeps), with C = gx gy gz, gx = ceil(nx/32), gy = ceil(ny/8), gz = ceil(nz/zc) and
+ * zc = min(nz, max(8, min(64, ceil(nz / ceil(2432 / (gx gy)))))).  Example: 256x256x1024 in FP32
+ * needs 256 + 131072 + 32 x 4096 = 262400 bytes, about 0.26 MB.
+ *
+ * Errors: PF_E_INVAL for null or misaligned fields, sizes < 1, bad parameters, PF_FP32_COMP, or a
+ * grid whose scratch exceeds PF_NOALLOC_SCRATCH_BYTES; PF_E_CUDA if a launch fails.
  *
  * Set-up: the first call on each device (with that device current) looks up the scratch
- * array's device address once; make that first call before any stream capture.  Every call
- * shares the one array and leaves its contents behind (each call rewrites what it reads), so
- * calls whose work overlaps on the GPU -- on different streams or different host threads --
- * race on the scratch and must be serialised by the caller.
+ * array's device address once and keeps it for the life of the process; make that first call
+ * before any stream capture.  A caller that resets the device (cudaDeviceReset) invalidates
+ * the kept address: do not call this entry point again after a reset in the same process.
+ * Every call shares the one array and leaves its contents behind (each call rewrites what it
+ * reads before reading it), so calls whose work overlaps on the GPU -- on different streams or
+ * different host threads -- race on the scratch and must be serialised by the caller.
  */
 #define PF_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
 int pf_step_noalloc(int nx, int ny, int nz, const pf_params *p, double t, double window_offset,

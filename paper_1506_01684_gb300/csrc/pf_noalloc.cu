@@ -57,6 +57,11 @@ __global__ void noalloc_state_kernel(pf::DevState *st, double t, double off)
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
+// The scratch layout the header documents: a 256-byte slot for the step state, 32 bytes per CTA partial.
+static_assert(sizeof(pf::DevState) <= 256, "the step state fits its 256-byte slot");
+static_assert(sizeof(pf::Partial) == 32, "one partial-sum record is 32 bytes");
+static_assert(sizeof(pf::PlaneT<float>) == 16 * 4 && sizeof(pf::PlaneT<double>) == 16 * 8, "16-word plane entries");
+
 template <typename R>
 int noalloc_step(int nx, int ny, int nz, const pf_params &p, double t, double off, const void *phi_src,
                  const void *mu_src, void *phi_dst, void *mu_dst, double *h_int_out, cudaStream_t s)

@@ -37,9 +37,11 @@ def _soa(t):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 2e-5), ("fp64", 1e-12)])
-def test_noalloc_step_matches_pf_step_on_two_calls_in_a_row(torch, precision, tol):
+@pytest.mark.parametrize("thermo", ["symmetric", "general"])
+def test_noalloc_step_matches_pf_step_on_two_calls_in_a_row(torch, precision, tol, thermo):
     nx, ny, nz = 48, 40, 36
-    p = W.symmetric_params(n_grains=7)
+    # the general set (matrix curvatures, pair relaxation times) runs the kernels' general branches
+    p = W.symmetric_params(n_grains=7) if thermo == "symmetric" else W.general_params(n_grains=7)
     # a state with diffuse interfaces: 10 steps from the Voronoi start through the regular path
     ref = pf.Simulation(nx, ny, nz, p, precision)
     ref.init(5)
@@ -90,3 +92,36 @@ def test_noalloc_step_rejects_what_it_cannot_do(torch):
     assert L.pf_step_noalloc(4, 4, 4, q, 0.0, 0.0, ptr, ptr, ptr, ptr, None, None) == pf.PF_E_INVAL
     assert L.pf_step_noalloc(4, 4, 4, p, 0.0, 0.0, None, ptr, ptr, ptr, None, None) == pf.PF_E_INVAL
     assert L.pf_step_noalloc(4, 4, 4, p, 0.0, 0.0, ptr + 4, ptr, ptr, ptr, None, None) == pf.PF_E_INVAL
+
+
+def noalloc_scratch_bytes(nx, ny, nz, word):
+    """The scratch a grid needs, by the formula the header states for pf_step_noalloc."""
+    gx, gy = -(-nx // 32), -(-ny // 8)
+    zc = min(nz, max(8, min(64, -(-nz // -(-2432 // (gx * gy))))))
+    gz = -(-nz // zc)
+    table = -(-(2 * nz * 16 * word) // 256) * 256
+    return 256 + table + 32 * gx * gy * gz
+
+
+def test_noalloc_scratch_limit_is_exact(torch):
+    limit = 8 * 1024 * 1024
+    # the header's example
+    assert noalloc_scratch_bytes(256, 256, 1024, 4) == 262400
+    # a 1 x 1 column whose scratch is just under the limit runs; one plane more is rejected
+    nz = 64000
+    while noalloc_scratch_bytes(1, 1, nz + 1, 4) <= limit:
+        nz += 1
+    assert noalloc_scratch_bytes(1, 1, nz, 4) <= limit < noalloc_scratch_bytes(1, 1, nz + 1, 4)
+    p = pf.params_from_dict(W.symmetric_params(G=0.0), pf.PF_FP32)
+    phi = torch.zeros((nz + 1, 4), dtype=torch.float32, device="cuda")
+    phi[:, 3] = 1.0  # pure liquid: a fixed point apart from the temperature drift (none at G = 0)
+    mu = torch.zeros((nz + 1, 2), dtype=torch.float32, device="cuda")
+    phi_o, mu_o = torch.empty_like(phi), torch.empty_like(mu)
+    L = pf.lib()
+    stream = torch.cuda.current_stream()
+    h = pf.pf_step_noalloc(1, 1, nz, p, 0.0, 0.0, phi.data_ptr(), mu.data_ptr(), phi_o.data_ptr(),
+                           mu_o.data_ptr(), True, stream)
+    assert h == 0.0
+    assert torch.equal(phi_o[:nz], phi[:nz]) and torch.equal(mu_o[:nz], mu[:nz])
+    assert L.pf_step_noalloc(1, 1, nz + 1, p, 0.0, 0.0, phi.data_ptr(), mu.data_ptr(), phi_o.data_ptr(),
+                             mu_o.data_ptr(), None, None) == pf.PF_E_INVAL
