@@ -23,24 +23,25 @@
 
 using namespace pf;
 
-// Launch shape of the fused step with the lean kernel: the persistent general-plane CTAs per SM,
-// and whether the general planes run on a second stream beside the lean kernel (1) or before it
-// on the sim's stream (0).  Measured on 256x256x1024 FP32 (GB300): the two orders give the same
-// step time (the general CTAs hold most of an SM's registers, so the lean kernel gets little of
-// the GPU until they finish); the default is the plain order.
+// Launch shape of the fused step with the lean kernel: the persistent general-plane CTAs per SM (two
+// take all of an SM's registers; a second stream for the general planes beside the lean kernel gained
+// nothing for that reason, measured on 256x256x1024 FP32).
 #ifndef PF_GENERAL_CTAS_PER_SM
 #define PF_GENERAL_CTAS_PER_SM 2
 #endif
 #ifndef PF_LEAN_PLANES
 #define PF_LEAN_PLANES 64  // at most planes per lean CTA (the kernels' limit, PF_LEAN_PLANES in pf_kernels.cuh)
 #endif
-#ifndef PF_OVERLAP_GENERAL
-#define PF_OVERLAP_GENERAL 0
+// the step's kernels launched with programmatic dependent launch (1), or plainly (0)
+#ifndef PF_PDL
+#define PF_PDL 1
 #endif
+
 // the general planes as the two sweeps of Algorithm 1 (1) or as the fused tile (0)
 #ifndef PF_GENERAL_SWEEPS
 #define PF_GENERAL_SWEEPS 1
 #endif
+
 
 // ------------------------------------------------------------------------------------------
 // allocator hooks
@@ -132,10 +133,10 @@ struct pf_sim {
     DevBuf lean_stats;  // LeanStats
     DevBuf splits;      // int2 per (tile, chunk) of the fused grid: the lean / general split
     DevBuf glist;       // int per (tile, chunk): the items with general planes
+    DevBuf subparts;    // Partial per work unit of the general planes (kMaxUnits per item)
+    DevBuf subcnt;      // unsigned per (tile, chunk): units of the item finished in this step
     int general_ctas = 0;  // persistent CTAs of the general kernel
     int gphi_ctas = 0, gmu_ctas = 0;  // persistent CTAs of the general planes' two sweeps
-    cudaStream_t aux = nullptr;  // the fused step's general planes, concurrent with the lean kernel
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool lean_ok = false;
     int lean_nsub = 1;  // lean CTAs per z chunk of the fused grid
     DevBuf state;          // DevState
@@ -432,20 +433,6 @@ static cudaError_t timed(pf_sim *s, int cls, F &&f, cudaStream_t st = nullptr)
     return e;
 }
 
-// The second stream of the fused step: its general planes run there, beside the lean kernel on the
-// sim's stream (fork after the previous step's post kernel, join before finalize).  Created on
-// first use, with the highest priority so that the general CTAs are placed first.
-static cudaError_t ensure_aux(pf_sim *s)
-{
-    if (s->aux) return cudaSuccess;
-    int lo = 0, hi = 0;
-    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->aux, cudaStreamNonBlocking, hi);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
-    return e;
-}
-
 static bool use_fused(const pf_sim *s)
 {
     if (s->comp()) return false;  // the compensated state runs on the two sweeps
@@ -500,48 +487,40 @@ static int do_step_direct(pf_sim *s, int n)
                                                     s->mu[b].p, st, tab, parts, s->stream, tin, tout, true);
                     });
             } else {
-                // plan the step (splits, list of items with general planes), then the general planes
-                // on the second stream beside the lean planes (a disjoint set of planes, map entries
-                // and partials) on the sim's stream
-                if (e == cudaSuccess)
-                    e = timed(s, PF_K_PLAN, [&] {
-                        return launch_plan<R>(kp, s->geo_fused, st, tin, (int2 *)s->splits.p, (int *)s->glist.p, ls,
-                                              parts, s->stream);
-                    });
-                cudaStream_t gs = s->stream;
-                if (PF_OVERLAP_GENERAL) {
-                    if (e == cudaSuccess) e = ensure_aux(s);
-                    if (e == cudaSuccess) e = cudaEventRecord(s->ev_fork, s->stream);
-                    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->aux, s->ev_fork, 0);
-                    gs = s->aux;
-                }
-                if (e == cudaSuccess && PF_GENERAL_SWEEPS)
-                    e = timed(
-                        s, PF_K_GENERAL,
-                        [&] {
+                // plan the step (splits, list of items with general planes), the lean planes, then the
+                // general planes' two sweeps.  The general planes touch other planes, map entries and
+                // partials than the lean kernel, so with programmatic dependent launch the phi-sweep's
+                // CTAs start as the lean kernel's last CTAs retire
+                const bool pdl = PF_PDL != 0;
+                auto general = [&]() -> cudaError_t {
+                    if (PF_GENERAL_SWEEPS)
+                        return timed(s, PF_K_GENERAL, [&] {
                             return launch_general_sweeps<R>(kp, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st,
                                                             tab, parts, tout, (const int2 *)s->splits.p,
                                                             (const int *)s->glist.p, ls, s->gphi_ctas, s->gmu_ctas,
-                                                            gs);
-                        },
-                        gs);
-                if (e == cudaSuccess && !PF_GENERAL_SWEEPS)
-                    e = timed(
-                        s, PF_K_FUSED,
-                        [&] {
-                            return launch_general_step<R>(kp, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st,
-                                                          tab, parts, tin, tout, (const int2 *)s->splits.p,
-                                                          (const int *)s->glist.p, ls, s->general_ctas, gs);
-                        },
-                        gs);
-                if (e == cudaSuccess)
-                    e = timed(s, PF_K_LEAN, [&] {
+                                                            s->stream, (Partial *)s->subparts.p,
+                                                            (unsigned *)s->subcnt.p, pdl, true);
+                        });
+                    return timed(s, PF_K_FUSED, [&] {
+                        return launch_general_step<R>(kp, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st, tab,
+                                                      parts, tin, tout, (const int2 *)s->splits.p,
+                                                      (const int *)s->glist.p, ls, s->general_ctas, s->stream);
+                    });
+                };
+                auto leanp = [&]() -> cudaError_t {
+                    return timed(s, PF_K_LEAN, [&] {
                         return launch_lean_step<R>(kp, s->geo_fused, s->lean_nsub, &s->mu_map[a], s->mu[a].p,
                                                    s->phi[b].p, s->mu[b].p, st, ls, s->stream, tin, tout,
-                                                   (const int2 *)s->splits.p);
+                                                   (const int2 *)s->splits.p, pdl);
                     });
-                if (PF_OVERLAP_GENERAL && e == cudaSuccess) e = cudaEventRecord(s->ev_join, s->aux);
-                if (PF_OVERLAP_GENERAL && e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+                };
+                if (e == cudaSuccess)
+                    e = timed(s, PF_K_PLAN, [&] {
+                        return launch_plan<R>(kp, s->geo_fused, st, tin, (int2 *)s->splits.p, (int *)s->glist.p, ls,
+                                              parts, s->stream, pdl);
+                    });
+                if (e == cudaSuccess) e = leanp();
+                if (e == cudaSuccess) e = general();
             }
         } else if (s->comp()) {
             const KParams<float> &kf = reinterpret_cast<const KParams<float> &>(kp);
@@ -568,12 +547,12 @@ static int do_step_direct(pf_sim *s, int n)
         if (e == cudaSuccess)
             e = timed(s, PF_K_FINALIZE, [&] {
                 return launch_finalize<R>(kp, st, parts, nparts, s->stream,
-                                          lean ? (LeanStats *)s->lean_stats.p : nullptr);
+                                          lean ? (LeanStats *)s->lean_stats.p : nullptr, lean && PF_PDL);
             });
         if (e == cudaSuccess)
             e = timed(s, PF_K_POST, [&] {
                 return launch_post<R>(kp, st, s->phi[b].p, s->mu[b].p, tab, s->stream, s->lo_phi(b), s->lo_mu(b),
-                                      fused ? (unsigned char *)s->tmap[b].p : nullptr);
+                                      fused ? (unsigned char *)s->tmap[b].p : nullptr, lean && PF_PDL);
             });
         if (e != cudaSuccess) return latch(s, cuda_status(e));
         s->tmap_ok[b] = fused;
@@ -1085,6 +1064,8 @@ int pf_destroy(pf_sim *s)
     dev_free(s->lean_stats, s->stream);
     dev_free(s->splits, s->stream);
     dev_free(s->glist, s->stream);
+    dev_free(s->subparts, s->stream);
+    dev_free(s->subcnt, s->stream);
     dev_free(s->tab, s->stream);
     dev_free(s->seeds, s->stream);
     dev_free(s->red, s->stream);
@@ -1094,12 +1075,6 @@ int pf_destroy(pf_sim *s)
     }
     for (auto e : s->pool) cudaEventDestroy(e);
     if (s->graph) cudaGraphExecDestroy(s->graph);
-    if (s->aux) {
-        cudaStreamSynchronize(s->aux);
-        cudaStreamDestroy(s->aux);
-    }
-    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
-    if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
     return PF_OK;
@@ -1157,7 +1132,17 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
                       s->stream);
     if (r == PF_OK) r = dev_alloc(s->lean_stats, sizeof(LeanStats), s->stream);
     if (r == PF_OK) r = dev_alloc(s->splits, (size_t)s->geo_fused.nparts() * sizeof(int2), s->stream);
-    if (r == PF_OK) r = dev_alloc(s->glist, (size_t)s->geo_fused.nparts() * sizeof(int), s->stream);
+    {
+        // work units of the general planes: up to kMaxUnits per item
+        const size_t units = (size_t)s->geo_fused.nparts() * kMaxUnits;
+        if (r == PF_OK) r = dev_alloc(s->glist, (size_t)s->geo_fused.nparts() * sizeof(int), s->stream);
+        if (r == PF_OK) r = dev_alloc(s->subparts, units * sizeof(Partial), s->stream);
+        if (r == PF_OK) r = dev_alloc(s->subcnt, (size_t)s->geo_fused.nparts() * sizeof(unsigned), s->stream);
+        if (r == PF_OK) {
+            cudaError_t e = cudaMemsetAsync(s->subcnt.p, 0, s->subcnt.bytes, s->stream);
+            if (e != cudaSuccess) r = cuda_status(e);
+        }
+    }
     if (r == PF_OK) {
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
@@ -1172,8 +1157,9 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
             general_sweep_ctas_per_sm<double>(&pp, &pm);
         else
             general_sweep_ctas_per_sm<float>(&pp, &pm);
-        s->gphi_ctas = std::max(1, std::min(s->geo_fused.nparts(), std::min(pp, PF_GENERAL_CTAS_PER_SM) * sms));
-        s->gmu_ctas = std::max(1, std::min(s->geo_fused.nparts(), std::min(pm, PF_GENERAL_CTAS_PER_SM) * sms));
+        const int units = s->geo_fused.nparts() * kMaxUnits;
+        s->gphi_ctas = std::max(1, std::min(units, std::min(pp, PF_GENERAL_CTAS_PER_SM) * sms));
+        s->gmu_ctas = std::max(1, std::min(units, std::min(pm, PF_GENERAL_CTAS_PER_SM) * sms));
     }
     if (r == PF_OK) {
         cudaError_t e = cudaMemsetAsync(s->lean_stats.p, 0, sizeof(LeanStats), s->stream);

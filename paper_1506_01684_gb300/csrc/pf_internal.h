@@ -115,6 +115,9 @@ struct BatchItem {
     int dom, bx, by, bz;
 };
 
+// Most work units an item of the general planes is cut into (the general planes' sweeps, pf_kernels.cuh).
+constexpr int kMaxUnits = 8;
+
 // Launch geometry of the sweep kernels.
 struct Geometry {
     int tx, ty;     // CTA tile in x and y (columns)
@@ -131,7 +134,9 @@ KParams<R> kparams_for(const pf_params &p, int nx, int ny, int nz, const Geometr
 double resolved_dt(const pf_params &p, int nz);
 int validate_params(const pf_params *p);
 
-// Launchers (defined in pf_kernels.cuh, instantiated for float and double).
+// Launchers (defined in pf_kernels.cuh, instantiated for float and double).  pdl: launch with
+// programmatic stream serialisation (the kernel may be scheduled while the one ahead of it in the stream
+// is still running and waits for it on the device before it depends on its results).
 template <typename R>
 cudaError_t launch_phi_sweep(const KParams<R> &kp, const Geometry &g, const void *phi, const void *mu,
                              void *phi_out, const DevState *st, const PlaneT<R> *tab, cudaStream_t s);
@@ -155,13 +160,14 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
 template <typename R>
 cudaError_t launch_lean_step(const KParams<R> &kp, const Geometry &g, int nsub, const void *mu_map, const void *mu,
                              void *phi_out, void *mu_out, const DevState *st, LeanStats *stats, cudaStream_t s,
-                             const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits);
+                             const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits,
+                             bool pdl = false);
 // Plan of a fused step with the lean kernel (plan_kernel): each (tile, chunk) item's split into
 // lean and general planes (splits, gx*gy*gz), the list of items with general planes (glist,
 // count in stats->gcount; finalize resets the counters), zeroed partials for the all-lean items.
 template <typename R>
 cudaError_t launch_plan(const KParams<R> &kp, const Geometry &g, const DevState *st, const unsigned char *tmap_in,
-                        int2 *splits, int *glist, LeanStats *stats, Partial *parts, cudaStream_t s);
+                        int2 *splits, int *glist, LeanStats *stats, Partial *parts, cudaStream_t s, bool pdl = false);
 // The general planes of the listed items: ctas persistent CTAs (general_step_kernel).
 template <typename R>
 cudaError_t launch_general_step(const KParams<R> &kp, const void *phi, const void *mu, void *phi_out, void *mu_out,
@@ -173,11 +179,16 @@ int general_ctas_per_sm();
 // The general planes of the listed items as Algorithm 1's two sweeps: the phi-sweep (phi^{n+1} and
 // its liquid-map entries) and then the mu-sweep (phi^{n+1} of lean tile planes taken as e_l), each
 // by persistent CTAs over the list; the mu partials carry both sweeps' bytes (22 words a cell).
+// Each listed item's general range is cut into U units (U from the list length and the persistent CTA
+// count, the same in both sweeps); with U > 1 each unit's mu-sweep partial goes to subparts (kMaxUnits
+// slots per item) and the item's last unit to finish sums them in unit order into parts[item] (subcnt:
+// one counter per item, zero between steps).
 template <typename R>
 cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const void *mu, void *phi_out, void *mu_out,
                                   const DevState *st, const PlaneT<R> *tab, Partial *parts, unsigned char *tmap_out,
                                   const int2 *splits, const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas,
-                                  cudaStream_t s);
+                                  cudaStream_t s, Partial *subparts, unsigned *subcnt, bool pdl = false,
+                                  bool after_lean = false);  // after_lean: launched right behind the lean kernel
 template <typename R>
 void general_sweep_ctas_per_sm(int *phi_per_sm, int *mu_per_sm);
 // liquid map of a field (for states not produced by a fused step)
@@ -186,7 +197,7 @@ cudaError_t launch_classify(const KParams<R> &kp, const DevState *st, const void
                             cudaStream_t s);
 template <typename R>
 cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s,
-                            LeanStats *lean = nullptr);
+                            LeanStats *lean = nullptr, bool pdl = false);
 // Batched fused step of ndoms domains: counter reset, persistent kernel (ctas CTAs) over the
 // work items, per-domain finalize and post.  parity: index of the source buffers.
 template <typename R>
@@ -209,7 +220,7 @@ void batched_general_ctas_per_sm(int *phi_per_sm, int *mu_per_sm);
 template <typename R>
 cudaError_t launch_post(const KParams<R> &kp, const DevState *st, void *phi, void *mu, PlaneT<R> *tab,
                         cudaStream_t s, void *phi_lo = nullptr, void *mu_lo = nullptr,
-                        unsigned char *tmap = nullptr);
+                        unsigned char *tmap = nullptr, bool pdl = false);
 template <typename R>
 cudaError_t launch_init(const KParams<R> &kp, void *phi, void *mu, const double *seeds, int n_grains, int H,
                         cudaStream_t s);

@@ -15,6 +15,7 @@
 #pragma once
 
 #include <atomic>
+#include <utility>
 #include <climits>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -82,6 +83,14 @@ __device__ __forceinline__ int wrapi(int x, int n)
     x %= n;
     return x < 0 ? x + n : x;
 }
+
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with the programmatic stream
+// serialisation attribute may be scheduled before the kernel ahead of it in the stream has finished:
+// pdl_wait() blocks until that kernel has completed and its memory operations are visible (it returns
+// at once for a launch without the attribute); pdl_trigger() lets the kernel behind this one be
+// scheduled once every CTA of this one has triggered or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Liquid map layout: tile-major, the storage planes of one fused-step tile contiguous, so that the
 // threads of a warp testing consecutive planes of one tile read consecutive bytes.
@@ -1472,6 +1481,22 @@ __device__ __forceinline__ void zero_partial(Partial *p)
     *p = z;
 }
 
+// Work units of the general planes.  With G items on the list and `slots` persistent CTAs, each item's
+// general range [lo, hi) is cut into U = max(1, min(kMaxUnits, slots / G)) units of nearly equal length
+// (unit u: lo + len u / U .. lo + len (u + 1) / U; a unit may be empty), so that a short list still gives
+// every CTA a unit: a z-marching unit pays a prologue, so items are cut only when CTAs would idle.
+__device__ __forceinline__ int general_units(unsigned G, int slots)
+{
+    const int u = G > 0u ? slots / (int)G : 1;
+    return u < 1 ? 1 : (u > kMaxUnits ? kMaxUnits : u);
+}
+__device__ __forceinline__ void unit_range(int lo, int hi, int U, int u, int &a, int &b)
+{
+    const int len = hi - lo;
+    a = lo + (len * u) / U;
+    b = lo + (len * (u + 1)) / U;
+}
+
 // Plan of one domain: four items per CTA; items with general planes are appended to glist (count
 // in stats->gcount) for the general-plane kernels, the partials of the others are zeroed (their
 // planes are all lean: no liquid deficit, no general-path value).
@@ -1484,6 +1509,8 @@ __global__ void __launch_bounds__(256) plan_kernel(int nx, int ny, int nz, int t
                                                    Partial *__restrict__ parts)
 {
     __shared__ int kred[8][2];
+    pdl_wait();  // the previous step's post kernel (window fill, map entries, zbase)
+    pdl_trigger();
     const int item = blockIdx.x * 4 + (threadIdx.x >> 6);
     const bool live = item < tgx * tgy * gz;
     int lo_end, hi_beg;
@@ -2067,25 +2094,39 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_phi_kerne
                                                             unsigned char *__restrict__ tmap_out,
                                                             const int2 *__restrict__ splits,
                                                             const int *__restrict__ glist,
-                                                            LeanStats *__restrict__ stats)
+                                                            LeanStats *__restrict__ stats, int slots,
+                                                            int after_lean)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
+    // after_lean: the kernel ahead of this one in the stream is the lean kernel of the same step, whose
+    // CTAs all passed their wait for the plan before this kernel could be scheduled.  This sweep reads
+    // nothing the lean kernel writes (other planes, other map entries), so it starts as lean CTAs retire
+    // and waits for the lean kernel only before it exits (its own completion then still implies the
+    // lean kernel's).  Any other predecessor is waited for first: the plan's list must be complete.
+    if (!after_lean) pdl_wait();
+    pdl_trigger();
     const int ntl = kp.tgx * kp.tgy;
+    const unsigned G = __ldcg(&stats->gcount);
+    const int U = general_units(G, slots);
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
             const unsigned it = atomicAdd(&stats->gnext, 1u);
-            s_item = it < *(volatile unsigned *)&stats->gcount ? glist[it] : -1;
+            s_item = it < G * (unsigned)U ? (int)it : -1;
         }
         __syncthreads();
-        const int item = s_item;
-        if (item < 0) break;
-        const int tile = item % ntl;
-        const int2 sp = splits[item];
-        phi_sweep_tile<R, TX, TY, false, SYM>(kp, phi, mu, phi_out, st, tab, nullptr, nullptr, tile % kp.tgx,
-                                              tile / kp.tgx, sp.x, sp.y, smem_raw, tmap_out);
+        const int entry = s_item;
+        if (entry < 0) break;
+        const int item = __ldcg(glist + entry / U), unit = entry % U, tile = item % ntl;
+        const int2 sp = __ldcg(splits + item);
+        int za, zb;
+        unit_range(sp.x, sp.y, U, unit, za, zb);
+        if (za < zb)
+            phi_sweep_tile<R, TX, TY, false, SYM>(kp, phi, mu, phi_out, st, tab, nullptr, nullptr, tile % kp.tgx,
+                                              tile / kp.tgx, za, zb, smem_raw, tmap_out);
     }
+    pdl_wait();
 }
 template <typename R, int TX, int TY, bool SYM>
 __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_mu_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi_old,
@@ -2096,27 +2137,59 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_mu_kernel
                                                            Partial *__restrict__ partials,
                                                            const int2 *__restrict__ splits,
                                                            const int *__restrict__ glist,
-                                                           LeanStats *__restrict__ stats)
+                                                           LeanStats *__restrict__ stats,
+                                                           Partial *__restrict__ subparts,
+                                                           unsigned *__restrict__ subcnt, int slots)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
+    pdl_wait();  // phi^{n+1} of the phi-sweep (and, through its own wait, the lean kernel)
+    pdl_trigger();
     const int ntl = kp.tgx * kp.tgy;
+    const unsigned G = __ldcg(&stats->gcount);
+    const int U = general_units(G, slots);
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
             const unsigned it = atomicAdd(&stats->gnext_mu, 1u);
-            s_item = it < *(volatile unsigned *)&stats->gcount ? glist[it] : -1;
+            s_item = it < G * (unsigned)U ? (int)it : -1;
         }
         __syncthreads();
-        const int item = s_item;
-        if (item < 0) break;
-        const int tile = item % ntl;
+        const int entry = s_item;
+        if (entry < 0) break;
+        const int item = glist[entry / U], unit = entry % U, tile = item % ntl;
         const int2 sp = splits[item];
+        int za, zb;
+        unit_range(sp.x, sp.y, U, unit, za, zb);
         // both sweeps' compulsory words: phi^n, mu^n in, phi^{n+1} out; phi^n, phi^{n+1}, mu^n in,
-        // mu^{n+1} out
-        mu_sweep_tile<R, TX, TY, false, SYM>(kp, phi_old, phi_new, mu, mu_out, st, tab, partials + item, nullptr,
-                                             nullptr, tile % kp.tgx, tile / kp.tgx, sp.x, sp.y, smem_raw, 22.0, splits,
-                                             kp.zchunk);
+        // mu^{n+1} out.  An item of one unit writes its partial directly; otherwise each unit writes
+        // its own (an empty unit a zero one) and the item's last unit to finish sums them in unit
+        // order (a fixed order, so the FP64 sums do not depend on which unit finishes last).
+        Partial *mine = U == 1 ? partials + item : subparts + (size_t)item * kMaxUnits + unit;
+        if (za < zb)
+            mu_sweep_tile<R, TX, TY, false, SYM>(kp, phi_old, phi_new, mu, mu_out, st, tab, mine, nullptr, nullptr,
+                                                 tile % kp.tgx, tile / kp.tgx, za, zb, smem_raw, 22.0, splits,
+                                                 kp.zchunk);
+        else if (threadIdx.x == 0)
+            zero_partial(mine);
+        if (U > 1 && threadIdx.x == 0) {
+            __threadfence();  // this unit's partial is visible before its arrival is counted
+            const unsigned done = atomicAdd(subcnt + item, 1u);
+            if (done == (unsigned)(U - 1)) {
+                __threadfence();
+                Partial sum;
+                sum.liq_deficit = sum.nonfinite = sum.bytes = sum.timeout = 0.0;
+                for (int u = 0; u < U; u++) {
+                    const volatile Partial *q = subparts + (size_t)item * kMaxUnits + u;
+                    sum.liq_deficit += q->liq_deficit;
+                    sum.nonfinite += q->nonfinite;
+                    sum.bytes += q->bytes;
+                    sum.timeout += q->timeout;
+                }
+                partials[item] = sum;
+                subcnt[item] = 0u;  // ready for the next step
+            }
+        }
     }
 }
 
@@ -2323,6 +2396,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(const KParams<R> kp, DevS
                                                       const Partial *__restrict__ parts, int nparts,
                                                       LeanStats *__restrict__ lean)
 {
+    pdl_wait();
+    pdl_trigger();
     finalize_body(kp, st, parts, nparts, lean);
 }
 
@@ -2389,6 +2464,8 @@ __global__ void __launch_bounds__(256) post_kernel(const KParams<R> kp, const De
                                                   PlaneT<R> *__restrict__ tab, Ph<R> *__restrict__ phi_lo,
                                                   Mu<R> *__restrict__ mu_lo, unsigned char *__restrict__ tmap)
 {
+    pdl_wait();
+    pdl_trigger();
     post_body(kp, st, phi, mu, tab, phi_lo, mu_lo, (size_t)blockIdx.x * blockDim.x + threadIdx.x,
               (size_t)gridDim.x * blockDim.x, tmap);
 }
@@ -2603,6 +2680,55 @@ __global__ void __launch_bounds__(TX *TY) classify_kernel(const KParams<R> kp, c
 // ---------------------------------------------------------------------------------------
 constexpr int kTX = 32, kTY = 8;
 
+// A set-up done once per device: a kernel's maximum dynamic shared memory is a per-device setting, so
+// every device that launches the kernel needs it.  done() tells whether the current device has been
+// set up, mark() records it.  Safe across host threads (two threads may both run the idempotent
+// set-up once); a device index beyond the table runs the set-up on every launch.
+struct DeviceOnce {
+    static constexpr int kMax = 64;
+    std::atomic<bool> flag[kMax] = {};
+    static int device()
+    {
+        int d = -1;
+        if (cudaGetDevice(&d) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        return d;
+    }
+    bool done() const
+    {
+        const int d = device();
+        return d >= 0 && d < kMax && flag[d].load(std::memory_order_acquire);
+    }
+    void mark()
+    {
+        const int d = device();
+        if (d >= 0 && d < kMax) flag[d].store(true, std::memory_order_release);
+    }
+};
+
+
+// Launch of kernel k with the programmatic stream serialisation attribute when pdl is set (the kernel
+// may then be scheduled while the one ahead of it in the stream is still running; it calls pdl_wait()
+// before it depends on that kernel's results), a plain launch otherwise.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                            Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 template <typename R>
 static size_t phi_smem_bytes()
 {
@@ -2628,13 +2754,13 @@ template <typename R>
 cudaError_t launch_phi_sweep(const KParams<R> &kp, const Geometry &g, const void *phi, const void *mu,
                              void *phi_out, const DevState *st, const PlaneT<R> *tab, cudaStream_t s)
 {
-    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
+    static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
     const size_t sm = phi_smem_bytes<R>();
-    if (!attr) {
+    if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(phi_sweep_kernel<R, kTX, kTY>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.mark();
     }
     dim3 grid(g.gx, g.gy, g.gz);
     phi_sweep_kernel<R, kTX, kTY><<<grid, kTX * kTY, sm, s>>>(kp, (const Ph<R> *)phi, (const Mu<R> *)mu,
@@ -2647,13 +2773,13 @@ cudaError_t launch_mu_sweep(const KParams<R> &kp, const Geometry &g, const void 
                             const void *mu, void *mu_out, const DevState *st, const PlaneT<R> *tab,
                             Partial *parts, cudaStream_t s)
 {
-    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
+    static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
     const size_t sm = mu_smem_bytes<R>();
-    if (!attr) {
+    if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(mu_sweep_kernel<R, kTX, kTY>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.mark();
     }
     dim3 grid(g.gx, g.gy, g.gz);
     mu_sweep_kernel<R, kTX, kTY><<<grid, kTX * kTY, sm, s>>>(kp, (const Ph<R> *)phi_old, (const Ph<R> *)phi_new,
@@ -2687,13 +2813,13 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
                               cudaStream_t s, const unsigned char *tmap_in, unsigned char *tmap_out, bool lean_here)
 {
     if ((tmap_in || tmap_out) && (kp.tgx != g.gx || kp.tgy != g.gy)) return cudaErrorInvalidValue;
-    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
+    static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
     const size_t sm = fused_smem_bytes<R>();
-    if (!attr) {
+    if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<R, kTX, kTY>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.mark();
     }
     dim3 grid(g.gx, g.gy, g.gz);
     fused_step_kernel<R, kTX, kTY><<<grid, kTX * kTY, sm, s>>>(kp, (const Ph<R> *)phi, (const Mu<R> *)mu,
@@ -2716,14 +2842,13 @@ constexpr int kLeanStages = PF_LEAN_STAGES, kLeanMaxSub = PF_LEAN_PLANES, kLeanR
 
 template <typename R>
 cudaError_t launch_plan(const KParams<R> &kp, const Geometry &g, const DevState *st, const unsigned char *tmap_in,
-                        int2 *splits, int *glist, LeanStats *stats, Partial *parts, cudaStream_t s)
+                        int2 *splits, int *glist, LeanStats *stats, Partial *parts, cudaStream_t s, bool pdl)
 {
     if (kp.tgx != g.gx || kp.tgy != g.gy) return cudaErrorInvalidValue;
     if (kp.zchunk + 4 > 64 * PLAN_PER) return cudaErrorInvalidValue;
     const int items = g.gx * g.gy * g.gz;
-    plan_kernel<kTX, kTY><<<(items + 3) / 4, 256, 0, s>>>(kp.nx, kp.ny, kp.nz, kp.tgx, kp.tgy, kp.zchunk, g.gz, st,
-                                                          tmap_in, splits, glist, stats, parts);
-    return cudaGetLastError();
+    return launch_k(plan_kernel<kTX, kTY>, dim3((items + 3) / 4), dim3(256), 0, s, pdl, kp.nx, kp.ny, kp.nz, kp.tgx,
+                    kp.tgy, kp.zchunk, g.gz, st, tmap_in, splits, glist, stats, parts);
 }
 
 template <typename R>
@@ -2732,13 +2857,13 @@ cudaError_t launch_general_step(const KParams<R> &kp, const void *phi, const voi
                                 const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits,
                                 const int *glist, LeanStats *stats, int ctas, cudaStream_t s)
 {
-    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
+    static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
     const size_t sm = fused_smem_bytes<R>();
-    if (!attr) {
+    if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(general_step_kernel<R, kTX, kTY>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.mark();
     }
     general_step_kernel<R, kTX, kTY><<<ctas, kTX * kTY, sm, s>>>(kp, (const Ph<R> *)phi, (const Mu<R> *)mu,
                                                                 (Ph<R> *)phi_out, (Mu<R> *)mu_out, st, tab, parts,
@@ -2746,38 +2871,52 @@ cudaError_t launch_general_step(const KParams<R> &kp, const void *phi, const voi
     return cudaGetLastError();
 }
 
+// Dynamic shared memory limits of the general planes' sweeps, and the largest shared-memory carveout
+// (so that as many CTAs as the registers allow fit beside each other).
+template <typename R>
+static cudaError_t general_sweep_attributes(bool sym)
+{
+    const void *kphi = sym ? (const void *)general_phi_kernel<R, kTX, kTY, true>
+                           : (const void *)general_phi_kernel<R, kTX, kTY, false>;
+    const void *kmu = sym ? (const void *)general_mu_kernel<R, kTX, kTY, true>
+                          : (const void *)general_mu_kernel<R, kTX, kTY, false>;
+    cudaError_t e = cudaFuncSetAttribute(kphi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)phi_smem_bytes<R>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kmu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mu_smem_bytes<R>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kphi, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kmu, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 template <typename R>
 cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const void *mu, void *phi_out, void *mu_out,
                                   const DevState *st, const PlaneT<R> *tab, Partial *parts, unsigned char *tmap_out,
                                   const int2 *splits, const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas,
-                                  cudaStream_t s)
+                                  cudaStream_t s, Partial *subparts, unsigned *subcnt, bool pdl, bool after_lean)
 {
-    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
+    if (!subparts || !subcnt) return cudaErrorInvalidValue;
+    const int slots = phi_ctas < mu_ctas ? phi_ctas : mu_ctas;  // both sweeps cut the items alike
+    static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
     const size_t smp = phi_smem_bytes<R>(), smm = mu_smem_bytes<R>();
-    if (!attr) {
+    if (!attr.done()) {
         cudaError_t e = cudaSuccess;
-        for (int sym = 0; sym < 2 && e == cudaSuccess; sym++) {
-            e = cudaFuncSetAttribute(sym ? general_phi_kernel<R, kTX, kTY, true> : general_phi_kernel<R, kTX, kTY, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(sym ? general_mu_kernel<R, kTX, kTY, true> : general_mu_kernel<R, kTX, kTY, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm);
-        }
+        for (int sym = 0; sym < 2 && e == cudaSuccess; sym++) e = general_sweep_attributes<R>(sym != 0);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.mark();
     }
     // the symmetric set (identity curvatures, one relaxation time) runs the instantiation compiled
     // without the general branches
     const bool sym = !kp.gen && !kp.gen_tau;
     auto kphi = sym ? general_phi_kernel<R, kTX, kTY, true> : general_phi_kernel<R, kTX, kTY, false>;
     auto kmu = sym ? general_mu_kernel<R, kTX, kTY, true> : general_mu_kernel<R, kTX, kTY, false>;
-    kphi<<<phi_ctas, kTX * kTY, smp, s>>>(kp, (const Ph<R> *)phi, (const Mu<R> *)mu, (Ph<R> *)phi_out, st, tab,
-                                          tmap_out, splits, glist, stats);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_k(kphi, dim3(phi_ctas), dim3(kTX * kTY), smp, s, pdl, kp, (const Ph<R> *)phi,
+                             (const Mu<R> *)mu, (Ph<R> *)phi_out, st, tab, tmap_out, splits, glist, stats, slots,
+                             pdl && after_lean ? 1 : 0);
     if (e != cudaSuccess) return e;
-    kmu<<<mu_ctas, kTX * kTY, smm, s>>>(kp, (const Ph<R> *)phi, (const Ph<R> *)phi_out, (const Mu<R> *)mu,
-                                        (Mu<R> *)mu_out, st, tab, parts, splits, glist, stats);
-    return cudaGetLastError();
+    return launch_k(kmu, dim3(mu_ctas), dim3(kTX * kTY), smm, s, pdl, kp, (const Ph<R> *)phi, (const Ph<R> *)phi_out,
+                    (const Mu<R> *)mu, (Mu<R> *)mu_out, st, tab, parts, splits, glist, stats, subparts, subcnt, slots);
 }
 
 template <typename R>
@@ -2785,14 +2924,11 @@ void general_sweep_ctas_per_sm(int *phi_per_sm, int *mu_per_sm)
 {
     int a = 0, b = 0;
     // the instantiation with the general branches (it needs at least the symmetric one's registers)
-    if (cudaFuncSetAttribute(general_phi_kernel<R, kTX, kTY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)phi_smem_bytes<R>()) != cudaSuccess ||
+    if (general_sweep_attributes<R>(false) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, general_phi_kernel<R, kTX, kTY, false>, kTX * kTY,
                                                       phi_smem_bytes<R>()) != cudaSuccess)
         a = 1;
-    if (cudaFuncSetAttribute(general_mu_kernel<R, kTX, kTY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)mu_smem_bytes<R>()) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, general_mu_kernel<R, kTX, kTY, false>, kTX * kTY,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, general_mu_kernel<R, kTX, kTY, false>, kTX * kTY,
                                                       mu_smem_bytes<R>()) != cudaSuccess)
         b = 1;
     cudaGetLastError();
@@ -2818,26 +2954,25 @@ int general_ctas_per_sm()
 template <typename R>
 cudaError_t launch_lean_step(const KParams<R> &kp, const Geometry &g, int nsub, const void *mu_map, const void *mu,
                              void *phi_out, void *mu_out, const DevState *st, LeanStats *stats, cudaStream_t s,
-                             const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits)
+                             const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits, bool pdl)
 {
     using L = LeanLayout<R, kTX, kTY>;
     if (!mu_map || !tmap_in || !tmap_out || !splits || nsub < 1 || kp.tgx != g.gx || kp.tgy != g.gy)
         return cudaErrorInvalidValue;
     if ((kp.zchunk + nsub - 1) / nsub > kLeanMaxSub) return cudaErrorInvalidValue;  // planes per lean CTA
     if (sizeof(R) == 4 && (kp.nx & 1)) return cudaErrorInvalidValue;  // rows must be 16-byte multiples
-    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
+    static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
     const size_t sm = L::smem_bytes(kLeanStages);
-    if (!attr) {
+    if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(lean_step_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.mark();
     }
     dim3 grid(g.gx, g.gy, g.gz * nsub);
-    lean_step_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows><<<grid, kTX * kTY / kLeanRows + 32, sm, s>>>(
-        kp, *reinterpret_cast<const CUtensorMap *>(mu_map), (const Mu<R> *)mu, (Ph<R> *)phi_out, (Mu<R> *)mu_out, st,
-        stats, tmap_out, splits, nsub);
-    return cudaGetLastError();
+    return launch_k(lean_step_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>, grid,
+                    dim3(kTX * kTY / kLeanRows + 32), sm, s, pdl, kp, *reinterpret_cast<const CUtensorMap *>(mu_map),
+                    (const Mu<R> *)mu, (Ph<R> *)phi_out, (Mu<R> *)mu_out, st, stats, tmap_out, splits, nsub);
 }
 
 #ifdef PF_FLOAT_UNIT
@@ -2846,13 +2981,13 @@ cudaError_t launch_phi_sweep_comp(const KParams<float> &kp, const Geometry &g, c
                                   const void *mu, void *phi_out, void *phi_out_lo, const DevState *st,
                                   const PlaneT<float> *tab, cudaStream_t s)
 {
-    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
+    static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
     const size_t sm = phi_smem_bytes<float>() + sizeof(Ph<float>) * 4 * kTX * kTY;
-    if (!attr) {
+    if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(phi_sweep_kernel<float, kTX, kTY, true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.mark();
     }
     dim3 grid(g.gx, g.gy, g.gz);
     phi_sweep_kernel<float, kTX, kTY, true><<<grid, kTX * kTY, sm, s>>>(
@@ -2866,13 +3001,13 @@ cudaError_t launch_mu_sweep_comp(const KParams<float> &kp, const Geometry &g, co
                                  void *mu_out_lo, const DevState *st, const PlaneT<float> *tab, Partial *parts,
                                  cudaStream_t s)
 {
-    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
+    static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
     const size_t sm = mu_smem_bytes<float>();
-    if (!attr) {
+    if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(mu_sweep_kernel<float, kTX, kTY, true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.mark();
     }
     dim3 grid(g.gx, g.gy, g.gz);
     mu_sweep_kernel<float, kTX, kTY, true><<<grid, kTX * kTY, sm, s>>>(
@@ -2886,13 +3021,13 @@ template <typename R>
 cudaError_t launch_batched_step(const BatchDomain<R> *doms, int ndoms, const BatchItem *items, int nitems,
                                 unsigned *counter, int parity, int ctas, int post_blocks, cudaStream_t s)
 {
-    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
+    static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
     const size_t sm = fused_smem_bytes<R>();
-    if (!attr) {
+    if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(batched_fused_kernel<R, kTX, kTY>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.mark();
     }
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
@@ -2911,10 +3046,10 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
                                      bool sym)
 {
     using L = LeanLayout<R, kTX, kTY>;
-    static std::atomic<bool> attr{false};  // the one-time attribute setup, safe across host threads
+    static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
     const size_t smp = phi_smem_bytes<R>(), smm = mu_smem_bytes<R>(), sml = L::smem_bytes(kLeanStages);
     const size_t smf = fused_smem_bytes<R>();
-    if (!attr) {
+    if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 0, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
         if (e == cudaSuccess)
@@ -2933,7 +3068,7 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
             e = cudaFuncSetAttribute(batched_fused_kernel<R, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smf);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.mark();
     }
     cudaError_t e = cudaMemsetAsync(plan, 0, sizeof(BatchPlan), s);
     if (e != cudaSuccess) return e;
@@ -2996,21 +3131,19 @@ int fused_ctas_per_sm()
 
 template <typename R>
 cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s,
-                            LeanStats *lean)
+                            LeanStats *lean, bool pdl)
 {
-    finalize_kernel<R><<<1, 256, 0, s>>>(kp, st, parts, nparts, lean);
-    return cudaGetLastError();
+    return launch_k(finalize_kernel<R>, dim3(1), dim3(256), 0, s, pdl, kp, st, parts, nparts, lean);
 }
 
 template <typename R>
 cudaError_t launch_post(const KParams<R> &kp, const DevState *st, void *phi, void *mu, PlaneT<R> *tab,
-                        cudaStream_t s, void *phi_lo, void *mu_lo, unsigned char *tmap)
+                        cudaStream_t s, void *phi_lo, void *mu_lo, unsigned char *tmap, bool pdl)
 {
     // enough threads to fill one full plane per thread-sweep when the window moves
     const size_t work = (size_t)kp.nx * kp.ny;
-    post_kernel<R><<<grid1d(work > (size_t)2 * kp.nz ? work : (size_t)2 * kp.nz), 256, 0, s>>>(
-        kp, st, (Ph<R> *)phi, (Mu<R> *)mu, tab, (Ph<R> *)phi_lo, (Mu<R> *)mu_lo, tmap);
-    return cudaGetLastError();
+    return launch_k(post_kernel<R>, dim3(grid1d(work > (size_t)2 * kp.nz ? work : (size_t)2 * kp.nz)), dim3(256), 0,
+                    s, pdl, kp, st, (Ph<R> *)phi, (Mu<R> *)mu, tab, (Ph<R> *)phi_lo, (Mu<R> *)mu_lo, tmap);
 }
 
 template <typename R>
@@ -3093,10 +3226,10 @@ cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const voi
                                             cudaStream_t);                                                       \
     template cudaError_t launch_lean_step<R>(const KParams<R> &, const Geometry &, int, const void *, const void *, \
                                              void *, void *, const DevState *, LeanStats *, cudaStream_t,          \
-                                             const unsigned char *, unsigned char *, const int2 *);                \
+                                             const unsigned char *, unsigned char *, const int2 *, bool);          \
     template cudaError_t launch_plan<R>(const KParams<R> &, const Geometry &, const DevState *,                  \
                                         const unsigned char *, int2 *, int *, LeanStats *, Partial *,            \
-                                        cudaStream_t);                                                           \
+                                        cudaStream_t, bool);                                                     \
     template cudaError_t launch_general_step<R>(const KParams<R> &, const void *, const void *, void *, void *,  \
                                                 const DevState *, const PlaneT<R> *, Partial *,                  \
                                                 const unsigned char *, unsigned char *, const int2 *, const int *, \
@@ -3104,7 +3237,8 @@ cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const voi
     template int general_ctas_per_sm<R>();                                                                       \
     template cudaError_t launch_general_sweeps<R>(const KParams<R> &, const void *, const void *, void *, void *, \
                                                   const DevState *, const PlaneT<R> *, Partial *, unsigned char *, \
-                                                  const int2 *, const int *, LeanStats *, int, int, cudaStream_t); \
+                                                  const int2 *, const int *, LeanStats *, int, int, cudaStream_t, \
+                                                  Partial *, unsigned *, bool, bool);                              \
     template void general_sweep_ctas_per_sm<R>(int *, int *);                                                    \
     template cudaError_t launch_batched_step<R>(const BatchDomain<R> *, int, const BatchItem *, int, unsigned *, \
                                                 int, int, int, cudaStream_t);                                    \
@@ -3114,9 +3248,9 @@ cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const voi
                                                      unsigned *, int, int, int, cudaStream_t, bool);                \
     template void batched_general_ctas_per_sm<R>(int *, int *);                                                  \
     template cudaError_t launch_finalize<R>(const KParams<R> &, DevState *, const Partial *, int, cudaStream_t,   \
-                                            LeanStats *);                                                        \
+                                            LeanStats *, bool);                                                  \
     template cudaError_t launch_post<R>(const KParams<R> &, const DevState *, void *, void *, PlaneT<R> *,       \
-                                        cudaStream_t, void *, void *, unsigned char *);                          \
+                                        cudaStream_t, void *, void *, unsigned char *, bool);                    \
     template cudaError_t launch_init<R>(const KParams<R> &, void *, void *, const double *, int, int,            \
                                         cudaStream_t);                                                           \
     template cudaError_t launch_reduce<R>(const KParams<R> &, const DevState *, const void *, const void *,      \

@@ -555,6 +555,8 @@ __global__ void __launch_bounds__(TX *TY / ROWS + 32, sizeof(R) == 4 ? PF_LEAN_M
     Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st,
     LeanStats *__restrict__ stats, unsigned char *__restrict__ tmap_out, const int2 *__restrict__ splits, int nsub)
 {
+    pdl_wait();  // the step's plan; every CTA has passed it before the kernel behind may be scheduled
+    pdl_trigger();
     lean_tile<R, TX, TY, LD, MAXSUB, ROWS>(kp, &mu_map, mu, phi_out, mu_out, st, stats, tmap_out, splits, nsub,
                                            blockIdx.x, blockIdx.y, blockIdx.z);
 }
