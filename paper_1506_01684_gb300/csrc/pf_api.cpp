@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -444,6 +445,16 @@ static bool use_fused(const pf_sim *s)
 // The fused step trusts the liquid maps of both field buffers: the source's to find the
 // pure-liquid planes, the destination's (which describes the field two steps back) to skip the
 // phi stores of planes that stay pure liquid.  Rebuild whichever map is stale.
+// A rebuilt liquid map (the fields changed outside the lean path) makes the device-side plan stale: the
+// next plan kernel lists the items afresh.
+static cudaError_t invalidate_plan(pf_sim *s, cudaStream_t stream)
+{
+    unsigned char *ls = (unsigned char *)s->lean_stats.p;
+    cudaError_t e = cudaMemsetAsync(ls + offsetof(LeanStats, plan_valid), 0, sizeof(int), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ls + offsetof(LeanStats, gcount), 0, sizeof(unsigned), stream);
+    return e;
+}
+
 template <typename R>
 static cudaError_t ensure_maps(pf_sim *s, cudaStream_t stream)
 {
@@ -452,6 +463,7 @@ static cudaError_t ensure_maps(pf_sim *s, cudaStream_t stream)
         if (s->tmap_ok[b]) continue;
         cudaError_t e = launch_classify<R>(kp, (const DevState *)s->state.p, s->phi[b].p,
                                            (unsigned char *)s->tmap[b].p, stream);
+        if (e == cudaSuccess) e = invalidate_plan(s, stream);
         if (e != cudaSuccess) return e;
         s->tmap_ok[b] = true;
     }
@@ -496,7 +508,7 @@ static int do_step_direct(pf_sim *s, int n)
                     if (PF_GENERAL_SWEEPS)
                         return timed(s, PF_K_GENERAL, [&] {
                             return launch_general_sweeps<R>(kp, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st,
-                                                            tab, parts, tout, (const int2 *)s->splits.p,
+                                                            tab, parts, tin, tout, (const int2 *)s->splits.p,
                                                             (const int *)s->glist.p, ls, s->gphi_ctas, s->gmu_ctas,
                                                             s->stream, (Partial *)s->subparts.p,
                                                             (unsigned *)s->subcnt.p, pdl, true);

@@ -41,7 +41,11 @@ struct LeanStats {
     int timeout;                    // a bounded wait gave up
     unsigned long long last_bytes;  // bytes of the last finished step (read by the host)
     unsigned gcount, gnext;         // (tile, chunk) items with general planes; next one to take
-    unsigned gnext_mu, pad_;        // next item of the general planes' mu-sweep
+    unsigned gnext_mu;              // next item of the general planes' mu-sweep
+    int map_changed;                // a liquid-map entry of the new field differs from the source's
+    int plan_valid;                 // the plan (splits, item list, zeroed partials) describes the
+                                    // current source field: the next plan kernel has nothing to do
+    int pad_;
 };
 
 // Temperature-dependent constants of one x-y plane (cell centres) or one z-face level,
@@ -185,7 +189,8 @@ int general_ctas_per_sm();
 // one counter per item, zero between steps).
 template <typename R>
 cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const void *mu, void *phi_out, void *mu_out,
-                                  const DevState *st, const PlaneT<R> *tab, Partial *parts, unsigned char *tmap_out,
+                                  const DevState *st, const PlaneT<R> *tab, Partial *parts,
+                                  const unsigned char *tmap_in, unsigned char *tmap_out,
                                   const int2 *splits, const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas,
                                   cudaStream_t s, Partial *subparts, unsigned *subcnt, bool pdl = false,
                                   bool after_lean = false);  // after_lean: launched right behind the lean kernel

@@ -808,7 +808,9 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
                                                const DevState *__restrict__ st, const PlaneT<R> *__restrict__ tab,
                                                const Ph<R> *__restrict__ phi_lo, Ph<R> *__restrict__ phi_out_lo,
                                                int bx, int by, int z0, int z1, unsigned char *__restrict__ smem_raw,
-                                               unsigned char *__restrict__ tmap_out = nullptr)
+                                               unsigned char *__restrict__ tmap_out = nullptr,
+                                               const unsigned char *__restrict__ tmap_in = nullptr,
+                                               int *__restrict__ map_changed = nullptr)
 {
     constexpr int NT = TX * TY, SX = TX + 2, SY = TY + 2, SN = SX * SY, NR = SN - NT;
     constexpr int FX = TY * (TX + 1), FY = (TY + 1) * TX;
@@ -928,7 +930,12 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
         if (tmap_out) {
             // the barrier also gives the map entry of the new plane p
             const int all = __syncthreads_and(out_liquid);
-            if (tid == 0) tmap_out[map_idx((int)(plane_off(p, nz, zbase, plane) / plane), by * kp.tgx + bx, nz)] = all ? 1 : 0;
+            if (tid == 0) {
+                const size_t mi = map_idx((int)(plane_off(p, nz, zbase, plane) / plane), by * kp.tgx + bx, nz);
+                tmap_out[mi] = all ? 1 : 0;
+                // a tile plane whose pure-liquid status changed invalidates the step's plan
+                if (map_changed && tmap_in[mi] != (all ? 1 : 0)) atomicOr(map_changed, 1);
+            }
         } else {
             __syncthreads();
         }
@@ -1015,34 +1022,42 @@ __device__ __forceinline__ void mu_sweep_tile(const KParams<R> &kp, const Ph<R> 
     Ph<R> pfN0, pfN1, pfO0, pfO1;
     Mu<R> pfM0, pfM1;
     auto mod3 = [](int k) { return (k + 3) % 3; };  // k >= -3
-    // whether tile t's (logical, clamped) plane k is a lean plane of the step's plan
-    auto lean_plane = [&](int t, int k) {
-        const int kc = k < 0 ? 0 : (k >= nz ? nz - 1 : k);
-        const int2 sp = splits[(kc / split_zchunk) * ntl + t];
-        return kc < sp.x || kc >= sp.y;
-    };
+    // Whether the prefetched plane of this thread's own and ring cell is a lean plane of the step's
+    // plan (phi^{n+1} = e_l by construction there: not read, substituted when stored to shared
+    // memory).  The splits of the two tiles are kept for the current z chunk, so that no global load
+    // sits between a prefetch and the compute it is meant to overlap.
+    bool leanN0 = false, leanN1 = false;
+    int sp_chunk = -1;
+    int2 sp0 = make_int2(0, 0), sp1 = make_int2(0, 0);
     auto prefetch = [&](int k) {
         const size_t b = plane_off(k, nz, zbase, plane);
-        pfN0 = ldg_ph(phi_new + b + col0);
+        if (splits) {
+            const int kc = k < 0 ? 0 : (k >= nz ? nz - 1 : k);
+            const int ch = kc / split_zchunk;  // the same for every thread of the CTA
+            if (ch != sp_chunk) {
+                sp_chunk = ch;
+                sp0 = splits[ch * ntl + tile0];
+                if (s1 >= 0) sp1 = splits[ch * ntl + tile1];
+            }
+            leanN0 = kc < sp0.x || kc >= sp0.y;
+            leanN1 = s1 >= 0 && (kc < sp1.x || kc >= sp1.y);
+        }
+        if (!leanN0) pfN0 = ldg_ph(phi_new + b + col0);
         pfO0 = ldg_ph(phi_old + b + col0);
         pfM0 = ldg_mu(mu + b + col0);
         if (s1 >= 0) {
-            pfN1 = ldg_ph(phi_new + b + col1);
+            if (!leanN1) pfN1 = ldg_ph(phi_new + b + col1);
             pfO1 = ldg_ph(phi_old + b + col1);
             pfM1 = ldg_mu(mu + b + col1);
         }
-        if (splits) {
-            Ph<R> liq;
-            liq.v[0] = liq.v[1] = liq.v[2] = R(0);
-            liq.v[3] = R(1);
-            if (lean_plane(tile0, k)) pfN0 = liq;
-            if (s1 >= 0 && lean_plane(tile1, k)) pfN1 = liq;
-        }
     };
     auto commitN = [&](int k) {
+        Ph<R> liq;
+        liq.v[0] = liq.v[1] = liq.v[2] = R(0);
+        liq.v[3] = R(1);
         Ph<R> *d = sN + (k & 3) * SN;
-        d[s0] = pfN0;
-        if (s1 >= 0) d[s1] = pfN1;
+        d[s0] = leanN0 ? liq : pfN0;
+        if (s1 >= 0) d[s1] = leanN1 ? liq : pfN1;
     };
     auto commitOM = [&](int k) {
         const int o = mod3(k) * SN;
@@ -1511,6 +1526,9 @@ __global__ void __launch_bounds__(256) plan_kernel(int nx, int ny, int nz, int t
     __shared__ int kred[8][2];
     pdl_wait();  // the previous step's post kernel (window fill, map entries, zbase)
     pdl_trigger();
+    // No liquid-map entry changed and the window did not move since the last plan: its splits, list
+    // and zeroed partials still hold (finalize keeps the list then)
+    if (*(volatile int *)&stats->plan_valid) return;
     const int item = blockIdx.x * 4 + (threadIdx.x >> 6);
     const bool live = item < tgx * tgy * gz;
     int lo_end, hi_beg;
@@ -2091,6 +2109,7 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_phi_kerne
                                                             const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
                                                             const DevState *__restrict__ st,
                                                             const PlaneT<R> *__restrict__ tab,
+                                                            const unsigned char *__restrict__ tmap_in,
                                                             unsigned char *__restrict__ tmap_out,
                                                             const int2 *__restrict__ splits,
                                                             const int *__restrict__ glist,
@@ -2124,7 +2143,8 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_phi_kerne
         unit_range(sp.x, sp.y, U, unit, za, zb);
         if (za < zb)
             phi_sweep_tile<R, TX, TY, false, SYM>(kp, phi, mu, phi_out, st, tab, nullptr, nullptr, tile % kp.tgx,
-                                              tile / kp.tgx, za, zb, smem_raw, tmap_out);
+                                              tile / kp.tgx, za, zb, smem_raw, tmap_out, tmap_in,
+                                              &stats->map_changed);
     }
     pdl_wait();
 }
@@ -2366,7 +2386,6 @@ __device__ __forceinline__ void finalize_body(const KParams<R> &kp, DevState *__
             lean->bytes = 0ull;
             lean->nonfinite = 0;
             lean->timeout = 0;
-            lean->gcount = 0u;
             lean->gnext = 0u;
             lean->gnext_mu = 0u;
         }
@@ -2381,6 +2400,14 @@ __device__ __forceinline__ void finalize_body(const KParams<R> &kp, DevState *__
             if (s < 0) s = 0;
         }
         st->shift = s;
+        if (lean) {
+            // the plan of this step still holds for the new field unless a liquid-map entry changed or
+            // the window moves; otherwise the next plan kernel lists the items afresh
+            const int valid = lean->map_changed == 0 && s == 0 ? 1 : 0;
+            lean->plan_valid = valid;
+            if (!valid) lean->gcount = 0u;
+            lean->map_changed = 0;
+        }
         if (s > 0) {
             int zb = st->zbase + s;
             if (zb >= kp.nz) zb -= kp.nz;
@@ -2892,7 +2919,8 @@ static cudaError_t general_sweep_attributes(bool sym)
 
 template <typename R>
 cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const void *mu, void *phi_out, void *mu_out,
-                                  const DevState *st, const PlaneT<R> *tab, Partial *parts, unsigned char *tmap_out,
+                                  const DevState *st, const PlaneT<R> *tab, Partial *parts,
+                                  const unsigned char *tmap_in, unsigned char *tmap_out,
                                   const int2 *splits, const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas,
                                   cudaStream_t s, Partial *subparts, unsigned *subcnt, bool pdl, bool after_lean)
 {
@@ -2912,8 +2940,8 @@ cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const v
     auto kphi = sym ? general_phi_kernel<R, kTX, kTY, true> : general_phi_kernel<R, kTX, kTY, false>;
     auto kmu = sym ? general_mu_kernel<R, kTX, kTY, true> : general_mu_kernel<R, kTX, kTY, false>;
     cudaError_t e = launch_k(kphi, dim3(phi_ctas), dim3(kTX * kTY), smp, s, pdl, kp, (const Ph<R> *)phi,
-                             (const Mu<R> *)mu, (Ph<R> *)phi_out, st, tab, tmap_out, splits, glist, stats, slots,
-                             pdl && after_lean ? 1 : 0);
+                             (const Mu<R> *)mu, (Ph<R> *)phi_out, st, tab, tmap_in, tmap_out, splits, glist, stats,
+                             slots, pdl && after_lean ? 1 : 0);
     if (e != cudaSuccess) return e;
     return launch_k(kmu, dim3(mu_ctas), dim3(kTX * kTY), smm, s, pdl, kp, (const Ph<R> *)phi, (const Ph<R> *)phi_out,
                     (const Mu<R> *)mu, (Mu<R> *)mu_out, st, tab, parts, splits, glist, stats, subparts, subcnt, slots);
@@ -3236,7 +3264,8 @@ cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const voi
                                                 LeanStats *, int, cudaStream_t);                                 \
     template int general_ctas_per_sm<R>();                                                                       \
     template cudaError_t launch_general_sweeps<R>(const KParams<R> &, const void *, const void *, void *, void *, \
-                                                  const DevState *, const PlaneT<R> *, Partial *, unsigned char *, \
+                                                  const DevState *, const PlaneT<R> *, Partial *,                  \
+                                                  const unsigned char *, unsigned char *,                           \
                                                   const int2 *, const int *, LeanStats *, int, int, cudaStream_t, \
                                                   Partial *, unsigned *, bool, bool);                              \
     template void general_sweep_ctas_per_sm<R>(int *, int *);                                                    \

@@ -544,7 +544,10 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
         const unsigned long long b = tile_cells * sizeof(R) * 4ull * (unsigned long long)(planes + phi_stores);
         if (b) atomicAdd(&stats->bytes, b);
         if (s_bad) atomicOr(&stats->nonfinite, 1);
-        if (s_abort) atomicOr(&stats->timeout, 1);
+        if (s_abort) {
+            atomicOr(&stats->timeout, 1);
+            atomicOr(&stats->map_changed, 1);  // its planes' map entries were set to 0 ("not known")
+        }
     }
 }
 
