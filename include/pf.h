@@ -254,8 +254,12 @@ int pf_test_withhold_copies(pf_sim *sim, int on);
  * Algorithm 1 as two kernels (the phi-sweep writes
  * phi^{n+1}, the mu-sweep reads it back: 88 algorithmic bytes per FP32 cell); FUSED computes
  * phi^{n+1} and mu^{n+1} in one pass (each CTA recomputes phi^{n+1} on a one-cell ring around its
- * tile: 48 bytes per FP32 cell).  Both give the same result up to rounding order.  AUTO (the
- * default) picks the variant measured fastest for the precision. */
+ * tile: 48 bytes per FP32 cell); where the lean kernel can run (FP64, and FP32 with an even nx), FUSED
+ * and AUTO take the lean path instead: the plan splits each tile's z chunk into pure-liquid planes (the
+ * lean kernel, 16 bytes per FP32 cell) and general planes (the two sweeps).  All give the same result
+ * up to rounding order.  AUTO (the default) takes the lean path wherever it can run, in every precision
+ * (compensated FP32 included), else the fused tile in FP32 and the two sweeps otherwise: a fixed rule,
+ * so that a run resumed from a checkpoint takes the same kernels as the uninterrupted run. */
 enum { PF_VARIANT_AUTO = 0, PF_VARIANT_UNFUSED = 1, PF_VARIANT_FUSED = 2 };
 int pf_set_variant(pf_sim *sim, int variant);
 

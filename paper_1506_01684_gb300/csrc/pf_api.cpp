@@ -130,7 +130,7 @@ struct pf_sim {
     bool tmap_ok[2] = {false, false};
     // TMA tensor maps of the two mu buffers for the lean kernel (the fused step's pure-liquid
     // planes); lean_ok when both could be encoded (FP32 rows must be 16-byte multiples: nx even)
-    CUtensorMap mu_map[2];
+    LeanMaps mu_map[2];
     DevBuf lean_stats;  // LeanStats
     DevBuf splits;      // int2 per (tile, chunk) of the fused grid: the lean / general split
     DevBuf glist;       // int per (tile, chunk): the items with general planes
@@ -188,21 +188,29 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// Tensor map of one mu buffer for the lean kernel: 3D (2 nx words, ny rows, nz storage planes),
-// box of (TX + 4) cells x (TY + 2) rows x 1 plane, zero fill outside (the kernel copies the
-// periodic images there itself).  False when the layout does not allow it.
-static bool encode_mu_map(CUtensorMap *m, void *base, int nx, int ny, int nz, size_t w, int tx, int ty)
+// Tensor maps of one mu buffer for the lean kernel (LeanMaps): 3D (2 nx words, ny rows, nz storage
+// planes), boxes of (TX + 4) cells x (TY + 2) rows (the tile with its halo), 2 cells x TY rows (the
+// periodic x images) and (TX + 4) cells x 1 row (the periodic y images); zero fill outside.  False when
+// the layout does not allow them (rows must be 16-byte multiples).
+static bool encode_lean_maps(LeanMaps *m, void *base, int nx, int ny, int nz, size_t w, int tx, int ty)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || !base || ((uintptr_t)base & 15) || ((size_t)2 * nx * w) % 16 != 0) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)2 * nx, (cuuint64_t)ny, (cuuint64_t)nz};
     const cuuint64_t strides[2] = {(cuuint64_t)2 * nx * w, (cuuint64_t)2 * nx * ny * w};
-    const cuuint32_t box[3] = {(cuuint32_t)(2 * (tx + 4)), (cuuint32_t)(ty + 2), 1};
     const cuuint32_t es[3] = {1, 1, 1};
-    const CUresult r = enc(m, w == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
-                           dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
+    const cuuint32_t boxes[3][3] = {{(cuuint32_t)(2 * (tx + 4)), (cuuint32_t)(ty + 2), 1},
+                                    {4, (cuuint32_t)ty, 1},
+                                    {(cuuint32_t)(2 * (tx + 4)), 1, 1}};
+    CUtensorMap *out[3] = {&m->box, &m->ximg, &m->yimg};
+    for (int k = 0; k < 3; k++) {
+        const CUresult r = enc(out[k], w == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                               base, dims, strides, boxes[k], es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
 }
 
 namespace pf {
@@ -434,12 +442,19 @@ static cudaError_t timed(pf_sim *s, int cls, F &&f, cudaStream_t st = nullptr)
     return e;
 }
 
+// AUTO: the lean path (plan, lean kernel, general planes' sweeps) wherever the lean kernel's tensor maps
+// exist, in every precision (measured on 256x256x1024 after 2000 steps: FP64 11.5 against 2.1 GLUP/s with
+// the two whole-domain sweeps, compensated FP32 130 against 22); without them the fused tile in FP32
+// and the two sweeps otherwise.  A fixed rule, not a timing: a run resumed from a checkpoint takes the
+// same kernels as the uninterrupted run.
 static bool use_fused(const pf_sim *s)
 {
-    if (s->comp()) return false;  // the compensated state runs on the two sweeps
+    // the compensated state has a lean path (lean kernel and general planes' sweeps with the low
+    // words), but no fused tile: without the lean path it runs on the two sweeps
+    if (s->comp()) return s->lean_ok && s->variant != PF_VARIANT_UNFUSED;
     if (s->variant == PF_VARIANT_FUSED) return true;
     if (s->variant == PF_VARIANT_UNFUSED) return false;
-    return s->p.precision == PF_FP32;  // AUTO: fused for FP32 (measured faster), the two sweeps for FP64
+    return s->lean_ok || s->p.precision == PF_FP32;
 }
 
 // The fused step trusts the liquid maps of both field buffers: the source's to find the
@@ -462,7 +477,7 @@ static cudaError_t ensure_maps(pf_sim *s, cudaStream_t stream)
     for (int b = 0; b < 2; b++) {
         if (s->tmap_ok[b]) continue;
         cudaError_t e = launch_classify<R>(kp, (const DevState *)s->state.p, s->phi[b].p,
-                                           (unsigned char *)s->tmap[b].p, stream);
+                                           (unsigned char *)s->tmap[b].p, stream, s->lo_phi(b));
         if (e == cudaSuccess) e = invalidate_plan(s, stream);
         if (e != cudaSuccess) return e;
         s->tmap_ok[b] = true;
@@ -511,7 +526,8 @@ static int do_step_direct(pf_sim *s, int n)
                                                             tab, parts, tin, tout, (const int2 *)s->splits.p,
                                                             (const int *)s->glist.p, ls, s->gphi_ctas, s->gmu_ctas,
                                                             s->stream, (Partial *)s->subparts.p,
-                                                            (unsigned *)s->subcnt.p, pdl, true);
+                                                            (unsigned *)s->subcnt.p, pdl, true, s->lo_phi(a),
+                                                            s->lo_phi(b), s->lo_mu(a), s->lo_mu(b));
                         });
                     return timed(s, PF_K_FUSED, [&] {
                         return launch_general_step<R>(kp, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st, tab,
@@ -523,7 +539,8 @@ static int do_step_direct(pf_sim *s, int n)
                     return timed(s, PF_K_LEAN, [&] {
                         return launch_lean_step<R>(kp, s->geo_fused, s->lean_nsub, &s->mu_map[a], s->mu[a].p,
                                                    s->phi[b].p, s->mu[b].p, st, ls, s->stream, tin, tout,
-                                                   (const int2 *)s->splits.p, pdl);
+                                                   (const int2 *)s->splits.p, pdl, s->lo_mu(a), s->lo_phi(b),
+                                                   s->lo_mu(b));
                     });
                 };
                 if (e == cudaSuccess)
@@ -1177,11 +1194,11 @@ int pf_create(int nx, int ny, int nz, const pf_params *p, void *stream, pf_sim *
         cudaError_t e = cudaMemsetAsync(s->lean_stats.p, 0, sizeof(LeanStats), s->stream);
         if (e != cudaSuccess) r = cuda_status(e);
     }
-    if (r == PF_OK && !s->comp()) {
-        // the compensated state never takes the fused step
+    if (r == PF_OK) {
+        // the lean kernel's tensor maps of the two mu buffers (the compensated state: its high words)
         s->lean_ok = true;
         for (int b = 0; b < 2; b++)
-            s->lean_ok = s->lean_ok && encode_mu_map(&s->mu_map[b], s->mu[b].p, nx, ny, nz, w, s->geo_fused.tx,
+            s->lean_ok = s->lean_ok && encode_lean_maps(&s->mu_map[b], s->mu[b].p, nx, ny, nz, w, s->geo_fused.tx,
                                                      s->geo_fused.ty);
     }
     if (r == PF_OK) r = dev_alloc(s->tab, tabsz, s->stream);

@@ -94,12 +94,20 @@ struct KParams {
     double K64[4][3];   // K_a in FP64 (reductions)
 };
 
+// The lean kernel's tensor maps of one mu buffer, all over the same 3D tensor (2 nx words, ny rows,
+// nz storage planes): the tile box with its one-cell halo (TX + 4 cells x TY + 2 rows), the box of the
+// periodic x images (2 cells x TY rows: the wrapped column at x = -1 or x = nx) and the box of the
+// periodic y images (TX + 4 cells x 1 row: the wrapped row at y = -1 or y = ny).
+struct alignas(64) LeanMaps {
+    CUtensorMap box, ximg, yimg;
+};
+
 // One domain of a batched step: its parameters, ping-pong field buffers, state, plane table and
 // partial sums, and its fused-step tile grid; for the lean path also the TMA tensor maps of its mu
 // buffers, its plan (splits per (tile, chunk)) and its lean statistics.
 template <typename R>
 struct alignas(128) BatchDomain {  // the alignment of its tensor maps
-    CUtensorMap mu_map[2];   // TMA maps of mu[0], mu[1] (lean path)
+    LeanMaps mu_map[2];      // TMA maps of mu[0], mu[1] (lean path)
     KParams<R> kp;
     void *phi[2], *mu[2];
     unsigned char *tmap[2];  // liquid maps of the two field buffers
@@ -120,7 +128,10 @@ struct BatchItem {
 };
 
 // Most work units an item of the general planes is cut into (the general planes' sweeps, pf_kernels.cuh).
-constexpr int kMaxUnits = 8;
+#ifndef PF_MAX_UNITS
+#define PF_MAX_UNITS 8
+#endif
+constexpr int kMaxUnits = PF_MAX_UNITS;
 
 // Launch geometry of the sweep kernels.
 struct Geometry {
@@ -158,14 +169,15 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
                               unsigned char *tmap_out = nullptr, bool lean_here = true);
 // The pure-liquid planes of the fused step (lean_step_kernel), launched beside the fused kernel
 // run with lean_here = 0: grid (tgx, tgy, gz * nsub), one CTA per tile and sub-chunk of a z chunk.
-// mu_map: TMA tensor map of the source mu buffer (3D: 2 nx words, ny, nz); stats: the sim's lean
+// mu_map: the LeanMaps of the source mu buffer (3D: 2 nx words, ny, nz); stats: the sim's lean
 // statistics (folded in by the next finalize).  Returns cudaErrorInvalidValue when the map layout
 // or the chunking does not fit the kernel.
 template <typename R>
 cudaError_t launch_lean_step(const KParams<R> &kp, const Geometry &g, int nsub, const void *mu_map, const void *mu,
                              void *phi_out, void *mu_out, const DevState *st, LeanStats *stats, cudaStream_t s,
                              const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits,
-                             bool pdl = false);
+                             bool pdl = false, const void *mu_lo = nullptr, void *phi_out_lo = nullptr,
+                             void *mu_out_lo = nullptr);  // compensated FP32: the low words
 // Plan of a fused step with the lean kernel (plan_kernel): each (tile, chunk) item's split into
 // lean and general planes (splits, gx*gy*gz), the list of items with general planes (glist,
 // count in stats->gcount; finalize resets the counters), zeroed partials for the all-lean items.
@@ -193,13 +205,15 @@ cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const v
                                   const unsigned char *tmap_in, unsigned char *tmap_out,
                                   const int2 *splits, const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas,
                                   cudaStream_t s, Partial *subparts, unsigned *subcnt, bool pdl = false,
-                                  bool after_lean = false);  // after_lean: launched right behind the lean kernel
+                                  bool after_lean = false,  // after_lean: launched right behind the lean kernel
+                                  const void *phi_lo = nullptr, void *phi_out_lo = nullptr,  // compensated FP32:
+                                  const void *mu_lo = nullptr, void *mu_out_lo = nullptr);   // the low words
 template <typename R>
 void general_sweep_ctas_per_sm(int *phi_per_sm, int *mu_per_sm);
 // liquid map of a field (for states not produced by a fused step)
 template <typename R>
 cudaError_t launch_classify(const KParams<R> &kp, const DevState *st, const void *phi, unsigned char *tmap,
-                            cudaStream_t s);
+                            cudaStream_t s, const void *phi_lo = nullptr);  // phi_lo: compensated low words
 template <typename R>
 cudaError_t launch_finalize(const KParams<R> &kp, DevState *st, const Partial *parts, int nparts, cudaStream_t s,
                             LeanStats *lean = nullptr, bool pdl = false);

@@ -917,6 +917,9 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
                 if constexpr (COMP) st_ph(phi_out_lo + plane_off(p, nz, zbase, plane) + col0, out_lo);
             }
             out_liquid = !valid || (out.v[3] == R(1) && out.v[0] == R(0) && out.v[1] == R(0) && out.v[2] == R(0));
+            if constexpr (COMP)  // exactly pure liquid: zero low words too
+                out_liquid = out_liquid && (!valid || (out_lo.v[0] == R(0) && out_lo.v[1] == R(0) &&
+                                                       out_lo.v[2] == R(0) && out_lo.v[3] == R(0)));
         }
         // B(p+1), A(p+3)
         Ph<R> Fz_next = Fz_cur;
@@ -1528,7 +1531,10 @@ __global__ void __launch_bounds__(256) plan_kernel(int nx, int ny, int nz, int t
     pdl_trigger();
     // No liquid-map entry changed and the window did not move since the last plan: its splits, list
     // and zeroed partials still hold (finalize keeps the list then)
-    if (*(volatile int *)&stats->plan_valid) return;
+#ifndef PF_PLAN_REUSE
+#define PF_PLAN_REUSE 1
+#endif
+    if (PF_PLAN_REUSE && *(volatile int *)&stats->plan_valid) return;
     const int item = blockIdx.x * 4 + (threadIdx.x >> 6);
     const bool live = item < tgx * tgy * gz;
     int lo_end, hi_beg;
@@ -2104,7 +2110,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) general_step_k
 #ifndef PF_GENERAL_MIN_CTAS
 #define PF_GENERAL_MIN_CTAS 2
 #endif
-template <typename R, int TX, int TY, bool SYM>
+template <typename R, int TX, int TY, bool SYM, bool COMP = false>
 __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_phi_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
                                                             const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
                                                             const DevState *__restrict__ st,
@@ -2114,7 +2120,8 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_phi_kerne
                                                             const int2 *__restrict__ splits,
                                                             const int *__restrict__ glist,
                                                             LeanStats *__restrict__ stats, int slots,
-                                                            int after_lean)
+                                                            int after_lean, const Ph<R> *__restrict__ phi_lo,
+                                                            Ph<R> *__restrict__ phi_out_lo)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -2142,13 +2149,13 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_phi_kerne
         int za, zb;
         unit_range(sp.x, sp.y, U, unit, za, zb);
         if (za < zb)
-            phi_sweep_tile<R, TX, TY, false, SYM>(kp, phi, mu, phi_out, st, tab, nullptr, nullptr, tile % kp.tgx,
-                                              tile / kp.tgx, za, zb, smem_raw, tmap_out, tmap_in,
-                                              &stats->map_changed);
+            phi_sweep_tile<R, TX, TY, COMP, SYM>(kp, phi, mu, phi_out, st, tab, phi_lo, phi_out_lo, tile % kp.tgx,
+                                                 tile / kp.tgx, za, zb, smem_raw, tmap_out, tmap_in,
+                                                 &stats->map_changed);
     }
     pdl_wait();
 }
-template <typename R, int TX, int TY, bool SYM>
+template <typename R, int TX, int TY, bool SYM, bool COMP = false>
 __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_mu_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi_old,
                                                            const Ph<R> *__restrict__ phi_new,
                                                            const Mu<R> *__restrict__ mu, Mu<R> *__restrict__ mu_out,
@@ -2159,7 +2166,9 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_mu_kernel
                                                            const int *__restrict__ glist,
                                                            LeanStats *__restrict__ stats,
                                                            Partial *__restrict__ subparts,
-                                                           unsigned *__restrict__ subcnt, int slots)
+                                                           unsigned *__restrict__ subcnt, int slots,
+                                                           const Mu<R> *__restrict__ mu_lo,
+                                                           Mu<R> *__restrict__ mu_out_lo)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -2186,10 +2195,11 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_mu_kernel
         // its own (an empty unit a zero one) and the item's last unit to finish sums them in unit
         // order (a fixed order, so the FP64 sums do not depend on which unit finishes last).
         Partial *mine = U == 1 ? partials + item : subparts + (size_t)item * kMaxUnits + unit;
+        // (the compensated state adds the low words of phi in and out, of mu in and out: 34 words)
         if (za < zb)
-            mu_sweep_tile<R, TX, TY, false, SYM>(kp, phi_old, phi_new, mu, mu_out, st, tab, mine, nullptr, nullptr,
-                                                 tile % kp.tgx, tile / kp.tgx, za, zb, smem_raw, 22.0, splits,
-                                                 kp.zchunk);
+            mu_sweep_tile<R, TX, TY, COMP, SYM>(kp, phi_old, phi_new, mu, mu_out, st, tab, mine, mu_lo, mu_out_lo,
+                                                tile % kp.tgx, tile / kp.tgx, za, zb, smem_raw, COMP ? 34.0 : 22.0,
+                                                splits, kp.zchunk);
         else if (threadIdx.x == 0)
             zero_partial(mine);
         if (U > 1 && threadIdx.x == 0) {
@@ -2686,7 +2696,8 @@ __global__ void __launch_bounds__(256) unpack_kernel(const KParams<R> kp, const 
 template <typename R, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY) classify_kernel(const KParams<R> kp, const DevState *__restrict__ st,
                                                          const Ph<R> *__restrict__ phi,
-                                                         unsigned char *__restrict__ tmap)
+                                                         unsigned char *__restrict__ tmap,
+                                                         const Ph<R> *__restrict__ phi_lo)
 {
     const int tile = blockIdx.x, bx = tile % kp.tgx, by = tile / kp.tgx;
     const int i = bx * TX + (int)threadIdx.x % TX, j = by * TY + (int)threadIdx.x / TX;
@@ -2696,7 +2707,11 @@ __global__ void __launch_bounds__(TX *TY) classify_kernel(const KParams<R> kp, c
     const int k0 = blockIdx.y * 32, k1 = min(k0 + 32, kp.nz);
     for (int k = k0; k < k1; k++) {
         const size_t off = plane_off(k, kp.nz, zbase, plane);
-        const bool liq = !valid || code_of(ldg_ph(phi + off + (size_t)j * kp.nx + i)) == 3;
+        bool liq = !valid || code_of(ldg_ph(phi + off + (size_t)j * kp.nx + i)) == 3;
+        if (phi_lo && valid) {  // a compensated state is exactly pure liquid with zero low words only
+            const Ph<R> l = ldg_ph(phi_lo + off + (size_t)j * kp.nx + i);
+            liq = liq && l.v[0] == R(0) && l.v[1] == R(0) && l.v[2] == R(0) && l.v[3] == R(0);
+        }
         const int all = __syncthreads_and(liq);
         if (threadIdx.x == 0) tmap[map_idx((int)(off / plane), tile, kp.nz)] = all ? 1 : 0;
     }
@@ -2826,11 +2841,11 @@ static size_t fused_smem_bytes()
 
 template <typename R>
 cudaError_t launch_classify(const KParams<R> &kp, const DevState *st, const void *phi, unsigned char *tmap,
-                            cudaStream_t s)
+                            cudaStream_t s, const void *phi_lo)
 {
     if (kp.tgx * kTX < kp.nx || kp.tgy * kTY < kp.ny) return cudaErrorInvalidValue;
     dim3 grid(kp.tgx * kp.tgy, (kp.nz + 31) / 32);
-    classify_kernel<R, kTX, kTY><<<grid, kTX * kTY, 0, s>>>(kp, st, (const Ph<R> *)phi, tmap);
+    classify_kernel<R, kTX, kTY><<<grid, kTX * kTY, 0, s>>>(kp, st, (const Ph<R> *)phi, tmap, (const Ph<R> *)phi_lo);
     return cudaGetLastError();
 }
 
@@ -2898,16 +2913,23 @@ cudaError_t launch_general_step(const KParams<R> &kp, const void *phi, const voi
     return cudaGetLastError();
 }
 
-// Dynamic shared memory limits of the general planes' sweeps, and the largest shared-memory carveout
-// (so that as many CTAs as the registers allow fit beside each other).
-template <typename R>
-static cudaError_t general_sweep_attributes(bool sym)
+// Dynamic shared memory of the general planes' phi-sweep (the compensated state adds a ring of its
+// low words)
+template <typename R, bool COMP>
+static size_t general_phi_smem_bytes()
 {
-    const void *kphi = sym ? (const void *)general_phi_kernel<R, kTX, kTY, true>
-                           : (const void *)general_phi_kernel<R, kTX, kTY, false>;
-    const void *kmu = sym ? (const void *)general_mu_kernel<R, kTX, kTY, true>
-                          : (const void *)general_mu_kernel<R, kTX, kTY, false>;
-    cudaError_t e = cudaFuncSetAttribute(kphi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)phi_smem_bytes<R>());
+    return phi_smem_bytes<R>() + (COMP ? sizeof(Ph<R>) * 4 * kTX * kTY : 0);
+}
+// Dynamic shared memory limits of one instantiation of the general planes' sweeps (SYM: the symmetric
+// set, COMP: compensated FP32), and the largest shared-memory carveout (so that as many CTAs as the
+// registers allow fit beside each other)
+template <typename R, bool SYM, bool COMP>
+static cudaError_t general_sweep_attributes_of()
+{
+    const void *kphi = (const void *)general_phi_kernel<R, kTX, kTY, SYM, COMP>;
+    const void *kmu = (const void *)general_mu_kernel<R, kTX, kTY, SYM, COMP>;
+    cudaError_t e = cudaFuncSetAttribute(kphi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)general_phi_smem_bytes<R, COMP>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kmu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mu_smem_bytes<R>());
     if (e == cudaSuccess)
@@ -2916,35 +2938,67 @@ static cudaError_t general_sweep_attributes(bool sym)
         e = cudaFuncSetAttribute(kmu, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     return e;
 }
+template <typename R>
+static cudaError_t general_sweep_attributes()
+{
+    cudaError_t e = general_sweep_attributes_of<R, false, false>();
+    if (e == cudaSuccess) e = general_sweep_attributes_of<R, true, false>();
+    if constexpr (sizeof(R) == 4)
+        if (e == cudaSuccess) e = general_sweep_attributes_of<R, false, true>();
+    return e;
+}
+
+template <typename R, bool SYM, bool COMP>
+static cudaError_t launch_general_pair(const KParams<R> &kp, const void *phi, const void *mu, void *phi_out,
+                                       void *mu_out, const DevState *st, const PlaneT<R> *tab, Partial *parts,
+                                       const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits,
+                                       const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas, cudaStream_t s,
+                                       Partial *subparts, unsigned *subcnt, bool pdl, bool after_lean,
+                                       const void *phi_lo, void *phi_out_lo, const void *mu_lo, void *mu_out_lo)
+{
+    const int slots = phi_ctas < mu_ctas ? phi_ctas : mu_ctas;  // both sweeps cut the items alike
+    cudaError_t e = launch_k(general_phi_kernel<R, kTX, kTY, SYM, COMP>, dim3(phi_ctas), dim3(kTX * kTY),
+                             general_phi_smem_bytes<R, COMP>(), s, pdl, kp, (const Ph<R> *)phi, (const Mu<R> *)mu,
+                             (Ph<R> *)phi_out, st, tab, tmap_in, tmap_out, splits, glist, stats, slots,
+                             pdl && after_lean ? 1 : 0, (const Ph<R> *)phi_lo, (Ph<R> *)phi_out_lo);
+    if (e != cudaSuccess) return e;
+    return launch_k(general_mu_kernel<R, kTX, kTY, SYM, COMP>, dim3(mu_ctas), dim3(kTX * kTY), mu_smem_bytes<R>(), s,
+                    pdl, kp, (const Ph<R> *)phi, (const Ph<R> *)phi_out, (const Mu<R> *)mu, (Mu<R> *)mu_out, st, tab,
+                    parts, splits, glist, stats, subparts, subcnt, slots, (const Mu<R> *)mu_lo, (Mu<R> *)mu_out_lo);
+}
 
 template <typename R>
 cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const void *mu, void *phi_out, void *mu_out,
                                   const DevState *st, const PlaneT<R> *tab, Partial *parts,
-                                  const unsigned char *tmap_in, unsigned char *tmap_out,
-                                  const int2 *splits, const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas,
-                                  cudaStream_t s, Partial *subparts, unsigned *subcnt, bool pdl, bool after_lean)
+                                  const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits,
+                                  const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas, cudaStream_t s,
+                                  Partial *subparts, unsigned *subcnt, bool pdl, bool after_lean, const void *phi_lo,
+                                  void *phi_out_lo, const void *mu_lo, void *mu_out_lo)
 {
     if (!subparts || !subcnt) return cudaErrorInvalidValue;
-    const int slots = phi_ctas < mu_ctas ? phi_ctas : mu_ctas;  // both sweeps cut the items alike
+    const bool comp = phi_lo != nullptr;
+    if (comp && (sizeof(R) != 4 || !phi_out_lo || !mu_lo || !mu_out_lo)) return cudaErrorInvalidValue;
     static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
-    const size_t smp = phi_smem_bytes<R>(), smm = mu_smem_bytes<R>();
     if (!attr.done()) {
-        cudaError_t e = cudaSuccess;
-        for (int sym = 0; sym < 2 && e == cudaSuccess; sym++) e = general_sweep_attributes<R>(sym != 0);
+        cudaError_t e = general_sweep_attributes<R>();
         if (e != cudaSuccess) return e;
         attr.mark();
     }
+    if constexpr (sizeof(R) == 4) {
+        if (comp)
+            return launch_general_pair<R, false, true>(kp, phi, mu, phi_out, mu_out, st, tab, parts, tmap_in, tmap_out,
+                                                       splits, glist, stats, phi_ctas, mu_ctas, s, subparts, subcnt,
+                                                       pdl, after_lean, phi_lo, phi_out_lo, mu_lo, mu_out_lo);
+    }
     // the symmetric set (identity curvatures, one relaxation time) runs the instantiation compiled
     // without the general branches
-    const bool sym = !kp.gen && !kp.gen_tau;
-    auto kphi = sym ? general_phi_kernel<R, kTX, kTY, true> : general_phi_kernel<R, kTX, kTY, false>;
-    auto kmu = sym ? general_mu_kernel<R, kTX, kTY, true> : general_mu_kernel<R, kTX, kTY, false>;
-    cudaError_t e = launch_k(kphi, dim3(phi_ctas), dim3(kTX * kTY), smp, s, pdl, kp, (const Ph<R> *)phi,
-                             (const Mu<R> *)mu, (Ph<R> *)phi_out, st, tab, tmap_in, tmap_out, splits, glist, stats,
-                             slots, pdl && after_lean ? 1 : 0);
-    if (e != cudaSuccess) return e;
-    return launch_k(kmu, dim3(mu_ctas), dim3(kTX * kTY), smm, s, pdl, kp, (const Ph<R> *)phi, (const Ph<R> *)phi_out,
-                    (const Mu<R> *)mu, (Mu<R> *)mu_out, st, tab, parts, splits, glist, stats, subparts, subcnt, slots);
+    if (!kp.gen && !kp.gen_tau)
+        return launch_general_pair<R, true, false>(kp, phi, mu, phi_out, mu_out, st, tab, parts, tmap_in, tmap_out,
+                                                   splits, glist, stats, phi_ctas, mu_ctas, s, subparts, subcnt, pdl,
+                                                   after_lean, nullptr, nullptr, nullptr, nullptr);
+    return launch_general_pair<R, false, false>(kp, phi, mu, phi_out, mu_out, st, tab, parts, tmap_in, tmap_out,
+                                                splits, glist, stats, phi_ctas, mu_ctas, s, subparts, subcnt, pdl,
+                                                after_lean, nullptr, nullptr, nullptr, nullptr);
 }
 
 template <typename R>
@@ -2952,7 +3006,7 @@ void general_sweep_ctas_per_sm(int *phi_per_sm, int *mu_per_sm)
 {
     int a = 0, b = 0;
     // the instantiation with the general branches (it needs at least the symmetric one's registers)
-    if (general_sweep_attributes<R>(false) != cudaSuccess ||
+    if (general_sweep_attributes<R>() != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, general_phi_kernel<R, kTX, kTY, false>, kTX * kTY,
                                                       phi_smem_bytes<R>()) != cudaSuccess)
         a = 1;
@@ -2982,9 +3036,14 @@ int general_ctas_per_sm()
 template <typename R>
 cudaError_t launch_lean_step(const KParams<R> &kp, const Geometry &g, int nsub, const void *mu_map, const void *mu,
                              void *phi_out, void *mu_out, const DevState *st, LeanStats *stats, cudaStream_t s,
-                             const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits, bool pdl)
+                             const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits, bool pdl,
+                             const void *mu_lo, void *phi_out_lo, void *mu_out_lo)
 {
     using L = LeanLayout<R, kTX, kTY>;
+    // the compensated form is written for the FP32 column-pair consumers
+    constexpr bool kComp = sizeof(R) == 4 && PF_LEAN_PAIRS != 0;
+    const bool comp = mu_lo != nullptr;
+    if (comp && (!kComp || !phi_out_lo || !mu_out_lo)) return cudaErrorInvalidValue;
     if (!mu_map || !tmap_in || !tmap_out || !splits || nsub < 1 || kp.tgx != g.gx || kp.tgy != g.gy)
         return cudaErrorInvalidValue;
     if ((kp.zchunk + nsub - 1) / nsub > kLeanMaxSub) return cudaErrorInvalidValue;  // planes per lean CTA
@@ -2994,13 +3053,26 @@ cudaError_t launch_lean_step(const KParams<R> &kp, const Geometry &g, int nsub, 
     if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(lean_step_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if constexpr (kComp)
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(lean_step_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         attr.mark();
     }
     dim3 grid(g.gx, g.gy, g.gz * nsub);
+    if constexpr (kComp) {
+        if (comp)
+            return launch_k(lean_step_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows, true>, grid,
+                            dim3(kTX * kTY / kLeanRows + 32), sm, s, pdl, kp,
+                            *reinterpret_cast<const LeanMaps *>(mu_map), (const Mu<R> *)mu, (Ph<R> *)phi_out,
+                            (Mu<R> *)mu_out, st, stats, tmap_out, splits, nsub, (const Mu<R> *)mu_lo,
+                            (Ph<R> *)phi_out_lo, (Mu<R> *)mu_out_lo);
+    }
     return launch_k(lean_step_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>, grid,
-                    dim3(kTX * kTY / kLeanRows + 32), sm, s, pdl, kp, *reinterpret_cast<const CUtensorMap *>(mu_map),
-                    (const Mu<R> *)mu, (Ph<R> *)phi_out, (Mu<R> *)mu_out, st, stats, tmap_out, splits, nsub);
+                    dim3(kTX * kTY / kLeanRows + 32), sm, s, pdl, kp, *reinterpret_cast<const LeanMaps *>(mu_map),
+                    (const Mu<R> *)mu, (Ph<R> *)phi_out, (Mu<R> *)mu_out, st, stats, tmap_out, splits, nsub,
+                    (const Mu<R> *)nullptr, (Ph<R> *)nullptr, (Mu<R> *)nullptr);
 }
 
 #ifdef PF_FLOAT_UNIT
@@ -3251,10 +3323,11 @@ cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const voi
                                               void *, void *, const DevState *, const PlaneT<R> *, Partial *,     \
                                               cudaStream_t, const unsigned char *, unsigned char *, bool);        \
     template cudaError_t launch_classify<R>(const KParams<R> &, const DevState *, const void *, unsigned char *, \
-                                            cudaStream_t);                                                       \
+                                            cudaStream_t, const void *);                                         \
     template cudaError_t launch_lean_step<R>(const KParams<R> &, const Geometry &, int, const void *, const void *, \
                                              void *, void *, const DevState *, LeanStats *, cudaStream_t,          \
-                                             const unsigned char *, unsigned char *, const int2 *, bool);          \
+                                             const unsigned char *, unsigned char *, const int2 *, bool,           \
+                                             const void *, void *, void *);                                        \
     template cudaError_t launch_plan<R>(const KParams<R> &, const Geometry &, const DevState *,                  \
                                         const unsigned char *, int2 *, int *, LeanStats *, Partial *,            \
                                         cudaStream_t, bool);                                                     \
@@ -3267,7 +3340,8 @@ cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const voi
                                                   const DevState *, const PlaneT<R> *, Partial *,                  \
                                                   const unsigned char *, unsigned char *,                           \
                                                   const int2 *, const int *, LeanStats *, int, int, cudaStream_t, \
-                                                  Partial *, unsigned *, bool, bool);                              \
+                                                  Partial *, unsigned *, bool, bool, const void *, void *,        \
+                                                  const void *, void *);                                           \
     template void general_sweep_ctas_per_sm<R>(int *, int *);                                                    \
     template cudaError_t launch_batched_step<R>(const BatchDomain<R> *, int, const BatchItem *, int, unsigned *, \
                                                 int, int, int, cudaStream_t);                                    \

@@ -8,9 +8,10 @@
 //
 // The kernel streams mu planes through shared memory with TMA: a producer warp issues one tensor
 // copy per plane (the tile plus a one-cell halo, columns i0-2 .. i0+TX+1 so that the box starts on
-// a 16-byte boundary, rows j0-1 .. j0+TY) into a ring of LD stages, plus asynchronous copies of
-// the periodic images that fall outside the tensor (the wrapped column / row at the domain edge);
-// both complete on the stage's "full" mbarrier.  TY / ROWS consumer warps wait on it, update the
+// a 16-byte boundary, rows j0-1 .. j0+TY) into a ring of LD stages; at the domain's edges some
+// producer lanes also store the periodic images that fall outside the tensor (the wrapped column /
+// row, loaded from L2 ahead of time) into the stage; the stage's "full" mbarrier completes on the
+// tensor copy's bytes and those lanes' arrivals.  TY / ROWS consumer warps wait on it, update the
 // plane and release the stage through its "empty" mbarrier; a consumer thread holds ROWS cells of
 // one column (FP64), or two adjacent columns of ROWS / 2 rows so that each 16-byte shared load and
 // global store carries two cells (FP32).  Nothing of
@@ -106,18 +107,6 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         "l"(map), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z)
         : "memory");
 }
-// asynchronous copy of B bytes (one mu cell) from global to shared memory
-template <int B>
-__device__ __forceinline__ void cp_async_bytes(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(B) : "memory");
-}
-// one expected arrival on bar, made once this thread's earlier cp.async copies have landed
-__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar)
-{
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // barrier of the consumer warps only (the producer warp does not take part)
 template <int N>
 __device__ __forceinline__ void consumer_sync()
@@ -125,16 +114,23 @@ __device__ __forceinline__ void consumer_sync()
     asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
 }
 
-// Shared-memory layout of one stage: the TMA box (BH rows of BW cells) and four 32-cell rows of
-// wrapped halo cells: x = -1 (-> nx-1) per tile row, x = nx (-> 0) per tile row, y = -1
-// (-> ny-1) per tile column, y = ny (-> 0) per tile column.  A tensor copy's shared-memory
-// destination must be 128-byte aligned: stages are 128-byte multiples from a 128-byte aligned base
-// (the launch adds 128 bytes of slack for the alignment).
+// Shared-memory layout of one stage: the tensor copy of the tile box (BH rows of BW cells), then at
+// 128-byte aligned offsets (a tensor copy's shared-memory destination must be 128-byte aligned) the
+// boxes of the periodic images: XL the column x = nx-1 (wrapped to x = -1) and XR the column x = 0
+// (wrapped to x = nx), each 2 cells x TY rows (the image is the second / first cell of each row: a
+// box's first coordinate must sit on a 16-byte boundary), and YL the row y = ny-1 (wrapped to y = -1),
+// YH the row y = 0 (wrapped to y = ny), each BW cells from x = i0 - 2.  Stages are 128-byte multiples
+// from a 128-byte aligned base (the launch adds 128 bytes of slack for the alignment).
 template <typename R, int TX, int TY>
 struct LeanLayout {
-    static constexpr int BW = TX + 4, BH = TY + 2, BOX = BW * BH, FIX = 4 * 32;
-    static constexpr unsigned BOX_BYTES = BOX * sizeof(Mu<R>);
-    static constexpr unsigned STAGE_BYTES = ((BOX + FIX) * sizeof(Mu<R>) + 127) / 128 * 128;
+    static constexpr int BW = TX + 4, BH = TY + 2, BOX = BW * BH;
+    static constexpr unsigned CB = sizeof(Mu<R>);
+    static constexpr unsigned up128(unsigned b) { return (b + 127u) / 128u * 128u; }
+    static constexpr unsigned BOX_BYTES = BOX * CB;
+    static constexpr unsigned XIMG_BYTES = 2u * TY * CB, YIMG_BYTES = BW * CB;
+    static constexpr unsigned XL = up128(BOX_BYTES), XR = XL + up128(XIMG_BYTES);
+    static constexpr unsigned YL = XR + up128(XIMG_BYTES), YH = YL + up128(YIMG_BYTES);
+    static constexpr unsigned STAGE_BYTES = up128(YH + YIMG_BYTES);
     static constexpr size_t smem_bytes(int stages) { return (size_t)stages * STAGE_BYTES + 128; }
 };
 
@@ -159,18 +155,25 @@ __device__ __forceinline__ Mu<R> lds_cell(const unsigned char *p)
 // and of that chunk the sub-chunk blockIdx.z % nsub of at most MAXSUB planes.  The CTA updates the
 // chunk's lean planes (its split, from plan_kernel) that fall into its sub-chunk.  TY/ROWS consumer warps own ROWS
 // consecutive tile rows each (lane = tile column), one producer warp feeds them.
-template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS>
-__device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMap *mu_map, const Mu<R> *__restrict__ mu,
+// COMP: the compensated FP32 state (value = high + low word): the tensor copies carry the high words of
+// mu, each consumer loads its own cells' low words, forms the increment C1 (neighbour sum - 6 mu) + C0
+// from the high words and adds it to high + low with the error-free two-sum (the compensated update of
+// the two sweeps); a stored pure-liquid phi gets zero low words.
+template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS, bool COMP = false>
+__device__ __forceinline__ void lean_tile(const KParams<R> &kp, const LeanMaps *maps, const Mu<R> *__restrict__ mu,
                                           Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out,
                                           const DevState *__restrict__ st, LeanStats *__restrict__ stats,
                                           unsigned char *__restrict__ tmap_out, const int2 *__restrict__ splits,
-                                          int nsub, int bx, int by, int zsub)
+                                          int nsub, int bx, int by, int zsub, const Mu<R> *__restrict__ mu_lo = nullptr,
+                                          Ph<R> *__restrict__ phi_out_lo = nullptr,
+                                          Mu<R> *__restrict__ mu_out_lo = nullptr)
 {
     using L = LeanLayout<R, TX, TY>;
     static_assert(TY % ROWS == 0, "whole rows per consumer warp");
     constexpr int NCW = TY / ROWS, NC = 32 * NCW, NTH = NC + 32;
     constexpr int CB = (int)sizeof(Mu<R>);
     constexpr bool PAIR = PF_LEAN_PAIRS != 0 && sizeof(R) == 4;
+    static_assert(!COMP || PAIR, "the compensated form runs the FP32 column pairs");
     constexpr int UNR = sizeof(R) == 4 ? kLeanUnroll : 1;  // FP64 values take twice the registers
     static_assert(TX == 32 && TY % 2 == 0 && TY <= 32 && (LD & (LD - 1)) == 0, "layout");
     constexpr int LDLOG = LD == 2 ? 1 : (LD == 4 ? 2 : (LD == 8 ? 3 : 4));
@@ -196,22 +199,16 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
         const int sp = k + zbase;
         return sp >= nz ? sp - nz : sp;
     };
-    // producer lane l copies periodic images outside the tensor box: x = -1 and x = nx of tile row
-    // l, y = -1 and y = ny of tile column l (only at the domain's edges)
-    auto fixes = [&](int l) {
-        const bool row = l < TY && j0 + l < ny, colv = i0 + l < nx;
-        return (bx == 0 && row) || (i0 + TX >= nx && row) || (by == 0 && colv) || (j0 + TY >= ny && colv);
-    };
+    // the periodic images this tile needs (only at the domain's edges), copied with the tile box
+    const bool img_xl = bx == 0, img_xr = i0 + TX >= nx, img_yl = by == 0, img_yh = j0 + TY >= ny;
 
     // (the launch guarantees s1 - s0 <= MAXSUB) the destination's map entries, read before any is
     // replaced
     for (int q = s0 + tid; q < s1; q += NTH) s_dst_liquid[q - s0] = tmap_out[map_idx(splane(q), tile, nz)];
     if (tid == 0) {
-        int nfix = 0;
-        for (int l = 0; l < 32; l++) nfix += fixes(l) ? 1 : 0;
         for (int s = 0; s < LD; s++) {
-            mbar_init(&full[s], 1 + nfix);  // the producer's expect-tx arrival + one per copying lane
-            mbar_init(&empty[s], NCW);      // one per consumer warp
+            mbar_init(&full[s], 1);    // the producer's expect-tx arrival (completion: the copies' bytes)
+            mbar_init(&empty[s], NCW);  // one per consumer warp
         }
         s_abort = 0;
         s_bad = 0;
@@ -231,9 +228,11 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
     if (tid >= NC) {
         // ---------------- producer warp ----------------
         const int lane = tid - NC;
-        const bool fix = fixes(lane);
         unsigned u = 0;  // stage uses issued
         bool ok = true;
+        // bytes of one stage use: the tile box and the periodic images of an edge tile
+        const unsigned tx_bytes = L::BOX_BYTES + (img_xl ? L::XIMG_BYTES : 0u) + (img_xr ? L::XIMG_BYTES : 0u) +
+                                  (img_yl ? L::YIMG_BYTES : 0u) + (img_yh ? L::YIMG_BYTES : 0u);
         // (test hook: no copies at all, so that the consumers' bounded waits run out)
         for (int g = 0; g < 2 && ok && !(kp.test_flags & 1); g++) {
             if (qb[g] <= qa[g]) continue;
@@ -249,24 +248,17 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
                 unsigned char *stg = stage_base + s * L::STAGE_BYTES;
                 const int sp = splane(p);
                 if (lane == 0) {
-                    mbar_arrive_expect_tx(&full[s], L::BOX_BYTES);
-                    tma_load_3d(stg, mu_map, &full[s], 2 * (i0 - 2), j0 - 1, sp);
-                }
-                if (fix) {
-                    const Mu<R> *mp = mu + (size_t)sp * plane;
-                    Mu<R> *fx = reinterpret_cast<Mu<R> *>(stg + L::BOX_BYTES);
-                    if (bx == 0 && lane < TY && j0 + lane < ny)
-                        cp_async_bytes<CB>(fx + lane, mp + (size_t)(j0 + lane) * nx + (nx - 1));
-                    if (i0 + TX >= nx && lane < TY && j0 + lane < ny)
-                        cp_async_bytes<CB>(fx + 32 + lane, mp + (size_t)(j0 + lane) * nx);
-                    if (by == 0 && i0 + lane < nx)
-                        cp_async_bytes<CB>(fx + 64 + lane, mp + (size_t)(ny - 1) * nx + i0 + lane);
-                    if (j0 + TY >= ny && i0 + lane < nx) cp_async_bytes<CB>(fx + 96 + lane, mp + i0 + lane);
-                    cp_async_arrive_noinc(&full[s]);
+                    // every copy completes on the stage's full barrier, all in the asynchronous proxy; x
+                    // coordinates in words (2 a cell) sit on 16-byte boundaries (nx even in FP32)
+                    mbar_arrive_expect_tx(&full[s], tx_bytes);
+                    tma_load_3d(stg, &maps->box, &full[s], 2 * (i0 - 2), j0 - 1, sp);
+                    if (img_xl) tma_load_3d(stg + L::XL, &maps->ximg, &full[s], 2 * (nx - 2), j0, sp);
+                    if (img_xr) tma_load_3d(stg + L::XR, &maps->ximg, &full[s], 0, j0, sp);
+                    if (img_yl) tma_load_3d(stg + L::YL, &maps->yimg, &full[s], 2 * (i0 - 2), ny - 1, sp);
+                    if (img_yh) tma_load_3d(stg + L::YH, &maps->yimg, &full[s], 2 * (i0 - 2), 0, sp);
                 }
             }
         }
-        cp_async_wait_all();
         if (!ok && lane == 0) {
             // drain: the tensor copies of the last LD uses may still be landing in shared memory
             for (unsigned v = u > (unsigned)LD ? u - LD : 0; v < u; v++) {
@@ -280,8 +272,9 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
 
     // ---------------- consumer warps ----------------
     const int lane = tid & 31, w = tid >> 5;
-    // byte offsets of the periodic images of the stage (x = -1, x = nx, y = -1, y = ny)
-    const int fixx0 = L::BOX_BYTES, fixx1 = fixx0 + 32 * CB, fixy0 = fixx1 + 32 * CB, fixy1 = fixy0 + 32 * CB;
+    // byte offsets of the periodic images in a stage: x = -1 of tile row r at XL + (2 r + 1) CB, x = nx
+    // at XR + 2 r CB, y = -1 of tile column c at YL + (c + 2) CB, y = ny at YH + (c + 2) CB
+    constexpr int XL = (int)L::XL, XR = (int)L::XR, YL = (int)L::YL, YH = (int)L::YH;
     // The liquid update with constant mobility M = D_l/(2 A_l), h = e_l and no phase change (the
     // short form of Eq. 3 for a cell whose neighbourhood is pure liquid): the six face fluxes
     // M (mu_nb - mu)/dx reduce to the 7-point sum, so
@@ -318,12 +311,12 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
         for (int k = 0; k < PR; k++) {
             const int own = own0 + k * L::BW * CB, tyr = trow0 + k, j = jr + k;
             vr[k] = ia < nx && j < ny;  // nx is even on this path: ia < nx implies ib < nx
-            oxm[k] = ia == 0 ? fixx0 + tyr * CB : own - CB;
-            oxp[k] = ib == nx - 1 ? fixx1 + tyr * CB : own + 2 * CB;
+            oxm[k] = ia == 0 ? XL + (2 * tyr + 1) * CB : own - CB;
+            oxp[k] = ib == nx - 1 ? XR + 2 * tyr * CB : own + 2 * CB;
             top[k] = j == ny - 1;
-            oyw[k] = top[k] ? fixy1 + ca * CB : own + L::BW * CB;  // the pair above row k
+            oyw[k] = top[k] ? YH + (ca + 2) * CB : own + L::BW * CB;  // the pair above row k
         }
-        const int oyb = jr == 0 ? fixy0 + ca * CB : own0 - L::BW * CB;  // the pair below row 0
+        const int oyb = jr == 0 ? YL + (ca + 2) * CB : own0 - L::BW * CB;  // the pair below row 0
         const size_t col0 = (size_t)jr * nx + (size_t)min(ia, nx - 2);
         auto lds_pair = [](const unsigned char *p) { return *reinterpret_cast<const float4 *>(p); };
         auto lds_one = [](const unsigned char *p) { return *reinterpret_cast<const float2 *>(p); };
@@ -335,6 +328,10 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
                 return __all_sync(0xffffffffu, mbar_wait(&full[v & (LD - 1)], (v >> LDLOG) & 1, &s_abort));
             };
             auto release = [&](unsigned v) {
+                // the warp's shared-memory reads of the stage (generic proxy) are ordered before the
+                // tensor copy that refills it (asynchronous proxy) once the producer sees this arrival;
+                // without the proxy fence that copy could overwrite values still being read
+                fence_proxy_async_shared();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[v & (LD - 1)]);
             };
@@ -357,6 +354,14 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
             }
 #pragma unroll UNR
             for (int q = qa[g]; q < qb[g] && ok; q++, v++) {
+                const size_t o = (size_t)splane(q) * plane + col0;
+                float4 wl[PR];  // compensated: low words of the own cells' mu^n, loaded before the waits
+                if constexpr (COMP) {
+#pragma unroll
+                    for (int k = 0; k < PR; k++)
+                        wl[k] = vr[k] ? __ldg(reinterpret_cast<const float4 *>(mu_lo + o + (size_t)k * nx))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 const unsigned char *S = stg(v);
                 float4 mn[PR];
 #pragma unroll
@@ -384,7 +389,7 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
                         yhi[k] = top[k] ? lds_pair(S + oyw[k]) : m[k + 1];
                 }
                 release(v);
-                float4 out[PR];
+                float4 out[PR], outl[PR];
 #pragma unroll
                 for (int k = 0; k < PR; k++) {
                     const float4 c = m[k], yl = k == 0 ? ylo0 : m[k - 1], yh = yhi[k], lo = mlo[k], hi = mn[k];
@@ -393,23 +398,50 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
                     const float sa1 = ((xm[k].y + c.w) + (yl.y + yh.y)) + (lo.y + hi.y);
                     const float sb0 = ((c.x + xp[k].x) + (yl.z + yh.z)) + (lo.z + hi.z);
                     const float sb1 = ((c.y + xp[k].y) + (yl.w + yh.w)) + (lo.w + hi.w);
-                    out[k].x = C1 * (sa0 - 6.f * c.x) + (c.x + C0[0]);
-                    out[k].y = C1 * (sa1 - 6.f * c.y) + (c.y + C0[1]);
-                    out[k].z = C1 * (sb0 - 6.f * c.z) + (c.z + C0[0]);
-                    out[k].w = C1 * (sb1 - 6.f * c.w) + (c.w + C0[1]);
+                    if constexpr (COMP) {
+                        // The increment of a compensated state must be accurate relative to itself, not
+                        // to mu: the Laplacian as a sum of neighbour differences (each exact when the
+                        // values are close, as in the flux form), not as the neighbour sum minus 6 mu
+                        // (whose FP32 rounding is relative to |mu|)
+                        const float da0 = (((xm[k].x - c.x) + (c.z - c.x)) + ((yl.x - c.x) + (yh.x - c.x))) +
+                                          ((lo.x - c.x) + (hi.x - c.x));
+                        const float da1 = (((xm[k].y - c.y) + (c.w - c.y)) + ((yl.y - c.y) + (yh.y - c.y))) +
+                                          ((lo.y - c.y) + (hi.y - c.y));
+                        const float db0 = (((c.x - c.z) + (xp[k].x - c.z)) + ((yl.z - c.z) + (yh.z - c.z))) +
+                                          ((lo.z - c.z) + (hi.z - c.z));
+                        const float db1 = (((c.y - c.w) + (xp[k].y - c.w)) + ((yl.w - c.w) + (yh.w - c.w))) +
+                                          ((lo.w - c.w) + (hi.w - c.w));
+                        const DF r0 = df_add_f(DF{c.x, wl[k].x}, C1 * da0 + C0[0]);
+                        const DF r1 = df_add_f(DF{c.y, wl[k].y}, C1 * da1 + C0[1]);
+                        const DF r2 = df_add_f(DF{c.z, wl[k].z}, C1 * db0 + C0[0]);
+                        const DF r3 = df_add_f(DF{c.w, wl[k].w}, C1 * db1 + C0[1]);
+                        out[k] = make_float4(r0.h, r1.h, r2.h, r3.h);
+                        outl[k] = make_float4(r0.l, r1.l, r2.l, r3.l);
+                    } else {
+                        out[k].x = C1 * (sa0 - 6.f * c.x) + (c.x + C0[0]);
+                        out[k].y = C1 * (sa1 - 6.f * c.y) + (c.y + C0[1]);
+                        out[k].z = C1 * (sb0 - 6.f * c.z) + (c.z + C0[0]);
+                        out[k].w = C1 * (sb1 - 6.f * c.w) + (c.w + C0[1]);
+                    }
                 }
                 const bool store_phi = s_dst_liquid[q - s0] != 1;
                 phi_stores += store_phi ? 1 : 0;
                 planes++;
-                const size_t o = (size_t)splane(q) * plane + col0;
 #pragma unroll
                 for (int k = 0; k < PR; k++) {
                     if (vr[k]) {
                         if (store_phi) {
                             st_ph(phi_out + o + (size_t)k * nx, liquid);
                             st_ph(phi_out + o + (size_t)k * nx + 1, liquid);
+                            if constexpr (COMP) {
+                                Ph<R> zero;
+                                zero.v[0] = zero.v[1] = zero.v[2] = zero.v[3] = R(0);
+                                st_ph(phi_out_lo + o + (size_t)k * nx, zero);
+                                st_ph(phi_out_lo + o + (size_t)k * nx + 1, zero);
+                            }
                         }
                         *reinterpret_cast<float4 *>(mu_out + o + (size_t)k * nx) = out[k];
+                        if constexpr (COMP) *reinterpret_cast<float4 *>(mu_out_lo + o + (size_t)k * nx) = outl[k];
                         acc += (out[k].x + out[k].y) + (out[k].z + out[k].w);
                     }
                     mlo[k] = m[k];
@@ -432,11 +464,11 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
         for (int r = 0; r < ROWS; r++) {
             const int own = own0 + r * L::BW * CB, tyr = w * ROWS + r, j = jr0 + r;
             vr[r] = i < nx && j < ny;
-            oxm[r] = i == 0 ? fixx0 + tyr * CB : own - CB;
-            oxp[r] = i == nx - 1 ? fixx1 + tyr * CB : own + CB;
-            oyu[r] = j == ny - 1 ? fixy1 + lane * CB : own + L::BW * CB;
+            oxm[r] = i == 0 ? XL + (2 * tyr + 1) * CB : own - CB;
+            oxp[r] = i == nx - 1 ? XR + 2 * tyr * CB : own + CB;
+            oyu[r] = j == ny - 1 ? YH + (lane + 2) * CB : own + L::BW * CB;
         }
-        const int oyb = jr0 == 0 ? fixy0 + lane * CB : own0 - L::BW * CB;
+        const int oyb = jr0 == 0 ? YL + (lane + 2) * CB : own0 - L::BW * CB;
         const size_t col0 = (size_t)jr0 * nx + (size_t)min(i, nx - 1);
         for (int g = 0; g < 2 && ok; g++) {
             if (qb[g] <= qa[g]) continue;
@@ -447,6 +479,10 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
                 return __all_sync(0xffffffffu, mbar_wait(&full[v & (LD - 1)], (v >> LDLOG) & 1, &s_abort));
             };
             auto release = [&](unsigned v) {
+                // the warp's shared-memory reads of the stage (generic proxy) are ordered before the
+                // tensor copy that refills it (asynchronous proxy) once the producer sees this arrival;
+                // without the proxy fence that copy could overwrite values still being read
+                fence_proxy_async_shared();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[v & (LD - 1)]);
             };
@@ -541,7 +577,9 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
     if (tid == 0) {
         const unsigned long long tile_cells = (unsigned long long)min(TX, nx - i0) * (unsigned long long)min(TY, ny - j0);
         // mu^n in, mu^{n+1} out (4 words a cell), plus phi^{n+1} where it was stored
-        const unsigned long long b = tile_cells * sizeof(R) * 4ull * (unsigned long long)(planes + phi_stores);
+        // (the compensated state moves the low words too: twice the words)
+        const unsigned long long b =
+            tile_cells * sizeof(R) * (COMP ? 8ull : 4ull) * (unsigned long long)(planes + phi_stores);
         if (b) atomicAdd(&stats->bytes, b);
         if (s_bad) atomicOr(&stats->nonfinite, 1);
         if (s_abort) {
@@ -551,17 +589,19 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const CUtensorMa
     }
 }
 
-// The lean planes of one domain: grid (tgx, tgy, gz * nsub).
-template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS>
+// The lean planes of one domain: grid (tgx, tgy, gz * nsub).  COMP: the compensated FP32 state (the low
+// words of mu in and out, of phi out).
+template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS, bool COMP = false>
 __global__ void __launch_bounds__(TX *TY / ROWS + 32, sizeof(R) == 4 ? PF_LEAN_MIN_CTAS : 3) lean_step_kernel(
-    const KParams<R> kp, const __grid_constant__ CUtensorMap mu_map, const Mu<R> *__restrict__ mu,
+    const KParams<R> kp, const __grid_constant__ LeanMaps mu_map, const Mu<R> *__restrict__ mu,
     Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out, const DevState *__restrict__ st,
-    LeanStats *__restrict__ stats, unsigned char *__restrict__ tmap_out, const int2 *__restrict__ splits, int nsub)
+    LeanStats *__restrict__ stats, unsigned char *__restrict__ tmap_out, const int2 *__restrict__ splits, int nsub,
+    const Mu<R> *__restrict__ mu_lo, Ph<R> *__restrict__ phi_out_lo, Mu<R> *__restrict__ mu_out_lo)
 {
     pdl_wait();  // the step's plan; every CTA has passed it before the kernel behind may be scheduled
     pdl_trigger();
-    lean_tile<R, TX, TY, LD, MAXSUB, ROWS>(kp, &mu_map, mu, phi_out, mu_out, st, stats, tmap_out, splits, nsub,
-                                           blockIdx.x, blockIdx.y, blockIdx.z);
+    lean_tile<R, TX, TY, LD, MAXSUB, ROWS, COMP>(kp, &mu_map, mu, phi_out, mu_out, st, stats, tmap_out, splits, nsub,
+                                                 blockIdx.x, blockIdx.y, blockIdx.z, mu_lo, phi_out_lo, mu_out_lo);
 }
 
 // One lean work item of a batched step: CTA blockIdx.x takes (domain, tile x, tile y, chunk * nsub +

@@ -48,11 +48,15 @@ def test_compensated_state_keeps_increments_below_the_fp32_spacing():
     assert err["fp32"] > 1e4 * err["fp32c"]
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 64), (37, 21, 19), (1, 1, 16)])
-def test_compensated_path_matches_the_oracle(shape):
+# (32, 32, 64) and (40, 24, 48) run the lean path by default (plan, lean kernel and general planes'
+# sweeps in compensated form); an odd nx or nx = 1 has no tensor map for the lean kernel and runs the
+# two whole-domain sweeps, as does the explicit "unfused" variant
+@pytest.mark.parametrize("variant", ["auto", "unfused"])
+@pytest.mark.parametrize("shape", [(32, 32, 64), (40, 24, 48), (37, 21, 19), (1, 1, 16)])
+def test_compensated_path_matches_the_oracle(shape, variant):
     nx, ny, nz = shape
     p = W.symmetric_params(n_grains=6)
-    sim = pf.Simulation(nx, ny, nz, p, "fp32c")
+    sim = pf.Simulation(nx, ny, nz, p, "fp32c", variant=variant)
     ref = oracle.State(p, nx, ny, nz)
     sim.init(7)
     ref.init(7)
@@ -93,3 +97,39 @@ def test_compensated_window_shift_matches_the_oracle():
     phi, mu = sim.fields()
     assert np.abs(phi - ref.phi).max() <= 2e-5
     assert np.abs(mu - ref.mu).max() / max(np.abs(ref.mu).max(), 1e-8) <= 2e-5
+
+
+def test_compensated_lean_kernel_moves_the_low_words():
+    # pure liquid: every plane is lean; the lean kernel's tally is mu^n in and mu^{n+1} out with their
+    # low words, 32 bytes a cell (16 in plain FP32), once phi^{n+1} = e_l is known to be stored
+    nx, ny, nz = 64, 32, 48
+    p = W.symmetric_params()
+    phi = np.zeros((4, nz, ny, nx))
+    phi[3] = 1.0
+    rng = np.random.default_rng(2)
+    mu = rng.uniform(-1e-3, 1e-3, (2, nz, ny, nx))
+    for prec, per_cell in (("fp32", 16.0), ("fp32c", 32.0)):
+        sim = pf.Simulation(nx, ny, nz, p, prec)
+        sim.set_fields(phi, mu)
+        sim.step(4)
+        b = sim.step_bytes()
+        assert set(b) == {"lean_step"}, b
+        assert b["lean_step"] == per_cell * nx * ny * nz
+        sim.close()
+
+
+def test_compensated_lean_and_sweeps_agree_over_a_growing_front():
+    # the lean path (its general planes included) and the whole-domain sweeps compute the same step
+    # in compensated form: after 300 steps of a growing front they agree far inside the FP32 tolerance
+    nx, ny, nz = 64, 32, 64
+    p = W.symmetric_params(n_grains=8, G=2e-3)
+    out = {}
+    for variant in ("auto", "unfused"):
+        sim = pf.Simulation(nx, ny, nz, p, "fp32c", variant=variant)
+        sim.init(11)
+        sim.step(300)
+        out[variant] = sim.fields()
+        sim.close()
+    (pa, ma), (pu, mu_) = out["auto"], out["unfused"]
+    assert np.abs(pa - pu).max() <= 2e-6
+    assert np.abs(ma - mu_).max() / max(np.abs(mu_).max(), 1e-8) <= 2e-6
