@@ -376,6 +376,54 @@ def run_serving_study(args):
     print(json.dumps(line), flush=True)
 
 
+def run_split_study(args):
+    """The block decomposition on one GPU (pf_split: y-slabs with ghost rows, Algorithm 1's exchanges
+    and Algorithm 2's overlap) against the undivided domain stepped with the same two sweeps
+    (PF_VARIANT_UNFUSED) and with the library's default step, FP32, 64 grains, from the 200-step
+    state: MLUP/s by CUDA events over the timed steps, and whether the fields agree bit for bit."""
+    import numpy as np
+    import torch
+
+    from paper_1506_01684_gb300 import pf
+    from paper_1506_01684_gb300 import workloads as W
+
+    nx, ny, nz = (int(x) for x in args.split_shape.split("x"))
+    p = W.symmetric_params(n_grains=GRAINS, window_trigger_z=nz / 2)
+    cells = nx * ny * nz
+    pre, k = 200, max(args.steps, 10)
+
+    def timed(obj):
+        obj.step(pre + args.warmup)
+        obj.sync()
+        torch.cuda.synchronize()
+        # the split runs on several streams of its own: wall clock between two full synchronisations
+        t0 = time.perf_counter()
+        obj.step(k)
+        obj.sync()
+        wall = time.perf_counter() - t0
+        return cells * k / wall / 1e6
+
+    res = {}
+    whole = pf.Simulation(nx, ny, nz, p, "fp32", variant="unfused").init(SEED)
+    res["undivided_unfused"] = {"mlups": timed(whole)}
+    ref_phi, ref_mu = whole.fields()
+    whole.close()
+    auto = pf.Simulation(nx, ny, nz, p, "fp32").init(SEED)
+    res["undivided_default"] = {"mlups": timed(auto)}
+    auto.close()
+    for n in (1, 2, 4, 8, 16):
+        sp = pf.Split(nx, ny, nz, p, n, "fp32").init(SEED)
+        m = timed(sp)
+        phi, mu = sp.fields()
+        res[f"split_{n}"] = {"mlups": m, "bitwise_equal_to_unfused": bool(np.array_equal(phi, ref_phi)
+                                                                           and np.array_equal(mu, ref_mu))}
+        sp.close()
+    print(json.dumps({"metric": "block decomposition on one GPU: MLUP/s (FP32)",
+                      "config": {"workload": f"{nx}x{ny}x{nz}, {GRAINS} grains, seed {SEED}, timed {k} steps "
+                                             f"after {pre + args.warmup}, wall clock between synchronisations"},
+                      "results": res, "data": "synthetic"}), flush=True)
+
+
 def run_precision_study(args):
     """128x128x512 cells, 20000 steps by default: compensated FP32 vs plain FP32 vs FP64 on the GPU.
     First each GPU path's agreement with the CPU oracle on the small case (32x32x64, 200 steps);
@@ -542,7 +590,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="steps of the FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=["batched", "serving", "precision", "regions", "mesh"],
+    ap.add_argument("--study", default=None, choices=["batched", "serving", "precision", "regions", "mesh", "split"],
                     help="run a secondary study instead of the headline line")
     ap.add_argument("--requests", type=int, default=100, help="serving study: number of requests")
     ap.add_argument("--min-steps", type=int, default=100, help="serving study: fewest steps per request")
@@ -562,6 +610,11 @@ def main():
     ap.add_argument("--pre-steps", type=int, default=PRE_STEPS,
                     help="untimed steps before the warm-up: the timed steps start from the state the "
                          "single-large-domain configuration reaches after its 2000 steps (0: the sharp initial state)")
+    ap.add_argument("--state-file", default=None,
+                    help="checkpoint of the pre-stepped state: written after the pre-steps when the file does not "
+                         "exist, restored instead of the pre-steps when it does (a profiling capture then starts "
+                         "from the same state without thousands of launches before the captured one)")
+    ap.add_argument("--split-shape", default="256x256x256", help="split study: domain")
     ap.add_argument("--clocks-csv", default=None,
                     help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
     args = ap.parse_args()
@@ -603,6 +656,9 @@ def main():
     if args.study == "regions":
         run_region_study(args)
         return
+    if args.study == "split":
+        run_split_study(args)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -627,8 +683,13 @@ def main():
     sol0 = sim.stats()["solute"]
     # the configuration's state: pre-steps advance the front from its sharp Voronoi start to the
     # diffuse, growing interface the configuration's 2000 steps reach (untimed)
-    if args.pre_steps > 0:
-        sim.step(args.pre_steps)
+    if args.state_file and os.path.exists(args.state_file):
+        sim.restore(args.state_file)  # FP32 values: the pre-stepped state itself, bit for bit
+    else:
+        if args.pre_steps > 0:
+            sim.step(args.pre_steps)
+        if args.state_file:
+            sim.checkpoint(args.state_file)
     sim.step(args.warmup)
     sim.sync()
     st_pre = sim.stats()

@@ -360,6 +360,45 @@ int pf_cancel(pf_server *srv, uint64_t ticket);
 int pf_server_stats(pf_server *srv, double *mlups, int *running, int *queued, size_t *used_bytes);
 
 /*
+ * Domain decomposition on one device (Section 3.1: the domain is cut into blocks, each with one
+ * ghost layer of cells around it; Algorithm 1: after the phi-sweep and after the mu-sweep of every
+ * block, the ghost layers take the neighbouring blocks' new boundary layers; Algorithm 2: the
+ * exchange of the mu ghost layers runs while the phi-sweep, which does not read them, computes).
+ *
+ * The domain nx x ny x nz (periodic in x and y) is cut along y into nslabs slabs of
+ * floor/ceil(ny / nslabs) rows; slab q owns global rows [floor(q ny / nslabs), floor((q+1) ny / nslabs))
+ * and is a pf_sim of nx x (own rows + 2) x nz cells whose first and last rows are ghost rows (the
+ * previous and next slab's boundary rows; periodic, so one slab is its own neighbour).  Each step:
+ * the phi-sweep of every slab on its own stream; the phi ghost rows copied once both neighbours'
+ * phi-sweeps are done; the mu-sweep of every slab once its mu ghost rows have arrived; one kernel
+ * that sums the slabs' interface sums, decides the moving-window shift (Section 3.3) for the whole
+ * domain and hands it to every slab; each slab's plane table and window fill; the mu ghost rows
+ * copied on a separate stream per slab, overlapping the next phi-sweep.  Every cell is updated by
+ * the same arithmetic as in an undivided pf_sim stepped with PF_VARIANT_UNFUSED, so the fields
+ * agree with such a run bit for bit (FP32 and FP64).  Ghost-row copies are device-to-device
+ * strided copies (cudaMemcpy2DAsync), the stand-in on one GPU for the paper's messages between
+ * processes.
+ */
+typedef struct pf_split pf_split;
+
+/* Create the slabs.  nslabs in [1, ny]; p as for pf_create (dt <= 0: the default for nz).
+ * PF_E_INVAL for bad sizes or parameters and for PF_FP32_COMP; PF_E_NOMEM / PF_E_CUDA as pf_create. */
+int pf_split_create(int nx, int ny, int nz, const pf_params *p, int nslabs, pf_split **out);
+/* Wait for the split's work and release the slabs, streams and events. */
+int pf_split_destroy(pf_split *d);
+/* The initial state of pf_init(seed) of the undivided domain, in every slab (ghost rows included). */
+int pf_split_init(pf_split *d, uint64_t seed);
+/* nsteps steps of the whole domain (asynchronous); returns the first latched error. */
+int pf_split_step(pf_split *d, int nsteps);
+/* Wait for every slab; returns and clears the first latched error (PF_E_UNSTABLE, PF_E_CUDA, ...). */
+int pf_split_sync(pf_split *d);
+/* The fields of the whole domain, layout as pf_read_fields (cap_cells >= nx ny nz); waits first. */
+int pf_split_read_fields(pf_split *d, double *phi, double *mu, size_t cap_cells);
+/* Simulation time, window offset (planes), interface height sum(1 - phi_l)/(nx ny) of the whole
+ * domain and the planes shifted so far; any pointer may be NULL; waits first. */
+int pf_split_stats(pf_split *d, double *t, double *window_offset, double *h_int, int *planes_shifted);
+
+/*
  * Allocation-free step.  The paper has no counterpart; this entry point serves callers that
  * cannot allocate device memory: code that must live inside a device-memory budget owned by
  * another allocator (a framework's caching pool or a fixed serving arena, where a private

@@ -291,6 +291,15 @@ def reduce(d, phi, mu, t=0.0, off=0.0):
     return fr, so, hh.value, bool(bad.value)
 
 
+def window_shift(d, phi, mu, h_int, off):
+    """The moving window (Section 3.3) on (phi, mu) in place: returns (planes shifted, new offset)."""
+    _, nz, ny, nx = phi.shape
+    assert phi.dtype == np.float64 and phi.flags["C_CONTIGUOUS"] and mu.dtype == np.float64 and mu.flags["C_CONTIGUOUS"]
+    o = ctypes.c_double(off)
+    s = lib().orc_window_shift(ctypes.byref(make_params(d)), nx, ny, nz, h_int, ctypes.byref(o), _dp(phi), _dp(mu))
+    return s, o.value
+
+
 class State:
     """A simulation state held by the oracle: fields, time and window offset."""
 

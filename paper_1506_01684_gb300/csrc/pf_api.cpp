@@ -163,6 +163,9 @@ struct pf_sim {
     int last_nparts = 0;  // partial sums written by the last step's kernels
     int last_kind = -1;   // 0: two sweeps, 1: fused kernel alone, 2: fused kernel + lean kernel
     bool test_withhold = false;  // test hook: the lean kernel's producer issues no copies
+    // a slab of a decomposed domain (pf_split): local row j is global row (j + gy0) mod gny; own rows
+    // [red_j0, red_j1) (gny = 0: not a slab)
+    int gy0 = 0, gny = 0, red_j0 = 0, red_j1 = 0;
     size_t ncell() const { return (size_t)nx * ny * nz; }
     size_t wbytes() const { return p.precision == PF_FP64 ? 8 : 4; }
     bool comp() const { return p.precision == PF_FP32_COMP; }
@@ -252,6 +255,10 @@ static KParams<R> make_kparams(const pf_sim *s)
     k.tgx = s->geo_fused.gx;
     k.tgy = s->geo_fused.gy;
     k.test_flags = s->test_withhold ? 1 : 0;
+    k.gy0 = s->gy0;
+    k.gny = s->gny;
+    k.red_j0 = s->red_j0;
+    k.red_j1 = s->red_j1;
     k.dx = (R)p.dx;
     k.inv_dx = (R)(1.0 / p.dx);
     k.inv_2dx = (R)(1.0 / (2.0 * p.dx));
@@ -657,7 +664,7 @@ static int do_init(pf_sim *s, uint64_t seed, int ng)
     uint64_t stt = seed;
     for (int g = 0; g < ng; g++) {
         seeds[4 * g + 0] = unit53(stt) * (double)s->nx;
-        seeds[4 * g + 1] = unit53(stt) * (double)s->ny;
+        seeds[4 * g + 1] = unit53(stt) * (double)(s->gny > 0 ? s->gny : s->ny);  // a slab: the global domain's rows
         seeds[4 * g + 2] = unit53(stt) * (double)s->p.seed_layers;
         seeds[4 * g + 3] = floor(3.0 * unit53(stt));
     }
@@ -2176,6 +2183,285 @@ int pf_server_stats(pf_server *v, double *mlups, int *running, int *queued, size
     if (running) *running = (int)v->running.size();
     if (queued) *queued = (int)v->queue.size();
     if (used_bytes) *used_bytes = v->used;
+    return PF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// domain decomposition on one device: slabs with ghost rows (the paper's blocks with ghost layers,
+// Section 3.1; Algorithm 1's ghost-layer exchange after each sweep, with Algorithm 2's overlap of the
+// mu exchange and the phi-sweep)
+// ------------------------------------------------------------------------------------------
+struct pf_split {
+    int nx = 0, ny = 0, nz = 0, n = 0;
+    pf_params p;                       // the domain's parameters (dt resolved)
+    std::vector<pf_sim *> slabs;       // slab q: nx x (nys[q] + 2) x nz, own rows 1 .. nys[q]
+    std::vector<int> y0, nys;          // first global row and number of own rows of each slab
+    std::vector<cudaStream_t> xch;     // the mu ghost exchange of each slab (beside its next phi-sweep)
+    std::vector<cudaEvent_t> ev_phi, ev_fin, ev_post, ev_mux;
+    cudaEvent_t ev_comb = nullptr;
+    DevBuf states;                     // DevState * per slab, the combine kernel's argument
+    int latched = PF_OK;
+};
+
+namespace {
+// Row src_row of field src (src_ny rows a plane) into row dst_row of dst (dst_ny rows a plane), in every
+// storage plane: one strided copy of nz rows of nx cells.  The slabs shift their rings alike, so a
+// storage plane holds the same logical plane in every slab.
+cudaError_t copy_row(void *dst, int dst_ny, int dst_row, const void *src, int src_ny, int src_row, int nx, int nz,
+                     size_t cell, cudaStream_t st)
+{
+    const size_t rowb = (size_t)nx * cell;
+    return cudaMemcpy2DAsync((char *)dst + (size_t)dst_row * rowb, (size_t)dst_ny * rowb,
+                             (const char *)src + (size_t)src_row * rowb, (size_t)src_ny * rowb, rowb, (size_t)nz,
+                             cudaMemcpyDeviceToDevice, st);
+}
+
+// The ghost rows of slab q from its neighbours' own boundary rows (periodic in y): row 0 takes the
+// previous slab's last own row, row nys + 1 the next slab's first own row.
+cudaError_t exchange_rows(pf_split *d, int q, int buf, bool phi, cudaStream_t st)
+{
+    const int P = d->n, qp = (q + P - 1) % P, qn = (q + 1) % P;
+    pf_sim *me = d->slabs[q], *pv = d->slabs[qp], *nx_ = d->slabs[qn];
+    const size_t w = me->wbytes(), cell = (phi ? 4 : 2) * w;
+    void *dst = phi ? me->phi[buf].p : me->mu[buf].p;
+    const void *sp = phi ? pv->phi[buf].p : pv->mu[buf].p;
+    const void *sn = phi ? nx_->phi[buf].p : nx_->mu[buf].p;
+    cudaError_t e = copy_row(dst, me->ny, 0, sp, pv->ny, d->nys[qp], d->nx, d->nz, cell, st);
+    if (e == cudaSuccess) e = copy_row(dst, me->ny, d->nys[q] + 1, sn, nx_->ny, 1, d->nx, d->nz, cell, st);
+    return e;
+}
+
+template <typename R>
+int split_step(pf_split *d, int nsteps)
+{
+    const int P = d->n;
+    for (int it = 0; it < nsteps; it++) {
+        cudaError_t e = cudaSuccess;
+        std::vector<KParams<R>> kp(P);
+        for (int q = 0; q < P; q++) kp[q] = make_kparams<R>(d->slabs[q]);
+        const int a = d->slabs[0]->cur, b = 1 - a;  // every slab is on the same buffer
+        // phi-sweep of every slab: it reads mu^n of its own cells only, so it runs while the mu ghost rows
+        // of the previous step are still being copied (Algorithm 2)
+        for (int q = 0; q < P && e == cudaSuccess; q++) {
+            pf_sim *s = d->slabs[q];
+            e = launch_phi_sweep<R>(kp[q], s->geo, s->phi[a].p, s->mu[a].p, s->phi[b].p, (const DevState *)s->state.p,
+                                    (const PlaneT<R> *)s->tab.p, s->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(d->ev_phi[q], s->stream);
+        }
+        // phi^{n+1} ghost rows once the neighbours' phi-sweeps are done (Algorithm 1), then the mu-sweep
+        // once the mu^n ghost rows have arrived
+        for (int q = 0; q < P && e == cudaSuccess; q++) {
+            pf_sim *s = d->slabs[q];
+            e = cudaStreamWaitEvent(s->stream, d->ev_phi[(q + P - 1) % P], 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, d->ev_phi[(q + 1) % P], 0);
+            if (e == cudaSuccess) e = exchange_rows(d, q, b, true, s->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, d->ev_mux[q], 0);
+            if (e == cudaSuccess)
+                e = launch_mu_sweep<R>(kp[q], s->geo, s->phi[a].p, s->phi[b].p, s->mu[a].p, s->mu[b].p,
+                                       (const DevState *)s->state.p, (const PlaneT<R> *)s->tab.p, (Partial *)s->parts.p,
+                                       s->stream);
+            // the slab's own sums (its finalize runs with the window off)
+            if (e == cudaSuccess)
+                e = launch_finalize<R>(kp[q], (DevState *)s->state.p, (const Partial *)s->parts.p, s->geo.nparts(),
+                                       s->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(d->ev_fin[q], s->stream);
+        }
+        // one window decision on the global interface height, applied to every slab
+        cudaStream_t s0 = d->slabs[0]->stream;
+        for (int q = 1; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(s0, d->ev_fin[q], 0);
+        if (e == cudaSuccess)
+            e = launch_split_combine((DevState *const *)d->states.p, P, d->nx, d->ny, d->nz,
+                                     d->p.window_trigger_z > 0.0 ? 1 : 0, d->p.window_trigger_z, s0);
+        if (e == cudaSuccess) e = cudaEventRecord(d->ev_comb, s0);
+        for (int q = 0; q < P && e == cudaSuccess; q++) {
+            pf_sim *s = d->slabs[q];
+            if (q > 0) e = cudaStreamWaitEvent(s->stream, d->ev_comb, 0);
+            if (e == cudaSuccess)
+                e = launch_post<R>(kp[q], (const DevState *)s->state.p, s->phi[b].p, s->mu[b].p, (PlaneT<R> *)s->tab.p,
+                                   s->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(d->ev_post[q], s->stream);
+        }
+        // mu^{n+1} ghost rows after every neighbour's post (its window fill included), on the exchange
+        // streams: they overlap the next phi-sweep, and the next mu-sweep waits for them
+        for (int q = 0; q < P && e == cudaSuccess; q++) {
+            e = cudaStreamWaitEvent(d->xch[q], d->ev_post[(q + P - 1) % P], 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(d->xch[q], d->ev_post[q], 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(d->xch[q], d->ev_post[(q + 1) % P], 0);
+            if (e == cudaSuccess) e = exchange_rows(d, q, b, false, d->xch[q]);
+            if (e == cudaSuccess) e = cudaEventRecord(d->ev_mux[q], d->xch[q]);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (d->latched == PF_OK) d->latched = cuda_status(e);
+            return d->latched;
+        }
+        for (pf_sim *s : d->slabs) {
+            s->cur = b;
+            s->tmap_ok[0] = s->tmap_ok[1] = false;
+            s->last_kind = 0;
+        }
+    }
+    return PF_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int pf_split_destroy(pf_split *d)
+{
+    if (!d) return PF_E_INVAL;
+    for (cudaStream_t x : d->xch)
+        if (x) cudaStreamSynchronize(x);
+    for (pf_sim *s : d->slabs)
+        if (s) pf_destroy(s);
+    for (cudaStream_t x : d->xch)
+        if (x) cudaStreamDestroy(x);
+    for (auto *v : {&d->ev_phi, &d->ev_fin, &d->ev_post, &d->ev_mux})
+        for (cudaEvent_t ev : *v)
+            if (ev) cudaEventDestroy(ev);
+    if (d->ev_comb) cudaEventDestroy(d->ev_comb);
+    dev_free(d->states, nullptr);
+    delete d;
+    return PF_OK;
+}
+
+int pf_split_create(int nx, int ny, int nz, const pf_params *p, int nslabs, pf_split **out)
+{
+    if (!out) return PF_E_INVAL;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || nslabs < 1 || nslabs > ny) return PF_E_INVAL;
+    int r = check_params(p);
+    if (r != PF_OK) return r;
+    if (p->precision == PF_FP32_COMP) return PF_E_INVAL;
+    pf_split *d = new (std::nothrow) pf_split;
+    if (!d) return PF_E_NOMEM;
+    d->nx = nx;
+    d->ny = ny;
+    d->nz = nz;
+    d->n = nslabs;
+    d->p = *p;
+    if (!(d->p.dt > 0.0)) d->p.dt = default_dt(d->p, nz);
+    pf_params q = d->p;
+    q.window_trigger_z = 0.0;  // the slabs never move their windows on their own: the combine kernel does
+    for (int k = 0; k < nslabs && r == PF_OK; k++) {
+        const int y0 = (int)((long long)k * ny / nslabs), y1 = (int)((long long)(k + 1) * ny / nslabs);
+        d->y0.push_back(y0);
+        d->nys.push_back(y1 - y0);
+        pf_sim *s = nullptr;
+        r = pf_create(nx, y1 - y0 + 2, nz, &q, nullptr, &s);
+        if (r != PF_OK) break;
+        d->slabs.push_back(s);
+        s->variant = PF_VARIANT_UNFUSED;  // Algorithm 1's two sweeps
+        s->gy0 = y0 - 1;                  // local row 0 is the ghost row below the slab
+        s->gny = ny;
+        s->red_j0 = 1;
+        s->red_j1 = y1 - y0 + 1;
+        cudaStream_t x = nullptr;
+        cudaEvent_t e4[4] = {nullptr, nullptr, nullptr, nullptr};
+        cudaError_t e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+        for (int j = 0; j < 4 && e == cudaSuccess; j++) e = cudaEventCreateWithFlags(&e4[j], cudaEventDisableTiming);
+        d->xch.push_back(x);
+        d->ev_phi.push_back(e4[0]);
+        d->ev_fin.push_back(e4[1]);
+        d->ev_post.push_back(e4[2]);
+        d->ev_mux.push_back(e4[3]);
+        if (e != cudaSuccess) r = cuda_status(e);
+    }
+    if (r == PF_OK) {
+        cudaError_t e = cudaEventCreateWithFlags(&d->ev_comb, cudaEventDisableTiming);
+        if (e != cudaSuccess) r = cuda_status(e);
+    }
+    if (r == PF_OK) r = dev_alloc(d->states, sizeof(DevState *) * nslabs, nullptr);
+    if (r == PF_OK) {
+        std::vector<DevState *> ptr;
+        for (pf_sim *s : d->slabs) ptr.push_back((DevState *)s->state.p);
+        cudaError_t e = cudaMemcpy(d->states.p, ptr.data(), sizeof(DevState *) * nslabs, cudaMemcpyHostToDevice);
+        // the exchange events start recorded (an initial state has valid ghost rows)
+        for (int k = 0; k < nslabs && e == cudaSuccess; k++) e = cudaEventRecord(d->ev_mux[k], d->xch[k]);
+        if (e != cudaSuccess) r = cuda_status(e);
+    }
+    if (r != PF_OK) {
+        pf_split_destroy(d);
+        return r;
+    }
+    *out = d;
+    return PF_OK;
+}
+
+int pf_split_sync(pf_split *d)
+{
+    if (!d) return PF_E_INVAL;
+    int r = d->latched;
+    d->latched = PF_OK;
+    for (cudaStream_t x : d->xch)
+        if (cudaStreamSynchronize(x) != cudaSuccess && r == PF_OK) r = PF_E_CUDA;
+    for (pf_sim *s : d->slabs) {
+        const int rs = pf_sync(s);
+        if (r == PF_OK) r = rs;
+    }
+    return r;
+}
+
+int pf_split_init(pf_split *d, uint64_t seed)
+{
+    if (!d) return PF_E_INVAL;
+    int r = pf_split_sync(d);
+    (void)r;
+    // every slab, its ghost rows included, takes the rows of the global domain it covers
+    for (pf_sim *s : d->slabs) {
+        const int ri = pf_init(s, seed);
+        if (ri != PF_OK) return ri;
+    }
+    return PF_OK;
+}
+
+int pf_split_step(pf_split *d, int nsteps)
+{
+    if (!d || nsteps < 0) return PF_E_INVAL;
+    if (d->latched != PF_OK) return d->latched;
+    return d->p.precision == PF_FP64 ? split_step<double>(d, nsteps) : split_step<float>(d, nsteps);
+}
+
+int pf_split_read_fields(pf_split *d, double *phi, double *mu, size_t cap_cells)
+{
+    if (!d || cap_cells < (size_t)d->nx * d->ny * d->nz) return PF_E_INVAL;
+    int r = pf_split_sync(d);
+    if (r != PF_OK) return r;
+    const size_t nxy = (size_t)d->nx, plane = (size_t)d->nx * d->ny, n = plane * d->nz;
+    for (int q = 0; q < d->n; q++) {
+        pf_sim *s = d->slabs[q];
+        const size_t sn = s->ncell(), splane = (size_t)d->nx * s->ny;
+        std::vector<double> tp(phi ? 4 * sn : 0), tm(mu ? 2 * sn : 0);
+        r = pf_read_fields(s, phi ? tp.data() : nullptr, mu ? tm.data() : nullptr, sn);
+        if (r != PF_OK) return r;
+        // the slab's own rows 1 .. nys into global rows y0 ..
+        for (int k = 0; k < d->nz; k++)
+            for (int j = 0; j < d->nys[q]; j++) {
+                const size_t gsrc = (size_t)k * splane + (size_t)(j + 1) * nxy;
+                const size_t gdst = (size_t)k * plane + (size_t)(d->y0[q] + j) * nxy;
+                for (int c = 0; c < 4 && phi; c++)
+                    memcpy(phi + c * n + gdst, tp.data() + c * sn + gsrc, nxy * sizeof(double));
+                for (int c = 0; c < 2 && mu; c++)
+                    memcpy(mu + c * n + gdst, tm.data() + c * sn + gsrc, nxy * sizeof(double));
+            }
+    }
+    return PF_OK;
+}
+
+int pf_split_stats(pf_split *d, double *t, double *window_offset, double *h_int, int *planes_shifted)
+{
+    if (!d) return PF_E_INVAL;
+    int r = pf_split_sync(d);
+    if (r != PF_OK) return r;
+    DevState ds;
+    r = read_state(d->slabs[0], &ds);
+    if (r != PF_OK) return r;
+    if (t) *t = ds.t;
+    if (window_offset) *window_offset = ds.off;
+    if (h_int) *h_int = ds.h_int;
+    if (planes_shifted) *planes_shifted = ds.nshift_total;
     return PF_OK;
 }
 

@@ -22,6 +22,7 @@ struct DevState {
     int shift;         // planes shifted by the last finalize (0: none); read by post_kernel
     int nonfinite;     // sticky: 1 a non-finite value was seen, 2 a bounded device wait gave up
     int nshift_total;  // planes shifted since init
+    double liq;        // sum over the counted cells of (1 - phi_l) measured after the last step (FP64)
 };
 
 // Per-CTA partial sums written by the mu-sweep epilogue (FP64).
@@ -66,6 +67,10 @@ struct KParams {
     int window;  // 1: moving window enabled
     int tgx, tgy;  // tile grid of the fused step (liquid map layout)
     int test_flags;  // bit 0: the lean kernel's producer withholds its copies (tests of the bounded waits)
+    // a slab of a decomposed domain (pf_split): local row j is global row (j + gy0) mod gny of a domain
+    // gny rows high (gny = 0: the domain itself); rows [red_j0, red_j1) are the slab's own rows, the only
+    // ones the reductions count (the others are ghost rows)
+    int gy0, gny, red_j0, red_j1;
     R dx, inv_dx, inv_2dx, inv_4dx;
     R eps, inv_eps;
     R c_phi;  // dt / (tau eps)
@@ -236,6 +241,11 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
                                      bool sym);  // sym: every domain has the symmetric parameter set
 template <typename R>
 void batched_general_ctas_per_sm(int *phi_per_sm, int *mu_per_sm);
+// The window decision of a decomposed domain (one thread): the global interface height from the slabs'
+// liquid-deficit sums (in slab order) over nx * ny_global cells, then the same shift applied to every
+// slab's state (each slab's finalize ran with the window off).
+cudaError_t launch_split_combine(DevState *const *states, int nslabs, int nx, int ny_global, int nz, int window,
+                                 double trigger, cudaStream_t s);
 template <typename R>
 cudaError_t launch_post(const KParams<R> &kp, const DevState *st, void *phi, void *mu, PlaneT<R> *tab,
                         cudaStream_t s, void *phi_lo = nullptr, void *mu_lo = nullptr,

@@ -1021,6 +1021,7 @@ __device__ __forceinline__ void mu_sweep_tile(const KParams<R> &kp, const Ph<R> 
     const int ntl = kp.tgx * kp.tgy;
     const bool xtra_y = ty == 0;
     const bool xtra_x = ty == 1 % TY && tx < TY;
+    const bool counted = kp.gny == 0 || (j0 + ty >= kp.red_j0 && j0 + ty < kp.red_j1);
 
     Ph<R> pfN0, pfN1, pfO0, pfO1;
     Mu<R> pfM0, pfM1;
@@ -1156,8 +1157,10 @@ __device__ __forceinline__ void mu_sweep_tile(const KParams<R> &kp, const Ph<R> 
             }
             if (valid) {
                 st_mu(mu_out + plane_off(p, nz, zbase, plane) + col0, out);
-                liq_def += 1.0 - (double)ownN.v[3];
-                bad = bad || !isfinite(out.v[0]) || !isfinite(out.v[1]) || !finite4(ownN);
+                if (counted) {  // (a slab's ghost rows are not its own)
+                    liq_def += 1.0 - (double)ownN.v[3];
+                    bad = bad || !isfinite(out.v[0]) || !isfinite(out.v[1]) || !finite4(ownN);
+                }
             }
         }
         // B(p+1), A(p+3)
@@ -2403,6 +2406,7 @@ __device__ __forceinline__ void finalize_body(const KParams<R> &kp, DevState *__
         if (tmo) st->nonfinite = 2;
         const double h = sa[0] / ((double)kp.nx * (double)kp.ny);
         st->h_int = h;
+        st->liq = sa[0];
         int s = 0;
         if (kp.window && h >= kp.window_trigger_z) {
             s = (int)floor(h - kp.window_trigger_z) + 1;
@@ -2527,9 +2531,12 @@ __global__ void __launch_bounds__(256) init_kernel(const KParams<R> kp, Ph<R> *_
                                                   int n_grains, int H)
 {
     const size_t plane = (size_t)kp.nx * kp.ny, n = plane * kp.nz;
+    // a slab of a decomposed domain takes the rows of the global domain it covers
+    const int nyg = kp.gny > 0 ? kp.gny : kp.ny;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(q / plane);
-        const int j = (int)((q % plane) / kp.nx);
+        const int jl = (int)((q % plane) / kp.nx);
+        const int j = kp.gny > 0 ? ((jl + kp.gy0) % nyg + nyg) % nyg : jl;
         const int i = (int)(q % kp.nx);
         int ph = 3;
         if (k < H && n_grains > 0) {
@@ -2539,7 +2546,7 @@ __global__ void __launch_bounds__(256) init_kernel(const KParams<R> kp, Ph<R> *_
                 double ddx = fabs(__dadd_rn((double)i + 0.5, -seeds[4 * g + 0]));
                 double ddy = fabs(__dadd_rn((double)j + 0.5, -seeds[4 * g + 1]));
                 double ddz = fabs(__dadd_rn((double)k + 0.5, -seeds[4 * g + 2]));
-                const double wx = __dadd_rn((double)kp.nx, -ddx), wy = __dadd_rn((double)kp.ny, -ddy);
+                const double wx = __dadd_rn((double)kp.nx, -ddx), wy = __dadd_rn((double)nyg, -ddy);
                 if (wx < ddx) ddx = wx;
                 if (wy < ddy) ddy = wy;
                 const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
@@ -3076,6 +3083,43 @@ cudaError_t launch_lean_step(const KParams<R> &kp, const Geometry &g, int nsub, 
 }
 
 #ifdef PF_FLOAT_UNIT
+// The window decision of a decomposed domain (reading R11 on the global interface height): one thread
+// sums the slabs' liquid deficits in slab order, decides the shift as finalize_body does, and applies it
+// to every slab's state, so that all slabs move their rings alike.  Defined in the FP32 unit only (it
+// does not depend on the stencil precision).
+__global__ void split_combine_kernel(DevState *const *states, int nslabs, int nx, int ny_global, int nz, int window,
+                                     double trigger)
+{
+    pdl_wait();
+    double liq = 0.0;
+    for (int q = 0; q < nslabs; q++) liq += states[q]->liq;
+    const double h = liq / ((double)nx * (double)ny_global);
+    int sh = 0;
+    if (window && h >= trigger) {
+        sh = (int)floor(h - trigger) + 1;
+        if (sh > nz - 1) sh = nz - 1;
+        if (sh < 0) sh = 0;
+    }
+    for (int q = 0; q < nslabs; q++) {
+        DevState *st = states[q];
+        st->h_int = h;
+        st->shift = sh;
+        if (sh > 0) {
+            int zb = st->zbase + sh;
+            if (zb >= nz) zb -= nz;
+            st->zbase = zb;
+            st->off = st->off + (double)sh;
+            st->nshift_total += sh;
+        }
+    }
+}
+cudaError_t launch_split_combine(DevState *const *states, int nslabs, int nx, int ny_global, int nz, int window,
+                                 double trigger, cudaStream_t s)
+{
+    split_combine_kernel<<<1, 1, 0, s>>>(states, nslabs, nx, ny_global, nz, window, trigger);
+    return cudaGetLastError();
+}
+
 // compensated FP32 sweeps (the low words of the state ride along); defined in the FP32 unit only
 cudaError_t launch_phi_sweep_comp(const KParams<float> &kp, const Geometry &g, const void *phi, const void *phi_lo,
                                   const void *mu, void *phi_out, void *phi_out_lo, const DevState *st,

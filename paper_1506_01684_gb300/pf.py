@@ -110,6 +110,13 @@ SIGNATURES = {
     "pf_poll": (_I, [_VP, ctypes.c_uint64, _DP, ctypes.POINTER(ctypes.c_float), _DP]),
     "pf_cancel": (_I, [_VP, ctypes.c_uint64]),
     "pf_server_stats": (_I, [_VP, _DP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
+    "pf_split_create": (_I, [_I, _I, _I, ctypes.POINTER(pf_params), _I, ctypes.POINTER(_VP)]),
+    "pf_split_destroy": (_I, [_VP]),
+    "pf_split_init": (_I, [_VP, ctypes.c_uint64]),
+    "pf_split_step": (_I, [_VP, _I]),
+    "pf_split_sync": (_I, [_VP]),
+    "pf_split_read_fields": (_I, [_VP, _DP, _DP, ctypes.c_size_t]),
+    "pf_split_stats": (_I, [_VP, _DP, _DP, _DP, ctypes.POINTER(_I)]),
 }
 
 PF_K_PHI, PF_K_MU, PF_K_FINALIZE, PF_K_POST, PF_K_FUSED, PF_K_LEAN, PF_K_PLAN, PF_K_GENERAL = 0, 1, 2, 3, 4, 5, 6, 7
@@ -442,6 +449,87 @@ def pf_server_stats(srv):
     _check(lib().pf_server_stats(srv, ctypes.byref(m), ctypes.byref(r), ctypes.byref(q), ctypes.byref(u)),
            "pf_server_stats")
     return {"mlups": m.value, "running": r.value, "queued": q.value, "used_bytes": u.value}
+
+
+def pf_split_create(nx, ny, nz, params: pf_params, nslabs: int):
+    h = _VP()
+    _check(lib().pf_split_create(nx, ny, nz, ctypes.byref(params), nslabs, ctypes.byref(h)), "pf_split_create")
+    return h.value
+
+
+def pf_split_destroy(d):
+    return _check(lib().pf_split_destroy(d), "pf_split_destroy")
+
+
+def pf_split_init(d, seed: int):
+    return _check(lib().pf_split_init(d, seed), "pf_split_init")
+
+
+def pf_split_step(d, nsteps: int):
+    return _check(lib().pf_split_step(d, nsteps), "pf_split_step")
+
+
+def pf_split_sync(d):
+    return _check(lib().pf_split_sync(d), "pf_split_sync")
+
+
+def pf_split_read_fields(d, phi: np.ndarray | None, mu: np.ndarray | None):
+    n = None
+    for a in (phi, mu):
+        if a is not None:
+            n = a.shape[-1] * a.shape[-2] * a.shape[-3]
+    return _check(lib().pf_split_read_fields(d, _dp(phi) if phi is not None else None,
+                                             _dp(mu) if mu is not None else None, n or 0), "pf_split_read_fields")
+
+
+def pf_split_stats(d):
+    t, off, h, n = _D(), _D(), _D(), _I()
+    _check(lib().pf_split_stats(d, ctypes.byref(t), ctypes.byref(off), ctypes.byref(h), ctypes.byref(n)),
+           "pf_split_stats")
+    return {"t": t.value, "window_offset": off.value, "h_int": h.value, "shifts": n.value}
+
+
+class Split:
+    """Owns one pf_split: one domain cut into y-slabs with ghost rows, stepped as separate blocks."""
+
+    def __init__(self, nx, ny, nz, params: dict | pf_params, nslabs, precision="fp64"):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        p = params if isinstance(params, pf_params) else params_from_dict(params, prec)
+        p.precision = prec
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.h = pf_split_create(nx, ny, nz, p, nslabs)
+
+    def close(self):
+        if self.h:
+            pf_split_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, seed: int):
+        pf_split_init(self.h, seed)
+        return self
+
+    def step(self, n: int = 1):
+        pf_split_step(self.h, n)
+        return self
+
+    def sync(self):
+        pf_split_sync(self.h)
+        return self
+
+    def fields(self):
+        phi = np.empty((4, self.nz, self.ny, self.nx))
+        mu = np.empty((2, self.nz, self.ny, self.nx))
+        pf_split_read_fields(self.h, phi, mu)
+        return phi, mu
+
+    def stats(self):
+        return pf_split_stats(self.h)
 
 
 class Batch:
