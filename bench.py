@@ -62,16 +62,17 @@ METRIC = "phi+mu step MLUP/s (FP32 stencil; FP64 GPU path and error reported bes
 # depth, mu larger than L2; the capture and its command are in profiles/lean_step_traffic_fp32_256x256x512.md);
 # traffic of a full launch = this ratio x the launch's algorithmic bytes (traffic grows with the lean
 # cells).  Remove an entry when its kernel changes.
-TRAFFIC_RATIO = {"lean_step": 0.94}
+TRAFFIC_RATIO = {"lean_step": 0.93}
 
 
 # The general planes' two sweeps (the interface cells) are bound by the FP32 units, not HBM: per general
 # cell, the FP32 operations (FADD, FMUL = 1, FFMA = 2) and the thread instructions of both sweeps, halo
 # and prologue work included, from the SASS counters of an ncu capture of the kernels as they are now
 # (summed over general_phi_kernel and general_mu_kernel, divided by the general cells the launch
-# processed).  None: not measured for the current kernels.  Remove the entries when the kernels change.
-GENERAL_FLOPS_PER_CELL = None
-GENERAL_INSTS_PER_CELL = None
+# processed; the capture and its command are in profiles/general_sweeps_flops_fp32_256x256x512.md).
+# None: not measured for the current kernels.  Remove the entries when the kernels change.
+GENERAL_FLOPS_PER_CELL = 730.0
+GENERAL_INSTS_PER_CELL = 1389.0
 
 
 def alu_roofline(k, general_cells, clk):
@@ -284,6 +285,13 @@ def run_batched_study(args):
     torch.cuda.synchronize()
     ms_batch = e0.elapsed_time(e1) / args.steps
     b.sync()
+    # algorithmic bytes of a step (the kernels' own tally of the last step): the whole batched step
+    # against the HBM roofline, and the design bound its bytes set
+    sb = pf.pf_batch_step_bytes(b.h)
+    step_bytes = sb["general_and_fused"] + sb["lean_step"]
+    hbm, peak_kind = _peaks()
+    achieved = step_bytes / (ms_batch / 1e3) / 1e9
+    design_bound = hbm * 1e9 / (step_bytes / cells) / 1e6 if step_bytes else None
     b.close()
     # one by one: each domain its own pf_sim (fused kernel, graph replay), run back to back
     sims = []
@@ -306,6 +314,12 @@ def run_batched_study(args):
             "speedup_vs_one_by_one": ms_single / ms_batch, "ms_per_step": ms_batch,
             "ms_per_step_one_by_one": ms_single, "cells": cells, "domains": len(shapes),
             "autotuned_zchunk": zc, "autotune_ms_per_step": tune_ms, "steps": args.steps, "warmup": args.warmup,
+            "roofline": {"bound": "hbm", "kernel": "whole batched step", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+                         "bytes_per_cell": step_bytes / cells,
+                         "lean_share_of_bytes": sb["lean_step"] / step_bytes if step_bytes else None,
+                         "what": "algorithmic bytes of one step (the kernels' tally) / the step's time"},
+            "frac_of_design_bound": (cells / (ms_batch / 1e3) / 1e6) / design_bound if design_bound else None,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "64 domains, x,y in {32,64,96,128}, z in {128,256,512}, v in [5e-3,2e-2], "
                                    "G in [5e-4,2e-3], 12 grains each (numpy PCG64 seed 0)"}}

@@ -176,6 +176,14 @@ int pf_write_fields_f32(pf_sim *sim, const float *phi, const float *mu);
  * PF_E_INVAL if the file cannot be written.  Synchronising. */
 int pf_checkpoint_write(pf_sim *sim, const char *path);
 
+/* The paper's single-precision checkpoint (Section 3.2: the computation in double precision, the
+ * checkpoints in single): the file of pf_checkpoint_write with 4 bytes per value and writer
+ * precision PF_FP32, each value of an FP64 or compensated state rounded once to FP32 (an FP32 state
+ * is written exactly).  Half the bytes of an FP64 checkpoint; a run resumed from it starts from
+ * the rounded state, so it departs from the uninterrupted run by the FP32 rounding (relative
+ * 2^-24 of each value) carried forward by the dynamics.  Errors as pf_checkpoint_write. */
+int pf_checkpoint_write_f32(pf_sim *sim, const char *path);
+
 /* Restore a checkpoint written for the same grid (any precision: values are converted to this
  * simulation's): fields, time, window offset and shift count; the plane table is rebuilt and no
  * window shift is pending.  A run resumed from a checkpoint of its own precision continues bitwise
@@ -323,6 +331,10 @@ int pf_batch_set_zchunk(pf_batch *b, int zchunk);
  * fields, clocks and windows are restored afterwards), keeps the fastest and returns it in
  * *best (may be NULL) and its measured milliseconds per step in *best_ms (may be NULL). */
 int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms);
+/* Algorithmic bytes of the batch's last step, as its kernels tallied them (compulsory traffic of
+ * each cell's words, the measure of pf_step_bytes): bytes[0] the general planes' sweeps and the fused
+ * tiles, bytes[1] the lean kernel's pure-liquid planes.  Synchronising. */
+int pf_batch_step_bytes(pf_batch *b, double bytes[2]);
 
 /*
  * Serving.  No counterpart in the paper: a request loop of the library that runs many independent
@@ -394,8 +406,9 @@ int pf_split_step(pf_split *d, int nsteps);
 int pf_split_sync(pf_split *d);
 /* The fields of the whole domain, layout as pf_read_fields (cap_cells >= nx ny nz); waits first. */
 int pf_split_read_fields(pf_split *d, double *phi, double *mu, size_t cap_cells);
-/* Simulation time, window offset (planes), interface height sum(1 - phi_l)/(nx ny) of the whole
- * domain and the planes shifted so far; any pointer may be NULL; waits first. */
+/* Simulation time, window offset (planes), interface height sum(1 - phi_l)/(nx ny) of the current
+ * fields of the whole domain (each slab's FP64 sum over its own rows) and the planes shifted so far;
+ * any pointer may be NULL; waits first. */
 int pf_split_stats(pf_split *d, double *t, double *window_offset, double *h_int, int *planes_shifted);
 
 /*

@@ -24,11 +24,25 @@
 
 using namespace pf;
 
-// Launch shape of the fused step with the lean kernel: the persistent general-plane CTAs per SM (two
-// take all of an SM's registers; a second stream for the general planes beside the lean kernel gained
-// nothing for that reason, measured on 256x256x1024 FP32).
+// Launch shape of the fused step with the lean kernel.  The general planes' sweeps (latency-bound) run
+// on a second stream of the highest priority beside the lean kernel (HBM-bound), launched first, so
+// that their persistent CTAs are placed before the lean CTAs and the two kernels fill each other's
+// tails (PF_CONCURRENT 1; 0: the sweeps after the lean kernel on the simulation's stream).  Persistent
+// general CTAs per SM: two (they take all of an SM's registers while they run; one makes the sweeps
+// 1.5x slower and the step slower than the serial form, measured on 256x256x1024 FP32).
+#ifndef PF_CONCURRENT
+#define PF_CONCURRENT 1
+#endif
 #ifndef PF_GENERAL_CTAS_PER_SM
 #define PF_GENERAL_CTAS_PER_SM 2
+#endif
+// with PF_CONCURRENT: the sweeps' launches carry the highest priority (1) or none (0), and are made
+// before the lean kernel's (1) or after it (0)
+#ifndef PF_GENERAL_PRIO
+#define PF_GENERAL_PRIO 1
+#endif
+#ifndef PF_GENERAL_FIRST
+#define PF_GENERAL_FIRST 1
 #endif
 #ifndef PF_LEAN_PLANES
 #define PF_LEAN_PLANES 64  // at most planes per lean CTA (the kernels' limit, PF_LEAN_PLANES in pf_kernels.cuh)
@@ -118,6 +132,10 @@ struct pf_sim {
     pf_params p;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the general planes' sweeps beside the lean kernel: a stream of the highest priority, so that
+    // their persistent CTAs are placed before the lean kernel's; events for the fork and the join
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     Geometry geo;          // unfused sweeps
     Geometry geo_fused;    // fused step (longer z chunks: its prologue recomputes two planes)
     int variant = PF_VARIANT_AUTO;
@@ -492,6 +510,36 @@ static cudaError_t ensure_maps(pf_sim *s, cudaStream_t stream)
     return cudaSuccess;
 }
 
+// The second stream and the fork / join events of the general planes' sweeps beside the lean kernel,
+// made on the first step that takes the lean path (not while the simulation's stream is being
+// captured: such a step runs the sweeps after the lean kernel).
+static void ensure_aux(pf_sim *s)
+{
+    if (!PF_CONCURRENT || s->aux) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return;
+    }
+    int lo = 0, hi = 0;
+    cudaStream_t x = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&x, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming);
+    if (e != cudaSuccess) {  // the serial form needs none of them
+        cudaGetLastError();
+        if (x) cudaStreamDestroy(x);
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        return;
+    }
+    s->aux = x;
+    s->ev_fork = a;
+    s->ev_join = b;
+}
+
 template <typename R>
 static int do_step_direct(pf_sim *s, int n)
 {
@@ -502,6 +550,7 @@ static int do_step_direct(pf_sim *s, int n)
     PlaneT<R> *tab = (PlaneT<R> *)s->tab.p;
     Partial *parts = (Partial *)s->parts.p;
     const bool lean = fused && s->lean_ok;
+    if (lean) ensure_aux(s);
     const int np_fused = s->geo_fused.nparts();
     const int nparts = fused ? np_fused : s->geo.nparts();
     s->last_nparts = nparts;
@@ -555,8 +604,27 @@ static int do_step_direct(pf_sim *s, int n)
                         return launch_plan<R>(kp, s->geo_fused, st, tin, (int2 *)s->splits.p, (int *)s->glist.p, ls,
                                               parts, s->stream, pdl);
                     });
-                if (e == cudaSuccess) e = leanp();
-                if (e == cudaSuccess) e = general();
+                if (s->aux && !s->prof && PF_GENERAL_SWEEPS) {
+                    // the general planes' sweeps (latency-bound) beside the lean kernel (HBM-bound): both
+                    // start once the plan is done; the general sweeps go first, on the stream of the
+                    // highest priority, and finalize waits for both
+                    if (e == cudaSuccess) e = cudaEventRecord(s->ev_fork, s->stream);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->aux, s->ev_fork, 0);
+                    if (e == cudaSuccess && !PF_GENERAL_FIRST) e = leanp();
+                    if (e == cudaSuccess)
+                        e = launch_general_sweeps<R>(kp, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st, tab,
+                                                     parts, tin, tout, (const int2 *)s->splits.p,
+                                                     (const int *)s->glist.p, ls, s->gphi_ctas, s->gmu_ctas, s->aux,
+                                                     (Partial *)s->subparts.p, (unsigned *)s->subcnt.p, false, false,
+                                                     s->lo_phi(a), s->lo_phi(b), s->lo_mu(a), s->lo_mu(b),
+                                                     PF_GENERAL_PRIO != 0);
+                    if (e == cudaSuccess) e = cudaEventRecord(s->ev_join, s->aux);
+                    if (e == cudaSuccess && PF_GENERAL_FIRST) e = leanp();
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+                } else {
+                    if (e == cudaSuccess) e = leanp();
+                    if (e == cudaSuccess) e = general();
+                }
             }
         } else if (s->comp()) {
             const KParams<float> &kf = reinterpret_cast<const KParams<float> &>(kp);
@@ -583,7 +651,8 @@ static int do_step_direct(pf_sim *s, int n)
         if (e == cudaSuccess)
             e = timed(s, PF_K_FINALIZE, [&] {
                 return launch_finalize<R>(kp, st, parts, nparts, s->stream,
-                                          lean ? (LeanStats *)s->lean_stats.p : nullptr, lean && PF_PDL);
+                                          lean ? (LeanStats *)s->lean_stats.p : nullptr,
+                                          lean && PF_PDL && !(s->aux && !s->prof));
             });
         if (e == cudaSuccess)
             e = timed(s, PF_K_POST, [&] {
@@ -625,6 +694,7 @@ static int do_step(pf_sim *s, int n)
         cudaError_t e = ensure_maps<R>(s, s->stream);
         if (e != cudaSuccess) return latch(s, cuda_status(e));
     }
+    if (want && s->lean_ok) ensure_aux(s);  // before the capture: the graph holds the fork and the join
     if (!s->graph || s->graph_variant != want) {
         if (s->graph) {
             cudaGraphExecDestroy(s->graph);
@@ -639,7 +709,8 @@ static int do_step(pf_sim *s, int n)
             if (g) cudaGraphDestroy(g);
             return latch(s, r != PF_OK ? r : cuda_status(e));
         }
-        e = cudaGraphInstantiate(&s->graph, g, 0);
+        // the kernel nodes' launch priorities (the general planes' sweeps beside the lean kernel) apply
+        e = cudaGraphInstantiate(&s->graph, g, s->aux ? cudaGraphInstantiateFlagUseNodePriority : 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             s->graph = nullptr;
@@ -861,7 +932,7 @@ const char kCkptMagic[8] = {'P', 'F', 'C', 'K', 'P', 'T', '0', '1'};
 }  // namespace
 
 template <typename R>
-static int do_checkpoint_write(pf_sim *s, const char *path)
+static int do_checkpoint_write(pf_sim *s, const char *path, int single)
 {
     DevState ds;
     int r = read_state(s, &ds);
@@ -875,9 +946,11 @@ static int do_checkpoint_write(pf_sim *s, const char *path)
     h.nz = s->nz;
     // the state's own values, exactly: FP32 words for FP32, FP64 for FP64, and for the compensated
     // state its two FP32 words (a high/low pair need not be one FP64 value)
-    const bool pairs = s->comp();
-    h.elem = s->p.precision == PF_FP64 ? 8 : 4;
-    h.precision = s->p.precision;
+    // (single: the paper's single-precision checkpoint, every value rounded once to FP32 and written as
+    // an FP32 writer's file)
+    const bool pairs = s->comp() && !single;
+    h.elem = s->p.precision == PF_FP64 && !single ? 8 : 4;
+    h.precision = single ? PF_FP32 : s->p.precision;
     h.nshift = ds.nshift_total;
     h.t = ds.t;
     h.off = ds.off;
@@ -1111,6 +1184,12 @@ int pf_destroy(pf_sim *s)
     }
     for (auto e : s->pool) cudaEventDestroy(e);
     if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->aux) {
+        cudaStreamSynchronize(s->aux);
+        cudaStreamDestroy(s->aux);
+    }
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
     return PF_OK;
@@ -1291,7 +1370,13 @@ int pf_write_fields_f32(pf_sim *s, const float *phi, const float *mu)
 int pf_checkpoint_write(pf_sim *s, const char *path)
 {
     if (!s || !path) return PF_E_INVAL;
-    return PF_DISPATCH(s, do_checkpoint_write, s, path);
+    return PF_DISPATCH(s, do_checkpoint_write, s, path, 0);
+}
+
+int pf_checkpoint_write_f32(pf_sim *s, const char *path)
+{
+    if (!s || !path) return PF_E_INVAL;
+    return PF_DISPATCH(s, do_checkpoint_write, s, path, 1);
 }
 
 int pf_checkpoint_read(pf_sim *s, const char *path)
@@ -1453,6 +1538,8 @@ struct pf_batch {
     int nplan = 0, nlean = 0, gphi_ctas = 1, gmu_ctas = 1;
     bool lean_mode = false;
     bool sym = true;  // every domain has the symmetric set (no matrix curvature, no pair times)
+    size_t nparts_total = 0;  // partial sums of all domains (their algorithmic-byte tallies)
+    std::vector<char> dom_lean;  // the domain runs the lean path
 };
 
 template <typename R>
@@ -1497,6 +1584,8 @@ static int batch_build(pf_batch *b)
         part_total += (size_t)g.nparts();
         // the lean path needs the TMA maps and a chunk the batched plan covers
         const bool lean = s->lean_ok && g.zchunk + 4 <= 64 * 9;
+        if (q == 0) b->dom_lean.assign(n, 0);
+        b->dom_lean[q] = lean ? 1 : 0;
         if (lean) {
             split_off[q] = split_total;
             split_total += (size_t)g.nparts();
@@ -1585,6 +1674,7 @@ static int batch_build(pf_batch *b)
         b->gmu_ctas = std::max(1, std::min(b->nplan, std::min(pm, PF_GENERAL_CTAS_PER_SM) * sms));
     }
     b->post_blocks = post;
+    b->nparts_total = part_total;
     b->built = true;
     b->parity = 0;
     b->cur0.resize(n);
@@ -1780,6 +1870,28 @@ int pf_batch_set_zchunk(pf_batch *b, int zchunk)
         b->zchunk = zchunk;
         b->built = false;
     }
+    return PF_OK;
+}
+
+int pf_batch_step_bytes(pf_batch *b, double bytes[2])
+{
+    if (!b || !bytes) return PF_E_INVAL;
+    bytes[0] = bytes[1] = 0.0;
+    if (!b->built) return PF_OK;
+    std::vector<Partial> h(b->nparts_total);
+    cudaError_t e = cudaSuccess;
+    if (!h.empty())
+        e = cudaMemcpyAsync(h.data(), b->parts.p, h.size() * sizeof(Partial), cudaMemcpyDeviceToHost, b->stream);
+    std::vector<LeanStats> ls(b->sims.size());
+    for (size_t q = 0; q < b->sims.size() && e == cudaSuccess; q++)
+        e = cudaMemcpyAsync(&ls[q], b->sims[q]->lean_stats.p, sizeof(LeanStats), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (const Partial &x : h) bytes[0] += x.bytes;
+    // the lean kernel's tally of each domain on the lean path (zero for the others)
+    if (b->lean_mode)
+        for (size_t q = 0; q < ls.size(); q++)
+            if (q < b->dom_lean.size() && b->dom_lean[q]) bytes[1] += (double)ls[q].last_bytes;
     return PF_OK;
 }
 
@@ -2460,8 +2572,18 @@ int pf_split_stats(pf_split *d, double *t, double *window_offset, double *h_int,
     if (r != PF_OK) return r;
     if (t) *t = ds.t;
     if (window_offset) *window_offset = ds.off;
-    if (h_int) *h_int = ds.h_int;
     if (planes_shifted) *planes_shifted = ds.nshift_total;
+    if (h_int) {
+        // of the current fields: each slab's FP64 sum over its own rows
+        double liq = 0.0;
+        for (pf_sim *s : d->slabs) {
+            double acc[8];
+            r = PF_DISPATCH(s, do_reduce, s, acc);
+            if (r != PF_OK) return r;
+            liq += acc[6];
+        }
+        *h_int = liq / ((double)d->nx * (double)d->ny);
+    }
     return PF_OK;
 }
 

@@ -212,7 +212,8 @@ cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const v
                                   cudaStream_t s, Partial *subparts, unsigned *subcnt, bool pdl = false,
                                   bool after_lean = false,  // after_lean: launched right behind the lean kernel
                                   const void *phi_lo = nullptr, void *phi_out_lo = nullptr,  // compensated FP32:
-                                  const void *mu_lo = nullptr, void *mu_out_lo = nullptr);   // the low words
+                                  const void *mu_lo = nullptr, void *mu_out_lo = nullptr,    // the low words
+                                  bool prio = false);  // prio: the device's highest launch priority
 template <typename R>
 void general_sweep_ctas_per_sm(int *phi_per_sm, int *mu_per_sm);
 // liquid map of a field (for states not produced by a fused step)

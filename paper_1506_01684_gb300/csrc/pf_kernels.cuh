@@ -2586,7 +2586,9 @@ __global__ void __launch_bounds__(256) reduce_kernel(const KParams<R> kp, const 
         ch[a][1] = kp.cE[a][1] + kp.kT64[a][1] * (T - kp.TE);
     }
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (size_t q = threadIdx.x; q < plane; q += 256) {
+    // a slab of a decomposed domain sums its own rows only
+    const size_t q0 = kp.gny > 0 ? (size_t)kp.red_j0 * kp.nx : 0, q1 = kp.gny > 0 ? (size_t)kp.red_j1 * kp.nx : plane;
+    for (size_t q = q0 + threadIdx.x; q < q1; q += 256) {
         const Ph<R> p = ldg_ph(phi + base + q);
         const Mu<R> m = ldg_mu(mu + base + q);
         Ph<R> pl;
@@ -2761,21 +2763,41 @@ struct DeviceOnce {
 // Launch of kernel k with the programmatic stream serialisation attribute when pdl is set (the kernel
 // may then be scheduled while the one ahead of it in the stream is still running; it calls pdl_wait()
 // before it depends on that kernel's results), a plain launch otherwise.
+// prio: with the device's highest priority (kept in a captured graph's kernel node), so that the
+// launch's CTAs are placed before those of a concurrent launch of lower priority.
 template <typename... KArgs, typename... Args>
-static cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
-                            Args &&...args)
+static cudaError_t launch_kp(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                             bool prio, Args &&...args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = pdl ? at : nullptr;
-    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchAttribute at[2];
+    int na = 0;
+    if (pdl) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na].val.programmaticStreamSerializationAllowed = 1;
+        na++;
+    }
+    if (prio) {
+        int lo = 0, hi = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess) {
+            at[na].id = cudaLaunchAttributePriority;
+            at[na].val.priority = hi;
+            na++;
+        }
+    }
+    cfg.attrs = na ? at : nullptr;
+    cfg.numAttrs = na;
     return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                            Args &&...args)
+{
+    return launch_kp(k, grid, block, smem, s, pdl, false, std::forward<Args>(args)...);
 }
 
 template <typename R>
@@ -2961,16 +2983,18 @@ static cudaError_t launch_general_pair(const KParams<R> &kp, const void *phi, co
                                        const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits,
                                        const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas, cudaStream_t s,
                                        Partial *subparts, unsigned *subcnt, bool pdl, bool after_lean,
-                                       const void *phi_lo, void *phi_out_lo, const void *mu_lo, void *mu_out_lo)
+                                       const void *phi_lo, void *phi_out_lo, const void *mu_lo, void *mu_out_lo,
+                                       bool prio)
 {
     const int slots = phi_ctas < mu_ctas ? phi_ctas : mu_ctas;  // both sweeps cut the items alike
-    cudaError_t e = launch_k(general_phi_kernel<R, kTX, kTY, SYM, COMP>, dim3(phi_ctas), dim3(kTX * kTY),
-                             general_phi_smem_bytes<R, COMP>(), s, pdl, kp, (const Ph<R> *)phi, (const Mu<R> *)mu,
+    cudaError_t e = launch_kp(general_phi_kernel<R, kTX, kTY, SYM, COMP>, dim3(phi_ctas), dim3(kTX * kTY),
+                              general_phi_smem_bytes<R, COMP>(), s, pdl, prio, kp, (const Ph<R> *)phi, (const Mu<R> *)mu,
                              (Ph<R> *)phi_out, st, tab, tmap_in, tmap_out, splits, glist, stats, slots,
                              pdl && after_lean ? 1 : 0, (const Ph<R> *)phi_lo, (Ph<R> *)phi_out_lo);
     if (e != cudaSuccess) return e;
-    return launch_k(general_mu_kernel<R, kTX, kTY, SYM, COMP>, dim3(mu_ctas), dim3(kTX * kTY), mu_smem_bytes<R>(), s,
-                    pdl, kp, (const Ph<R> *)phi, (const Ph<R> *)phi_out, (const Mu<R> *)mu, (Mu<R> *)mu_out, st, tab,
+    return launch_kp(general_mu_kernel<R, kTX, kTY, SYM, COMP>, dim3(mu_ctas), dim3(kTX * kTY), mu_smem_bytes<R>(),
+                     s, pdl, prio, kp, (const Ph<R> *)phi, (const Ph<R> *)phi_out, (const Mu<R> *)mu, (Mu<R> *)mu_out,
+                     st, tab,
                     parts, splits, glist, stats, subparts, subcnt, slots, (const Mu<R> *)mu_lo, (Mu<R> *)mu_out_lo);
 }
 
@@ -2980,7 +3004,7 @@ cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const v
                                   const unsigned char *tmap_in, unsigned char *tmap_out, const int2 *splits,
                                   const int *glist, LeanStats *stats, int phi_ctas, int mu_ctas, cudaStream_t s,
                                   Partial *subparts, unsigned *subcnt, bool pdl, bool after_lean, const void *phi_lo,
-                                  void *phi_out_lo, const void *mu_lo, void *mu_out_lo)
+                                  void *phi_out_lo, const void *mu_lo, void *mu_out_lo, bool prio)
 {
     if (!subparts || !subcnt) return cudaErrorInvalidValue;
     const bool comp = phi_lo != nullptr;
@@ -2995,17 +3019,17 @@ cudaError_t launch_general_sweeps(const KParams<R> &kp, const void *phi, const v
         if (comp)
             return launch_general_pair<R, false, true>(kp, phi, mu, phi_out, mu_out, st, tab, parts, tmap_in, tmap_out,
                                                        splits, glist, stats, phi_ctas, mu_ctas, s, subparts, subcnt,
-                                                       pdl, after_lean, phi_lo, phi_out_lo, mu_lo, mu_out_lo);
+                                                       pdl, after_lean, phi_lo, phi_out_lo, mu_lo, mu_out_lo, prio);
     }
     // the symmetric set (identity curvatures, one relaxation time) runs the instantiation compiled
     // without the general branches
     if (!kp.gen && !kp.gen_tau)
         return launch_general_pair<R, true, false>(kp, phi, mu, phi_out, mu_out, st, tab, parts, tmap_in, tmap_out,
                                                    splits, glist, stats, phi_ctas, mu_ctas, s, subparts, subcnt, pdl,
-                                                   after_lean, nullptr, nullptr, nullptr, nullptr);
+                                                   after_lean, nullptr, nullptr, nullptr, nullptr, prio);
     return launch_general_pair<R, false, false>(kp, phi, mu, phi_out, mu_out, st, tab, parts, tmap_in, tmap_out,
                                                 splits, glist, stats, phi_ctas, mu_ctas, s, subparts, subcnt, pdl,
-                                                after_lean, nullptr, nullptr, nullptr, nullptr);
+                                                after_lean, nullptr, nullptr, nullptr, nullptr, prio);
 }
 
 template <typename R>
@@ -3385,7 +3409,7 @@ cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const voi
                                                   const unsigned char *, unsigned char *,                           \
                                                   const int2 *, const int *, LeanStats *, int, int, cudaStream_t, \
                                                   Partial *, unsigned *, bool, bool, const void *, void *,        \
-                                                  const void *, void *);                                           \
+                                                  const void *, void *, bool);                                     \
     template void general_sweep_ctas_per_sm<R>(int *, int *);                                                    \
     template cudaError_t launch_batched_step<R>(const BatchDomain<R> *, int, const BatchItem *, int, unsigned *, \
                                                 int, int, int, cudaStream_t);                                    \

@@ -154,8 +154,32 @@ __device__ __forceinline__ int tet_emit(const R (&f)[8], int q, R iso, R bx, R b
 // row piece, one thread per cube, the x + 1 corners taken from the next lane); pass 2 (one CTA)
 // scans the counts into the offsets of the segments that have triangles and lists them; pass 3
 // writes the triangles of the listed segments.
-constexpr int MESH_W = 256;  // cubes of a row per segment (one thread each)
-constexpr int MESH_KC = 32;  // layers per counting CTA
+constexpr int MESH_W = 256;  // cubes of a row per segment (one thread each; one mask-table entry each)
+#ifndef PF_MESH_KC
+#define PF_MESH_KC 32
+#endif
+#ifndef PF_MESH_DEPTH
+#define PF_MESH_DEPTH 1
+#endif
+constexpr int MESH_KC = PF_MESH_KC;        // layers per counting CTA
+constexpr int MESH_DEPTH = PF_MESH_DEPTH;  // layers loaded ahead of the one being classified
+
+// Triangles of a cube from its inside mask (bit n set when corner n is inside): the tetrahedron
+// rule of tet_count on the mask's bits.
+__device__ __forceinline__ int mask_count(int m)
+{
+    int t = 0;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        int v[4];
+        kuhn_tet(q, v);
+        int n = 0;
+#pragma unroll
+        for (int s = 0; s < 4; s++) n += (m >> v[s]) & 1;
+        t += n == 0 || n == 4 ? 0 : (n == 2 ? 2 : 1);
+    }
+    return t;
+}
 
 template <typename R>
 __global__ void __launch_bounds__(MESH_W) mesh_count_kernel(const Ph<R> *__restrict__ phi, const DevState *__restrict__ st,
@@ -163,6 +187,8 @@ __global__ void __launch_bounds__(MESH_W) mesh_count_kernel(const Ph<R> *__restr
                                                            unsigned *__restrict__ seg_counts)
 {
     __shared__ unsigned wsum[MESH_KC][MESH_W / 32];
+    __shared__ unsigned char table[256];  // triangles of a cube by its inside mask
+    table[threadIdx.x] = (unsigned char)mask_count((int)threadIdx.x);
     const int nb = (nx + MESH_W - 1) / MESH_W;
     const int b = blockIdx.x % nb, j = blockIdx.x / nb;
     const int k0 = blockIdx.y * MESH_KC, k1 = min(nz - 1, k0 + MESH_KC);
@@ -175,42 +201,47 @@ __global__ void __launch_bounds__(MESH_W) mesh_count_kernel(const Ph<R> *__restr
     const size_t plane = (size_t)nx * ny;
     const int zbase = st->zbase;
     auto ld = [&](int k, int jj, int ii) { return phi[plane_off(k, nz, zbase, plane) + (size_t)jj * nx + ii].v[phase]; };
-    // corner values of layer k: a0 = (i, j), a2 = (i, j+1), a1 = (i+1, j), a3 = (i+1, j+1)
-    R a0 = ld(k0, j, ic), a2 = ld(k0, j1, ic);
-    R a1 = __shfl_down_sync(0xffffffffu, a0, 1), a3 = __shfl_down_sync(0xffffffffu, a2, 1);
-    if (!from_lane) {
-        a1 = ld(k0, j, i1);
-        a3 = ld(k0, j1, i1);
-    }
-    // layer k + 1 is loaded one iteration ahead, so that two layers' loads are in flight
-    R p0 = ld(k0 + 1, j, ic), p2 = ld(k0 + 1, j1, ic), p1 = p0, p3 = p2;
-    if (!from_lane) {
-        p1 = ld(k0 + 1, j, i1);
-        p3 = ld(k0 + 1, j1, i1);
-    }
-    for (int k = k0; k < k1; k++) {
-        const R c0 = p0, c2 = p2;
-        R c1 = __shfl_down_sync(0xffffffffu, c0, 1), c3 = __shfl_down_sync(0xffffffffu, c2, 1);
+    // the inside bits of a layer's four corners of this thread's cube (bit 0: (i, j), 1: (i+1, j),
+    // 2: (i, j+1), 3: (i+1, j+1)); each cell is classified once, the x + 1 corners come from the
+    // next lane's ballot bit
+    auto layer_bits = [&](R v0, R v2, R v1, R v3) {
+        const bool b0 = v0 >= iso, b2 = v2 >= iso;
+        const unsigned m0 = __ballot_sync(0xffffffffu, b0), m2 = __ballot_sync(0xffffffffu, b2);
+        const bool b1 = from_lane ? ((m0 >> (lane + 1)) & 1u) != 0 : v1 >= iso;
+        const bool b3 = from_lane ? ((m2 >> (lane + 1)) & 1u) != 0 : v3 >= iso;
+        return (unsigned)b0 | ((unsigned)b1 << 1) | ((unsigned)b2 << 2) | ((unsigned)b3 << 3);
+    };
+    // the four corner values of layer k (the x + 1 ones loaded only where no lane holds them)
+    auto load4 = [&](int k, R (&v)[4]) {
+        v[0] = ld(k, j, ic);
+        v[2] = ld(k, j1, ic);
+        v[1] = v[0];
+        v[3] = v[2];
         if (!from_lane) {
-            c1 = p1;
-            c3 = p3;
+            v[1] = ld(k, j, i1);
+            v[3] = ld(k, j1, i1);
         }
-        if (k + 2 <= k1) {
-            p0 = ld(k + 2, j, ic);
-            p2 = ld(k + 2, j1, ic);
-            if (!from_lane) {
-                p1 = ld(k + 2, j, i1);
-                p3 = ld(k + 2, j1, i1);
-            }
-        }
-        const R f[8] = {a0, a1, a2, a3, c0, c1, c2, c3};
-        unsigned n = act ? (unsigned)cube_count(f, iso) : 0u;
+    };
+    R a[4];
+    load4(k0, a);
+    // layers k + 1 .. k + MESH_DEPTH are loaded ahead, so that their loads are in flight together
+    R q[MESH_DEPTH][4] = {};
+#pragma unroll
+    for (int d = 0; d < MESH_DEPTH; d++)
+        if (k0 + 1 + d <= k1) load4(k0 + 1 + d, q[d]);
+    unsigned lo = layer_bits(a[0], a[2], a[1], a[3]);
+    __syncthreads();  // the table
+    for (int k = k0; k < k1; k++) {
+        const unsigned hi = layer_bits(q[0][0], q[0][2], q[0][1], q[0][3]);
+#pragma unroll
+        for (int d = 0; d + 1 < MESH_DEPTH; d++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) q[d][c] = q[d + 1][c];
+        if (k + 1 + MESH_DEPTH <= k1) load4(k + 1 + MESH_DEPTH, q[MESH_DEPTH - 1]);
+        unsigned n = act ? (unsigned)table[lo | (hi << 4)] : 0u;
         n = __reduce_add_sync(0xffffffffu, n);
         if (lane == 0) wsum[k - k0][w] = n;
-        a0 = c0;
-        a1 = c1;
-        a2 = c2;
-        a3 = c3;
+        lo = hi;
     }
     __syncthreads();
     if ((int)threadIdx.x < k1 - k0) {

@@ -88,6 +88,7 @@ SIGNATURES = {
     "pf_test_withhold_copies": (_I, [_VP, _I]),
     "pf_checkpoint_write": (_I, [_VP, ctypes.c_char_p]),
     "pf_checkpoint_read": (_I, [_VP, ctypes.c_char_p]),
+    "pf_checkpoint_write_f32": (_I, [_VP, ctypes.c_char_p]),
     "pf_interface_mesh": (_I, [_VP, _I, _D, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t,
                                ctypes.POINTER(ctypes.c_size_t)]),
     "pf_profile": (_I, [_VP, _I]),
@@ -103,6 +104,7 @@ SIGNATURES = {
     "pf_batch_sync": (_I, [_VP]),
     "pf_batch_set_zchunk": (_I, [_VP, _I]),
     "pf_batch_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), _DP]),
+    "pf_batch_step_bytes": (_I, [_VP, _DP]),
     "pf_server_create": (_I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_VP)]),
     "pf_server_destroy": (_I, [_VP]),
     "pf_submit": (_I, [_VP, _I, _I, _I, ctypes.POINTER(pf_params), ctypes.c_uint64, _I,
@@ -308,6 +310,10 @@ def pf_checkpoint_write(sim, path: str):
     _check(lib().pf_checkpoint_write(sim, os.fsencode(path)), "pf_checkpoint_write")
 
 
+def pf_checkpoint_write_f32(sim, path: str):
+    _check(lib().pf_checkpoint_write_f32(sim, os.fsencode(path)), "pf_checkpoint_write_f32")
+
+
 def pf_checkpoint_read(sim, path: str):
     _check(lib().pf_checkpoint_read(sim, os.fsencode(path)), "pf_checkpoint_read")
 
@@ -405,6 +411,12 @@ def pf_batch_autotune(b, trial_steps=10):
     ms = _D()
     _check(lib().pf_batch_autotune(b, trial_steps, ctypes.byref(best), ctypes.byref(ms)), "pf_batch_autotune")
     return best.value, ms.value
+
+
+def pf_batch_step_bytes(b):
+    out = np.zeros(2)
+    _check(lib().pf_batch_step_bytes(b, _dp(out)), "pf_batch_step_bytes")
+    return {"general_and_fused": float(out[0]), "lean_step": float(out[1])}
 
 
 def pf_server_create(hbm_budget_bytes: int = 0, max_active: int = 0, chunk: int = 0):
@@ -691,8 +703,9 @@ class Simulation:
     def interface_mesh(self, phase, iso=0.5):
         return pf_interface_mesh(self.h, phase, iso)
 
-    def checkpoint(self, path):
-        pf_checkpoint_write(self.h, path)
+    def checkpoint(self, path, single=False):
+        """single: the single-precision checkpoint (values rounded once to FP32)."""
+        (pf_checkpoint_write_f32 if single else pf_checkpoint_write)(self.h, path)
         return self
 
     def restore(self, path):

@@ -143,3 +143,28 @@ def test_odd_width_domain_with_a_moving_window_in_a_batch(general, precision, to
         sim.close()
     assert b.shifts(0) > 0
     b.close()
+
+
+def test_batch_step_bytes_tally_each_domains_cells():
+    # two pure-liquid domains on the lean path: the lean kernel moves mu^n in and mu^{n+1} out, 16
+    # bytes a cell, once phi^{n+1} = e_l is known to be stored; the same domains with a front add
+    # the general planes' 88 bytes a general cell
+    shapes = [(64, 32, 48), (32, 32, 64)]
+    p = W.symmetric_params()
+    b = pf.Batch(shapes, [p, p], "fp32")
+    rng = np.random.default_rng(3)
+    for d, (nx, ny, nz) in enumerate(shapes):
+        phi = np.zeros((4, nz, ny, nx))
+        phi[3] = 1.0
+        pf.pf_write_fields(b.domain(d), phi, rng.uniform(-1e-3, 1e-3, (2, nz, ny, nx)))
+    b.step(4)
+    b.sync()
+    cells = sum(x * y * z for x, y, z in shapes)
+    got = pf.pf_batch_step_bytes(b.h)
+    assert got == {"general_and_fused": 0.0, "lean_step": 16.0 * cells}
+    b.init([1, 2])
+    b.step(4)
+    got = pf.pf_batch_step_bytes(b.h)
+    assert got["general_and_fused"] > 0 and got["general_and_fused"] % 88.0 == 0
+    assert 0 < got["lean_step"] < 16.0 * cells
+    b.close()

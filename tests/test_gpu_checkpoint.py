@@ -134,3 +134,39 @@ def test_checkpoint_errors(tmp_path):
         a.checkpoint(str(tmp_path / "no_such_dir" / "ck.pfc"))
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_single_precision_checkpoint_of_a_high_precision_run(tmp_path, precision):
+    # Section 3.2: the run in double precision, the checkpoint in single.  The resumed run starts
+    # from the state rounded once to FP32 and stays within the FP32 tolerance of the uninterrupted
+    # run; the file is half an FP64 checkpoint
+    nx, ny, nz = 32, 32, 64
+    p = _params()
+    path = str(tmp_path / f"ck32_{precision}.pfc")
+    a = pf.Simulation(nx, ny, nz, p, precision)
+    a.init(3)
+    a.step(25)
+    p0, m0 = a.fields()
+    a.checkpoint(path, single=True)
+    st_ck = a.stats()
+    assert os.path.getsize(path) == 64 + nz * 6 * nx * ny * 4
+    b = pf.Simulation(nx, ny, nz, p, precision)
+    b.restore(path)
+    pb0, mb0 = b.fields()
+    # the restored state is the FP32 rounding of the checkpointed one
+    assert np.array_equal(pb0, p0.astype(np.float32).astype(np.float64))
+    assert np.array_equal(mb0, m0.astype(np.float32).astype(np.float64))
+    assert b.stats()["t"] == st_ck["t"] and b.stats()["window_offset"] == st_ck["window_offset"]
+    n = 200
+    a.step(n)
+    b.step(n)
+    pa, ma = a.fields()
+    pb, mb = b.fields()
+    e_phi = np.abs(pa - pb).max()
+    e_mu = np.abs(ma - mb).max() / max(np.abs(ma).max(), 1e-8)
+    print(f"{precision}: resume error after {n} steps from the single-precision checkpoint: "
+          f"max|dphi| {e_phi:.3e}, |dmu|/scale {e_mu:.3e}")
+    assert 0 < max(e_phi, e_mu)
+    assert e_phi <= 2e-5 and e_mu <= 2e-5
+    assert a.shifts() == b.shifts() and a.stats()["window_offset"] == b.stats()["window_offset"]
