@@ -25,25 +25,19 @@
 using namespace pf;
 
 // Launch shape of the fused step with the lean kernel.  The general planes' sweeps (latency-bound) run
-// on a second stream of the highest priority beside the lean kernel (HBM-bound), launched first, so
-// that their persistent CTAs are placed before the lean CTAs and the two kernels fill each other's
-// tails (PF_CONCURRENT 1; 0: the sweeps after the lean kernel on the simulation's stream).  Persistent
+// on a second stream beside the lean kernel (HBM-bound), so that the two kernels fill each other's
+// tails (PF_CONCURRENT 1; 0: the sweeps after the lean kernel on the simulation's stream): 0.273
+// against 0.293 ms a step on 256x256x1024 FP32.  The sweeps are launched first and with the device's
+// highest priority; neither the order nor the priority changed the time measurably.  Persistent
 // general CTAs per SM: two (they take all of an SM's registers while they run; one makes the sweeps
-// 1.5x slower and the step slower than the serial form, measured on 256x256x1024 FP32).
+// 1.5x slower and the step slower than the serial form).
 #ifndef PF_CONCURRENT
 #define PF_CONCURRENT 1
 #endif
 #ifndef PF_GENERAL_CTAS_PER_SM
 #define PF_GENERAL_CTAS_PER_SM 2
 #endif
-// with PF_CONCURRENT: the sweeps' launches carry the highest priority (1) or none (0), and are made
-// before the lean kernel's (1) or after it (0)
-#ifndef PF_GENERAL_PRIO
-#define PF_GENERAL_PRIO 1
-#endif
-#ifndef PF_GENERAL_FIRST
-#define PF_GENERAL_FIRST 1
-#endif
+
 #ifndef PF_LEAN_PLANES
 #define PF_LEAN_PLANES 64  // at most planes per lean CTA (the kernels' limit, PF_LEAN_PLANES in pf_kernels.cuh)
 #endif
@@ -139,6 +133,9 @@ struct pf_sim {
     Geometry geo;          // unfused sweeps
     Geometry geo_fused;    // fused step (longer z chunks: its prologue recomputes two planes)
     int variant = PF_VARIANT_AUTO;
+    // PF_VARIANT_AUTO's measured choice for the current run: -1 not yet measured, 0 the default rule's
+    // path, 1 the two whole-domain sweeps (faster on this domain's composition)
+    int auto_choice = -1;
     DevBuf phi[2], mu[2];  // AoS fields of the stencil precision
     DevBuf philo[2], mulo[2];  // low words of the compensated FP32 state (PF_FP32_COMP only)
     // liquid maps of the two field buffers (one byte per storage plane and fused-step tile: 1 when
@@ -472,14 +469,21 @@ static cudaError_t timed(pf_sim *s, int cls, F &&f, cudaStream_t st = nullptr)
 // the two whole-domain sweeps, compensated FP32 130 against 22); without them the fused tile in FP32
 // and the two sweeps otherwise.  A fixed rule, not a timing: a run resumed from a checkpoint takes the
 // same kernels as the uninterrupted run.
-static bool use_fused(const pf_sim *s)
+// The step's path under the default rule: the lean path wherever it can run (FP32 rows of 16-byte
+// multiples, every precision), else in FP32 the fused tile, else the two whole-domain sweeps.
+static bool rule_fused(const pf_sim *s)
 {
     // the compensated state has a lean path (lean kernel and general planes' sweeps with the low
     // words), but no fused tile: without the lean path it runs on the two sweeps
-    if (s->comp()) return s->lean_ok && s->variant != PF_VARIANT_UNFUSED;
-    if (s->variant == PF_VARIANT_FUSED) return true;
-    if (s->variant == PF_VARIANT_UNFUSED) return false;
+    if (s->comp()) return s->lean_ok;
     return s->lean_ok || s->p.precision == PF_FP32;
+}
+static bool use_fused(const pf_sim *s)
+{
+    if (s->variant == PF_VARIANT_UNFUSED) return false;
+    if (s->variant == PF_VARIANT_FUSED) return s->comp() ? s->lean_ok : true;
+    // AUTO: the rule's path unless a measurement on this run's state found the two sweeps faster
+    return s->auto_choice != 1 && rule_fused(s);
 }
 
 // The fused step trusts the liquid maps of both field buffers: the source's to find the
@@ -610,16 +614,14 @@ static int do_step_direct(pf_sim *s, int n)
                     // highest priority, and finalize waits for both
                     if (e == cudaSuccess) e = cudaEventRecord(s->ev_fork, s->stream);
                     if (e == cudaSuccess) e = cudaStreamWaitEvent(s->aux, s->ev_fork, 0);
-                    if (e == cudaSuccess && !PF_GENERAL_FIRST) e = leanp();
                     if (e == cudaSuccess)
                         e = launch_general_sweeps<R>(kp, s->phi[a].p, s->mu[a].p, s->phi[b].p, s->mu[b].p, st, tab,
                                                      parts, tin, tout, (const int2 *)s->splits.p,
                                                      (const int *)s->glist.p, ls, s->gphi_ctas, s->gmu_ctas, s->aux,
                                                      (Partial *)s->subparts.p, (unsigned *)s->subcnt.p, false, false,
-                                                     s->lo_phi(a), s->lo_phi(b), s->lo_mu(a), s->lo_mu(b),
-                                                     PF_GENERAL_PRIO != 0);
+                                                     s->lo_phi(a), s->lo_phi(b), s->lo_mu(a), s->lo_mu(b), true);
                     if (e == cudaSuccess) e = cudaEventRecord(s->ev_join, s->aux);
-                    if (e == cudaSuccess && PF_GENERAL_FIRST) e = leanp();
+                    if (e == cudaSuccess) e = leanp();
                     if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_join, 0);
                 } else {
                     if (e == cudaSuccess) e = leanp();
@@ -669,6 +671,43 @@ static int do_step_direct(pf_sim *s, int n)
 // pf_step's driver: direct launches while profiling (every kernel bracketed by events), for the
 // first steps, for short calls and inside a caller's own stream capture; otherwise replays of a
 // captured two-step graph (launch overhead of the four kernels per step paid once).
+// PF_VARIANT_AUTO's choice for a run, made on the first step after its state was set (pf_init,
+// pf_write_fields*, a checkpoint without a stored choice) from the state itself, so that two runs from
+// the same state choose alike.  The lean path moves 16 bytes a pure-liquid cell and runs the general
+// planes' persistent sweeps beside the lean kernel; the two whole-domain sweeps are grid launches.
+// The measure is the fraction f of the (tile, plane) entries of the current field's liquid map that
+// are exactly pure liquid; the lean path is kept when f reaches a threshold that depends on the
+// domain's size, set from the region study (the paper's liquid, solid and interface blocks at 60^3,
+// 128^3 and 256^3, FP32, GB300): below 2^20 cells the lean path was as fast or faster on every block
+// (0: always kept); up to 2^23 cells the sweeps were 17-48 % faster on the solid and interface blocks
+// (f <= 0.48) and the lean path 4.3x faster on pure liquid (0.6); above, the lean path was 7 % faster
+// on the interface block (f ~ 0.48) and the sweeps 14 % on the solid one (0.45).
+constexpr double kAutoLeanFractionMid = 0.6, kAutoLeanFractionLarge = 0.45;
+constexpr size_t kAutoSmallCells = (size_t)1 << 20, kAutoLargeCells = (size_t)1 << 23;
+
+template <typename R>
+static int auto_choose(pf_sim *s)
+{
+    s->auto_choice = 0;
+    if (!rule_fused(s) || !s->lean_ok) return PF_OK;  // the lean path cannot run: the rule stands
+    cudaError_t e = ensure_maps<R>(s, s->stream);
+    const size_t nmap = s->tmap[0].bytes;
+    std::vector<unsigned char> h(nmap);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), s->tmap[s->cur].p, nmap, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return latch(s, cuda_status(e));
+    const int tiles = s->geo_fused.gx * s->geo_fused.gy;
+    size_t liq = 0, tot = (size_t)tiles * s->nz;
+    for (size_t q = 0; q < tot && q < nmap; q++) liq += h[q] != 0;
+    const double f = tot ? (double)liq / (double)tot : 0.0;
+    const size_t n = s->ncell();
+    const double need = n < kAutoSmallCells ? 0.0 : (n < kAutoLargeCells ? kAutoLeanFractionMid : kAutoLeanFractionLarge);
+    const bool lean = f >= need;
+    s->auto_choice = lean ? 0 : 1;
+    return PF_OK;
+}
+
 template <typename R>
 static int do_step(pf_sim *s, int n)
 {
@@ -676,6 +715,10 @@ static int do_step(pf_sim *s, int n)
     if (cudaStreamIsCapturing(s->stream, &cs) != cudaSuccess) {
         cudaGetLastError();
         cs = cudaStreamCaptureStatusActive;
+    }
+    if (s->variant == PF_VARIANT_AUTO && s->auto_choice < 0 && cs == cudaStreamCaptureStatusNone) {
+        int r = auto_choose<R>(s);
+        if (r != PF_OK) return r;
     }
     if (s->prof || !s->use_graphs || cs != cudaStreamCaptureStatusNone || n < 4 || s->direct_steps < 2) {
         int r = do_step_direct<R>(s, n);
@@ -923,7 +966,8 @@ struct CkptHeader {
     int32_t elem;       // bytes per value: 4 (FP32) or 8 (FP64)
     int32_t precision;  // PF_FP64 / PF_FP32 / PF_FP32_COMP of the writer
     int32_t nshift;     // planes shifted since init
-    int32_t pad0;
+    int32_t auto_path;  // PF_VARIANT_AUTO's choice of the writer's run: 0 not made, 1 the lean path
+                        // (the default rule), 2 the two whole-domain sweeps
     double t, off;      // simulation time, window offset
     int32_t pad[2];
 };
@@ -952,6 +996,7 @@ static int do_checkpoint_write(pf_sim *s, const char *path, int single)
     h.elem = s->p.precision == PF_FP64 && !single ? 8 : 4;
     h.precision = single ? PF_FP32 : s->p.precision;
     h.nshift = ds.nshift_total;
+    h.auto_path = s->auto_choice + 1;
     h.t = ds.t;
     h.off = ds.off;
     const KParams<R> kp = make_kparams<R>(s);
@@ -1083,6 +1128,8 @@ static int do_checkpoint_read(pf_sim *s, const char *path)
         ds.shift = 0;
         ds.nonfinite = 0;
         ds.nshift_total = h.nshift;
+        // the writer's run's choice of path continues (a file without one: chosen at the next step)
+        s->auto_choice = h.auto_path == 1 || h.auto_path == 2 ? h.auto_path - 1 : -1;
         e = cudaMemcpyAsync(s->state.p, &ds, sizeof ds, cudaMemcpyHostToDevice, s->stream);
         if (e == cudaSuccess)
             e = launch_post<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p,
@@ -1313,6 +1360,7 @@ int pf_get_params(const pf_sim *s, pf_params *out)
 int pf_init(pf_sim *s, uint64_t seed)
 {
     if (!s) return PF_E_INVAL;
+    s->auto_choice = -1;
     return PF_DISPATCH(s, do_init, s, seed, s->p.n_grains);
 }
 
@@ -1351,6 +1399,7 @@ int pf_read_fields(pf_sim *s, double *phi, double *mu, size_t cap_cells)
 int pf_write_fields(pf_sim *s, const double *phi, const double *mu)
 {
     if (!s || !phi || !mu) return PF_E_INVAL;
+    s->auto_choice = -1;
     return PF_DISPATCH(s, do_write, s, phi, mu);
 }
 
@@ -1364,6 +1413,7 @@ int pf_read_fields_f32(pf_sim *s, float *phi, float *mu, size_t cap_cells)
 int pf_write_fields_f32(pf_sim *s, const float *phi, const float *mu)
 {
     if (!s || !phi || !mu) return PF_E_INVAL;
+    s->auto_choice = -1;
     return PF_DISPATCH(s, do_write, s, phi, mu);
 }
 
@@ -1474,6 +1524,7 @@ int pf_set_variant(pf_sim *s, int variant)
 {
     if (!s || variant < PF_VARIANT_AUTO || variant > PF_VARIANT_FUSED) return PF_E_INVAL;
     s->variant = variant;
+    s->auto_choice = -1;  // AUTO chooses again from the state at the next step
     return PF_OK;
 }
 
@@ -1539,6 +1590,9 @@ struct pf_batch {
     bool lean_mode = false;
     bool sym = true;  // every domain has the symmetric set (no matrix curvature, no pair times)
     size_t nparts_total = 0;  // partial sums of all domains (their algorithmic-byte tallies)
+    // the general planes' sweeps beside the lean kernel (as a single domain's, PF_CONCURRENT)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<char> dom_lean;  // the domain runs the lean path
 };
 
@@ -1675,6 +1729,30 @@ static int batch_build(pf_batch *b)
     }
     b->post_blocks = post;
     b->nparts_total = part_total;
+    if (PF_CONCURRENT && b->lean_mode && !b->aux) {
+        // the second stream and its fork / join events (not while the batch's stream is being
+        // captured: such a step runs the general sweeps in line)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(b->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            int lo = 0, hi = 0;
+            cudaStream_t x = nullptr;
+            cudaEvent_t f0 = nullptr, f1 = nullptr;
+            cudaError_t ea = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+            if (ea == cudaSuccess) ea = cudaStreamCreateWithPriority(&x, cudaStreamNonBlocking, hi);
+            if (ea == cudaSuccess) ea = cudaEventCreateWithFlags(&f0, cudaEventDisableTiming);
+            if (ea == cudaSuccess) ea = cudaEventCreateWithFlags(&f1, cudaEventDisableTiming);
+            if (ea == cudaSuccess) {
+                b->aux = x;
+                b->ev_fork = f0;
+                b->ev_join = f1;
+            } else {
+                if (x) cudaStreamDestroy(x);
+                if (f0) cudaEventDestroy(f0);
+                if (f1) cudaEventDestroy(f1);
+            }
+        }
+        cudaGetLastError();
+    }
     b->built = true;
     b->parity = 0;
     b->cur0.resize(n);
@@ -1697,7 +1775,7 @@ static int batch_step_direct(pf_batch *b, int n)
                                             b->nlean, (int2 *)b->glist.p, (BatchPlan *)b->plan.p, b->gphi_ctas,
                                             b->gmu_ctas, (const BatchItem *)b->items.p, b->nitems,
                                             (unsigned *)b->counter.p, b->ctas, b->parity, b->post_blocks, b->stream,
-                                            b->sym);
+                                            b->sym, b->aux, b->ev_fork, b->ev_join);
         else
             e = launch_batched_step<R>((const BatchDomain<R> *)b->doms.p, (int)b->sims.size(),
                                        (const BatchItem *)b->items.p, b->nitems, (unsigned *)b->counter.p, b->parity,
@@ -1786,6 +1864,12 @@ int pf_batch_destroy(pf_batch *b)
     dev_free(b->splits, b->stream);
     dev_free(b->glist, b->stream);
     dev_free(b->plan, b->stream);
+    if (b->aux) {
+        cudaStreamSynchronize(b->aux);
+        cudaStreamDestroy(b->aux);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return PF_OK;

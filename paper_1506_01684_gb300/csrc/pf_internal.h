@@ -239,7 +239,8 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
                                      const int4 *lean_items, int nlean, int2 *glist, BatchPlan *plan,
                                      int phi_ctas, int mu_ctas, const BatchItem *fitems, int nfitems,
                                      unsigned *counter, int fctas, int parity, int post_blocks, cudaStream_t s,
-                                     bool sym);  // sym: every domain has the symmetric parameter set
+                                     bool sym, cudaStream_t aux = nullptr, cudaEvent_t fork = nullptr,
+                                     cudaEvent_t join = nullptr);  // aux: the general sweeps beside the lean kernel  // sym: every domain has the symmetric parameter set
 template <typename R>
 void batched_general_ctas_per_sm(int *phi_per_sm, int *mu_per_sm);
 // The window decision of a decomposed domain (one thread): the global interface height from the slabs'

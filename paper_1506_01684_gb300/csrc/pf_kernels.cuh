@@ -2113,8 +2113,15 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 2 : 1) general_step_k
 #ifndef PF_GENERAL_MIN_CTAS
 #define PF_GENERAL_MIN_CTAS 2
 #endif
+// PF_GENERAL_MAXNREG > 0: the single-domain general kernels take that register cap instead (so that
+// lean CTAs fit beside two general CTAs on an SM)
+#if defined(PF_GENERAL_MAXNREG) && PF_GENERAL_MAXNREG > 0
+#define PF_GENERAL_BOUNDS(n) __maxnreg__(PF_GENERAL_MAXNREG)
+#else
+#define PF_GENERAL_BOUNDS(n) __launch_bounds__(n, PF_GENERAL_MIN_CTAS)
+#endif
 template <typename R, int TX, int TY, bool SYM, bool COMP = false>
-__global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_phi_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
+__global__ void PF_GENERAL_BOUNDS(TX *TY) general_phi_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi,
                                                             const Mu<R> *__restrict__ mu, Ph<R> *__restrict__ phi_out,
                                                             const DevState *__restrict__ st,
                                                             const PlaneT<R> *__restrict__ tab,
@@ -2159,7 +2166,7 @@ __global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_phi_kerne
     pdl_wait();
 }
 template <typename R, int TX, int TY, bool SYM, bool COMP = false>
-__global__ void __launch_bounds__(TX *TY, PF_GENERAL_MIN_CTAS) general_mu_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi_old,
+__global__ void PF_GENERAL_BOUNDS(TX *TY) general_mu_kernel(const KParams<R> kp, const Ph<R> *__restrict__ phi_old,
                                                            const Ph<R> *__restrict__ phi_new,
                                                            const Mu<R> *__restrict__ mu, Mu<R> *__restrict__ mu_out,
                                                            const DevState *__restrict__ st,
@@ -3211,7 +3218,7 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
                                      const int4 *lean_items, int nlean, int2 *glist, BatchPlan *plan,
                                      int phi_ctas, int mu_ctas, const BatchItem *fitems, int nfitems,
                                      unsigned *counter, int fctas, int parity, int post_blocks, cudaStream_t s,
-                                     bool sym)
+                                     bool sym, cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join)
 {
     using L = LeanLayout<R, kTX, kTY>;
     static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
@@ -3240,15 +3247,29 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
     }
     cudaError_t e = cudaMemsetAsync(plan, 0, sizeof(BatchPlan), s);
     if (e != cudaSuccess) return e;
+    // with a second stream the general planes' sweeps run beside the lean and fused kernels (they
+    // touch other planes, map entries and partials); finalize waits for both
+    const bool conc = aux && fork && join && nplan > 0;
     if (nplan > 0) {
         batched_plan_kernel<R, kTX, kTY><<<(nplan + 3) / 4, 256, 0, s>>>(doms, plan_entries, nplan, parity, glist,
                                                                           plan);
+        cudaStream_t g = s;
+        if (conc) {
+            e = cudaEventRecord(fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, fork, 0);
+            if (e != cudaSuccess) return e;
+            g = aux;
+        }
         if (sym) {
-            batched_general_kernel<R, kTX, kTY, 0, true><<<phi_ctas, kTX * kTY, smp, s>>>(doms, glist, plan, parity);
-            batched_general_kernel<R, kTX, kTY, 1, true><<<mu_ctas, kTX * kTY, smm, s>>>(doms, glist, plan, parity);
+            batched_general_kernel<R, kTX, kTY, 0, true><<<phi_ctas, kTX * kTY, smp, g>>>(doms, glist, plan, parity);
+            batched_general_kernel<R, kTX, kTY, 1, true><<<mu_ctas, kTX * kTY, smm, g>>>(doms, glist, plan, parity);
         } else {
-            batched_general_kernel<R, kTX, kTY, 0, false><<<phi_ctas, kTX * kTY, smp, s>>>(doms, glist, plan, parity);
-            batched_general_kernel<R, kTX, kTY, 1, false><<<mu_ctas, kTX * kTY, smm, s>>>(doms, glist, plan, parity);
+            batched_general_kernel<R, kTX, kTY, 0, false><<<phi_ctas, kTX * kTY, smp, g>>>(doms, glist, plan, parity);
+            batched_general_kernel<R, kTX, kTY, 1, false><<<mu_ctas, kTX * kTY, smm, g>>>(doms, glist, plan, parity);
+        }
+        if (conc) {
+            e = cudaEventRecord(join, aux);
+            if (e != cudaSuccess) return e;
         }
     }
     if (nlean > 0)
@@ -3258,6 +3279,10 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
         e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
         batched_fused_kernel<R, kTX, kTY><<<fctas, kTX * kTY, smf, s>>>(doms, fitems, nfitems, counter, parity);
+    }
+    if (conc) {
+        e = cudaStreamWaitEvent(s, join, 0);
+        if (e != cudaSuccess) return e;
     }
     batched_finalize_kernel<R><<<ndoms, 256, 0, s>>>(doms);
     batched_post_kernel<R><<<dim3(post_blocks, ndoms), 256, 0, s>>>(doms, parity);
@@ -3416,7 +3441,7 @@ cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const voi
     template int fused_ctas_per_sm<R>();                                                                         \
     template cudaError_t launch_batched_lean_step<R>(const BatchDomain<R> *, int, const int2 *, int, const int4 *, \
                                                      int, int2 *, BatchPlan *, int, int, const BatchItem *, int,   \
-                                                     unsigned *, int, int, int, cudaStream_t, bool);                \
+                                                     unsigned *, int, int, int, cudaStream_t, bool, cudaStream_t, cudaEvent_t, cudaEvent_t);                \
     template void batched_general_ctas_per_sm<R>(int *, int *);                                                  \
     template cudaError_t launch_finalize<R>(const KParams<R> &, DevState *, const Partial *, int, cudaStream_t,   \
                                             LeanStats *, bool);                                                  \

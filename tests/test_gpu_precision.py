@@ -48,10 +48,11 @@ def test_compensated_state_keeps_increments_below_the_fp32_spacing():
     assert err["fp32"] > 1e4 * err["fp32c"]
 
 
-# (32, 32, 64) and (40, 24, 48) run the lean path by default (plan, lean kernel and general planes'
-# sweeps in compensated form); an odd nx or nx = 1 has no tensor map for the lean kernel and runs the
-# two whole-domain sweeps, as does the explicit "unfused" variant
-@pytest.mark.parametrize("variant", ["auto", "unfused"])
+# "fused" takes the lean path wherever it can run: (32, 32, 64) and (40, 24, 48) run the plan, the lean
+# kernel and the general planes' sweeps in compensated form; an odd nx or nx = 1 has no tensor map for
+# the lean kernel and runs the two whole-domain sweeps, as does the explicit "unfused" variant; "auto"
+# chooses between the two from the state
+@pytest.mark.parametrize("variant", ["auto", "fused", "unfused"])
 @pytest.mark.parametrize("shape", [(32, 32, 64), (40, 24, 48), (37, 21, 19), (1, 1, 16)])
 def test_compensated_path_matches_the_oracle(shape, variant):
     nx, ny, nz = shape
@@ -124,12 +125,14 @@ def test_compensated_lean_and_sweeps_agree_over_a_growing_front():
     nx, ny, nz = 64, 32, 64
     p = W.symmetric_params(n_grains=8, G=2e-3)
     out = {}
-    for variant in ("auto", "unfused"):
+    for variant in ("fused", "unfused"):
         sim = pf.Simulation(nx, ny, nz, p, "fp32c", variant=variant)
         sim.init(11)
         sim.step(300)
+        if variant == "fused":
+            assert "lean_step" in sim.step_bytes()
         out[variant] = sim.fields()
         sim.close()
-    (pa, ma), (pu, mu_) = out["auto"], out["unfused"]
+    (pa, ma), (pu, mu_) = out["fused"], out["unfused"]
     assert np.abs(pa - pu).max() <= 2e-6
     assert np.abs(ma - mu_).max() / max(np.abs(mu_).max(), 1e-8) <= 2e-6
