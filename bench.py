@@ -538,7 +538,9 @@ def run_region_study(args):
             dt = _t.perf_counter() - t0
             row[variant + "_mlups"] = nx * ny * nz * args.steps / dt / 1e6
             if variant == "auto":  # the path the default chose from the block's state
-                row["auto_path"] = "lean path" if "lean_step" in sim.step_bytes() else "two sweeps"
+                # (the lean path tallies its lean kernel and its general planes, a block without
+                # pure-liquid planes only the latter)
+                row["auto_path"] = "lean path" if set(sim.step_bytes()) & {"lean_step", "general_sweeps"} else "two sweeps"
             sim.close()
         row["auto_vs_best"] = row["auto_mlups"] / max(row["fused_mlups"], row["unfused_mlups"])
         out[kind] = row

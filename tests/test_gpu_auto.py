@@ -23,8 +23,11 @@ def _need_gpu():
 
 
 def _path(sim):
+    # the lean path tallies its lean kernel and its general planes' sweeps (a domain without pure-
+    # liquid planes has only the latter); the two whole-domain sweeps tally phi_sweep and mu_sweep
     b = sim.step_bytes()
-    if "lean_step" in b:
+    if set(b) & {"lean_step", "general_sweeps"}:
+        assert not set(b) & {"phi_sweep", "mu_sweep"}, b
         return "lean"
     assert set(b) == {"phi_sweep", "mu_sweep"}, b
     return "sweeps"
