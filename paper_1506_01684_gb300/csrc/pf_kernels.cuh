@@ -58,6 +58,47 @@ __device__ __forceinline__ Mu<double> ldg_mu(const Mu<double> *p)
     double2 a = __ldg(reinterpret_cast<const double2 *>(p));
     return Mu<double>{{a.x, a.y}};
 }
+
+// Asynchronous global -> shared copies of one cell (cp.async; completion per commit group): the
+// sweeps stage the planes ahead straight into their shared-memory ring, with no registers held for
+// the copy.  Both addresses are aligned to the cell (16 bytes for a phi cell, 8 or 16 for a mu cell).
+__device__ __forceinline__ void cpa16(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(__cvta_generic_to_global(src)) : "memory");
+}
+__device__ __forceinline__ void cpa8(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(__cvta_generic_to_global(src)) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cpa_cell(T *dst, const T *src)
+{
+    static_assert(sizeof(T) % 8 == 0 && sizeof(T) <= 32, "8, 16 or 32-byte cells");
+    if constexpr (sizeof(T) == 8) {
+        cpa8(dst, src);
+    } else {
+#pragma unroll
+        for (int q = 0; q < (int)sizeof(T) / 16; q++)
+            cpa16(reinterpret_cast<char *>(dst) + 16 * q, reinterpret_cast<const char *>(src) + 16 * q);
+    }
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Planes of the phi-sweep's shared-memory ring: with asynchronous staging (PF_SWEEP_ASYNC) 8 in FP32
+// (7 planes in flight ahead of the plane being updated) and 4 in FP64 (its cells are twice as large);
+// without it 4 (one plane ahead, staged through registers).
+#ifndef PF_SWEEP_ASYNC
+#define PF_SWEEP_ASYNC 0  // 1: 0.7 % faster general planes, 17 % slower whole-domain phi-sweep (GB300)
+#endif
+template <typename R>
+__host__ __device__ constexpr int phi_ring() { return PF_SWEEP_ASYNC ? (sizeof(R) == 4 ? 8 : 4) : 4; }
 __device__ __forceinline__ void st_ph(Ph<float> *p, const Ph<float> &x)
 {
     *reinterpret_cast<float4 *>(p) = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
@@ -814,12 +855,14 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
 {
     constexpr int NT = TX * TY, SX = TX + 2, SY = TY + 2, SN = SX * SY, NR = SN - NT;
     constexpr int FX = TY * (TX + 1), FY = (TY + 1) * TX;
+    constexpr int NS = phi_ring<R>(), D = NS - 1;  // ring planes; planes loaded ahead (asynchronous staging)
     static_assert(NR <= NT, "one halo cell per thread at most");
-    Ph<R> *sP = reinterpret_cast<Ph<R> *>(smem_raw);  // [4][SN]
-    Ph<R> *sFx = sP + 4 * SN;                          // [2][FX]
+    static_assert((NS & (NS - 1)) == 0 && NS >= 4, "a power-of-two ring of at least 4 planes");
+    Ph<R> *sP = reinterpret_cast<Ph<R> *>(smem_raw);  // [NS][SN]
+    Ph<R> *sFx = sP + NS * SN;                         // [2][FX]
     Ph<R> *sFy = sFx + 2 * FX;                         // [2][FY]
-    Mu<R> *sMu = reinterpret_cast<Mu<R> *>(sFy + 2 * FY);  // [4][NT]: own-column mu
-    Ph<R> *sLo = reinterpret_cast<Ph<R> *>(sMu + 4 * NT);   // [4][NT]: own-column low words (COMP)
+    Mu<R> *sMu = reinterpret_cast<Mu<R> *>(sFy + 2 * FY);  // [NS][NT]: own-column mu
+    Ph<R> *sLo = reinterpret_cast<Ph<R> *>(sMu + NS * NT);  // [NS][NT]: own-column low words (COMP)
 
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     const int tid = threadIdx.x;
@@ -842,6 +885,18 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
     const bool xtra_y = ty == 0;
     const bool xtra_x = ty == 1 % TY && tx < TY;
 
+#if PF_SWEEP_ASYNC
+    // plane k of the ring: copied straight from global memory (one commit group a plane)
+    auto issue = [&](int k) {
+        const size_t b = plane_off(k, nz, zbase, plane);
+        const int sl = k & (NS - 1);
+        cpa_cell(sP + sl * SN + s0, phi + b + col0);
+        if (s1 >= 0) cpa_cell(sP + sl * SN + s1, phi + b + col1);
+        cpa_cell(sMu + sl * NT + tid, mu + b + col0);
+        if constexpr (COMP) cpa_cell(sLo + sl * NT + tid, phi_lo + b + col0);
+        cpa_commit();
+    };
+#else
     Ph<R> pf0, pf1, pfl;
     Mu<R> pfm;
     auto prefetch = [&](int k) {
@@ -858,7 +913,8 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
         sMu[(k & 3) * NT + tid] = pfm;
         if constexpr (COMP) sLo[(k & 3) * NT + tid] = pfl;
     };
-    auto S = [&](int k, int li, int lj) -> const Ph<R> & { return sP[(k & 3) * SN + (lj + 1) * SX + (li + 1)]; };
+#endif
+    auto S = [&](int k, int li, int lj) -> const Ph<R> & { return sP[(k & (NS - 1)) * SN + (lj + 1) * SX + (li + 1)]; };
     // x/y face terms of plane q and the z face (q, q+1) of this column
     auto faces = [&](int q, Ph<R> &Fz) {
         Ph<R> *fx = sFx + (q & 1) * FX;
@@ -870,20 +926,32 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
         Fz = face_phi(kp, S(q, tx, ty), S(q + 1, tx, ty));
     };
 
-    // prologue: planes z0-1 .. z0+2 in the ring, faces of plane z0
+    // prologue: planes z0-1 .. z0+2 in the ring (with asynchronous staging also the planes up to
+    // z0+D-1 in flight), faces of plane z0
+#if PF_SWEEP_ASYNC
+    for (int k = z0 - 1; k <= z0 + D - 1; k++) issue(k);
+    cpa_wait<D - 3>();  // planes z0-1 .. z0+2 have landed (this thread's copies)
+#else
     for (int k = z0 - 1; k <= z0 + 2; k++) {
         prefetch(k);
         commit(k);
     }
+#endif
     __syncthreads();
     Ph<R> pm = S(z0 - 1, tx, ty), pc = S(z0, tx, ty), pn = S(z0 + 1, tx, ty);
     Ph<R> Fz_prev = face_phi(kp, pm, pc), Fz_cur;
     faces(z0, Fz_cur);
+#if !PF_SWEEP_ASYNC
     prefetch(z0 + 3);
+#endif
     __syncthreads();
 
     bool out_liquid = true;
     for (int p = z0; p < z1; ++p) {
+#if PF_SWEEP_ASYNC
+        // plane p+D into the slot of plane p-1 (no thread reads it after the last barrier)
+        issue(p + D);
+#endif
         // C(p)
         {
             const Ph<R> xm = S(p, tx - 1, ty), xp = S(p, tx + 1, ty);
@@ -893,7 +961,7 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
             Ph<R> out = pc, out_lo;
             if constexpr (COMP) {
                 // a compensated bulk cell also needs a zero low word to be a fixed point
-                out_lo = sLo[(p & 3) * NT + tid];
+                out_lo = sLo[(p & (NS - 1)) * NT + tid];
                 bulk = bulk && out_lo.v[0] == R(0) && out_lo.v[1] == R(0) && out_lo.v[2] == R(0) && out_lo.v[3] == R(0);
             }
             // bulk cells (one-hot, all six neighbours equal) are fixed points of the step; a warp
@@ -905,11 +973,11 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
                 if constexpr (COMP) {
                     phi_cell_comp(kp, T, pc, out_lo, xm, xp, ym, yp, pm, pn, fx[ty * (TX + 1) + tx],
                                   fx[ty * (TX + 1) + tx + 1], fy[ty * TX + tx], fy[(ty + 1) * TX + tx], Fz_prev, Fz_cur,
-                                  sMu[(p & 3) * NT + tid], out, out_lo);
+                                  sMu[(p & (NS - 1)) * NT + tid], out, out_lo);
                 } else {
                     out = phi_cell<R, SYM>(kp, T, pc, xm, xp, ym, yp, pm, pn, fx[ty * (TX + 1) + tx],
                                    fx[ty * (TX + 1) + tx + 1], fy[ty * TX + tx], fy[(ty + 1) * TX + tx], Fz_prev, Fz_cur,
-                                   sMu[(p & 3) * NT + tid]);
+                                   sMu[(p & (NS - 1)) * NT + tid]);
                 }
             }
             if (valid) {
@@ -928,8 +996,12 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
             faces(p + 1, Fz_next);
             pnn = S(p + 2, tx, ty);
         }
+#if PF_SWEEP_ASYNC
+        cpa_wait<D - 3>();  // plane p+3 has landed: the next iteration's faces read it
+#else
         commit(p + 3);
         prefetch(p + 4);
+#endif
         if (tmap_out) {
             // the barrier also gives the map entry of the new plane p
             const int all = __syncthreads_and(out_liquid);
@@ -948,6 +1020,9 @@ __device__ __forceinline__ void phi_sweep_tile(const KParams<R> &kp, const Ph<R>
         Fz_prev = Fz_cur;
         Fz_cur = Fz_next;
     }
+#if PF_SWEEP_ASYNC
+    cpa_wait<0>();  // no copy of this tile lands in shared memory after the tile is done
+#endif
 }
 
 template <typename R, int TX, int TY, bool COMP = false>
@@ -2810,8 +2885,8 @@ static cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t s
 template <typename R>
 static size_t phi_smem_bytes()
 {
-    constexpr int SN = (kTX + 2) * (kTY + 2), FX = kTY * (kTX + 1), FY = (kTY + 1) * kTX;
-    return sizeof(Ph<R>) * (4 * SN + 2 * FX + 2 * FY) + sizeof(Mu<R>) * 4 * kTX * kTY;
+    constexpr int SN = (kTX + 2) * (kTY + 2), FX = kTY * (kTX + 1), FY = (kTY + 1) * kTX, NS = phi_ring<R>();
+    return sizeof(Ph<R>) * (NS * SN + 2 * FX + 2 * FY) + sizeof(Mu<R>) * NS * kTX * kTY;
 }
 template <typename R>
 static size_t mu_smem_bytes()
@@ -2954,7 +3029,7 @@ cudaError_t launch_general_step(const KParams<R> &kp, const void *phi, const voi
 template <typename R, bool COMP>
 static size_t general_phi_smem_bytes()
 {
-    return phi_smem_bytes<R>() + (COMP ? sizeof(Ph<R>) * 4 * kTX * kTY : 0);
+    return phi_smem_bytes<R>() + (COMP ? sizeof(Ph<R>) * phi_ring<R>() * kTX * kTY : 0);
 }
 // Dynamic shared memory limits of one instantiation of the general planes' sweeps (SYM: the symmetric
 // set, COMP: compensated FP32), and the largest shared-memory carveout (so that as many CTAs as the
@@ -3157,7 +3232,7 @@ cudaError_t launch_phi_sweep_comp(const KParams<float> &kp, const Geometry &g, c
                                   const PlaneT<float> *tab, cudaStream_t s)
 {
     static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
-    const size_t sm = phi_smem_bytes<float>() + sizeof(Ph<float>) * 4 * kTX * kTY;
+    const size_t sm = phi_smem_bytes<float>() + sizeof(Ph<float>) * phi_ring<float>() * kTX * kTY;
     if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(phi_sweep_kernel<float, kTX, kTY, true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
