@@ -263,11 +263,17 @@ int pf_test_withhold_copies(pf_sim *sim, int on);
  * phi^{n+1}, the mu-sweep reads it back: 88 algorithmic bytes per FP32 cell); FUSED computes
  * phi^{n+1} and mu^{n+1} in one pass (each CTA recomputes phi^{n+1} on a one-cell ring around its
  * tile: 48 bytes per FP32 cell); where the lean kernel can run (FP64, and FP32 with an even nx), FUSED
- * and AUTO take the lean path instead: the plan splits each tile's z chunk into pure-liquid planes (the
- * lean kernel, 16 bytes per FP32 cell) and general planes (the two sweeps).  All give the same result
- * up to rounding order.  AUTO (the default) takes the lean path wherever it can run, in every precision
- * (compensated FP32 included), else the fused tile in FP32 and the two sweeps otherwise: a fixed rule,
- * so that a run resumed from a checkpoint takes the same kernels as the uninterrupted run. */
+ * takes the lean path instead: the plan splits each tile's z chunk into pure-liquid planes (the lean
+ * kernel, 16 bytes per FP32 cell) and general planes (the two sweeps, run beside the lean kernel).
+ * All give the same result up to rounding order (the lean kernel's 7-point form of a pure-liquid cell
+ * and the sweeps' flux form round differently).  AUTO (the default) chooses between the lean path and
+ * the two sweeps from the state, on the first step after the state was set (pf_init, pf_write_fields*,
+ * a checkpoint without a stored choice): with f the fraction of (tile, plane) entries of the current
+ * field that are exactly pure liquid, it takes the lean path on domains below 2^20 cells, and when
+ * f >= 0.6 (2^20 to 2^23 cells) or f >= 0.45 (larger); where the lean kernel cannot run, the fused tile
+ * in FP32 and the two sweeps otherwise.  The choice depends on the state only, so two runs from one
+ * state take the same kernels; checkpoints store it, so a resumed run continues as the uninterrupted
+ * one.  pf_set_variant(AUTO) makes the choice again at the next step. */
 enum { PF_VARIANT_AUTO = 0, PF_VARIANT_UNFUSED = 1, PF_VARIANT_FUSED = 2 };
 int pf_set_variant(pf_sim *sim, int variant);
 
