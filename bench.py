@@ -278,6 +278,7 @@ def run_batched_study(args):
     b = pf.Batch(shapes, params, "fp32", stream=stream)
     b.init(seeds)
     zc, tune_ms = pf.pf_batch_autotune(b.h, 5)
+    tuned = pf.pf_batch_config(b.h)
     b.step(args.warmup)
     b.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -316,7 +317,8 @@ def run_batched_study(args):
             "value": cells / (ms_batch / 1e3) / 1e6, "one_by_one": cells / (ms_single / 1e3) / 1e6,
             "speedup_vs_one_by_one": ms_single / ms_batch, "ms_per_step": ms_batch,
             "ms_per_step_one_by_one": ms_single, "cells": cells, "domains": len(shapes),
-            "autotuned_zchunk": zc, "autotune_ms_per_step": tune_ms, "steps": args.steps, "warmup": args.warmup,
+            "autotuned_zchunk": zc, "autotuned_general_ctas_per_sm": tuned["general_ctas_per_sm"],
+            "autotune_ms_per_step": tune_ms, "steps": args.steps, "warmup": args.warmup,
             "roofline": {"bound": "hbm", "kernel": "whole batched step", "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
                          "bytes_per_cell": step_bytes / cells,

@@ -167,7 +167,8 @@ int pf_write_fields_f32(pf_sim *sim, const float *phi, const float *mu);
 /* Checkpoint (the paper's infrequent field checkpoints, Section 3.2): write the current fields,
  * simulation time and window offset to the file at path.  Layout: a 64-byte header (magic
  * "PFCKPT01"; int32 version 1, nx, ny, nz, bytes per value, writer precision, planes shifted since
- * init, 4 bytes of padding; FP64 time and window offset; 8 bytes of padding; little-endian), then for each logical
+ * init, PF_VARIANT_AUTO's choice of the writer's run (0 none yet, 1 the lean path, 2 the two sweeps);
+ * FP64 time and window offset; 8 bytes of padding; little-endian), then for each logical
  * plane k = 0 .. nz-1 the six nx*ny arrays (x fastest) phi_0, phi_1, phi_2, phi_3, mu_0, mu_1.
  * Values are the state's own words, so that nothing is rounded: FP32 for an FP32 simulation, FP64
  * for FP64, and for compensated FP32 (writer precision PF_FP32_COMP, 4 bytes per value) the six
@@ -333,10 +334,16 @@ int pf_batch_step(pf_batch *b, int nsteps);
 int pf_batch_sync(pf_batch *b);
 /* z planes per work item (0: the default, about 6 CTAs of work per SM in total). */
 int pf_batch_set_zchunk(pf_batch *b, int zchunk);
-/* Autotuner: times trial_steps steps for each candidate z-chunk depth on the batch itself (the
- * fields, clocks and windows are restored afterwards), keeps the fastest and returns it in
- * *best (may be NULL) and its measured milliseconds per step in *best_ms (may be NULL). */
+/* Autotuner: times trial_steps steps for each candidate launch shape on the batch itself -- z-chunk
+ * depth (16 to 512 planes) x persistent general-plane CTAs per SM (1 or 2); the tile is 32x8
+ * throughout, the unit of the liquid maps, the plan and the lean kernel's tensor-map boxes -- (the
+ * fields, clocks, windows and plane tables are restored afterwards), keeps the fastest and returns
+ * its z-chunk depth in *best (may be NULL) and its measured milliseconds per step in *best_ms (may
+ * be NULL); pf_batch_config reports the whole shape. */
 int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms);
+/* The batch's launch shape: z-chunk depth (0: the default) and persistent general-plane CTAs per SM;
+ * either pointer may be NULL. */
+int pf_batch_config(pf_batch *b, int *zchunk, int *general_ctas_per_sm);
 /* Algorithmic bytes of the batch's last step, as its kernels tallied them (compulsory traffic of
  * each cell's words, the measure of pf_step_bytes): bytes[0] the general planes' sweeps and the fused
  * tiles, bytes[1] the lean kernel's pure-liquid planes.  Synchronising. */

@@ -871,6 +871,16 @@ static int do_write(pf_sim *s, const H *phi, const H *mu)
     return e == cudaSuccess ? PF_OK : latch(s, cuda_status(e));
 }
 
+// The plane table of the current clock and window (no shift pending), after the state was put back.
+template <typename R>
+static int rebuild_table(pf_sim *s, cudaStream_t st)
+{
+    const KParams<R> kp = make_kparams<R>(s);
+    const cudaError_t e = launch_post<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p,
+                                         (PlaneT<R> *)s->tab.p, st, s->lo_phi(s->cur), s->lo_mu(s->cur));
+    return e == cudaSuccess ? PF_OK : cuda_status(e);
+}
+
 template <typename R>
 static int do_reduce(pf_sim *s, double out[8])
 {
@@ -1568,6 +1578,7 @@ struct pf_batch {
     bool own_stream = false;
     int precision = PF_FP32;
     int zchunk = 0;
+    int general_per_sm = PF_GENERAL_CTAS_PER_SM;  // persistent general CTAs per SM (autotuned)
     DevBuf doms;     // BatchDomain<R>[n]
     DevBuf items;    // BatchItem[nitems]
     DevBuf parts;    // Partial[sum of tiles]
@@ -1724,8 +1735,8 @@ static int batch_build(pf_batch *b)
     if (b->lean_mode) {
         int pp = 1, pm = 1;
         batched_general_ctas_per_sm<R>(&pp, &pm);
-        b->gphi_ctas = std::max(1, std::min(b->nplan, std::min(pp, PF_GENERAL_CTAS_PER_SM) * sms));
-        b->gmu_ctas = std::max(1, std::min(b->nplan, std::min(pm, PF_GENERAL_CTAS_PER_SM) * sms));
+        b->gphi_ctas = std::max(1, std::min(b->nplan, std::min(pp, b->general_per_sm) * sms));
+        b->gmu_ctas = std::max(1, std::min(b->nplan, std::min(pm, b->general_per_sm) * sms));
     }
     b->post_blocks = post;
     b->nparts_total = part_total;
@@ -1957,6 +1968,14 @@ int pf_batch_set_zchunk(pf_batch *b, int zchunk)
     return PF_OK;
 }
 
+int pf_batch_config(pf_batch *b, int *zchunk, int *general_ctas_per_sm)
+{
+    if (!b) return PF_E_INVAL;
+    if (zchunk) *zchunk = b->zchunk;
+    if (general_ctas_per_sm) *general_ctas_per_sm = b->general_per_sm;
+    return PF_OK;
+}
+
 int pf_batch_step_bytes(pf_batch *b, double bytes[2])
 {
     if (!b || !bytes) return PF_E_INVAL;
@@ -2016,22 +2035,31 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
             if (x == cudaSuccess)
                 x = cudaMemcpyAsync(s->mu[s->cur].p, (char *)snap[q].p + s->phi[0].bytes, s->mu[0].bytes,
                                     cudaMemcpyDeviceToDevice, b->stream);
-            if (x == cudaSuccess)
+            if (x == cudaSuccess) {
+                ds[q].shift = 0;  // the snapshot's last shift is in its fields already
                 x = cudaMemcpyAsync(s->state.p, &ds[q], sizeof(DevState), cudaMemcpyHostToDevice, b->stream);
+            }
+            // the plane table of the restored clock and window
+            if (x == cudaSuccess && PF_DISPATCH(s, rebuild_table, s, b->stream) != PF_OK) x = cudaErrorLaunchFailure;
         }
         if (x == cudaSuccess) x = cudaStreamSynchronize(b->stream);
         return x;
     };
+    // candidates: z-chunk depth x persistent general CTAs per SM (the tile is 32x8 throughout: the
+    // liquid maps, the plan and the lean kernel's tensor-map boxes are built per 32x8 tile)
     const int cands[] = {16, 32, 64, 128, 256, 512};
-    int bestz = b->zchunk;
+    const int gcands[] = {1, 2};
+    int bestz = b->zchunk, bestg = b->general_per_sm;
     double bestt = 1e300;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    for (int zc : cands) {
+    for (int trial = 0; trial < 12; trial++) {
+        const int zc = cands[trial / 2], gc = gcands[trial % 2];
         if (e != cudaSuccess) break;
         if (zc > 2 * nzmax && zc != cands[0]) continue;
         b->zchunk = zc;
+        b->general_per_sm = gc;
         b->built = false;
         b->direct_steps = 0;
         int r = PF_BDISPATCH(b, batch_step, b, 1);  // builds the table, warms up
@@ -2048,6 +2076,7 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
         if (e == cudaSuccess && ms / trial_steps < bestt) {
             bestt = ms / trial_steps;
             bestz = zc;
+            bestg = gc;
         }
         if (e == cudaSuccess) e = restore();
     }
@@ -2055,6 +2084,7 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
     if (e1) cudaEventDestroy(e1);
     for (auto &x : snap) dev_free(x, b->stream);
     b->zchunk = bestz;
+    b->general_per_sm = bestg;
     b->built = false;
     b->direct_steps = 0;
     if (e != cudaSuccess) return cuda_status(e);

@@ -168,3 +168,30 @@ def test_batch_step_bytes_tally_each_domains_cells():
     assert got["general_and_fused"] > 0 and got["general_and_fused"] % 88.0 == 0
     assert 0 < got["lean_step"] < 16.0 * cells
     b.close()
+
+
+def test_autotune_restores_the_plane_tables_too():
+    # FP64: a batch that tuned its launch shape (its state put back afterwards, plane tables
+    # included) steps on as one that never tuned: a stale plane table (the temperature of the last
+    # trial's clock) would show as a ~1e-7 relative error in mu after the first step; the schedule
+    # itself leaves the FP64 results equal up to rounding order
+    params = [_params(i, window=7.0) for i in range(len(SHAPES))]
+    seeds = list(range(1, len(SHAPES) + 1))
+    a = pf.Batch(SHAPES, params, "fp64")
+    b = pf.Batch(SHAPES, params, "fp64")
+    for x in (a, b):
+        x.init(seeds)
+        x.step(3)
+    zc, ms = pf.pf_batch_autotune(b.h, 4)
+    cfg = pf.pf_batch_config(b.h)
+    assert cfg["zchunk"] == zc and cfg["general_ctas_per_sm"] in (1, 2)
+    a.step(10)
+    b.step(10)
+    for d in range(len(SHAPES)):
+        pa, ma = a.fields(d)
+        pb, mb = b.fields(d)
+        assert np.abs(pa - pb).max() <= 1e-13
+        assert np.abs(ma - mb).max() <= 1e-13 * max(np.abs(ma).max(), 1e-8)
+        assert a.stats(d)["t"] == b.stats(d)["t"]
+    a.close()
+    b.close()
