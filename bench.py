@@ -49,7 +49,7 @@ TRIGGER = 512.0
 SEED = 0
 PRE_STEPS = 2000  # the single-large-domain configuration runs 2000 steps
 WORKLOAD = "single domain 256x256x1024, 64 grains, window trigger z=512, symmetric parameter set"
-METRIC = "phi+mu step MLUP/s (FP32 stencil; FP64 GPU path and error reported beside it)"
+METRIC = "phi+mu step MLUP/s (FP32 stencil; FP64 and compensated FP32 GPU paths and their errors reported beside it)"
 
 # Algorithmic bytes per kernel and launch come from the library (pf_step_bytes): the mu-sweep
 # reads phi^n, phi^{n+1} (16 B each) and mu^n (8 B) and writes mu^{n+1} (8 B); the phi-sweep
@@ -787,6 +787,7 @@ def main():
     # ---------------- FP64 GPU path on the same workload ----------------
     n64 = args.fp64_steps if args.fp64_steps is not None else steps_done
     fp64 = None
+    fp32c = None
     if n64 > 0:
         s64 = pf.Simulation(NX, NY, NZ, params, "fp64", stream=stream)
         s64.init(SEED)
@@ -808,8 +809,31 @@ def main():
             fp64["max_rel_dmu"] = float(np.abs(mu32 - mu64).max() / max(np.abs(mu64).max(), 1e-8))
             fp64["solute_drift_fp32"] = [float((st32["solute"][c] - sol0[c]) / sol0[c]) for c in range(2)]
             fp64["solute_drift_fp64"] = [float((st64["solute"][c] - sol0[c]) / sol0[c]) for c in range(2)]
-            del phi64, mu64
-        s64.close()
+            s64.close()
+            # the compensated FP32 path on the same workload: timed from the same state, and its error
+            # against the same FP64 run after the same steps
+            sc = pf.Simulation(NX, NY, NZ, params, "fp32c", stream=stream)
+            sc.init(SEED)
+            sc.step(args.pre_steps + args.warmup)
+            sc.sync()
+            f0.record(stream)
+            sc.step(args.steps)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            msc = f0.elapsed_time(f1)
+            sc.step(steps_done - args.pre_steps - args.warmup - args.steps)
+            phic, muc = sc.fields()
+            stc = sc.stats()
+            fp32c = {"mlups": cells * args.steps / (msc / 1e3) / 1e6, "ms_per_step": msc / args.steps,
+                     "steps": steps_done, "max_abs_dphi": float(np.abs(phic - phi64).max()),
+                     "max_rel_dmu": float(np.abs(muc - mu64).max() / max(np.abs(mu64).max(), 1e-8)),
+                     "solute_drift": [float((stc["solute"][c] - sol0[c]) / sol0[c]) for c in range(2)],
+                     "what": "compensated FP32 state (hi + lo words), timed over the same K steps from the "
+                             "same 2000-step state; error against the FP64 run after the same steps"}
+            sc.close()
+            del phi64, mu64, phic, muc
+        else:
+            s64.close()
 
     # ---------------- end to end through the public API with host buffers ----------------
     e2e = None
@@ -871,7 +895,7 @@ def main():
         "variant": ("lean kernel + general sweeps" if "lean_step" in prof
                     else ("fused" if "fused_step" in prof else "unfused")),
         "frac_of_unfused_bound": value / unfused_bound, "frac_of_fused_bound": value / fused_bound,
-        "fp64": fp64, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+        "fp64": fp64, "fp32c": fp32c, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
         "window": {"h_int": st32["h_int"], "offset": st32["window_offset"]},
     }
     print(json.dumps(line), flush=True)
