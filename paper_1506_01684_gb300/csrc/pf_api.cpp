@@ -812,11 +812,32 @@ static const size_t kChunkCells = (size_t)1 << 22;  // staging chunk for host tr
 
 // host SoA fields of element type H (double or float) <-> the device state, through a staging buffer
 // of a chunk of planes
+// The device's address of a host buffer it can read and write directly (pinned, mapped host memory:
+// on a Grace-Blackwell node the GPU reaches it over NVLink-C2C), else nullptr.
+static void *device_view(const void *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 template <typename R, typename H>
 static int do_read(pf_sim *s, H *phi, H *mu)
 {
     const KParams<R> kp = make_kparams<R>(s);
     const size_t plane = (size_t)s->nx * s->ny, n = s->ncell();
+    // host buffers the device can address: one pass of the pack kernel writes them directly
+    H *vphi = (H *)device_view(phi), *vmu = (H *)device_view(mu);
+    if ((!phi || vphi) && (!mu || vmu)) {
+        cudaError_t e = launch_pack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, vphi, vmu,
+                                       0, s->nz, s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        return e == cudaSuccess ? PF_OK : latch(s, cuda_status(e));
+    }
     int pk = (int)std::max<size_t>(1, std::min<size_t>(s->nz, kChunkCells / plane));
     DevBuf stg;
     int r = dev_alloc(stg, (size_t)pk * plane * 6 * sizeof(H), s->stream);
@@ -845,6 +866,15 @@ static int do_write(pf_sim *s, const H *phi, const H *mu)
 {
     const KParams<R> kp = make_kparams<R>(s);
     const size_t plane = (size_t)s->nx * s->ny, n = s->ncell();
+    // host buffers the device can address: one pass of the unpack kernel reads them directly
+    const H *vphi = (const H *)device_view(phi), *vmu = (const H *)device_view(mu);
+    if (vphi && vmu) {
+        s->tmap_ok[0] = s->tmap_ok[1] = false;
+        cudaError_t e = launch_unpack<R>(kp, (const DevState *)s->state.p, s->phi[s->cur].p, s->mu[s->cur].p, vphi,
+                                         vmu, 0, s->nz, s->stream, s->lo_phi(s->cur), s->lo_mu(s->cur));
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        return e == cudaSuccess ? PF_OK : latch(s, cuda_status(e));
+    }
     int pk = (int)std::max<size_t>(1, std::min<size_t>(s->nz, kChunkCells / plane));
     DevBuf stg;
     int r = dev_alloc(stg, (size_t)pk * plane * 6 * sizeof(H), s->stream);

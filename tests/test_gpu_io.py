@@ -72,3 +72,35 @@ def test_fp32_host_io_errors():
     assert L.pf_write_fields_f32(sim.h, buf.ctypes.data_as(fp), None) == pf.PF_E_INVAL
     assert L.pf_write_fields_f32(None, buf.ctypes.data_as(fp), buf.ctypes.data_as(fp)) == pf.PF_E_INVAL
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32c"])
+@pytest.mark.parametrize("host", ["f32", "f64"])
+def test_pinned_host_buffers_take_the_direct_path_with_the_same_result(precision, host):
+    # pinned (device-addressable) host buffers are read and written by the pack / unpack kernels
+    # directly; pageable ones go through the staging chunks: the values are the same
+    import torch
+    nx, ny, nz = 64, 40, 300  # more than one staging chunk (2^22 cells) would need nz > 1638
+    phi, mu = _state(nx, ny, nz, 11)
+    dt = np.float32 if host == "f32" else np.float64
+    write = pf.pf_write_fields_f32 if host == "f32" else pf.pf_write_fields
+    read = pf.pf_read_fields_f32 if host == "f32" else pf.pf_read_fields
+    out = {}
+    for kind in ("pageable", "pinned"):
+        sim = pf.Simulation(nx, ny, nz, W.symmetric_params(), precision)
+        if kind == "pinned":
+            hp = torch.from_numpy(phi.astype(dt)).pin_memory()
+            hm = torch.from_numpy(mu.astype(dt)).pin_memory()
+            sp, sm = hp.numpy(), hm.numpy()
+            op = torch.empty(phi.shape, dtype=hp.dtype).pin_memory().numpy()
+            om = torch.empty(mu.shape, dtype=hm.dtype).pin_memory().numpy()
+        else:
+            sp, sm = phi.astype(dt), mu.astype(dt)
+            op, om = np.empty(phi.shape, dtype=dt), np.empty(mu.shape, dtype=dt)
+        write(sim.h, np.ascontiguousarray(sp), np.ascontiguousarray(sm))
+        sim.step(5)
+        read(sim.h, op, om)
+        out[kind] = (op.copy(), om.copy())
+        sim.close()
+    assert np.array_equal(out["pinned"][0], out["pageable"][0])
+    assert np.array_equal(out["pinned"][1], out["pageable"][1])
