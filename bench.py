@@ -206,7 +206,83 @@ def cpu_baseline(min_seconds: float = 10.0, max_steps: int = 40):
     cells = NX * NY * nzs
     return {"value": cells * n / dt / 1e6, "unit": "MLUP/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{NX}x{NY}x{nzs} bottom slab of the workload (64 grains, seed 0), {n} FP64 steps, "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s",
+            "cpu_model": _cpu_model(), "samples": oracle_samples()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+# the oracle's two further samples: the small configuration (32x32x64, 12 grains, seed 0) and the
+# paper's interface block at 128^3 (columnar grains below z = 64, liquid above; 2 relaxation steps)
+ORACLE_SAMPLES = {"small_32x32x64": (32, 32, 64, 20), "interface_128x128x128": (128, 128, 128, 3)}
+
+
+def _sample_state(name):
+    import oracle
+    from paper_1506_01684_gb300 import workloads as W
+    nx, ny, nz, _ = ORACLE_SAMPLES[name]
+    if name.startswith("small"):
+        p = W.symmetric_params(n_grains=12)
+        return p, (nx, ny, nz), None
+    phi, mu = W.region_fields("interface", nx, ny, nz, seed=0)
+    return W.symmetric_params(), (nx, ny, nz), (phi, mu)
+
+
+def oracle_samples(reps: int = 3):
+    """The FP64 oracle on the host cores on the small configuration and a 128^3 interface block:
+    MLUP/s, the median of `reps` timed runs of a few steps each."""
+    import oracle
+    out = {}
+    for name, (nx, ny, nz, steps) in ORACLE_SAMPLES.items():
+        p, shape, fields = _sample_state(name)
+        st = oracle.State(p, *shape)
+        if fields is None:
+            st.init(SEED)
+        else:
+            st.phi, st.mu = fields[0].copy(), fields[1].copy()
+        st.step(2)
+        rates = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            st.step(steps)
+            rates.append(nx * ny * nz * steps / (time.perf_counter() - t0) / 1e6)
+        out[name] = {"mlups": statistics.median(rates), "runs_mlups": rates, "steps_per_run": steps}
+    return out
+
+
+def gpu_on_oracle_samples(stream, steps: int = 200):
+    """The FP32 GPU step (the library's variant choice) on the oracle's two further samples."""
+    import torch
+
+    from paper_1506_01684_gb300 import pf
+    out = {}
+    for name in ORACLE_SAMPLES:
+        p, shape, fields = _sample_state(name)
+        sim = pf.Simulation(*shape, p, "fp32", stream=stream)
+        if fields is None:
+            sim.init(SEED)
+        else:
+            sim.set_fields(*fields)
+        sim.step(5)
+        sim.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = shape[0] * shape[1] * shape[2] * steps / (e0.elapsed_time(e1) / 1e3) / 1e6
+        sim.close()
+    return out
 
 
 def gpu_on_cpu_sample(stream, steps: int = 200):
@@ -873,6 +949,9 @@ def main():
     if cpu is not None:
         cpu["gpu_same_sample_mlups"] = gpu_on_cpu_sample(stream)
         cpu["gpu_same_sample_what"] = "the FP32 GPU step on the same 256x256x16 slab, 200 steps, CUDA events"
+        g = gpu_on_oracle_samples(stream)
+        for name, v in g.items():
+            cpu["samples"][name]["gpu_fp32_mlups"] = v
 
     if rank != 0:
         return
