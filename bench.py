@@ -212,10 +212,18 @@ def cpu_baseline(min_seconds: float = 10.0, max_steps: int = 40):
 
 def _cpu_model():
     try:
+        impl = part = None
         with open("/proc/cpuinfo") as f:
             for line in f:
-                if line.lower().startswith(("model name", "cpu model")):
+                key = line.lower()
+                if key.startswith(("model name", "cpu model")):
                     return line.split(":", 1)[1].strip()
+                if key.startswith("cpu implementer") and impl is None:
+                    impl = line.split(":", 1)[1].strip()
+                if key.startswith("cpu part") and part is None:
+                    part = line.split(":", 1)[1].strip()
+        if impl and part:  # Arm: the implementer and part numbers (0x41 / 0xd4f: Arm Neoverse V2)
+            return f"Arm CPU implementer {impl}, part {part}"
     except OSError:
         pass
     import platform
