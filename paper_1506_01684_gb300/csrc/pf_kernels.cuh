@@ -3457,7 +3457,7 @@ cudaError_t launch_mesh_count(const KParams<R> &kp, const DevState *st, const vo
                               unsigned *seg_counts, cudaStream_t s)
 {
     const int nb = (kp.nx + MESH_W - 1) / MESH_W;
-    const dim3 grid((unsigned)(nb * kp.ny), (unsigned)((kp.nz - 1 + MESH_KC - 1) / MESH_KC));
+    const dim3 grid((unsigned)(nb * ((kp.ny + MESH_ROWS - 1) / MESH_ROWS)), (unsigned)((kp.nz - 1 + MESH_KC - 1) / MESH_KC));
     mesh_count_kernel<R><<<grid, MESH_W, 0, s>>>((const Ph<R> *)phi, st, kp.nx, kp.ny, kp.nz, phase, (R)iso,
                                                  seg_counts);
     return cudaGetLastError();

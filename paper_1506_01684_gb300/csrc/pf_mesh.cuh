@@ -158,11 +158,7 @@ constexpr int MESH_W = 256;  // cubes of a row per segment (one thread each; one
 #ifndef PF_MESH_KC
 #define PF_MESH_KC 32
 #endif
-#ifndef PF_MESH_DEPTH
-#define PF_MESH_DEPTH 2  // 1: 0.73, 2: 0.745, 3: 0.74 of the measured HBM copy rate (256x256x1024)
-#endif
 constexpr int MESH_KC = PF_MESH_KC;        // layers per counting CTA
-constexpr int MESH_DEPTH = PF_MESH_DEPTH;  // layers loaded ahead of the one being classified
 
 // Triangles of a cube from its inside mask (bit n set when corner n is inside): the tetrahedron
 // rule of tet_count on the mask's bits.
@@ -181,74 +177,94 @@ __device__ __forceinline__ int mask_count(int m)
     return t;
 }
 
+#ifndef PF_MESH_ROWS
+#define PF_MESH_ROWS 8  // 2: 0.89, 4: 0.88, 8: 0.90 of the measured HBM copy rate (256x256x1024, count kernel)
+#endif
+constexpr int MESH_ROWS = PF_MESH_ROWS;  // cube rows a counting CTA marches together
+
+// Pass 1: a CTA marches MESH_KC layers of MESH_ROWS cube rows of one 256-column piece, one thread a
+// column.  Each layer's MESH_ROWS + 1 cell rows are loaded and classified once (the inside bit of
+// column i + 1 from the next lane's ballot), shared by the two cube rows each touches; a cube's count
+// is a lookup by its 8-bit inside mask; the counts of each (layer, row, piece) segment are summed
+// over the piece's warps.
 template <typename R>
 __global__ void __launch_bounds__(MESH_W) mesh_count_kernel(const Ph<R> *__restrict__ phi, const DevState *__restrict__ st,
                                                            int nx, int ny, int nz, int phase, R iso,
                                                            unsigned *__restrict__ seg_counts)
 {
-    __shared__ unsigned wsum[MESH_KC][MESH_W / 32];
+    constexpr int NR = MESH_ROWS, NL = MESH_ROWS + 1;  // cube rows; cell rows they touch
+    __shared__ unsigned wsum[MESH_KC][NR][MESH_W / 32];
     __shared__ unsigned char table[256];  // triangles of a cube by its inside mask
     table[threadIdx.x] = (unsigned char)mask_count((int)threadIdx.x);
     const int nb = (nx + MESH_W - 1) / MESH_W;
-    const int b = blockIdx.x % nb, j = blockIdx.x / nb;
+    const int b = blockIdx.x % nb, jg = blockIdx.x / nb, j0 = jg * NR;
     const int k0 = blockIdx.y * MESH_KC, k1 = min(nz - 1, k0 + MESH_KC);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = b * MESH_W + threadIdx.x;
     const bool act = i < nx;
     const int ic = act ? i : nx - 1;
-    const int i1 = ic + 1 == nx ? 0 : ic + 1, j1 = j + 1 == ny ? 0 : j + 1;
+    const int i1 = ic + 1 == nx ? 0 : ic + 1;
     const bool from_lane = lane < 31 && ic + 1 < nx;  // the next lane holds column i + 1
     const size_t plane = (size_t)nx * ny;
     const int zbase = st->zbase;
+    // cell row r of the group: global row j0 + r, periodic
+    int row[NL];
+#pragma unroll
+    for (int r = 0; r < NL; r++) row[r] = (j0 + r) % ny;
     auto ld = [&](int k, int jj, int ii) { return phi[plane_off(k, nz, zbase, plane) + (size_t)jj * nx + ii].v[phase]; };
-    // the inside bits of a layer's four corners of this thread's cube (bit 0: (i, j), 1: (i+1, j),
-    // 2: (i, j+1), 3: (i+1, j+1)); each cell is classified once, the x + 1 corners come from the
-    // next lane's ballot bit
-    auto layer_bits = [&](R v0, R v2, R v1, R v3) {
-        const bool b0 = v0 >= iso, b2 = v2 >= iso;
-        const unsigned m0 = __ballot_sync(0xffffffffu, b0), m2 = __ballot_sync(0xffffffffu, b2);
-        const bool b1 = from_lane ? ((m0 >> (lane + 1)) & 1u) != 0 : v1 >= iso;
-        const bool b3 = from_lane ? ((m2 >> (lane + 1)) & 1u) != 0 : v3 >= iso;
-        return (unsigned)b0 | ((unsigned)b1 << 1) | ((unsigned)b2 << 2) | ((unsigned)b3 << 3);
+    // the inside bits of a layer: bit r of lo / hi: cell (i, row r) / (i + 1, row r)
+    struct Bits {
+        unsigned a, b;
     };
-    // the four corner values of layer k (the x + 1 ones loaded only where no lane holds them)
-    auto load4 = [&](int k, R (&v)[4]) {
-        v[0] = ld(k, j, ic);
-        v[2] = ld(k, j1, ic);
-        v[1] = v[0];
-        v[3] = v[2];
-        if (!from_lane) {
-            v[1] = ld(k, j, i1);
-            v[3] = ld(k, j1, i1);
+    auto layer = [&](const R (&v)[NL], const R (&v1)[NL]) {
+        Bits o{0u, 0u};
+#pragma unroll
+        for (int r = 0; r < NL; r++) {
+            const bool in = v[r] >= iso;
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            const bool in1 = from_lane ? ((m >> (lane + 1)) & 1u) != 0 : v1[r] >= iso;
+            o.a |= (unsigned)in << r;
+            o.b |= (unsigned)in1 << r;
+        }
+        return o;
+    };
+    auto load = [&](int k, R (&v)[NL], R (&v1)[NL]) {
+#pragma unroll
+        for (int r = 0; r < NL; r++) {
+            v[r] = ld(k, row[r], ic);
+            v1[r] = v[r];
+            if (!from_lane) v1[r] = ld(k, row[r], i1);
         }
     };
-    R a[4];
-    load4(k0, a);
-    // layers k + 1 .. k + MESH_DEPTH are loaded ahead, so that their loads are in flight together
-    R q[MESH_DEPTH][4] = {};
-#pragma unroll
-    for (int d = 0; d < MESH_DEPTH; d++)
-        if (k0 + 1 + d <= k1) load4(k0 + 1 + d, q[d]);
-    unsigned lo = layer_bits(a[0], a[2], a[1], a[3]);
+    R cv[NL], cv1[NL], qv[NL], qv1[NL];
+    load(k0, cv, cv1);
+    if (k0 + 1 <= k1) load(k0 + 1, qv, qv1);  // layer k + 1 in flight while layer k is classified
+    Bits lo = layer(cv, cv1);
     __syncthreads();  // the table
     for (int k = k0; k < k1; k++) {
-        const unsigned hi = layer_bits(q[0][0], q[0][2], q[0][1], q[0][3]);
+        const Bits hi = layer(qv, qv1);
+        if (k + 2 <= k1) load(k + 2, qv, qv1);
 #pragma unroll
-        for (int d = 0; d + 1 < MESH_DEPTH; d++)
-#pragma unroll
-            for (int c = 0; c < 4; c++) q[d][c] = q[d + 1][c];
-        if (k + 1 + MESH_DEPTH <= k1) load4(k + 1 + MESH_DEPTH, q[MESH_DEPTH - 1]);
-        unsigned n = act ? (unsigned)table[lo | (hi << 4)] : 0u;
-        n = __reduce_add_sync(0xffffffffu, n);
-        if (lane == 0) wsum[k - k0][w] = n;
+        for (int r = 0; r < NR; r++) {
+            // corners: 0 (i, j), 1 (i+1, j), 2 (i, j+1), 3 (i+1, j+1), then the same + 4 for layer k + 1
+            const unsigned m = ((lo.a >> r) & 1u) | (((lo.b >> r) & 1u) << 1) | (((lo.a >> (r + 1)) & 1u) << 2) |
+                               (((lo.b >> (r + 1)) & 1u) << 3) | (((hi.a >> r) & 1u) << 4) |
+                               (((hi.b >> r) & 1u) << 5) | (((hi.a >> (r + 1)) & 1u) << 6) |
+                               (((hi.b >> (r + 1)) & 1u) << 7);
+            unsigned n = act && j0 + r < ny ? (unsigned)table[m] : 0u;
+            n = __reduce_add_sync(0xffffffffu, n);
+            if (lane == 0) wsum[k - k0][r][w] = n;
+        }
         lo = hi;
     }
     __syncthreads();
-    if ((int)threadIdx.x < k1 - k0) {
+    for (int q = threadIdx.x; q < (k1 - k0) * NR; q += MESH_W) {
+        const int kk = q / NR, r = q % NR;
+        if (j0 + r >= ny) continue;
         unsigned sum = 0;
 #pragma unroll
-        for (int q = 0; q < MESH_W / 32; q++) sum += wsum[threadIdx.x][q];
-        seg_counts[((size_t)(k0 + threadIdx.x) * ny + j) * nb + b] = sum;
+        for (int u = 0; u < MESH_W / 32; u++) sum += wsum[kk][r][u];
+        seg_counts[((size_t)(k0 + kk) * ny + j0 + r) * nb + b] = sum;
     }
 }
 
