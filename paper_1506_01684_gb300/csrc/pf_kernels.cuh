@@ -3457,9 +3457,20 @@ cudaError_t launch_mesh_count(const KParams<R> &kp, const DevState *st, const vo
                               unsigned *seg_counts, cudaStream_t s)
 {
     const int nb = (kp.nx + MESH_W - 1) / MESH_W;
-    const dim3 grid((unsigned)(nb * ((kp.ny + MESH_ROWS - 1) / MESH_ROWS)), (unsigned)((kp.nz - 1 + MESH_KC - 1) / MESH_KC));
-    mesh_count_kernel<R><<<grid, MESH_W, 0, s>>>((const Ph<R> *)phi, st, kp.nx, kp.ny, kp.nz, phase, (R)iso,
-                                                 seg_counts);
+    const unsigned gz = (unsigned)((kp.nz - 1 + MESH_KC - 1) / MESH_KC);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long wide = (long)nb * ((kp.ny + MESH_ROWS_WIDE - 1) / MESH_ROWS_WIDE) * gz;
+    if (wide >= 4L * sms) {
+        const dim3 grid((unsigned)(nb * ((kp.ny + MESH_ROWS_WIDE - 1) / MESH_ROWS_WIDE)), gz);
+        mesh_count_kernel<R, MESH_ROWS_WIDE><<<grid, MESH_W, 0, s>>>((const Ph<R> *)phi, st, kp.nx, kp.ny, kp.nz,
+                                                                     phase, (R)iso, seg_counts);
+    } else {
+        const dim3 grid((unsigned)(nb * ((kp.ny + MESH_ROWS_NARROW - 1) / MESH_ROWS_NARROW)), gz);
+        mesh_count_kernel<R, MESH_ROWS_NARROW><<<grid, MESH_W, 0, s>>>((const Ph<R> *)phi, st, kp.nx, kp.ny, kp.nz,
+                                                                       phase, (R)iso, seg_counts);
+    }
     return cudaGetLastError();
 }
 

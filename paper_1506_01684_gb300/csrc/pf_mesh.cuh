@@ -177,22 +177,22 @@ __device__ __forceinline__ int mask_count(int m)
     return t;
 }
 
-#ifndef PF_MESH_ROWS
-#define PF_MESH_ROWS 8  // 2: 0.89, 4: 0.88, 8: 0.90 of the measured HBM copy rate (256x256x1024, count kernel)
-#endif
-constexpr int MESH_ROWS = PF_MESH_ROWS;  // cube rows a counting CTA marches together
+// Cube rows a counting CTA marches together: 8 where that still gives the launch at least 4 CTAs an
+// SM, else 2 (256x256x1024: 8 rows 0.90, 4 rows 0.88, 2 rows 0.89 of the measured HBM copy rate;
+// 256x256x256: 8 rows make only 256 CTAs and reach 0.55)
+constexpr int MESH_ROWS_WIDE = 8, MESH_ROWS_NARROW = 2;
 
-// Pass 1: a CTA marches MESH_KC layers of MESH_ROWS cube rows of one 256-column piece, one thread a
-// column.  Each layer's MESH_ROWS + 1 cell rows are loaded and classified once (the inside bit of
+// Pass 1: a CTA marches MESH_KC layers of NR cube rows of one 256-column piece, one thread a
+// column.  Each layer's NR + 1 cell rows are loaded and classified once (the inside bit of
 // column i + 1 from the next lane's ballot), shared by the two cube rows each touches; a cube's count
 // is a lookup by its 8-bit inside mask; the counts of each (layer, row, piece) segment are summed
 // over the piece's warps.
-template <typename R>
+template <typename R, int NR>
 __global__ void __launch_bounds__(MESH_W) mesh_count_kernel(const Ph<R> *__restrict__ phi, const DevState *__restrict__ st,
                                                            int nx, int ny, int nz, int phase, R iso,
                                                            unsigned *__restrict__ seg_counts)
 {
-    constexpr int NR = MESH_ROWS, NL = MESH_ROWS + 1;  // cube rows; cell rows they touch
+    constexpr int NL = NR + 1;  // cell rows the NR cube rows touch
     __shared__ unsigned wsum[MESH_KC][NR][MESH_W / 32];
     __shared__ unsigned char table[256];  // triangles of a cube by its inside mask
     table[threadIdx.x] = (unsigned char)mask_count((int)threadIdx.x);
