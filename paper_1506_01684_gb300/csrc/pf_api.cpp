@@ -2459,6 +2459,11 @@ struct pf_split {
     cudaEvent_t ev_comb = nullptr;
     DevBuf states;                     // DevState * per slab, the combine kernel's argument
     int latched = PF_OK;
+    // a captured graph of two steps (every slab's buffers 0 -> 1 -> 0), replayed on slab 0's stream:
+    // its first step forks the other streams off slab 0's, its end joins them back
+    cudaGraphExec_t graph = nullptr;
+    long long direct_steps = 0;
+    cudaEvent_t ev_fork = nullptr, ev_after = nullptr;
 };
 
 namespace {
@@ -2489,10 +2494,20 @@ cudaError_t exchange_rows(pf_split *d, int q, int buf, bool phi, cudaStream_t st
     return e;
 }
 
+// nsteps steps of every slab on the slabs' and exchange streams.  in_graph: the steps are being
+// captured on slab 0's stream as one graph -- the other streams are forked off it at the start (which
+// also orders the first step behind the previous mu exchange) and joined back at the end.
 template <typename R>
-int split_step(pf_split *d, int nsteps)
+int split_enqueue(pf_split *d, int nsteps, bool in_graph)
 {
     const int P = d->n;
+    cudaStream_t s0 = d->slabs[0]->stream;
+    if (in_graph) {
+        cudaError_t e = cudaEventRecord(d->ev_fork, s0);
+        for (int q = 1; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(d->slabs[q]->stream, d->ev_fork, 0);
+        for (int q = 0; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(d->xch[q], d->ev_fork, 0);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
     for (int it = 0; it < nsteps; it++) {
         cudaError_t e = cudaSuccess;
         std::vector<KParams<R>> kp(P);
@@ -2513,7 +2528,8 @@ int split_step(pf_split *d, int nsteps)
             e = cudaStreamWaitEvent(s->stream, d->ev_phi[(q + P - 1) % P], 0);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, d->ev_phi[(q + 1) % P], 0);
             if (e == cudaSuccess) e = exchange_rows(d, q, b, true, s->stream);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, d->ev_mux[q], 0);
+            // (the first step of a graph is ordered behind the last exchange by the fork)
+            if (e == cudaSuccess && !(in_graph && it == 0)) e = cudaStreamWaitEvent(s->stream, d->ev_mux[q], 0);
             if (e == cudaSuccess)
                 e = launch_mu_sweep<R>(kp[q], s->geo, s->phi[a].p, s->phi[b].p, s->mu[a].p, s->mu[b].p,
                                        (const DevState *)s->state.p, (const PlaneT<R> *)s->tab.p, (Partial *)s->parts.p,
@@ -2525,7 +2541,6 @@ int split_step(pf_split *d, int nsteps)
             if (e == cudaSuccess) e = cudaEventRecord(d->ev_fin[q], s->stream);
         }
         // one window decision on the global interface height, applied to every slab
-        cudaStream_t s0 = d->slabs[0]->stream;
         for (int q = 1; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(s0, d->ev_fin[q], 0);
         if (e == cudaSuccess)
             e = launch_split_combine((DevState *const *)d->states.p, P, d->nx, d->ny, d->nz,
@@ -2559,6 +2574,81 @@ int split_step(pf_split *d, int nsteps)
             s->last_kind = 0;
         }
     }
+    if (in_graph) {  // join: slab 0's stream waits for every other stream's last work
+        cudaError_t e = cudaSuccess;
+        for (int q = 1; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(s0, d->ev_post[q], 0);
+        for (int q = 0; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(s0, d->ev_mux[q], 0);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return PF_OK;
+}
+
+// pf_split_step's driver: the first steps and short calls launch directly; otherwise a captured graph of
+// two steps is replayed (the slabs' launches and copies are paid once).  Work launched directly before a
+// replay is gathered onto slab 0's stream first, and the other streams wait for the replays before
+// their next direct work (events recorded inside a graph do not order work outside it).
+template <typename R>
+int split_step(pf_split *d, int nsteps)
+{
+    const int P = d->n;
+    cudaStream_t s0 = d->slabs[0]->stream;
+    auto fail = [&](cudaError_t e) {
+        cudaGetLastError();
+        if (d->latched == PF_OK) d->latched = cuda_status(e);
+        return d->latched;
+    };
+    if (nsteps < 4 || d->direct_steps < 2) {
+        const int r = split_enqueue<R>(d, nsteps, false);
+        if (r == PF_OK) d->direct_steps += nsteps;
+        return r == PF_OK ? r : (d->latched = d->latched == PF_OK ? r : d->latched);
+    }
+    if (d->slabs[0]->cur != 0) {  // the graph starts from buffer 0
+        const int r = split_enqueue<R>(d, 1, false);
+        if (r != PF_OK) return d->latched = d->latched == PF_OK ? r : d->latched;
+        nsteps -= 1;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!d->graph) {
+        // ordered behind the direct steps (the capture starts on slab 0's stream)
+        for (int q = 1; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(s0, d->ev_post[q], 0);
+        for (int q = 0; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(s0, d->ev_mux[q], 0);
+        if (e != cudaSuccess) return fail(e);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return fail(e);
+        const int r = split_enqueue<R>(d, 2, true);  // recorded, not run: buffers end where they started
+        e = cudaStreamEndCapture(s0, &g);
+        if (r != PF_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(e != cudaSuccess ? e : cudaErrorUnknown);
+        }
+        e = cudaGraphInstantiate(&d->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            d->graph = nullptr;
+            return fail(e);
+        }
+    } else {
+        // the direct work since the last replay, gathered onto slab 0's stream (after a capture the
+        // events' last records are the capture's, which no work outside it may wait on: the gather
+        // before the capture stands for them)
+        for (int q = 1; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(s0, d->ev_post[q], 0);
+        for (int q = 0; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(s0, d->ev_mux[q], 0);
+    }
+    for (int q = 0; q + 1 < nsteps && e == cudaSuccess; q += 2) e = cudaGraphLaunch(d->graph, s0);
+    // the other streams' next direct work after the replays
+    if (e == cudaSuccess) e = cudaEventRecord(d->ev_after, s0);
+    for (int q = 1; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(d->slabs[q]->stream, d->ev_after, 0);
+    for (int q = 0; q < P && e == cudaSuccess; q++) e = cudaStreamWaitEvent(d->xch[q], d->ev_after, 0);
+    if (e != cudaSuccess) return fail(e);
+    // the exchange events' next use is a direct step: they must describe the replayed steps' end
+    for (int q = 0; q < P && e == cudaSuccess; q++) e = cudaEventRecord(d->ev_mux[q], d->xch[q]);
+    for (int q = 0; q < P && e == cudaSuccess; q++) e = cudaEventRecord(d->ev_post[q], d->slabs[q]->stream);
+    if (e != cudaSuccess) return fail(e);
+    if (nsteps & 1) {
+        const int r = split_enqueue<R>(d, 1, false);
+        if (r != PF_OK) return d->latched = d->latched == PF_OK ? r : d->latched;
+    }
     return PF_OK;
 }
 }  // namespace
@@ -2578,6 +2668,9 @@ int pf_split_destroy(pf_split *d)
         for (cudaEvent_t ev : *v)
             if (ev) cudaEventDestroy(ev);
     if (d->ev_comb) cudaEventDestroy(d->ev_comb);
+    if (d->ev_fork) cudaEventDestroy(d->ev_fork);
+    if (d->ev_after) cudaEventDestroy(d->ev_after);
+    if (d->graph) cudaGraphExecDestroy(d->graph);
     dev_free(d->states, nullptr);
     delete d;
     return PF_OK;
@@ -2627,6 +2720,8 @@ int pf_split_create(int nx, int ny, int nz, const pf_params *p, int nslabs, pf_s
     }
     if (r == PF_OK) {
         cudaError_t e = cudaEventCreateWithFlags(&d->ev_comb, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->ev_after, cudaEventDisableTiming);
         if (e != cudaSuccess) r = cuda_status(e);
     }
     if (r == PF_OK) r = dev_alloc(d->states, sizeof(DevState *) * nslabs, nullptr);
