@@ -67,3 +67,27 @@ def test_default_params_match_the_workload_parameter_set():
         else:
             assert list(map(lambda x: list(x) if hasattr(x, "__len__") else x, a)) == \
                 list(map(lambda x: list(x) if hasattr(x, "__len__") else x, b)), f
+
+
+def test_host_side_checks_of_the_split_batch_and_checkpoint_calls():
+    # argument checks that return before any device call
+    L = pf.lib()
+    p = pf.params_from_dict(W.symmetric_params(), pf.PF_FP64)
+    h = ctypes.c_void_p()
+    # slabs: at least one, at most one a row; compensated FP32 is not offered
+    assert L.pf_split_create(8, 6, 8, ctypes.byref(p), 0, ctypes.byref(h)) == pf.PF_E_INVAL
+    assert L.pf_split_create(8, 6, 8, ctypes.byref(p), 7, ctypes.byref(h)) == pf.PF_E_INVAL
+    assert L.pf_split_create(0, 6, 8, ctypes.byref(p), 2, ctypes.byref(h)) == pf.PF_E_INVAL
+    c = pf.params_from_dict(W.symmetric_params(), pf.PF_FP32_COMP)
+    assert L.pf_split_create(8, 6, 8, ctypes.byref(c), 2, ctypes.byref(h)) == pf.PF_E_INVAL
+    assert L.pf_split_create(8, 6, 8, ctypes.byref(p), 2, None) == pf.PF_E_INVAL
+    for name in ("pf_split_destroy", "pf_split_sync"):
+        assert getattr(L, name)(None) == pf.PF_E_INVAL
+    assert L.pf_split_step(None, 1) == pf.PF_E_INVAL
+    assert L.pf_split_init(None, 0) == pf.PF_E_INVAL
+    assert L.pf_split_read_fields(None, None, None, 0) == pf.PF_E_INVAL
+    assert L.pf_split_stats(None, None, None, None, None) == pf.PF_E_INVAL
+    # the batch's launch shape and byte tally, and the single-precision checkpoint, of no object
+    assert L.pf_batch_config(None, None, None) == pf.PF_E_INVAL
+    assert L.pf_batch_step_bytes(None, None) == pf.PF_E_INVAL
+    assert L.pf_checkpoint_write_f32(None, b"x") == pf.PF_E_INVAL
