@@ -209,17 +209,20 @@ def test_non_finite_values_are_reported_not_propagated_silently():
     sim.sync()
 
 
-@pytest.mark.parametrize("variant", ["unfused", "fused"])
-def test_fp32_full_size_step_matches_the_oracle_on_sampled_windows(variant):
-    # 256x256x1024 (the single large domain) in the launch configuration the benchmark times:
-    # advance 20 FP32 steps on the GPU, read the state, take one more GPU step, and compare
-    # windows of the result with one oracle step on the same (FP32-valued) input.  A cell's
-    # update depends on cells at most 2 away, so window interiors are exact.
+@pytest.mark.parametrize("variant,pre", [("unfused", 20), ("fused", 20), ("auto", 2000)])
+def test_fp32_full_size_step_matches_the_oracle_on_sampled_windows(variant, pre):
+    # 256x256x1024 (the single large domain) in the launch configuration the benchmark times (the
+    # default variant from the configuration's 2000-step state: the lean kernel with the general
+    # planes' sweeps beside it): advance `pre` FP32 steps on the GPU, read the state, take one more
+    # GPU step, and compare windows of the result with one oracle step on the same (FP32-valued)
+    # input.  A cell's update depends on cells at most 2 away, so window interiors are exact.
     nx, ny, nz = 256, 256, 1024
     p = W.symmetric_params(n_grains=64, window_trigger_z=512.0)
     sim = pf.Simulation(nx, ny, nz, p, "fp32", variant=variant)
     sim.init(0)
-    sim.step(20)
+    sim.step(pre)
+    if variant == "auto":
+        assert "lean_step" in sim.step_bytes()  # the lean path, as the benchmark runs it
     phi0, mu0 = sim.fields()
     st0 = sim.stats()
     sim.step(1)
