@@ -38,6 +38,7 @@ using namespace pf;
 #define PF_GENERAL_CTAS_PER_SM 2
 #endif
 
+
 #ifndef PF_LEAN_PLANES
 #define PF_LEAN_PLANES 64  // at most planes per lean CTA (the kernels' limit, PF_LEAN_PLANES in pf_kernels.cuh)
 #endif
