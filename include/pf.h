@@ -398,7 +398,8 @@ int pf_server_stats(pf_server *srv, double *mlups, int *running, int *queued, si
  * phi-sweeps are done; the mu-sweep of every slab once its mu ghost rows have arrived; one kernel
  * that sums the slabs' interface sums, decides the moving-window shift (Section 3.3) for the whole
  * domain and hands it to every slab; each slab's plane table and window fill; the mu ghost rows
- * copied on a separate stream per slab, overlapping the next phi-sweep.  Every cell is updated by
+ * copied on a separate stream per slab, overlapping the next phi-sweep.  After two steps launched
+ * directly, pf_split_step replays the schedule of two steps from a captured CUDA graph.  Every cell is updated by
  * the same arithmetic as in an undivided pf_sim stepped with PF_VARIANT_UNFUSED, so the fields
  * agree with such a run bit for bit (FP32 and FP64).  Ghost-row copies are device-to-device
  * strided copies (cudaMemcpy2DAsync), the stand-in on one GPU for the paper's messages between
