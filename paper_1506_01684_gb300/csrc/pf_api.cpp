@@ -1610,6 +1610,7 @@ struct pf_batch {
     int precision = PF_FP32;
     int zchunk = 0;
     int general_per_sm = PF_GENERAL_CTAS_PER_SM;  // persistent general CTAs per SM (autotuned)
+    int lean_split = 1;  // lean CTAs per z chunk: this many times the fewest that keep <= 64 planes a CTA (autotuned)
     DevBuf doms;     // BatchDomain<R>[n]
     DevBuf items;    // BatchItem[nitems]
     DevBuf parts;    // Partial[sum of tiles]
@@ -1676,7 +1677,7 @@ static int batch_build(pf_batch *b)
         d[q].gx = g.gx;
         d[q].gy = g.gy;
         d[q].gz = g.gz;
-        d[q].nsub = std::max(1, (g.zchunk + PF_LEAN_PLANES - 1) / PF_LEAN_PLANES);
+        d[q].nsub = std::min(g.zchunk, std::max(1, (g.zchunk + PF_LEAN_PLANES - 1) / PF_LEAN_PLANES) * b->lean_split);
         part_total += (size_t)g.nparts();
         // the lean path needs the TMA maps and a chunk the batched plan covers
         const bool lean = s->lean_ok && g.zchunk + 4 <= 64 * 9;
@@ -1999,11 +2000,12 @@ int pf_batch_set_zchunk(pf_batch *b, int zchunk)
     return PF_OK;
 }
 
-int pf_batch_config(pf_batch *b, int *zchunk, int *general_ctas_per_sm)
+int pf_batch_config(pf_batch *b, int *zchunk, int *general_ctas_per_sm, int *lean_split)
 {
     if (!b) return PF_E_INVAL;
     if (zchunk) *zchunk = b->zchunk;
     if (general_ctas_per_sm) *general_ctas_per_sm = b->general_per_sm;
+    if (lean_split) *lean_split = b->lean_split;
     return PF_OK;
 }
 
@@ -2080,17 +2082,19 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
     // liquid maps, the plan and the lean kernel's tensor-map boxes are built per 32x8 tile)
     const int cands[] = {16, 32, 64, 128, 256, 512};
     const int gcands[] = {1, 2};
-    int bestz = b->zchunk, bestg = b->general_per_sm;
+    const int lcands[] = {1, 2, 4};
+    int bestz = b->zchunk, bestg = b->general_per_sm, bestl = b->lean_split;
     double bestt = 1e300;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    for (int trial = 0; trial < 12; trial++) {
-        const int zc = cands[trial / 2], gc = gcands[trial % 2];
+    for (int trial = 0; trial < 36; trial++) {
+        const int zc = cands[trial / 6], gc = gcands[(trial / 3) % 2], lc = lcands[trial % 3];
         if (e != cudaSuccess) break;
         if (zc > 2 * nzmax && zc != cands[0]) continue;
         b->zchunk = zc;
         b->general_per_sm = gc;
+        b->lean_split = lc;
         b->built = false;
         b->direct_steps = 0;
         int r = PF_BDISPATCH(b, batch_step, b, 1);  // builds the table, warms up
@@ -2108,6 +2112,7 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
             bestt = ms / trial_steps;
             bestz = zc;
             bestg = gc;
+            bestl = lc;
         }
         if (e == cudaSuccess) e = restore();
     }
@@ -2116,6 +2121,7 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
     for (auto &x : snap) dev_free(x, b->stream);
     b->zchunk = bestz;
     b->general_per_sm = bestg;
+    b->lean_split = bestl;
     b->built = false;
     b->direct_steps = 0;
     if (e != cudaSuccess) return cuda_status(e);

@@ -105,7 +105,7 @@ SIGNATURES = {
     "pf_batch_set_zchunk": (_I, [_VP, _I]),
     "pf_batch_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), _DP]),
     "pf_batch_step_bytes": (_I, [_VP, _DP]),
-    "pf_batch_config": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "pf_batch_config": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "pf_server_create": (_I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_VP)]),
     "pf_server_destroy": (_I, [_VP]),
     "pf_submit": (_I, [_VP, _I, _I, _I, ctypes.POINTER(pf_params), ctypes.c_uint64, _I,
@@ -415,9 +415,9 @@ def pf_batch_autotune(b, trial_steps=10):
 
 
 def pf_batch_config(b):
-    z, g = _I(), _I()
-    _check(lib().pf_batch_config(b, ctypes.byref(z), ctypes.byref(g)), "pf_batch_config")
-    return {"zchunk": z.value, "general_ctas_per_sm": g.value}
+    z, g, l = _I(), _I(), _I()
+    _check(lib().pf_batch_config(b, ctypes.byref(z), ctypes.byref(g), ctypes.byref(l)), "pf_batch_config")
+    return {"zchunk": z.value, "general_ctas_per_sm": g.value, "lean_split": l.value}
 
 
 def pf_batch_step_bytes(b):
