@@ -402,7 +402,7 @@ def run_batched_study(args):
             "speedup_vs_one_by_one": ms_single / ms_batch, "ms_per_step": ms_batch,
             "ms_per_step_one_by_one": ms_single, "cells": cells, "domains": len(shapes),
             "autotuned_zchunk": zc, "autotuned_general_ctas_per_sm": tuned["general_ctas_per_sm"],
-            "autotuned_lean_split": tuned["lean_split"],
+            "autotuned_lean_split": tuned["lean_split"], "autotuned_lean_tile": [32, tuned["lean_tile_rows"]],
             "autotune_ms_per_step": tune_ms, "steps": args.steps, "warmup": args.warmup,
             "roofline": {"bound": "hbm", "kernel": "whole batched step", "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,

@@ -336,16 +336,20 @@ int pf_batch_sync(pf_batch *b);
 int pf_batch_set_zchunk(pf_batch *b, int zchunk);
 /* Autotuner: times trial_steps steps for each candidate launch shape on the batch itself -- z-chunk
  * depth (16 to 512 planes) x persistent general-plane CTAs per SM (1 or 2) x the lean kernel's
- * z-block depth (1, 2 or 4 times the fewest lean CTAs a chunk that keep <= 64 planes a CTA); the tile
- * is 32x8 throughout, the unit of the liquid maps, the plan and the lean kernel's tensor-map boxes --
- * (the fields, clocks, windows and plane tables are restored afterwards), keeps the fastest and
- * returns its z-chunk depth in *best (may be NULL) and its measured milliseconds per step in *best_ms
- * (may be NULL); pf_batch_config reports the whole shape. */
+ * z-block depth (1, 2 or 4 times the fewest lean CTAs a chunk that keep <= 64 planes a CTA) x its
+ * tile (32x8 cells, a liquid-map tile, or 32x4, half of one; the liquid maps, the plan and the
+ * general sweeps keep 32x8 tiles) -- (the fields, clocks, windows and plane tables are restored
+ * afterwards), keeps the fastest and returns its z-chunk depth in *best (may be NULL) and its measured
+ * milliseconds per step in *best_ms (may be NULL); pf_batch_config reports the whole shape. */
 int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms);
-/* The batch's launch shape: z-chunk depth (0: the default), persistent general-plane CTAs per SM, and
- * the lean kernel's split of a z chunk (lean CTAs a chunk / the fewest that keep <= 64 planes a CTA);
- * any pointer may be NULL. */
-int pf_batch_config(pf_batch *b, int *zchunk, int *general_ctas_per_sm, int *lean_split);
+/* The batch's launch shape: z-chunk depth (0: the default), persistent general-plane CTAs per SM, the
+ * lean kernel's split of a z chunk (lean CTAs a chunk / the fewest that keep <= 64 planes a CTA) and
+ * the rows of its tile (8 or 4); any pointer may be NULL. */
+int pf_batch_config(pf_batch *b, int *zchunk, int *general_ctas_per_sm, int *lean_split, int *lean_tile_rows);
+/* Sets the launch shape pf_batch_config reports: zchunk >= 0 (0: each domain's default), general CTAs
+ * per SM 1 or 2, lean split 1, 2 or 4, lean tile rows 8 or 4; anything else is PF_E_INVAL.  The shape
+ * changes no result: every cell's update is the same arithmetic under any shape. */
+int pf_batch_set_config(pf_batch *b, int zchunk, int general_ctas_per_sm, int lean_split, int lean_tile_rows);
 /* Algorithmic bytes of the batch's last step, as its kernels tallied them (compulsory traffic of
  * each cell's words, the measure of pf_step_bytes): bytes[0] the general planes' sweeps and the fused
  * tiles, bytes[1] the lean kernel's pure-liquid planes.  Synchronising. */

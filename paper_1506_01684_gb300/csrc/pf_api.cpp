@@ -1611,6 +1611,7 @@ struct pf_batch {
     int zchunk = 0;
     int general_per_sm = PF_GENERAL_CTAS_PER_SM;  // persistent general CTAs per SM (autotuned)
     int lean_split = 1;  // lean CTAs per z chunk: this many times the fewest that keep <= 64 planes a CTA (autotuned)
+    int lean_rows = 8;   // rows of a lean CTA's tile: 8 (a liquid-map tile) or 4 (half of one) (autotuned)
     DevBuf doms;     // BatchDomain<R>[n]
     DevBuf items;    // BatchItem[nitems]
     DevBuf parts;    // Partial[sum of tiles]
@@ -1668,6 +1669,12 @@ static int batch_build(pf_batch *b)
             d[q].tmap[k] = (unsigned char *)s->tmap[k ^ s->cur].p;
             d[q].mu_map[k] = s->mu_map[k ^ s->cur];
         }
+        // half-height lean tiles copy boxes of their own height
+        bool maps_ok = true;
+        if (b->lean_rows != g.ty)
+            for (int k = 0; k < 2; k++)
+                maps_ok = maps_ok && encode_lean_maps(&d[q].mu_map[k], s->mu[k ^ s->cur].p, s->nx, s->ny, s->nz,
+                                                      sizeof(R), g.tx, b->lean_rows);
         d[q].st = (DevState *)s->state.p;
         d[q].tab = (PlaneT<R> *)s->tab.p;
         d[q].parts = nullptr;  // set once the partial-sum array exists
@@ -1680,7 +1687,7 @@ static int batch_build(pf_batch *b)
         d[q].nsub = std::min(g.zchunk, std::max(1, (g.zchunk + PF_LEAN_PLANES - 1) / PF_LEAN_PLANES) * b->lean_split);
         part_total += (size_t)g.nparts();
         // the lean path needs the TMA maps and a chunk the batched plan covers
-        const bool lean = s->lean_ok && g.zchunk + 4 <= 64 * 9;
+        const bool lean = s->lean_ok && maps_ok && g.zchunk + 4 <= 64 * 9;
         if (q == 0) b->dom_lean.assign(n, 0);
         b->dom_lean[q] = lean ? 1 : 0;
         if (lean) {
@@ -1709,8 +1716,10 @@ static int batch_build(pf_batch *b)
                      [](const std::pair<long, int> &x, const std::pair<long, int> &y) { return x.first > y.first; });
     for (const auto &lo : lean_order) {
         const int q = lo.second;
+        // row blocks of lean_rows rows (those of a map tile share its split)
+        const int nby = (b->sims[q]->ny + b->lean_rows - 1) / b->lean_rows;
         for (int z = 0; z < d[q].gz * d[q].nsub; z++)
-            for (int by = 0; by < d[q].gy; by++)
+            for (int by = 0; by < nby; by++)
                 for (int bx = 0; bx < d[q].gx; bx++) lean_items.push_back(make_int4(q, bx, by, z));
     }
     std::stable_sort(order.begin(), order.end(), [](const std::pair<long, int> &x, const std::pair<long, int> &y) {
@@ -1818,7 +1827,7 @@ static int batch_step_direct(pf_batch *b, int n)
                                             b->nlean, (int2 *)b->glist.p, (BatchPlan *)b->plan.p, b->gphi_ctas,
                                             b->gmu_ctas, (const BatchItem *)b->items.p, b->nitems,
                                             (unsigned *)b->counter.p, b->ctas, b->parity, b->post_blocks, b->stream,
-                                            b->sym, b->aux, b->ev_fork, b->ev_join);
+                                            b->sym, b->aux, b->ev_fork, b->ev_join, b->lean_rows);
         else
             e = launch_batched_step<R>((const BatchDomain<R> *)b->doms.p, (int)b->sims.size(),
                                        (const BatchItem *)b->items.p, b->nitems, (unsigned *)b->counter.p, b->parity,
@@ -2000,12 +2009,28 @@ int pf_batch_set_zchunk(pf_batch *b, int zchunk)
     return PF_OK;
 }
 
-int pf_batch_config(pf_batch *b, int *zchunk, int *general_ctas_per_sm, int *lean_split)
+int pf_batch_config(pf_batch *b, int *zchunk, int *general_ctas_per_sm, int *lean_split, int *lean_tile_rows)
 {
     if (!b) return PF_E_INVAL;
     if (zchunk) *zchunk = b->zchunk;
     if (general_ctas_per_sm) *general_ctas_per_sm = b->general_per_sm;
     if (lean_split) *lean_split = b->lean_split;
+    if (lean_tile_rows) *lean_tile_rows = b->lean_rows;
+    return PF_OK;
+}
+
+int pf_batch_set_config(pf_batch *b, int zchunk, int general_ctas_per_sm, int lean_split, int lean_tile_rows)
+{
+    if (!b || zchunk < 0 || (general_ctas_per_sm != 1 && general_ctas_per_sm != 2) ||
+        (lean_split != 1 && lean_split != 2 && lean_split != 4) || (lean_tile_rows != 8 && lean_tile_rows != 4))
+        return PF_E_INVAL;
+    // the next step rebuilds the tables and the graph for the new shape
+    b->zchunk = zchunk;
+    b->general_per_sm = general_ctas_per_sm;
+    b->lean_split = lean_split;
+    b->lean_rows = lean_tile_rows;
+    b->built = false;
+    b->direct_steps = 0;
     return PF_OK;
 }
 
@@ -2083,18 +2108,21 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
     const int cands[] = {16, 32, 64, 128, 256, 512};
     const int gcands[] = {1, 2};
     const int lcands[] = {1, 2, 4};
-    int bestz = b->zchunk, bestg = b->general_per_sm, bestl = b->lean_split;
+    const int rcands[] = {8, 4};
+    int bestz = b->zchunk, bestg = b->general_per_sm, bestl = b->lean_split, bestr = b->lean_rows;
     double bestt = 1e300;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    for (int trial = 0; trial < 36; trial++) {
-        const int zc = cands[trial / 6], gc = gcands[(trial / 3) % 2], lc = lcands[trial % 3];
+    for (int trial = 0; trial < 72; trial++) {
+        const int zc = cands[trial / 12], gc = gcands[(trial / 6) % 2], lc = lcands[(trial / 2) % 3],
+                  rc = rcands[trial % 2];
         if (e != cudaSuccess) break;
         if (zc > 2 * nzmax && zc != cands[0]) continue;
         b->zchunk = zc;
         b->general_per_sm = gc;
         b->lean_split = lc;
+        b->lean_rows = rc;
         b->built = false;
         b->direct_steps = 0;
         int r = PF_BDISPATCH(b, batch_step, b, 1);  // builds the table, warms up
@@ -2113,6 +2141,7 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
             bestz = zc;
             bestg = gc;
             bestl = lc;
+            bestr = rc;
         }
         if (e == cudaSuccess) e = restore();
     }
@@ -2122,6 +2151,7 @@ int pf_batch_autotune(pf_batch *b, int trial_steps, int *best, double *best_ms)
     b->zchunk = bestz;
     b->general_per_sm = bestg;
     b->lean_split = bestl;
+    b->lean_rows = bestr;
     b->built = false;
     b->direct_steps = 0;
     if (e != cudaSuccess) return cuda_status(e);

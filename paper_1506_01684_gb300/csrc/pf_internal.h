@@ -232,15 +232,18 @@ template <typename R>
 int fused_ctas_per_sm();
 // Batched step on the lean path: counters reset, plan over the (domain, item) entries, the general
 // planes' two sweeps (persistent CTAs over the batch-wide list), the lean kernel over its items
-// (domain, tile x, tile y, chunk * nsub + sub); domains without TMA maps run the fused tile over
-// their items (fitems); then per-domain finalize and post.  parity: index of the source buffers.
+// (domain, tile x, row block y, chunk * nsub + sub) with lean_rows-row CTA tiles (8: a whole map tile,
+// 4: half of one; the domains' tensor maps must have the matching boxes); domains without TMA maps
+// run the fused tile over their items (fitems); then per-domain finalize and post.  parity: index of
+// the source buffers.  sym: every domain has the symmetric parameter set; aux: the general sweeps
+// run on it beside the lean kernel.
 template <typename R>
 cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, const int2 *plan_entries, int nplan,
                                      const int4 *lean_items, int nlean, int2 *glist, BatchPlan *plan,
                                      int phi_ctas, int mu_ctas, const BatchItem *fitems, int nfitems,
                                      unsigned *counter, int fctas, int parity, int post_blocks, cudaStream_t s,
                                      bool sym, cudaStream_t aux = nullptr, cudaEvent_t fork = nullptr,
-                                     cudaEvent_t join = nullptr);  // aux: the general sweeps beside the lean kernel  // sym: every domain has the symmetric parameter set
+                                     cudaEvent_t join = nullptr, int lean_rows = 8);
 template <typename R>
 void batched_general_ctas_per_sm(int *phi_per_sm, int *mu_per_sm);
 // The window decision of a decomposed domain (one thread): the global interface height from the slabs'

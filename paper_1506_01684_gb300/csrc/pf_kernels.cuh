@@ -2992,6 +2992,8 @@ cudaError_t launch_fused_step(const KParams<R> &kp, const Geometry &g, const voi
 #define PF_LEAN_ROWS 4
 #endif
 constexpr int kLeanStages = PF_LEAN_STAGES, kLeanMaxSub = PF_LEAN_PLANES, kLeanRows = PF_LEAN_ROWS;
+// rows a consumer warp owns in the half-height (32 x kTY/2) lean tile of a batched step
+constexpr int kLeanRowsHalf = PF_LEAN_ROWS < kTY / 2 ? PF_LEAN_ROWS : kTY / 2;
 
 template <typename R>
 cudaError_t launch_plan(const KParams<R> &kp, const Geometry &g, const DevState *st, const unsigned char *tmap_in,
@@ -3293,11 +3295,14 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
                                      const int4 *lean_items, int nlean, int2 *glist, BatchPlan *plan,
                                      int phi_ctas, int mu_ctas, const BatchItem *fitems, int nfitems,
                                      unsigned *counter, int fctas, int parity, int post_blocks, cudaStream_t s,
-                                     bool sym, cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join)
+                                     bool sym, cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join, int lean_rows)
 {
     using L = LeanLayout<R, kTX, kTY>;
+    using LH = LeanLayout<R, kTX, kTY / 2>;
+    if (lean_rows != kTY && lean_rows != kTY / 2) return cudaErrorInvalidValue;
     static DeviceOnce attr;  // the attribute is a per-device setting: set once on each device
     const size_t smp = phi_smem_bytes<R>(), smm = mu_smem_bytes<R>(), sml = L::smem_bytes(kLeanStages);
+    const size_t smlh = LH::smem_bytes(kLeanStages);
     const size_t smf = fused_smem_bytes<R>();
     if (!attr.done()) {
         cudaError_t e = cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 0, false>,
@@ -3312,8 +3317,11 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
             e = cudaFuncSetAttribute(batched_general_kernel<R, kTX, kTY, 1, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(batched_lean_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>,
+            e = cudaFuncSetAttribute(batched_lean_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows, kTY>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sml);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batched_lean_kernel<R, kTX, kTY / 2, kLeanStages, kLeanMaxSub, kLeanRowsHalf, kTY>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smlh);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(batched_fused_kernel<R, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smf);
@@ -3347,9 +3355,12 @@ cudaError_t launch_batched_lean_step(const BatchDomain<R> *doms, int ndoms, cons
             if (e != cudaSuccess) return e;
         }
     }
-    if (nlean > 0)
-        batched_lean_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows>
+    if (nlean > 0 && lean_rows == kTY)
+        batched_lean_kernel<R, kTX, kTY, kLeanStages, kLeanMaxSub, kLeanRows, kTY>
             <<<nlean, kTX * kTY / kLeanRows + 32, sml, s>>>(doms, lean_items, parity);
+    else if (nlean > 0)
+        batched_lean_kernel<R, kTX, kTY / 2, kLeanStages, kLeanMaxSub, kLeanRowsHalf, kTY>
+            <<<nlean, kTX * (kTY / 2) / kLeanRowsHalf + 32, smlh, s>>>(doms, lean_items, parity);
     if (nfitems > 0) {
         e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
@@ -3527,7 +3538,8 @@ cudaError_t launch_mesh_emit(const KParams<R> &kp, const DevState *st, const voi
     template int fused_ctas_per_sm<R>();                                                                         \
     template cudaError_t launch_batched_lean_step<R>(const BatchDomain<R> *, int, const int2 *, int, const int4 *, \
                                                      int, int2 *, BatchPlan *, int, int, const BatchItem *, int,   \
-                                                     unsigned *, int, int, int, cudaStream_t, bool, cudaStream_t, cudaEvent_t, cudaEvent_t);                \
+                                                     unsigned *, int, int, int, cudaStream_t, bool, cudaStream_t, cudaEvent_t, cudaEvent_t, \
+                                                     int);                                                       \
     template void batched_general_ctas_per_sm<R>(int *, int *);                                                  \
     template cudaError_t launch_finalize<R>(const KParams<R> &, DevState *, const Partial *, int, cudaStream_t,   \
                                             LeanStats *, bool);                                                  \

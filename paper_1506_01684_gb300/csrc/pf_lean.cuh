@@ -155,11 +155,16 @@ __device__ __forceinline__ Mu<R> lds_cell(const unsigned char *p)
 // and of that chunk the sub-chunk blockIdx.z % nsub of at most MAXSUB planes.  The CTA updates the
 // chunk's lean planes (its split, from plan_kernel) that fall into its sub-chunk.  TY/ROWS consumer warps own ROWS
 // consecutive tile rows each (lane = tile column), one producer warp feeds them.
+// MTY: the rows of a liquid-map tile (the unit of the maps and of the plan's splits).  A CTA of TY < MTY
+// rows updates the rows [by TY, by TY + TY) of map tile by / (MTY / TY) under that tile's split and
+// map entries; its siblings write the same entries.  (After a timed-out wait a sibling may overwrite
+// the "not known" 0 with 1; the step then latches PF_E_TIMEOUT and the maps are rebuilt when the
+// fields are next initialised or written.)
 // COMP: the compensated FP32 state (value = high + low word): the tensor copies carry the high words of
 // mu, each consumer loads its own cells' low words, forms the increment C1 (neighbour sum - 6 mu) + C0
 // from the high words and adds it to high + low with the error-free two-sum (the compensated update of
 // the two sweeps); a stored pure-liquid phi gets zero low words.
-template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS, bool COMP = false>
+template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS, bool COMP = false, int MTY = TY>
 __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const LeanMaps *maps, const Mu<R> *__restrict__ mu,
                                           Ph<R> *__restrict__ phi_out, Mu<R> *__restrict__ mu_out,
                                           const DevState *__restrict__ st, LeanStats *__restrict__ stats,
@@ -194,13 +199,14 @@ __device__ __forceinline__ void lean_tile(const KParams<R> &kp, const LeanMaps *
     const int s0 = min(z1, z0 + sub * sublen), s1 = min(z1, s0 + sublen);
     const int zbase = st->zbase;
     const size_t plane = (size_t)nx * ny;
-    const int ntl = kp.tgx * kp.tgy, tile = by * kp.tgx + bx;
+    static_assert(MTY % TY == 0, "whole CTA tiles per map tile");
+    const int ntl = kp.tgx * kp.tgy, tile = by / (MTY / TY) * kp.tgx + bx;
     auto splane = [&](int k) {
         const int sp = k + zbase;
         return sp >= nz ? sp - nz : sp;
     };
     // the periodic images this tile needs (only at the domain's edges), copied with the tile box
-    const bool img_xl = bx == 0, img_xr = i0 + TX >= nx, img_yl = by == 0, img_yh = j0 + TY >= ny;
+    const bool img_xl = bx == 0, img_xr = i0 + TX >= nx, img_yl = j0 == 0, img_yh = j0 + TY >= ny;
 
     // (the launch guarantees s1 - s0 <= MAXSUB) the destination's map entries, read before any is
     // replaced
@@ -604,16 +610,17 @@ __global__ void __launch_bounds__(TX *TY / ROWS + 32, sizeof(R) == 4 ? PF_LEAN_M
                                                  blockIdx.x, blockIdx.y, blockIdx.z, mu_lo, phi_out_lo, mu_out_lo);
 }
 
-// One lean work item of a batched step: CTA blockIdx.x takes (domain, tile x, tile y, chunk * nsub +
-// sub) from the table; the domain's tensor maps live in device memory (64-byte aligned).
-template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS>
+// One lean work item of a batched step: CTA blockIdx.x takes (domain, tile x, TY-row block y, chunk *
+// nsub + sub) from the table; the domain's tensor maps (boxes of TY + 2 rows) live in device memory
+// (64-byte aligned).  MTY: the rows of a liquid-map tile.
+template <typename R, int TX, int TY, int LD, int MAXSUB, int ROWS, int MTY>
 __global__ void __launch_bounds__(TX *TY / ROWS + 32, sizeof(R) == 4 ? PF_LEAN_MIN_CTAS : 3) batched_lean_kernel(
     const BatchDomain<R> *__restrict__ doms, const int4 *__restrict__ items, int parity)
 {
     const int4 w = items[blockIdx.x];
     const BatchDomain<R> *d = doms + w.x;
     const int a = parity, b = parity ^ 1;
-    lean_tile<R, TX, TY, LD, MAXSUB, ROWS>(d->kp, d->mu_map + a, (const Mu<R> *)d->mu[a], (Ph<R> *)d->phi[b],
+    lean_tile<R, TX, TY, LD, MAXSUB, ROWS, false, MTY>(d->kp, d->mu_map + a, (const Mu<R> *)d->mu[a], (Ph<R> *)d->phi[b],
                                            (Mu<R> *)d->mu[b], d->st, d->lean, d->tmap[b], d->splits, d->nsub, w.y,
                                            w.z, w.w);
 }

@@ -105,7 +105,8 @@ SIGNATURES = {
     "pf_batch_set_zchunk": (_I, [_VP, _I]),
     "pf_batch_autotune": (_I, [_VP, _I, ctypes.POINTER(_I), _DP]),
     "pf_batch_step_bytes": (_I, [_VP, _DP]),
-    "pf_batch_config": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "pf_batch_config": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "pf_batch_set_config": (_I, [_VP, _I, _I, _I, _I]),
     "pf_server_create": (_I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_VP)]),
     "pf_server_destroy": (_I, [_VP]),
     "pf_submit": (_I, [_VP, _I, _I, _I, ctypes.POINTER(pf_params), ctypes.c_uint64, _I,
@@ -415,9 +416,15 @@ def pf_batch_autotune(b, trial_steps=10):
 
 
 def pf_batch_config(b):
-    z, g, l = _I(), _I(), _I()
-    _check(lib().pf_batch_config(b, ctypes.byref(z), ctypes.byref(g), ctypes.byref(l)), "pf_batch_config")
-    return {"zchunk": z.value, "general_ctas_per_sm": g.value, "lean_split": l.value}
+    z, g, l, r = _I(), _I(), _I(), _I()
+    _check(lib().pf_batch_config(b, ctypes.byref(z), ctypes.byref(g), ctypes.byref(l), ctypes.byref(r)),
+           "pf_batch_config")
+    return {"zchunk": z.value, "general_ctas_per_sm": g.value, "lean_split": l.value, "lean_tile_rows": r.value}
+
+
+def pf_batch_set_config(b, zchunk=0, general_ctas_per_sm=2, lean_split=1, lean_tile_rows=8):
+    _check(lib().pf_batch_set_config(b, zchunk, general_ctas_per_sm, lean_split, lean_tile_rows),
+           "pf_batch_set_config")
 
 
 def pf_batch_step_bytes(b):

@@ -88,6 +88,7 @@ def test_host_side_checks_of_the_split_batch_and_checkpoint_calls():
     assert L.pf_split_read_fields(None, None, None, 0) == pf.PF_E_INVAL
     assert L.pf_split_stats(None, None, None, None, None) == pf.PF_E_INVAL
     # the batch's launch shape and byte tally, and the single-precision checkpoint, of no object
-    assert L.pf_batch_config(None, None, None, None) == pf.PF_E_INVAL
+    assert L.pf_batch_config(None, None, None, None, None) == pf.PF_E_INVAL
+    assert L.pf_batch_set_config(None, 0, 2, 1, 8) == pf.PF_E_INVAL
     assert L.pf_batch_step_bytes(None, None) == pf.PF_E_INVAL
     assert L.pf_checkpoint_write_f32(None, b"x") == pf.PF_E_INVAL

@@ -184,7 +184,8 @@ def test_autotune_restores_the_plane_tables_too():
         x.step(3)
     zc, ms = pf.pf_batch_autotune(b.h, 4)
     cfg = pf.pf_batch_config(b.h)
-    assert cfg["zchunk"] == zc and cfg["general_ctas_per_sm"] in (1, 2) and cfg["lean_split"] in (1, 2, 4)
+    assert cfg["zchunk"] == zc and cfg["general_ctas_per_sm"] in (1, 2) and cfg["lean_split"] in (1, 2, 4) \
+        and cfg["lean_tile_rows"] in (8, 4)
     a.step(10)
     b.step(10)
     for d in range(len(SHAPES)):
@@ -194,4 +195,69 @@ def test_autotune_restores_the_plane_tables_too():
         assert np.abs(ma - mb).max() <= 1e-13 * max(np.abs(ma).max(), 1e-8)
         assert a.stats(d)["t"] == b.stats(d)["t"]
     a.close()
+    b.close()
+
+
+# launch shapes: (z chunk, general CTAs an SM, lean split, lean tile rows)
+LAUNCH_SHAPES = [(0, 2, 1, 8), (0, 2, 1, 4), (16, 1, 2, 4), (32, 2, 4, 8), (64, 1, 4, 4)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_every_launch_shape_gives_the_same_fields(precision):
+    # a cell's update is the same arithmetic under any tile, z-chunk or z-block shape: FP64 (no
+    # multiply-add contraction) is bitwise; FP32 kernels of other tile shapes are other instantiations
+    # whose multiply-adds the compiler may contract differently: equal to FP32 rounding.  Domain 0's
+    # window moves; ny = 21 and 3 leave ragged 32x4 and 32x8 row blocks.
+    params = [_params(i, window=9.0 if i == 0 else 0.0) for i in range(len(SHAPES))]
+    params[0]["seed_layers"] = 12
+    seeds = [5 * i + 2 for i in range(len(SHAPES))]
+    runs = []
+    for shape in LAUNCH_SHAPES:
+        b = pf.Batch(SHAPES, params, precision)
+        pf.pf_batch_set_config(b.h, *shape)
+        assert tuple(pf.pf_batch_config(b.h).values()) == shape
+        b.init(seeds)
+        b.step(3)
+        b.step(24)  # graph-replayed
+        b.sync()
+        runs.append([b.fields(d) for d in range(len(SHAPES))] + [b.shifts(0)])
+        b.close()
+    assert runs[0][-1] > 0
+    for shape, run in zip(LAUNCH_SHAPES[1:], runs[1:]):
+        assert run[-1] == runs[0][-1], shape
+        for d in range(len(SHAPES)):
+            (p0, m0), (p1, m1) = runs[0][d], run[d]
+            if precision == "fp64":
+                assert (p0 == p1).all() and (m0 == m1).all(), (shape, d)
+            else:
+                assert np.abs(p0 - p1).max() <= 1e-6, (shape, d)
+                assert np.abs(m0 - m1).max() <= 1e-6 * max(np.abs(m0).max(), 1e-8), (shape, d)
+
+
+def test_half_height_lean_tiles_match_the_oracle():
+    params = [_params(i, window=9.0 if i == 0 else 0.0) for i in range(len(SHAPES))]
+    params[0]["seed_layers"] = 12
+    seeds = [7 * i + 3 for i in range(len(SHAPES))]
+    b = pf.Batch(SHAPES, params, "fp32")
+    pf.pf_batch_set_config(b.h, 16, 2, 2, 4)
+    b.init(seeds)
+    b.step(25)
+    b.sync()
+    assert pf.pf_batch_step_bytes(b.h)["lean_step"] > 0  # the half-height lean kernel ran
+    for d, (shape, p) in enumerate(zip(SHAPES, params)):
+        ref = oracle.State(p, *shape).init(seeds[d])
+        ref.step(25)
+        phi, mu = b.fields(d)
+        assert np.abs(phi - ref.phi).max() <= 2e-5, d
+        assert np.abs(mu - ref.mu).max() / max(np.abs(ref.mu).max(), 1e-8) <= 2e-5, d
+        assert b.shifts(d) == ref.shifts, d
+    b.close()
+
+
+def test_set_config_rejects_shapes_it_cannot_run():
+    b = pf.Batch(SHAPES[:2], [_params(0), _params(1)], "fp32")
+    for bad in [(-1, 2, 1, 8), (0, 3, 1, 8), (0, 2, 3, 8), (0, 2, 1, 2), (0, 0, 1, 8)]:
+        with pytest.raises(pf.PfError) as e:
+            pf.pf_batch_set_config(b.h, *bad)
+        assert e.value.status == pf.PF_E_INVAL
     b.close()
