@@ -534,6 +534,14 @@ __device__ __forceinline__ void phi_cell_comp(const KParams<float> &kp, const Pl
 // reciprocal: correctly rounded in both precisions (exact for 1), no full division in FP32
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+// approximate reciprocal (FP32: the hardware's, as the FP32 unit's divisions; FP64: IEEE division), for
+// the anti-trapping current only: the mu update's 1/chi and the weights' 1/sum(phi^2) keep the
+// correctly rounded one (the compensated state's solute balance depends on them)
+__device__ __forceinline__ float rcp_approx(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_approx(double x) { return 1.0 / x; }
+// reciprocal square root (the library's, in each precision)
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
 // one plane-table entry (16 words) through the read-only path; the same address for every
 // thread of a CTA, so the loads are broadcasts served by L1
@@ -656,7 +664,14 @@ __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const Pla
         const R gl2 = gl[0] * gl[0] + gl[1] * gl[1] + gl[2] * gl[2];
         if (gl2 > kp.grad_thr) {
             const Chat<R> ch = ldg_chat(tf);
+#ifndef PF_AT_RSQRT
+#define PF_AT_RSQRT 1  // the normals' products from reciprocal square roots (0: square roots and divisions)
+#endif
+#if PF_AT_RSQRT
+            const R inl = rsq(gl2);  // 1 / |grad phi_l|
+#else
             const R nl = sqrt(gl2);
+#endif
             const R mb0 = R(0.5) * (mL.v[0] + mR.v[0]);
             const R mb1 = R(0.5) * (mL.v[1] + mR.v[1]);
             R cl0, cl1;
@@ -670,9 +685,19 @@ __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const Pla
                 ga[2] = (bLp.v[a] - bLm.v[a] + bRp.v[a] - bRm.v[a]) * kp.inv_4dx;
                 const R ga2 = ga[0] * ga[0] + ga[1] * ga[1] + ga[2] * ga[2];
                 if (!(ga2 > kp.grad_thr)) continue;
+                const R pdot = R(0.5) * ((nL.v[a] - oL.v[a]) + (nR.v[a] - oR.v[a])) * kp.inv_dt;
+#if PF_AT_RSQRT
+                // (n_a . n_l) n_a,0 = (g_a . g_l) g_a,0 / (|g_a|^2 |g_l|) and phi_a / sqrt(phi_a phi_l)
+                // = phi_a rsqrt(phi_a phi_l): one reciprocal and one reciprocal square root a term
+                const R ndn = (ga[0] * gl[0] + ga[1] * gl[1] + ga[2] * gl[2]) * ga[0] * (rcp_approx(ga2) * inl);
+                const R pref = kp.at_pref * (pb[a] * rsq(pb[a] * pb[3]) * h[3]) * pdot * ndn;
+                R ca0, ca1;
+                c_alpha<R, SYM>(kp, a, mb0, mb1, ch.c[a][0], ch.c[a][1], ca0, ca1);
+                v.v[0] = v.v[0] - pref * (cl0 - ca0);
+                v.v[1] = v.v[1] - pref * (cl1 - ca1);
+#else
                 const R na = sqrt(ga2);
                 const R ndot = (ga[0] * gl[0] + ga[1] * gl[1] + ga[2] * gl[2]) / (na * nl);
-                const R pdot = R(0.5) * ((nL.v[a] - oL.v[a]) + (nR.v[a] - oR.v[a])) * kp.inv_dt;
                 const R pref = kp.at_pref * (pb[a] * h[3] / sqrt(pb[a] * pb[3])) * pdot * ndot;
                 R ca0, ca1;
                 c_alpha<R, SYM>(kp, a, mb0, mb1, ch.c[a][0], ch.c[a][1], ca0, ca1);
@@ -681,6 +706,7 @@ __device__ __forceinline__ Mu<R> face_mu_general(const KParams<R> &kp, const Pla
                 const R nd = ga[0] / na;  // normal component: the face direction is component 0
                 v.v[0] = v.v[0] - pref * dc0 * nd;
                 v.v[1] = v.v[1] - pref * dc1 * nd;
+#endif
             }
         }
     }
