@@ -74,8 +74,8 @@ KERNELS_PER_RECORD = {"general_sweeps": 2}
 # (summed over general_phi_kernel and general_mu_kernel, divided by the general cells the launch
 # processed; the capture and its command are in profiles/general_sweeps_flops_fp32_256x256x512.md).
 # None: not measured for the current kernels.  Remove the entries when the kernels change.
-GENERAL_FLOPS_PER_CELL = 730.0
-GENERAL_INSTS_PER_CELL = 1389.0
+GENERAL_FLOPS_PER_CELL = 728.0
+GENERAL_INSTS_PER_CELL = 1354.0
 
 
 def alu_roofline(k, general_cells, clk):
