@@ -261,3 +261,38 @@ def test_set_config_rejects_shapes_it_cannot_run():
             pf.pf_batch_set_config(b.h, *bad)
         assert e.value.status == pf.PF_E_INVAL
     b.close()
+
+
+def test_general_parameter_set_matches_the_oracle_under_every_launch_shape():
+    # matrix curvatures and pair relaxation times take other branches in every batched kernel, the
+    # lean kernel's liquid constants included; each launch shape (half-height lean tiles, split z
+    # chunks) must reach the oracle's fields.  Domain 0's window moves.  FP64 only: in plain FP32 a
+    # rounding residue can tip a single-phase cell across the jump of the pair relaxation time (the
+    # cases and the compensated state's answer are in test_gpu_precision.py).
+    precision, tol = "fp64", 1e-12
+    params = []
+    for i in range(len(SHAPES)):
+        rng = np.random.default_rng(200 + i)
+        q = W.general_params(G=float(rng.uniform(5e-4, 2e-3)), v=float(rng.uniform(5e-3, 2e-2)),
+                             n_grains=int(rng.integers(2, 9)), window_trigger_z=9.0 if i == 0 else 0.0)
+        params.append(q)
+    params[0]["seed_layers"] = 12
+    seeds = [4 * i + 9 for i in range(len(SHAPES))]
+    refs = []
+    for d, (shape, q) in enumerate(zip(SHAPES, params)):
+        ref = oracle.State(q, *shape).init(seeds[d])
+        ref.step(25)
+        refs.append(ref)
+    assert refs[0].shifts > 0
+    for launch in [(0, 2, 1, 4), (16, 1, 2, 4), (32, 2, 4, 8)]:
+        b = pf.Batch(SHAPES, params, precision)
+        pf.pf_batch_set_config(b.h, *launch)
+        b.init(seeds)
+        b.step(25)
+        b.sync()
+        for d, ref in enumerate(refs):
+            phi, mu = b.fields(d)
+            assert b.shifts(d) == ref.shifts, (launch, d)
+            assert np.abs(phi - ref.phi).max() <= tol, (launch, d)
+            assert np.abs(mu - ref.mu).max() / max(np.abs(ref.mu).max(), 1e-8) <= tol, (launch, d)
+        b.close()
